@@ -1,0 +1,353 @@
+"""Pins for the oracle's matching path: Eq. census_cost, argmin, Eq. subpixel,
+forward-backward check (Sec. 4.3.3), occlusion-aware sampling (Sec. 4.3.5),
+far/close split and aggregation (Sec. 4.3.4), Eq. 1."""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_2604_07980_gb300 import workloads as wl
+from tests.brute import census_np, cost_volume, longest_run_median
+
+
+def _params(**kw):
+    base = dict(wl.PARAMS["pair640"])
+    base.update(kw)
+    return orc.Params(**base)
+
+
+def _textured_pair(W, H, d, seed=5, gain=1.0, offset=0.0):
+    """Integer-shift pair: R(x) = L(x + d) (object at x in L is at x - d in R)."""
+    rng = np.random.default_rng(seed)
+    big = np.clip(np.rint(wl.texture(rng, H, W + d + 2)), 0, 255 - max(offset, 0))
+    L = big[:, :W]
+    R = np.clip(np.rint(gain * big[:, d:W + d] + offset), 0, 255)
+    return L.astype(np.uint8), R.astype(np.uint8)
+
+
+# ---------------------------------------------------------------- Eq. census_cost
+
+def test_costs_equal_brute_force_volume():
+    """Dense 3x3 blocks (every block pixel is a point): per-block cost vectors equal
+    an independent numpy cost volume, including the vertical search."""
+    W, H = 64, 40
+    rng = np.random.default_rng(1)
+    L = rng.integers(0, 256, (H, W), dtype=np.uint8)
+    R = rng.integers(0, 256, (H, W), dtype=np.uint8)
+    p = _params(win_w=5, win_h=3, far_side_px=0, close_factor=1, close_dmin=-2, close_dmax=9,
+                dy_min=-1, dy_max=1, grid_g=2, pts_side=16, min_pts=1, agg_nmin=1)
+    box = np.array([[20, 8, 44, 30, 0]], np.int32)
+    out = orc.match_frame(L, R, box, 2000.0, 0.3, p, debug=True)
+    CL, CR = census_np(L, 5, 3), census_np(R, 5, 3)
+    nd, ndy = 12, 3
+    for s in range(4):
+        a, b = s % 2, s // 2
+        x0, x1 = 20 + a * 12, 20 + (a + 1) * 12
+        y0, y1 = 8 + b * 11, 8 + (b + 1) * 11
+        mask = np.zeros((H, W), bool)
+        mask[y0:y1, x0:x1] = True
+        mask[:1, :] = mask[-1:, :] = False
+        mask[:, :2] = mask[:, -2:] = False
+        vol = cost_volume(CL, CR, mask, -2, 9, -1, 1)
+        got = out["cost_f"][0, s, :nd * ndy].reshape(ndy, nd)
+        assert np.array_equal(got, vol), s
+        assert out["blocks"][0, s]["n_valid"] == mask.sum()
+
+
+def test_self_match_zero_cost_at_zero():
+    rng = np.random.default_rng(2)
+    L = np.clip(np.rint(wl.texture(rng, 60, 90)), 0, 255).astype(np.uint8)
+    p = _params()
+    box = np.array([[30, 6, 78, 54, 0]], np.int32)
+    out = orc.match_frame(L, L, box, 2000.0, 0.3, p, debug=True)
+    b = out["blocks"][0]
+    assert np.all(out["cost_f"][0, :, 0] == 0)
+    assert np.all(b["d_f"] == 0) and np.all(b["d_b"] == 0)
+    assert np.all(b["flags"] & orc.BLK_VALID)
+
+
+@pytest.mark.parametrize("d", [0, 7, 23, 40])
+def test_planted_integer_shift_is_argmin(d):
+    L, R = _textured_pair(160, 64, d, seed=d, gain=1.0, offset=10.0)
+    p = _params()
+    box = np.array([[90, 8, 138, 56, 0]], np.int32)
+    out = orc.match_frame(L, R, box, 2000.0, 0.3, p, debug=True)
+    b = out["blocks"][0]
+    assert np.all(b["d_f"] == d) and np.all(b["d_b"] == d)
+    assert np.all(out["cost_f"][0, :, d] == 0)  # offset without clipping changes nothing
+    if d > 0:
+        assert out["flags"][0] & orc.BOX_VALID
+        assert out["disp"][0] == pytest.approx(d, abs=0.05)
+    else:  # Eq. 1 needs d > 0
+        assert out["flags"][0] & orc.BOX_NONPOS_DISP and not out["flags"][0] & orc.BOX_VALID
+
+
+def test_argmin_is_round_of_fractional_truth_on_clean_texture():
+    """Clean planted textures (no noise, gain 1, offset 0): argmin = round(d_true)."""
+    w = wl.pair640(seed=1000)
+    w2 = wl.pair640(seed=1000)  # same geometry
+    # rebuild the same pair without noise
+    rng = np.random.default_rng(1234)
+    fr = w.frames[0]
+    H, W = fr.left.shape
+    Lf = wl.texture(rng, H, W)
+    Rf = Lf.copy()
+    boxes = w.boxes[:, :4].tolist()
+    d = [float(v) for v in w.d_true]
+    d = [np.floor(v) + (0.2 if (v % 1) < 0.5 else 0.8) for v in d]  # stay away from .5
+    for i in sorted(range(len(boxes)), key=lambda i: boxes[i][3]):
+        wl._paint(Lf, Rf, rng, boxes[i], d[i])
+    L = np.clip(np.rint(Lf), 0, 255).astype(np.uint8)
+    R = np.clip(np.rint(Rf), 0, 255).astype(np.uint8)
+    out = orc.match_frame(L, R, w2.boxes, 2000.0, 0.3, orc.Params(**w.params), debug=True)
+    for i, di in enumerate(d):
+        assert np.all(out["blocks"][i]["d_f"] == int(np.rint(di))), (i, di)
+
+
+# ---------------------------------------------------------------- Eq. subpixel
+
+@pytest.mark.parametrize("sm,s0,sp", [(7, 3, 5), (25, 1, 9), (9, 1, 1), (4, 2, 4), (100, 0, 3)])
+def test_parabola_vertex_closed_form(sm, s0, sp):
+    """The vertex of the parabola through (-1,sm), (0,s0), (1,sp) is at
+    (sm - sp) / (2 (sm - 2 s0 + sp)) (exact rational arithmetic)."""
+    v = Fraction(sm - sp, 2 * (sm - 2 * s0 + sp))
+    got = orc.subpixel(40, sm, s0, sp)
+    assert got == pytest.approx(float(40 + v), abs=2e-6)
+
+
+def test_parabola_exact_quadratic():
+    """Costs sampled from 16 (d - 10.25)^2 + 1 give the vertex 10.25 exactly."""
+    S = lambda d: int(16 * (d - 10.25) ** 2 + 1)
+    assert orc.subpixel(10, S(9), S(10), S(11)) == 10.25
+
+
+def test_block_subpixel_uses_neighbour_costs():
+    L, R = _textured_pair(160, 64, 12, seed=9)
+    out = orc.match_frame(L, R, np.array([[90, 8, 138, 56, 0]], np.int32), 2000.0, 0.3,
+                          _params(), debug=True)
+    for b, cf in zip(out["blocks"][0], out["cost_f"][0]):
+        d = b["d_f"]
+        assert (b["s_m"], b["s_0"], b["s_p"]) == (cf[d - 1], cf[d], cf[d + 1])
+        assert b["d_sub"] == np.float32(orc.subpixel(d, cf[d - 1], cf[d], cf[d + 1]))
+
+
+def test_range_edge_keeps_integer_argmin():
+    L, R = _textured_pair(160, 64, 20, seed=4)
+    p = _params(close_dmin=0, close_dmax=20)
+    out = orc.match_frame(L, R, np.array([[90, 8, 138, 56, 0]], np.int32), 2000.0, 0.3, p, debug=True)
+    b = out["blocks"][0]
+    assert np.all(b["d_f"] == 20)
+    assert np.all(b["d_sub"] == 20.0)
+    assert np.all(b["flags"] & orc.BLK_SUBPIX_CLAMPED)
+
+
+# ---------------------------------------------------------------- Sec. 4.3.3
+
+def test_backward_cost_at_forward_match_equals_forward_cost():
+    w = wl.frame1080(W=480, H=270, n_boxes=12, side_range=(12, 120))
+    fr = w.frames[0]
+    out = orc.match_frame(fr.left, fr.right, w.boxes, fr.f_px, fr.baseline_m,
+                          orc.Params(**w.params), debug=True)
+    checked = 0
+    for i in range(w.n_boxes):
+        for s in range(out["blocks"].shape[1]):
+            b = out["blocks"][i, s]
+            if not (b["flags"] & orc.BLK_PRESENT) or b["flags"] & orc.BLK_FEW_POINTS:
+                continue
+            far = out["flags"][i] & orc.BOX_FAR
+            nd = (w.params["far_dmax"] if far else w.params["close_dmax"]) + 1
+            assert out["cost_b"][i, s, b["d_f"]] == out["cost_f"][i, s, b["d_f"]]
+            assert b["d_f"] < nd
+            checked += 1
+    assert checked > 20
+
+
+def test_mirrored_pair_forward_equals_original_backward():
+    """Swap and mirror the pair: the object keeps its disparity, and with dense
+    points the mirrored forward costs are the original backward costs of the
+    mirrored block (block column a <-> g-1-a)."""
+    d = 9
+    L, R = _textured_pair(200, 60, d, seed=21)
+    Wd = 200
+    p = _params(close_dmax=31)
+    box = np.array([[100, 6, 148, 54, 0]], np.int32)
+    out = orc.match_frame(L, R, box, 2000.0, 0.3, p, debug=True)
+    assert np.all(out["blocks"][0]["d_f"] == d)
+    Lm = np.ascontiguousarray(R[:, ::-1])
+    Rm = np.ascontiguousarray(L[:, ::-1])
+    x0r, x1r = 100 - d, 148 - d  # the object in R
+    boxm = np.array([[Wd - x1r, 6, Wd - x0r, 54, 0]], np.int32)
+    outm = orc.match_frame(Lm, Rm, boxm, 2000.0, 0.3, p, debug=True)
+    for s in range(9):
+        a, b = s % 3, s // 3
+        sm = b * 3 + (2 - a)
+        assert np.array_equal(outm["cost_f"][0, sm], out["cost_b"][0, s])
+    assert np.all(outm["blocks"][0]["d_f"] == d)
+
+
+def test_fb_rejects_inconsistent_match():
+    """An object whose right-image content is unrelated texture fails the check in
+    at least some blocks; FB_REJECT is then set on the box."""
+    rng = np.random.default_rng(8)
+    L = np.clip(np.rint(wl.texture(rng, 60, 160)), 0, 255).astype(np.uint8)
+    R = np.clip(np.rint(wl.texture(rng, 60, 160)), 0, 255).astype(np.uint8)
+    out = orc.match_frame(L, R, np.array([[90, 6, 138, 54, 0]], np.int32), 2000.0, 0.3,
+                          _params(fb_tol=0), debug=True)
+    b = out["blocks"][0]
+    rej = (b["flags"] & orc.BLK_FB_REJECT) != 0
+    assert rej.any()
+    assert np.all(np.abs(b["d_b"][rej] - b["d_f"][rej]) > 0)
+    assert out["flags"][0] & orc.BOX_FB_REJECT
+
+
+# ---------------------------------------------------------------- Sec. 4.3.5 / 4.3.4
+
+def test_occluder_points_are_excluded():
+    rng = np.random.default_rng(3)
+    L = np.clip(np.rint(wl.texture(rng, 120, 200)), 0, 255).astype(np.uint8)
+    a = [100, 20, 148, 68]
+    occ = [120, 40, 135, 80]  # bottom 80 > 68: occludes a
+    up = [90, 10, 110, 60]    # bottom 60 < 68: does not occlude a (a occludes it)
+    boxes = np.array([a + [0], occ + [0], up + [0]], np.int32)
+    out = orc.match_frame(L, L, boxes, 2000.0, 0.3, _params(), debug=True)
+    for s in range(9):
+        bx0, by0 = 100 + (s % 3) * 16, 20 + (s // 3) * 16
+        xs, ys = np.meshgrid(np.arange(bx0, bx0 + 16), np.arange(by0, by0 + 16))
+        hidden = (xs >= occ[0]) & (xs < occ[2]) & (ys >= occ[1]) & (ys < occ[3])
+        assert out["blocks"][0, s]["n_valid"] == 256 - hidden.sum()
+    # the upper box loses the part covered by a
+    nv_up = out["blocks"][2]["n_valid"].sum()
+    assert nv_up < out["blocks"][2]["n_pts"].sum()
+
+
+def test_equal_bottoms_do_not_occlude_and_cap_keeps_nearest():
+    rng = np.random.default_rng(4)
+    L = np.clip(np.rint(wl.texture(rng, 120, 200)), 0, 255).astype(np.uint8)
+    a = [100, 20, 148, 68]
+    same = [90, 30, 120, 68]
+    near1 = [140, 20, 160, 90]
+    near2 = [100, 60, 110, 80]
+    boxes = np.array([a + [0], same + [0], near1 + [0], near2 + [0]], np.int32)
+    full = orc.match_frame(L, L, boxes, 2000.0, 0.3, _params(), debug=True)
+    cap1 = orc.match_frame(L, L, boxes, 2000.0, 0.3, _params(max_occluders=1), debug=True)
+    xs, ys = np.meshgrid(np.arange(100, 148), np.arange(20, 68))
+    inside = lambda r: (xs >= r[0]) & (xs < r[2]) & (ys >= r[1]) & (ys < r[3])
+    assert full["blocks"][0]["n_valid"].sum() == (~(inside(near1) | inside(near2))).sum()
+    # cap 1 keeps near1 (bottom 90 > 80)
+    assert cap1["blocks"][0]["n_valid"].sum() == (~inside(near1)).sum()
+
+
+def test_far_close_threshold_and_empty_boxes():
+    rng = np.random.default_rng(6)
+    L = np.clip(np.rint(wl.texture(rng, 200, 300)), 0, 255).astype(np.uint8)
+    p = orc.Params(**wl.PARAMS["frame1080"])
+    boxes = np.array([[100, 50, 139, 80, 0],     # max side 39 -> FAR
+                      [100, 100, 140, 120, 0],   # max side 40 -> CLOSE
+                      [400, 10, 450, 40, 0],     # outside -> EMPTY
+                      [-30, 150, 20, 190, 0],    # clipped to 20 x 40 -> CLOSE
+                      [50, 60, 50, 90, 0]],      # zero width -> EMPTY
+                     np.int32)
+    out = orc.match_frame(L, L, boxes, 2000.0, 0.3, p, debug=True)
+    f = out["flags"]
+    assert f[0] & orc.BOX_FAR and not f[1] & orc.BOX_FAR
+    assert f[2] & orc.BOX_EMPTY and f[4] & orc.BOX_EMPTY
+    assert np.isnan(out["disp"][2])
+    assert not f[3] & orc.BOX_FAR and not f[3] & orc.BOX_EMPTY
+
+
+def test_dense_sampling_of_48px_box():
+    """A 48x48 box on a 3x3 grid at full resolution gives 16x16 dense blocks."""
+    rng = np.random.default_rng(1)
+    L = np.clip(np.rint(wl.texture(rng, 100, 200)), 0, 255).astype(np.uint8)
+    out = orc.match_frame(L, L, np.array([[80, 20, 128, 68, 0]], np.int32), 2000.0, 0.3,
+                          _params(), debug=True)
+    assert np.all(out["blocks"][0]["n_pts"] == 256)
+    assert np.all(out["blocks"][0]["n_valid"] == 256)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_aggregation_brute_force(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1, 26))
+    vals = np.round(rng.normal(30, 3, n) * 4) / 4
+    vals = vals.astype(np.float32)
+    for mode in (0, 1):
+        got = orc.aggregate(vals, 1.0, 3, mode, 0.2)
+        run = longest_run_median(vals, 1.0, 3)
+        if run is None:
+            assert got is None
+            continue
+        if mode == 0:
+            assert got == pytest.approx(float(np.median(run)), abs=1e-6)
+        else:
+            from scipy.stats import trim_mean
+            assert got == pytest.approx(float(trim_mean(run, 0.2)), abs=1e-5)
+
+
+def test_aggregation_hand_lists():
+    assert orc.aggregate([9.1, 5.2, 5.0, 9.0, 5.4], 1.0, 3) == pytest.approx(5.2)
+    assert orc.aggregate([4.5, 1.0, 4.0, 1.5], 1.0, 2) == pytest.approx(1.25)  # tie -> lower run
+    assert orc.aggregate([1.0, 3.0, 5.0], 1.0, 2) is None
+    assert orc.aggregate([2.0, 2.5, 2.75, 3.0], 1.0, 4) == pytest.approx(2.625)
+    assert orc.aggregate([], 1.0, 1) is None
+
+
+def test_depth_eq1_paper_examples():
+    """Sec. 1.2: b = 30 cm, f = 2000 px -> 200 m at d = 3.0 px; b = 12 cm -> d = 1.2 px."""
+    assert orc.depth(2000.0, 0.30, 3.0) == pytest.approx(200.0, rel=1e-6)
+    assert orc.depth(2000.0, 0.12, 1.2) == pytest.approx(200.0, rel=1e-6)
+    assert np.isnan(orc.depth(2000.0, 0.3, 0.0)) and np.isnan(orc.depth(2000.0, 0.3, -1.0))
+
+
+def test_pair640_end_to_end_accuracy_band():
+    """Parity-unpinned sanity band: sub-pixel estimates near the planted truth."""
+    w = wl.pair640()
+    fr = w.frames[0]
+    out = orc.match_frame(fr.left, fr.right, w.boxes, fr.f_px, fr.baseline_m,
+                          orc.Params(**w.params))
+    assert np.all(out["flags"] & orc.BOX_VALID)
+    assert np.median(np.abs(out["disp"] - w.d_true)) < 0.25
+    np.testing.assert_allclose(out["depth"], fr.f_px * fr.baseline_m / out["disp"], rtol=1e-6)
+
+
+def test_argmin_ties_take_first_candidate():
+    """All-equal costs (a flat scene): the first candidate in (dy, d) order wins."""
+    L = np.full((40, 120), 90, np.uint8)
+    p = _params(close_dmin=3, close_dmax=20, dy_min=-1, dy_max=1, min_pts=1)
+    out = orc.match_frame(L, L, np.array([[60, 8, 108, 32, 0]], np.int32), 2000.0, 0.3, p, debug=True)
+    b = out["blocks"][0]
+    assert np.all(b["d_f"] == 3) and np.all(b["dy_f"] == -1)
+    assert np.all(b["d_b"] == 3) and np.all(b["dy_b"] == -1)
+
+
+def test_fb_tolerance_is_inclusive():
+    """|d_b - d_f| <= fb_tol is accepted: a block's flag flips exactly at fb_tol."""
+    w = wl.frame1080(W=480, H=270, n_boxes=16, side_range=(12, 150))
+    fr = w.frames[0]
+    seen = 0
+    for tol in (0, 1, 2):
+        prm = dict(w.params)
+        prm["fb_tol"] = tol
+        out = orc.match_frame(fr.left, fr.right, w.boxes, fr.f_px, fr.baseline_m,
+                              orc.Params(**prm), debug=True)
+        b = out["blocks"].reshape(-1)
+        run = (b["flags"] & orc.BLK_PRESENT) != 0
+        run &= (b["flags"] & orc.BLK_FEW_POINTS) == 0
+        dxv = np.abs(b["d_b"] - b["d_f"])
+        valid = (b["flags"] & orc.BLK_VALID) != 0
+        assert np.array_equal(valid[run], dxv[run] <= tol)
+        seen += int(np.sum(run & (dxv == tol) & valid))
+    assert seen > 0
+
+
+def test_half_resolution_rescale():
+    """CLOSE matching at k = 2: an even shift d is found as d/2 on the decimated grid
+    and reported back as d full-res px (d_full = k d_sub)."""
+    L, R = _textured_pair(300, 100, 24, seed=13)
+    p = _params(close_factor=2, far_side_px=0, close_dmax=31, grid_g=3, min_pts=4)
+    out = orc.match_frame(L, R, np.array([[150, 10, 246, 90, 0]], np.int32), 2000.0, 0.3, p, debug=True)
+    b = out["blocks"][0]
+    assert np.all(b["d_f"] == 12)
+    np.testing.assert_array_equal(b["d_full"], b["d_sub"] * np.float32(2))
+    assert out["disp"][0] == pytest.approx(24.0, abs=0.2)
