@@ -1,0 +1,223 @@
+/*
+ * ctm.h -- C ABI of the GB300 census template-matching library (libctm.so).
+ *
+ * Object-centric stereo ranging by Census template matching, arXiv 2604.07980,
+ * Sec. 4.3 and Algorithm 2: for every detection box, census codes of the left
+ * and right images (Sec. 4.3.1), an exhaustive Hamming-cost search per block
+ * (Eq. census_cost) with first argmin and parabola refinement (Eq. subpixel),
+ * a backward search and consistency test (Sec. 4.3.3), occlusion-aware point
+ * sampling (Sec. 4.3.5), the far/close split and robust aggregation
+ * (Sec. 4.3.4), and depth Z = f b / d (Eq. 1).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named *_dev are CUDA device pointers; *_host are host pointers.
+ *    The caller owns every image, box and output buffer.  A context owns its
+ *    workspace (census planes, plan, block results, counters).
+ *  - Calls are asynchronous on `stream` unless stated otherwise; results are
+ *    valid once that stream has synchronized.  A context is not thread-safe and
+ *    must not run two calls concurrently on different streams.
+ *  - Return value: CTM_OK (0) or a negative CTM_E* status.  Per-box outcomes
+ *    are flags (CTM_BOX_*), never errors.  On error nothing has been enqueued
+ *    unless the status is CTM_ECUDA.
+ *  - Disparities are in full-resolution pixels; the right-image match of a left
+ *    pixel x is at x - d (d >= 0 for objects in front of the cameras).
+ *  - No entry point falls back to a CPU implementation.
+ */
+#ifndef CTM_H
+#define CTM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ctm_ctx ctm_ctx;
+/* A cudaStream_t; NULL means the legacy default stream. */
+typedef struct CUstream_st *ctm_stream;
+
+/* Status codes. */
+#define CTM_OK 0
+#define CTM_EINVAL (-1)   /* bad argument: null pointer, size, window, range, pitch */
+#define CTM_ENOMEM (-2)   /* workspace allocation failed or request exceeds capacity */
+#define CTM_ECUDA (-3)    /* a CUDA call or launch failed */
+#define CTM_ENODEV (-4)   /* no usable CUDA device */
+
+/* Per-box flags (uint8), written by the match calls. */
+#define CTM_BOX_VALID 0x01           /* disparity > 0 found; disp/depth finite         */
+#define CTM_BOX_FB_REJECT 0x02       /* some block failed the forward-backward test     */
+#define CTM_BOX_FEW_POINTS 0x04      /* some block had fewer than min_pts usable points */
+#define CTM_BOX_NO_SEGMENT 0x08      /* CLOSE: no run of >= agg_nmin consistent blocks   */
+#define CTM_BOX_NONPOS_DISP 0x10     /* the aggregated disparity was <= 0               */
+#define CTM_BOX_EMPTY 0x20           /* box empty after clipping to the image           */
+#define CTM_BOX_SUBPIX_CLAMPED 0x40  /* a valid block's argmin sat at a range end       */
+#define CTM_BOX_FAR 0x80             /* classified FAR (matched at full resolution)     */
+
+/* Per-block flags (ctm_block.flags). */
+#define CTM_BLK_VALID 0x01
+#define CTM_BLK_FB_REJECT 0x02
+#define CTM_BLK_FEW_POINTS 0x04
+#define CTM_BLK_SUBPIX_CLAMPED 0x08
+#define CTM_BLK_PRESENT 0x10
+
+/* Detection box: half-open rectangle [x0, x1) x [y0, y1) in full-resolution
+ * pixels of its frame.  `frame` is informational; frame membership comes from
+ * ctm_frame.box_begin / box_count. */
+typedef struct {
+    int32_t x0, y0, x1, y1, frame;
+} ctm_box;
+
+/* One stereo frame of a batch.  left/right: uint8 grayscale, `pitch` bytes per
+ * row (pitch >= width).  Boxes [box_begin, box_begin + box_count) belong to it.
+ * f_px * baseline_m is the Eq. 1 numerator. */
+typedef struct {
+    const uint8_t *left;
+    const uint8_t *right;
+    int32_t width, height, pitch;
+    int32_t box_begin, box_count;
+    float f_px, baseline_m;
+} ctm_frame;
+
+/* Matching parameters (Sec. 4.3).  Limits checked by ctm_create:
+ * odd win_w, win_h <= 15 with win_w*win_h + sentinel <= 64; close_factor 1..8;
+ * grid_g 1..8; pts_side 1..16; (dmax-dmin+1)*(dy_max-dy_min+1) <= 256 for both
+ * ranges; min_pts >= 1; fb_tol >= 0; agg_nmin >= 1; 0 <= trim_frac < 0.5;
+ * 0 <= max_occluders <= 32. */
+typedef struct {
+    int32_t win_w, win_h;     /* census window (Sec. 4.3.1: S_x = win_w/2, S_y = win_h/2) */
+    int32_t sentinel;         /* 1: leading 1 bit above the comparison bits (Algorithm 1) */
+    int32_t far_side_px;      /* tau_s: FAR iff max(clipped w, h) < tau_s; 0 = never FAR */
+    int32_t close_factor;     /* k: CLOSE boxes match on the census of I(k x, k y)        */
+    int32_t far_dmin, far_dmax;     /* FAR search range, full-res px                      */
+    int32_t close_dmin, close_dmax; /* CLOSE search range, px of the decimated grid       */
+    int32_t dy_min, dy_max;   /* vertical search range of both passes                    */
+    int32_t grid_g;           /* CLOSE box -> grid_g x grid_g blocks                      */
+    int32_t pts_side;         /* at most pts_side x pts_side points per block             */
+    int32_t min_pts;          /* a block needs >= min_pts usable points                   */
+    int32_t fb_tol;           /* accept iff |d_b - d_f| <= fb_tol (tau_v = fb_tol + 1)    */
+    float agg_tau_d;          /* run: consecutive sorted differences < tau_d (full-res)   */
+    int32_t agg_nmin;         /* run must hold >= agg_nmin blocks (N_min)                 */
+    int32_t agg_mode;         /* 0: median of the run; 1: trimmed mean of the run         */
+    float trim_frac;          /* trimmed mean drops floor(trim_frac * m) per end          */
+    int32_t max_occluders;    /* at most this many occluders per box, nearest first       */
+} ctm_params;
+
+/* Per-block diagnostic record (ctm_debug.blocks), slot = block index in
+ * row-major grid order (FAR boxes use slot 0). */
+typedef struct {
+    int32_t n_pts, n_valid;
+    int32_t d_f, dy_f, d_b, dy_b;
+    int32_t s_m, s_0, s_p;    /* forward costs at d_f-1, d_f, d_f+1 (0 outside range) */
+    float d_sub;              /* refined disparity on the matching grid                */
+    float d_full;             /* d_sub * k                                             */
+    int32_t flags;            /* CTM_BLK_*                                             */
+} ctm_block;
+
+/* Optional diagnostics for parity checks (all device pointers, may be NULL).
+ * blocks: n_boxes * slots entries, slots = grid_g^2 (records only for blocks
+ * that exist; the caller zero-fills).  cost_f / cost_b: n_boxes * slots * nc_stride
+ * int32, nc_stride = max FAR/CLOSE candidate count, candidate c =
+ * (dy - dy_min) * N_d + (d - dmin). */
+typedef struct {
+    ctm_block *blocks;
+    int32_t *cost_f;
+    int32_t *cost_b;
+} ctm_debug;
+
+/* Counters of the last match call (ctm_get_stats). */
+typedef struct {
+    uint64_t cost_evals;   /* popcount(C_L xor C_R) evaluations, both passes */
+    int32_t n_blocks;      /* blocks planned                                  */
+    int32_t n_boxes;       /* boxes planned                                   */
+} ctm_stats;
+
+/* Human-readable name of a status code (static string). */
+const char *ctm_status_str(int status);
+
+/* Fill *p with the library defaults (9x7 census with sentinel, tau_s 40, k 2,
+ * FAR 0..31, CLOSE 0..127, dy 0, 4x4 blocks of <= 16x16 points, min_pts 16,
+ * fb_tol 1, tau_d 1.0, N_min 6, median, 16 occluders). */
+int ctm_default_params(ctm_params *p);
+
+/* Create a context on the current CUDA device with capacity for max_frames
+ * frames of at most max_width x max_height pixels and max_boxes boxes per call.
+ * Allocates the device workspace (about 2.6 * 8 bytes per pixel per frame plus
+ * per-box plans).  Errors: CTM_EINVAL (params or sizes), CTM_ENOMEM, CTM_ENODEV. */
+int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width,
+               int max_height, int max_boxes);
+
+/* Free the context and its workspace (synchronizes the device). NULL is a no-op. */
+void ctm_destroy(ctm_ctx *ctx);
+
+/* Census transform, Sec. 4.3.1 / Algorithm 1, of the decimated image
+ * I_k(x, y) = I(k x, k y) (k = factor; k = 1 is the image itself).
+ * img_dev: width x height uint8, `pitch` bytes per row.  codes_dev: uint64,
+ * ceil(height/k) rows of codes_pitch elements (codes_pitch >= ceil(width/k)).
+ * Bits are in raster window order, first neighbour highest; xi(a, b) = a > b;
+ * with sentinel the bit win_w*win_h is set; pixels whose window leaves the
+ * decimated image are 0.  No context needed.  Errors: CTM_EINVAL, CTM_ECUDA. */
+int ctm_census_build(const uint8_t *img_dev, int width, int height, int pitch, int factor,
+                     int win_w, int win_h, int sentinel, uint64_t *codes_dev,
+                     int64_t codes_pitch, ctm_stream stream);
+
+/* Algorithm 2 on one frame.  boxes_dev: n_boxes ctm_box (0 <= n_boxes <=
+ * max_boxes).  Outputs (n_boxes each): disp_dev (float, full-res px, NaN unless
+ * VALID), depth_dev (float, f_px*baseline_m/disp, NaN unless VALID), flags_dev
+ * (uint8 CTM_BOX_*).  dbg may be NULL.  One fused path: census of both images at
+ * both resolutions, device planning, one persistent matching kernel whose last
+ * CTA per box aggregates.  Errors: CTM_EINVAL, CTM_ENOMEM (beyond capacity),
+ * CTM_ECUDA. */
+int ctm_match_boxes(ctm_ctx *ctx, const uint8_t *left_dev, const uint8_t *right_dev,
+                    int width, int height, int pitch, const ctm_box *boxes_dev, int n_boxes,
+                    float f_px, float baseline_m, float *disp_dev, float *depth_dev,
+                    uint8_t *flags_dev, const ctm_debug *dbg, ctm_stream stream);
+
+/* The plain per-box path: same inputs, outputs and results as ctm_match_boxes,
+ * but one matching launch per box (no persistent queue, no graph). */
+int ctm_match_boxes_plain(ctm_ctx *ctx, const uint8_t *left_dev, const uint8_t *right_dev,
+                          int width, int height, int pitch, const ctm_box *boxes_dev,
+                          int n_boxes, float f_px, float baseline_m, float *disp_dev,
+                          float *depth_dev, uint8_t *flags_dev, ctm_stream stream);
+
+/* Algorithm 2 on a batch of frames in one planned, persistent launch.
+ * frames_dev: ctm_frame array in device memory; counts_dev: int32[2] in device
+ * memory = {n_frames, n_boxes} (read on the device, so a captured graph replays
+ * with new counts); boxes and outputs as in ctm_match_boxes, indexed over the
+ * whole batch.  Counts beyond the context capacity are clamped on the device.
+ * use_graph != 0 captures the launches into a CUDA graph on first use and
+ * replays it while all pointers stay the same.  Errors: CTM_EINVAL, CTM_ECUDA. */
+int ctm_match_batch(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *counts_dev,
+                    const ctm_box *boxes_dev, float *disp_dev, float *depth_dev,
+                    uint8_t *flags_dev, const ctm_debug *dbg, int use_graph, ctm_stream stream);
+
+/* ctm_match_batch without a graph, recording four caller-created CUDA events
+ * (cudaEvent_t handles, created with timing enabled) on `stream`: events[0]
+ * before the census kernel, events[1] before planning, events[2] before the
+ * matching kernel, events[3] after it.  Used to time each phase on the stream
+ * the kernels run on.  Errors as ctm_match_batch. */
+int ctm_match_batch_profiled(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *counts_dev,
+                             const ctm_box *boxes_dev, float *disp_dev, float *depth_dev,
+                             uint8_t *flags_dev, void *const events[4], ctm_stream stream);
+
+/* End-to-end batch from host memory: frames_host[i].left/right are HOST images
+ * (page-locked for asynchronous copies), boxes_host and the outputs are host
+ * arrays.  Copies the images and boxes in, runs ctm_match_batch, copies the
+ * results out and synchronizes `stream` before returning.  Errors as above. */
+int ctm_match_batch_host(ctm_ctx *ctx, const ctm_frame *frames_host, int n_frames,
+                         const ctm_box *boxes_host, int n_boxes, float *disp_host,
+                         float *depth_host, uint8_t *flags_host, ctm_stream stream);
+
+/* Counters of the most recent match call on ctx.  Synchronizes `stream`. */
+int ctm_get_stats(ctm_ctx *ctx, ctm_stats *out, ctm_stream stream);
+
+/* Integer-pipe probe for roofline denominators (no counterpart in the paper):
+ * runs `iters` iterations of independent 32-bit popcount chains (kind 0) or
+ * of xor chains (kind 1) on every SM and returns the operations per SM clock
+ * per SM.  Synchronizes the device.  Errors: CTM_EINVAL, CTM_ECUDA. */
+int ctm_probe_int_rate(int kind, int iters, double *ops_per_clk_per_sm);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CTM_H */

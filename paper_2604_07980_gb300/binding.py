@@ -1,0 +1,336 @@
+"""Thin Python binding of libctm.so (include/ctm.h).
+
+Argument marshalling only: every step of the matching path runs in the CUDA
+library.  PyTorch supplies device memory and streams (``tensor.data_ptr()``,
+``torch.cuda.current_stream().cuda_stream``).  There is no CPU fallback: if the
+library cannot be loaded, or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libctm.so")
+
+CTM_OK, CTM_EINVAL, CTM_ENOMEM, CTM_ECUDA, CTM_ENODEV = 0, -1, -2, -3, -4
+
+BOX_VALID, BOX_FB_REJECT, BOX_FEW_POINTS, BOX_NO_SEGMENT = 0x01, 0x02, 0x04, 0x08
+BOX_NONPOS_DISP, BOX_EMPTY, BOX_SUBPIX_CLAMPED, BOX_FAR = 0x10, 0x20, 0x40, 0x80
+BLK_VALID, BLK_FB_REJECT, BLK_FEW_POINTS, BLK_SUBPIX_CLAMPED, BLK_PRESENT = 1, 2, 4, 8, 16
+
+# every symbol include/ctm.h declares
+EXPORTS = ("ctm_status_str", "ctm_default_params", "ctm_create", "ctm_destroy",
+           "ctm_census_build", "ctm_match_boxes", "ctm_match_boxes_plain", "ctm_match_batch",
+           "ctm_match_batch_profiled", "ctm_match_batch_host", "ctm_get_stats", "ctm_probe_int_rate")
+
+
+class CtmError(RuntimeError):
+    pass
+
+
+class ctm_params(ctypes.Structure):
+    _fields_ = [("win_w", ctypes.c_int32), ("win_h", ctypes.c_int32), ("sentinel", ctypes.c_int32),
+                ("far_side_px", ctypes.c_int32), ("close_factor", ctypes.c_int32),
+                ("far_dmin", ctypes.c_int32), ("far_dmax", ctypes.c_int32),
+                ("close_dmin", ctypes.c_int32), ("close_dmax", ctypes.c_int32),
+                ("dy_min", ctypes.c_int32), ("dy_max", ctypes.c_int32), ("grid_g", ctypes.c_int32),
+                ("pts_side", ctypes.c_int32), ("min_pts", ctypes.c_int32), ("fb_tol", ctypes.c_int32),
+                ("agg_tau_d", ctypes.c_float), ("agg_nmin", ctypes.c_int32),
+                ("agg_mode", ctypes.c_int32), ("trim_frac", ctypes.c_float),
+                ("max_occluders", ctypes.c_int32)]
+
+
+class ctm_frame(ctypes.Structure):
+    _fields_ = [("left", ctypes.c_void_p), ("right", ctypes.c_void_p), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("pitch", ctypes.c_int32), ("box_begin", ctypes.c_int32),
+                ("box_count", ctypes.c_int32), ("f_px", ctypes.c_float), ("baseline_m", ctypes.c_float)]
+
+
+class ctm_debug(ctypes.Structure):
+    _fields_ = [("blocks", ctypes.c_void_p), ("cost_f", ctypes.c_void_p), ("cost_b", ctypes.c_void_p)]
+
+
+class ctm_stats(ctypes.Structure):
+    _fields_ = [("cost_evals", ctypes.c_uint64), ("n_blocks", ctypes.c_int32), ("n_boxes", ctypes.c_int32)]
+
+
+BLOCK_DTYPE = np.dtype([("n_pts", "<i4"), ("n_valid", "<i4"), ("d_f", "<i4"), ("dy_f", "<i4"),
+                        ("d_b", "<i4"), ("dy_b", "<i4"), ("s_m", "<i4"), ("s_0", "<i4"),
+                        ("s_p", "<i4"), ("d_sub", "<f4"), ("d_full", "<f4"), ("flags", "<i4")])
+BLOCK_BYTES = 48
+FRAME_BYTES = ctypes.sizeof(ctm_frame)
+
+_lib = None
+
+
+def lib():
+    """Load libctm.so (raises if it is missing or cannot be loaded)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise CtmError(f"libctm.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, f32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+    L.ctm_status_str.argtypes = [i32]
+    L.ctm_status_str.restype = ctypes.c_char_p
+    L.ctm_default_params.argtypes = [ctypes.POINTER(ctm_params)]
+    L.ctm_default_params.restype = i32
+    L.ctm_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ctm_params), i32, i32, i32, i32]
+    L.ctm_create.restype = i32
+    L.ctm_destroy.argtypes = [vp]
+    L.ctm_destroy.restype = None
+    L.ctm_census_build.argtypes = [vp, i32, i32, i32, i32, i32, i32, i32, vp, ctypes.c_int64, vp]
+    L.ctm_census_build.restype = i32
+    L.ctm_match_boxes.argtypes = [vp, vp, vp, i32, i32, i32, vp, i32, f32, f32, vp, vp, vp,
+                                  ctypes.POINTER(ctm_debug), vp]
+    L.ctm_match_boxes.restype = i32
+    L.ctm_match_boxes_plain.argtypes = [vp, vp, vp, i32, i32, i32, vp, i32, f32, f32, vp, vp, vp, vp]
+    L.ctm_match_boxes_plain.restype = i32
+    L.ctm_match_batch.argtypes = [vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(ctm_debug), i32, vp]
+    L.ctm_match_batch.restype = i32
+    L.ctm_match_batch_profiled.argtypes = [vp, vp, vp, vp, vp, vp, vp, ctypes.POINTER(vp), vp]
+    L.ctm_match_batch_profiled.restype = i32
+    L.ctm_match_batch_host.argtypes = [vp, ctypes.POINTER(ctm_frame), i32, vp, i32, vp, vp, vp, vp]
+    L.ctm_match_batch_host.restype = i32
+    L.ctm_get_stats.argtypes = [vp, ctypes.POINTER(ctm_stats), vp]
+    L.ctm_get_stats.restype = i32
+    L.ctm_probe_int_rate.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double)]
+    L.ctm_probe_int_rate.restype = i32
+    _lib = L
+    return L
+
+
+def _check(status: int, what: str):
+    if status != CTM_OK:
+        msg = lib().ctm_status_str(status).decode()
+        raise CtmError(f"{what}: {msg} ({status})")
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise CtmError("no CUDA device: the census template matcher runs only on the GPU")
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_params(d: dict | None = None) -> ctm_params:
+    p = ctm_params()
+    _check(lib().ctm_default_params(ctypes.byref(p)), "ctm_default_params")
+    for k, v in (d or {}).items():
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def census_build(img, factor: int = 1, win_w: int = 9, win_h: int = 7, sentinel: int = 1,
+                 stream=None):
+    """Census codes (uint64 stored in an int64 tensor) of a uint8 device image."""
+    torch = _torch()
+    assert img.dtype == torch.uint8 and img.is_cuda and img.dim() == 2
+    H, W = img.shape
+    pitch = img.stride(0)
+    Hs, Ws = -(-H // factor), -(-W // factor)
+    out = torch.empty((Hs, Ws), dtype=torch.int64, device=img.device)
+    _check(lib().ctm_census_build(_ptr(img), W, H, pitch, factor, win_w, win_h, sentinel,
+                                  _ptr(out), Ws, _stream(stream)), "ctm_census_build")
+    return out
+
+
+@dataclass
+class DebugOut:
+    blocks: object   # torch uint8 [n, slots, 48] (view with BLOCK_DTYPE after .cpu())
+    cost_f: object   # torch int32 [n, slots, nc]
+    cost_b: object
+
+    def blocks_np(self):
+        return self.blocks.cpu().numpy().reshape(-1).view(BLOCK_DTYPE).reshape(self.blocks.shape[:2])
+
+
+def n_candidates(p: ctm_params) -> int:
+    nd = max(p.far_dmax - p.far_dmin + 1, p.close_dmax - p.close_dmin + 1)
+    return nd * (p.dy_max - p.dy_min + 1)
+
+
+class Context:
+    """A matching context (ctm_create) on the current CUDA device."""
+
+    def __init__(self, params: dict | None, max_frames: int, max_width: int, max_height: int,
+                 max_boxes: int):
+        _torch()
+        self.params = make_params(params)
+        h = ctypes.c_void_p()
+        _check(lib().ctm_create(ctypes.byref(h), ctypes.byref(self.params), max_frames, max_width,
+                                max_height, max_boxes), "ctm_create")
+        self._h = h
+        self.max_frames, self.max_width, self.max_height = max_frames, max_width, max_height
+        self.max_boxes = max_boxes
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().ctm_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def slots(self) -> int:
+        return max(1, self.params.grid_g * self.params.grid_g)
+
+    def _debug(self, n, device):
+        torch = _torch()
+        nc = n_candidates(self.params)
+        d = DebugOut(torch.zeros((n, self.slots, BLOCK_BYTES), dtype=torch.uint8, device=device),
+                     torch.zeros((n, self.slots, nc), dtype=torch.int32, device=device),
+                     torch.zeros((n, self.slots, nc), dtype=torch.int32, device=device))
+        c = ctm_debug(d.blocks.data_ptr(), d.cost_f.data_ptr(), d.cost_b.data_ptr())
+        return d, c
+
+    def _outputs(self, n, device):
+        torch = _torch()
+        return (torch.empty(n, dtype=torch.float32, device=device),
+                torch.empty(n, dtype=torch.float32, device=device),
+                torch.empty(n, dtype=torch.uint8, device=device))
+
+    def match_boxes(self, left, right, boxes, f_px: float, baseline_m: float, debug: bool = False,
+                    stream=None, out=None):
+        """One frame.  left/right: uint8 [H, W] device tensors; boxes: int32 [n, 5] device."""
+        torch = _torch()
+        H, W = left.shape
+        n = int(boxes.shape[0]) if boxes is not None else 0
+        disp, depth, flags = out if out is not None else self._outputs(max(n, 1), left.device)
+        dbg = cdbg = None
+        if debug:
+            dbg, cdbg = self._debug(max(n, 1), left.device)
+        _check(lib().ctm_match_boxes(self._h, _ptr(left), _ptr(right), W, H, left.stride(0),
+                                     _ptr(boxes), n, f_px, baseline_m, _ptr(disp), _ptr(depth),
+                                     _ptr(flags), ctypes.byref(cdbg) if cdbg else None,
+                                     _stream(stream)), "ctm_match_boxes")
+        res = {"disp": disp[:n], "depth": depth[:n], "flags": flags[:n]}
+        if debug:
+            res["debug"] = dbg
+        return res
+
+    def match_boxes_plain(self, left, right, boxes, f_px: float, baseline_m: float, stream=None,
+                          out=None):
+        H, W = left.shape
+        n = int(boxes.shape[0]) if boxes is not None else 0
+        disp, depth, flags = out if out is not None else self._outputs(max(n, 1), left.device)
+        _check(lib().ctm_match_boxes_plain(self._h, _ptr(left), _ptr(right), W, H, left.stride(0),
+                                           _ptr(boxes), n, f_px, baseline_m, _ptr(disp),
+                                           _ptr(depth), _ptr(flags), _stream(stream)),
+               "ctm_match_boxes_plain")
+        return {"disp": disp[:n], "depth": depth[:n], "flags": flags[:n]}
+
+    def match_batch(self, batch: "DeviceBatch", use_graph: bool = True, debug: bool = False,
+                    stream=None):
+        dbg = cdbg = None
+        if debug:
+            dbg, cdbg = self._debug(max(batch.n_boxes, 1), batch.boxes.device)
+        _check(lib().ctm_match_batch(self._h, _ptr(batch.frames), _ptr(batch.counts),
+                                     _ptr(batch.boxes), _ptr(batch.disp), _ptr(batch.depth),
+                                     _ptr(batch.flags), ctypes.byref(cdbg) if cdbg else None,
+                                     1 if use_graph else 0, _stream(stream)), "ctm_match_batch")
+        res = {"disp": batch.disp[:batch.n_boxes], "depth": batch.depth[:batch.n_boxes],
+               "flags": batch.flags[:batch.n_boxes]}
+        if debug:
+            res["debug"] = dbg
+        return res
+
+    def match_batch_profiled(self, batch: "DeviceBatch", events, stream=None):
+        """Non-graph batch recording 4 torch.cuda.Event(enable_timing=True) at the phase
+        boundaries (before census, before planning, before matching, after matching)."""
+        arr = (ctypes.c_void_p * 4)(*[e.cuda_event for e in events])
+        _check(lib().ctm_match_batch_profiled(self._h, _ptr(batch.frames), _ptr(batch.counts),
+                                              _ptr(batch.boxes), _ptr(batch.disp), _ptr(batch.depth),
+                                              _ptr(batch.flags), arr, _stream(stream)),
+               "ctm_match_batch_profiled")
+
+    def match_batch_host(self, frames_np, boxes_np, f_px, baseline_m, out=None, stream=None):
+        """Host arrays in, host arrays out (page-locked numpy views are fastest).
+        frames_np: list of (left, right) uint8 [H, W] arrays; boxes_np int32 [n, 5]
+        grouped by frame (column 4 = frame index)."""
+        n = int(boxes_np.shape[0])
+        counts = np.bincount(boxes_np[:, 4], minlength=len(frames_np)) if n else np.zeros(len(frames_np), int)
+        begins = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int64)
+        arr = (ctm_frame * len(frames_np))()
+        for i, (L, R) in enumerate(frames_np):
+            fp = f_px[i] if np.ndim(f_px) else f_px
+            bm = baseline_m[i] if np.ndim(baseline_m) else baseline_m
+            arr[i] = ctm_frame(L.ctypes.data, R.ctypes.data, L.shape[1], L.shape[0], L.strides[0],
+                               int(begins[i]), int(counts[i]), float(fp), float(bm))
+        if out is None:
+            out = (np.empty(max(n, 1), np.float32), np.empty(max(n, 1), np.float32),
+                   np.empty(max(n, 1), np.uint8))
+        disp, depth, flags = out
+        bx = np.ascontiguousarray(boxes_np, dtype=np.int32)
+        _check(lib().ctm_match_batch_host(self._h, arr, len(frames_np), bx.ctypes.data, n,
+                                          disp.ctypes.data, depth.ctypes.data, flags.ctypes.data,
+                                          _stream(stream)), "ctm_match_batch_host")
+        return {"disp": disp[:n], "depth": depth[:n], "flags": flags[:n]}
+
+    def stats(self, stream=None) -> dict:
+        s = ctm_stats()
+        _check(lib().ctm_get_stats(self._h, ctypes.byref(s), _stream(stream)), "ctm_get_stats")
+        return {"cost_evals": int(s.cost_evals), "n_blocks": int(s.n_blocks), "n_boxes": int(s.n_boxes)}
+
+
+class DeviceBatch:
+    """Device-resident batch: frame descriptors, counts, boxes and outputs.
+
+    frames: list of (left, right) uint8 device tensors; boxes: int32 [n, 5] with the
+    frame index in column 4, grouped by frame; calib: list of (f_px, baseline_m)."""
+
+    def __init__(self, frames, boxes, calib, device=None):
+        torch = _torch()
+        device = device or frames[0][0].device
+        n = int(boxes.shape[0])
+        bnp = boxes.cpu().numpy() if hasattr(boxes, "cpu") else np.asarray(boxes)
+        counts = np.bincount(bnp[:, 4], minlength=len(frames)) if n else np.zeros(len(frames), int)
+        begins = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int64)
+        arr = (ctm_frame * len(frames))()
+        for i, (L, R) in enumerate(frames):
+            arr[i] = ctm_frame(L.data_ptr(), R.data_ptr(), L.shape[1], L.shape[0], L.stride(0),
+                               int(begins[i]), int(counts[i]), float(calib[i][0]), float(calib[i][1]))
+        raw = np.frombuffer(bytes(arr), dtype=np.uint8)
+        self.frames_keep = frames
+        self.frames = torch.from_numpy(raw.copy()).to(device)
+        self.counts = torch.tensor([len(frames), n], dtype=torch.int32, device=device)
+        self.boxes = torch.as_tensor(np.ascontiguousarray(bnp, dtype=np.int32), device=device)
+        self.n_boxes = n
+        self.n_frames = len(frames)
+        self.disp = torch.empty(max(n, 1), dtype=torch.float32, device=device)
+        self.depth = torch.empty(max(n, 1), dtype=torch.float32, device=device)
+        self.flags = torch.empty(max(n, 1), dtype=torch.uint8, device=device)
+
+
+def frames_to_device(frames, device="cuda"):
+    """[(left, right)] uint8 device tensors from objects with .left/.right numpy arrays."""
+    torch = _torch()
+    return [(torch.from_numpy(np.ascontiguousarray(f.left)).to(device),
+             torch.from_numpy(np.ascontiguousarray(f.right)).to(device)) for f in frames]
+
+
+def probe_int_rate(kind: int, iters: int = 4096) -> float:
+    """Operations per SM clock per SM of 32-bit popcount (kind 0) or 3-input xor (kind 1)."""
+    _torch()
+    v = ctypes.c_double(0.0)
+    _check(lib().ctm_probe_int_rate(kind, iters, ctypes.byref(v)), "ctm_probe_int_rate")
+    return float(v.value)

@@ -1,0 +1,534 @@
+// api.cu -- the C ABI (include/ctm.h): context, workspace and launch sequences.
+//
+// A match call is four launches on one stream: census of both images at both
+// resolutions (one kernel), device planning (two kernels), and the matching
+// kernel whose last CTA per box aggregates and writes the outputs.  The batch
+// entry point reads its frame and box counts from device memory, so the whole
+// sequence can be captured once into a CUDA graph and replayed.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "ctm_internal.cuh"
+
+using namespace ctm;
+
+struct GraphKey {
+    const void *frames, *counts, *boxes, *disp, *depth, *flags, *dbg_blocks, *dbg_cf, *dbg_cb;
+    bool operator==(const GraphKey &o) const { return memcmp(this, &o, sizeof(*this)) == 0; }
+};
+
+struct ctm_ctx {
+    int device = 0;
+    int sm_count = 0;
+    int ctas_per_sm = 0;
+    ctm_params p{};
+    Caps caps{};
+    Workspace ws{};
+    int nc_stride = 0;
+    int strip_cols = 0;
+    int strip_rows = 0;
+    void *dev_mem = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    GraphKey gkey{};
+    // host end-to-end staging (allocated on first use)
+    uint8_t *img_dev = nullptr;
+    long long img_pitch = 0;
+    ctm_box *boxes_dev = nullptr;
+    float *disp_dev = nullptr;
+    float *depth_dev = nullptr;
+    uint8_t *flags_dev = nullptr;
+    ctm_frame *frames_host_pinned = nullptr;
+    int32_t *counts_host_pinned = nullptr;
+    ctm_frame *frames_dev2 = nullptr;
+    int32_t *counts_dev2 = nullptr;
+};
+
+namespace {
+
+inline long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
+
+bool params_valid(const ctm_params &p)
+{
+    if (p.win_w < 1 || p.win_h < 1 || (p.win_w & 1) == 0 || (p.win_h & 1) == 0) return false;
+    if (p.win_w > kMaxWin || p.win_h > kMaxWin) return false;
+    if (p.win_w * p.win_h + (p.sentinel ? 1 : 0) > 64) return false;
+    if (p.sentinel != 0 && p.sentinel != 1) return false;
+    if (p.close_factor < 1 || p.close_factor > 8) return false;
+    if (p.far_dmin > p.far_dmax || p.close_dmin > p.close_dmax || p.dy_min > p.dy_max) return false;
+    const long long ndy = (long long)p.dy_max - p.dy_min + 1;
+    if (((long long)p.far_dmax - p.far_dmin + 1) * ndy > kMaxCand) return false;
+    if (((long long)p.close_dmax - p.close_dmin + 1) * ndy > kMaxCand) return false;
+    if (p.grid_g < 1 || p.grid_g > kMaxGrid) return false;
+    if (p.pts_side < 1 || p.pts_side > kMaxPtsSide) return false;
+    if (p.min_pts < 1 || p.fb_tol < 0 || p.agg_nmin < 1) return false;
+    if (p.agg_mode != 0 && p.agg_mode != 1) return false;
+    if (!(p.trim_frac >= 0.0f && p.trim_frac < 0.5f)) return false;
+    if (!(p.agg_tau_d == p.agg_tau_d)) return false;
+    if (p.max_occluders < 0 || p.max_occluders > kMaxOcc) return false;
+    return true;
+}
+
+MatchArgs make_args(const ctm_ctx *ctx, const ctm_frame *frames, const int32_t *counts,
+                    const ctm_box *boxes, float *disp, float *depth, uint8_t *flags,
+                    const ctm_debug *dbg)
+{
+    MatchArgs a;
+    a.ws = ctx->ws;
+    a.caps = ctx->caps;
+    a.p = ctx->p;
+    a.frames = frames;
+    a.counts_in = counts;
+    a.boxes = boxes;
+    a.disp = disp;
+    a.depth = depth;
+    a.flags = flags;
+    a.dbg.blocks = dbg ? dbg->blocks : nullptr;
+    a.dbg.cost_f = dbg ? dbg->cost_f : nullptr;
+    a.dbg.cost_b = dbg ? dbg->cost_b : nullptr;
+    a.nc_stride = ctx->nc_stride;
+    a.strip_cols = ctx->strip_cols;
+    a.strip_rows = ctx->strip_rows;
+    return a;
+}
+
+int enqueue_batch(ctm_ctx *ctx, const MatchArgs &a, int frames_grid, int match_grid, cudaStream_t s)
+{
+    MatchArgs b = a;
+    b.caps.max_frames = std::min(ctx->caps.max_frames, frames_grid);
+    cudaError_t e = launch_census_batch(b, s);
+    if (e == cudaSuccess) e = launch_plan(b, s);
+    if (e == cudaSuccess) e = launch_match_persistent(b, match_grid, s);
+    return e == cudaSuccess ? CTM_OK : CTM_ECUDA;
+}
+
+int set_device(const ctm_ctx *ctx)
+{
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return CTM_ENODEV;
+    if (cur != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess) return CTM_ENODEV;
+    return CTM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ctm_status_str(int status)
+{
+    switch (status) {
+    case CTM_OK: return "ok";
+    case CTM_EINVAL: return "invalid argument";
+    case CTM_ENOMEM: return "out of memory or beyond context capacity";
+    case CTM_ECUDA: return "CUDA error";
+    case CTM_ENODEV: return "no usable CUDA device";
+    default: return "unknown status";
+    }
+}
+
+int ctm_default_params(ctm_params *p)
+{
+    if (!p) return CTM_EINVAL;
+    p->win_w = 9;
+    p->win_h = 7;
+    p->sentinel = 1;
+    p->far_side_px = 40;
+    p->close_factor = 2;
+    p->far_dmin = 0;
+    p->far_dmax = 31;
+    p->close_dmin = 0;
+    p->close_dmax = 127;
+    p->dy_min = 0;
+    p->dy_max = 0;
+    p->grid_g = 4;
+    p->pts_side = 16;
+    p->min_pts = 16;
+    p->fb_tol = 1;
+    p->agg_tau_d = 1.0f;
+    p->agg_nmin = 6;
+    p->agg_mode = 0;
+    p->trim_frac = 0.2f;
+    p->max_occluders = 16;
+    return CTM_OK;
+}
+
+int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width, int max_height,
+               int max_boxes)
+{
+    if (!out || !p) return CTM_EINVAL;
+    *out = nullptr;
+    if (!params_valid(*p)) return CTM_EINVAL;
+    if (max_frames < 1 || max_frames > 16383 || max_width < 1 || max_height < 1 ||
+        max_width > 32768 || max_height > 32768 || max_boxes < 1 || max_boxes > (1 << 22))
+        return CTM_EINVAL;
+    int dev = 0, n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n < 1) return CTM_ENODEV;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CTM_ENODEV;
+
+    ctm_ctx *ctx = new (std::nothrow) ctm_ctx();
+    if (!ctx) return CTM_ENOMEM;
+    ctx->device = dev;
+    ctx->p = *p;
+    cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    const int slots = p->grid_g * p->grid_g;
+    ctx->caps.max_frames = max_frames;
+    ctx->caps.max_width = max_width;
+    ctx->caps.max_height = max_height;
+    ctx->caps.max_boxes = max_boxes;
+    ctx->caps.max_blocks = max_boxes * std::max(slots, 1);
+    const int ndy = p->dy_max - p->dy_min + 1;
+    const int nd_max = std::max(p->far_dmax - p->far_dmin + 1, p->close_dmax - p->close_dmin + 1);
+    ctx->nc_stride = nd_max * ndy;
+    ctx->strip_rows = p->pts_side * ndy;
+    int cols = (int)round_up(std::max(nd_max + 128, 256), 32);
+    while (cols > nd_max && (long long)ctx->strip_rows * cols * 8 > 96 * 1024) cols -= 32;
+    cols = std::max(cols, (int)round_up(nd_max, 8));
+    if ((long long)ctx->strip_rows * cols * 8 > 180 * 1024) { delete ctx; return CTM_EINVAL; }
+    ctx->strip_cols = cols;
+
+    // workspace layout (one allocation)
+    const long long pitch1 = round_up(max_width, 32);
+    const int k = p->close_factor;
+    const long long Wk = (max_width + k - 1) / k, Hk = (max_height + k - 1) / k;
+    const long long pitchk = k == 1 ? 0 : round_up(Wk, 32);
+    const long long plane1 = pitch1 * max_height;
+    const long long planek = k == 1 ? 0 : pitchk * Hk;
+    const long long frame_stride = 2 * plane1 + 2 * planek;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = (size_t)round_up(off + bytes, 256); return o; };
+    const size_t o_census = take(sizeof(uint64_t) * (size_t)frame_stride * max_frames);
+    const size_t o_plans = take(sizeof(BoxPlan) * (size_t)max_boxes);
+    const size_t o_occ = take(sizeof(int4) * (size_t)max_boxes * kMaxOcc);
+    const size_t o_nblk = take(sizeof(int) * (size_t)max_boxes);
+    const size_t o_base = take(sizeof(int) * (size_t)max_boxes);
+    const size_t o_blocks = take(sizeof(int2) * (size_t)ctx->caps.max_blocks);
+    const size_t o_blkres = take(sizeof(BlockResult) * (size_t)ctx->caps.max_blocks);
+    const size_t o_done = take(sizeof(int) * (size_t)max_boxes);
+    const size_t o_counts = take(sizeof(Counts));
+    const size_t o_frames = take(sizeof(ctm_frame) * (size_t)max_frames);
+    const size_t o_cin = take(sizeof(int) * 4);
+    if (cudaMalloc(&ctx->dev_mem, off) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return CTM_ENOMEM;
+    }
+    char *base = static_cast<char *>(ctx->dev_mem);
+    Workspace &ws = ctx->ws;
+    ws.census = reinterpret_cast<uint64_t *>(base + o_census);
+    ws.frame_stride = frame_stride;
+    ws.plane1_elems = plane1;
+    ws.planek_elems = planek;
+    ws.pitch1 = pitch1;
+    ws.pitchk = pitchk;
+    ws.plans = reinterpret_cast<BoxPlan *>(base + o_plans);
+    ws.occ = reinterpret_cast<int4 *>(base + o_occ);
+    ws.nblk = reinterpret_cast<int *>(base + o_nblk);
+    ws.blk_base = reinterpret_cast<int *>(base + o_base);
+    ws.blocks = reinterpret_cast<int2 *>(base + o_blocks);
+    ws.blkres = reinterpret_cast<BlockResult *>(base + o_blkres);
+    ws.box_done = reinterpret_cast<int *>(base + o_done);
+    ws.counts = reinterpret_cast<Counts *>(base + o_counts);
+    ws.frames = reinterpret_cast<ctm_frame *>(base + o_frames);
+    ws.counts_in = reinterpret_cast<int *>(base + o_cin);
+    if (cudaMemset(ctx->dev_mem, 0, off) != cudaSuccess) {
+        ctm_destroy(ctx);
+        return CTM_ECUDA;
+    }
+    MatchArgs a = make_args(ctx, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    if (match_configure(a, &ctx->ctas_per_sm) != cudaSuccess || ctx->ctas_per_sm < 1) {
+        cudaGetLastError();
+        ctm_destroy(ctx);
+        return CTM_ECUDA;
+    }
+    if (cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        ctm_destroy(ctx);
+        return CTM_ECUDA;
+    }
+    *out = ctx;
+    return CTM_OK;
+}
+
+void ctm_destroy(ctm_ctx *ctx)
+{
+    if (!ctx) return;
+    set_device(ctx);
+    cudaDeviceSynchronize();
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+    if (ctx->dev_mem) cudaFree(ctx->dev_mem);
+    if (ctx->img_dev) cudaFree(ctx->img_dev);
+    if (ctx->frames_host_pinned) cudaFreeHost(ctx->frames_host_pinned);
+    if (ctx->counts_host_pinned) cudaFreeHost(ctx->counts_host_pinned);
+    cudaGetLastError();
+    delete ctx;
+}
+
+int ctm_census_build(const uint8_t *img_dev, int width, int height, int pitch, int factor,
+                     int win_w, int win_h, int sentinel, uint64_t *codes_dev, int64_t codes_pitch,
+                     ctm_stream stream)
+{
+    if (!img_dev || !codes_dev || width < 1 || height < 1 || pitch < width) return CTM_EINVAL;
+    if (factor < 1 || factor > 64) return CTM_EINVAL;
+    if (win_w < 1 || win_h < 1 || (win_w & 1) == 0 || (win_h & 1) == 0 || win_w > kMaxWin ||
+        win_h > kMaxWin || win_w * win_h + (sentinel ? 1 : 0) > 64 || (sentinel != 0 && sentinel != 1))
+        return CTM_EINVAL;
+    const int Ws = (width + factor - 1) / factor;
+    if (codes_pitch < Ws) return CTM_EINVAL;
+    cudaError_t e = launch_census_single(img_dev, width, height, pitch, factor, win_w, win_h,
+                                         sentinel, codes_dev, codes_pitch, (cudaStream_t)stream);
+    return e == cudaSuccess ? CTM_OK : CTM_ECUDA;
+}
+
+static int check_frame_args(const ctm_ctx *ctx, const uint8_t *l, const uint8_t *r, int width,
+                            int height, int pitch, const ctm_box *boxes, int n_boxes, const float *disp,
+                            const float *depth, const uint8_t *flags)
+{
+    if (!ctx || !l || !r || width < 1 || height < 1 || pitch < width || n_boxes < 0) return CTM_EINVAL;
+    if (n_boxes > 0 && (!boxes || !disp || !depth || !flags)) return CTM_EINVAL;
+    if (width > ctx->caps.max_width || height > ctx->caps.max_height || n_boxes > ctx->caps.max_boxes)
+        return CTM_ENOMEM;
+    return CTM_OK;
+}
+
+int ctm_match_boxes(ctm_ctx *ctx, const uint8_t *left_dev, const uint8_t *right_dev, int width,
+                    int height, int pitch, const ctm_box *boxes_dev, int n_boxes, float f_px,
+                    float baseline_m, float *disp_dev, float *depth_dev, uint8_t *flags_dev,
+                    const ctm_debug *dbg, ctm_stream stream)
+{
+    int st = check_frame_args(ctx, left_dev, right_dev, width, height, pitch, boxes_dev, n_boxes,
+                              disp_dev, depth_dev, flags_dev);
+    if (st != CTM_OK) return st;
+    if ((st = set_device(ctx)) != CTM_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    ctm_frame fr{left_dev, right_dev, width, height, pitch, 0, n_boxes, f_px, baseline_m};
+    MatchArgs a = make_args(ctx, ctx->ws.frames, ctx->ws.counts_in, boxes_dev, disp_dev, depth_dev,
+                            flags_dev, dbg);
+    a.caps.max_width = std::min(ctx->caps.max_width, width);
+    a.caps.max_height = std::min(ctx->caps.max_height, height);
+    if (launch_stage_frame(a, fr, n_boxes, s) != cudaSuccess) return CTM_ECUDA;
+    const int slots = std::max(1, ctx->p.grid_g * ctx->p.grid_g);
+    const long long blocks_ub = (long long)std::max(n_boxes, 1) * slots;
+    const int grid = (int)std::min<long long>((long long)ctx->sm_count * ctx->ctas_per_sm, blocks_ub);
+    MatchArgs b = a;
+    b.caps.max_width = ctx->caps.max_width;   // plan-time validation uses the capacity
+    b.caps.max_height = ctx->caps.max_height;
+    // census grid for this frame only
+    MatchArgs c = b;
+    c.caps.max_width = width;
+    c.caps.max_height = height;
+    c.caps.max_frames = 1;
+    cudaError_t e = launch_census_batch(c, s);
+    b.caps.max_frames = 1;
+    if (e == cudaSuccess) e = launch_plan(b, s);
+    if (e == cudaSuccess) e = launch_match_persistent(b, grid, s);
+    return e == cudaSuccess ? CTM_OK : CTM_ECUDA;
+}
+
+int ctm_match_boxes_plain(ctm_ctx *ctx, const uint8_t *left_dev, const uint8_t *right_dev,
+                          int width, int height, int pitch, const ctm_box *boxes_dev, int n_boxes,
+                          float f_px, float baseline_m, float *disp_dev, float *depth_dev,
+                          uint8_t *flags_dev, ctm_stream stream)
+{
+    int st = check_frame_args(ctx, left_dev, right_dev, width, height, pitch, boxes_dev, n_boxes,
+                              disp_dev, depth_dev, flags_dev);
+    if (st != CTM_OK) return st;
+    if ((st = set_device(ctx)) != CTM_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    ctm_frame fr{left_dev, right_dev, width, height, pitch, 0, n_boxes, f_px, baseline_m};
+    MatchArgs a = make_args(ctx, ctx->ws.frames, ctx->ws.counts_in, boxes_dev, disp_dev, depth_dev,
+                            flags_dev, nullptr);
+    if (launch_stage_frame(a, fr, n_boxes, s) != cudaSuccess) return CTM_ECUDA;
+    MatchArgs c = a;
+    c.caps.max_width = width;
+    c.caps.max_height = height;
+    c.caps.max_frames = 1;
+    cudaError_t e = launch_census_batch(c, s);
+    a.caps.max_frames = 1;
+    if (e == cudaSuccess) e = launch_plan(a, s);
+    for (int i = 0; i < n_boxes && e == cudaSuccess; ++i) e = launch_match_box(a, i, s);
+    return e == cudaSuccess ? CTM_OK : CTM_ECUDA;
+}
+
+int ctm_match_batch(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *counts_dev,
+                    const ctm_box *boxes_dev, float *disp_dev, float *depth_dev, uint8_t *flags_dev,
+                    const ctm_debug *dbg, int use_graph, ctm_stream stream)
+{
+    if (!ctx || !frames_dev || !counts_dev || !boxes_dev || !disp_dev || !depth_dev || !flags_dev)
+        return CTM_EINVAL;
+    int st = set_device(ctx);
+    if (st != CTM_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    MatchArgs a = make_args(ctx, frames_dev, counts_dev, boxes_dev, disp_dev, depth_dev, flags_dev, dbg);
+    const int grid = ctx->sm_count * ctx->ctas_per_sm;
+    if (!use_graph) return enqueue_batch(ctx, a, ctx->caps.max_frames, grid, s);
+
+    GraphKey key{frames_dev, counts_dev, boxes_dev, disp_dev, depth_dev, flags_dev,
+                 dbg ? (const void *)dbg->blocks : nullptr, dbg ? (const void *)dbg->cost_f : nullptr,
+                 dbg ? (const void *)dbg->cost_b : nullptr};
+    if (!ctx->gexec || !(key == ctx->gkey)) {
+        if (ctx->gexec) {
+            cudaGraphExecDestroy(ctx->gexec);
+            ctx->gexec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return CTM_ECUDA;
+        const int r = enqueue_batch(ctx, a, ctx->caps.max_frames, grid, ctx->capture_stream);
+        const cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &graph);
+        if (r != CTM_OK || e != cudaSuccess || !graph) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return CTM_ECUDA;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            ctx->gexec = nullptr;
+            cudaGetLastError();
+            return CTM_ECUDA;
+        }
+        ctx->gkey = key;
+    }
+    return cudaGraphLaunch(ctx->gexec, s) == cudaSuccess ? CTM_OK : CTM_ECUDA;
+}
+
+int ctm_match_batch_profiled(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *counts_dev,
+                             const ctm_box *boxes_dev, float *disp_dev, float *depth_dev,
+                             uint8_t *flags_dev, void *const events[4], ctm_stream stream)
+{
+    if (!ctx || !frames_dev || !counts_dev || !boxes_dev || !disp_dev || !depth_dev || !flags_dev ||
+        !events || !events[0] || !events[1] || !events[2] || !events[3])
+        return CTM_EINVAL;
+    int st = set_device(ctx);
+    if (st != CTM_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    MatchArgs a = make_args(ctx, frames_dev, counts_dev, boxes_dev, disp_dev, depth_dev, flags_dev,
+                            nullptr);
+    const int grid = ctx->sm_count * ctx->ctas_per_sm;
+    cudaError_t e = cudaEventRecord((cudaEvent_t)events[0], s);
+    if (e == cudaSuccess) e = launch_census_batch(a, s);
+    if (e == cudaSuccess) e = cudaEventRecord((cudaEvent_t)events[1], s);
+    if (e == cudaSuccess) e = launch_plan(a, s);
+    if (e == cudaSuccess) e = cudaEventRecord((cudaEvent_t)events[2], s);
+    if (e == cudaSuccess) e = launch_match_persistent(a, grid, s);
+    if (e == cudaSuccess) e = cudaEventRecord((cudaEvent_t)events[3], s);
+    if (e != cudaSuccess) { cudaGetLastError(); return CTM_ECUDA; }
+    return CTM_OK;
+}
+
+int ctm_match_batch_host(ctm_ctx *ctx, const ctm_frame *frames_host, int n_frames,
+                         const ctm_box *boxes_host, int n_boxes, float *disp_host,
+                         float *depth_host, uint8_t *flags_host, ctm_stream stream)
+{
+    if (!ctx || !frames_host || n_frames < 1 || n_boxes < 0) return CTM_EINVAL;
+    if (n_boxes > 0 && (!boxes_host || !disp_host || !depth_host || !flags_host)) return CTM_EINVAL;
+    if (n_frames > ctx->caps.max_frames || n_boxes > ctx->caps.max_boxes) return CTM_ENOMEM;
+    for (int i = 0; i < n_frames; ++i) {
+        const ctm_frame &f = frames_host[i];
+        if (!f.left || !f.right || f.width < 1 || f.height < 1 || f.pitch < f.width) return CTM_EINVAL;
+        if (f.width > ctx->caps.max_width || f.height > ctx->caps.max_height) return CTM_ENOMEM;
+    }
+    int st = set_device(ctx);
+    if (st != CTM_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!ctx->img_dev) {
+        ctx->img_pitch = round_up(ctx->caps.max_width, 128);
+        const size_t img_bytes = (size_t)ctx->img_pitch * ctx->caps.max_height * 2 * ctx->caps.max_frames;
+        size_t off = 0;
+        auto take = [&](size_t bytes) { size_t o = off; off = (size_t)round_up(off + bytes, 256); return o; };
+        const size_t o_img = take(img_bytes);
+        const size_t o_boxes = take(sizeof(ctm_box) * (size_t)ctx->caps.max_boxes);
+        const size_t o_disp = take(sizeof(float) * (size_t)ctx->caps.max_boxes);
+        const size_t o_depth = take(sizeof(float) * (size_t)ctx->caps.max_boxes);
+        const size_t o_flags = take((size_t)ctx->caps.max_boxes);
+        const size_t o_frames = take(sizeof(ctm_frame) * (size_t)ctx->caps.max_frames);
+        const size_t o_counts = take(sizeof(int32_t) * 4);
+        void *mem = nullptr;
+        if (cudaMalloc(&mem, off) != cudaSuccess) { cudaGetLastError(); return CTM_ENOMEM; }
+        if (cudaMallocHost(&ctx->frames_host_pinned, sizeof(ctm_frame) * ctx->caps.max_frames) != cudaSuccess ||
+            cudaMallocHost(&ctx->counts_host_pinned, sizeof(int32_t) * 4) != cudaSuccess) {
+            cudaFree(mem);
+            if (ctx->frames_host_pinned) cudaFreeHost(ctx->frames_host_pinned);
+            ctx->frames_host_pinned = nullptr;
+            cudaGetLastError();
+            return CTM_ENOMEM;
+        }
+        char *b = static_cast<char *>(mem);
+        ctx->img_dev = reinterpret_cast<uint8_t *>(b + o_img);
+        ctx->boxes_dev = reinterpret_cast<ctm_box *>(b + o_boxes);
+        ctx->disp_dev = reinterpret_cast<float *>(b + o_disp);
+        ctx->depth_dev = reinterpret_cast<float *>(b + o_depth);
+        ctx->flags_dev = reinterpret_cast<uint8_t *>(b + o_flags);
+        ctx->frames_dev2 = reinterpret_cast<ctm_frame *>(b + o_frames);
+        ctx->counts_dev2 = reinterpret_cast<int32_t *>(b + o_counts);
+    }
+    const size_t plane = (size_t)ctx->img_pitch * ctx->caps.max_height;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < n_frames && e == cudaSuccess; ++i) {
+        const ctm_frame &f = frames_host[i];
+        uint8_t *dl = ctx->img_dev + plane * (2 * (size_t)i);
+        uint8_t *dr = dl + plane;
+        e = cudaMemcpy2DAsync(dl, ctx->img_pitch, f.left, f.pitch, f.width, f.height, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(dr, ctx->img_pitch, f.right, f.pitch, f.width, f.height, cudaMemcpyHostToDevice, s);
+        ctm_frame g = f;
+        g.left = dl;
+        g.right = dr;
+        g.pitch = (int32_t)ctx->img_pitch;
+        ctx->frames_host_pinned[i] = g;
+    }
+    ctx->counts_host_pinned[0] = n_frames;
+    ctx->counts_host_pinned[1] = n_boxes;
+    if (e == cudaSuccess && n_boxes > 0)
+        e = cudaMemcpyAsync(ctx->boxes_dev, boxes_host, sizeof(ctm_box) * n_boxes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->frames_dev2, ctx->frames_host_pinned, sizeof(ctm_frame) * n_frames,
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->counts_dev2, ctx->counts_host_pinned, sizeof(int32_t) * 2,
+                            cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) { cudaGetLastError(); return CTM_ECUDA; }
+    st = ctm_match_batch(ctx, ctx->frames_dev2, ctx->counts_dev2, ctx->boxes_dev, ctx->disp_dev,
+                         ctx->depth_dev, ctx->flags_dev, nullptr, 1, stream);
+    if (st != CTM_OK) return st;
+    if (n_boxes > 0) {
+        e = cudaMemcpyAsync(disp_host, ctx->disp_dev, sizeof(float) * n_boxes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(depth_host, ctx->depth_dev, sizeof(float) * n_boxes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(flags_host, ctx->flags_dev, (size_t)n_boxes, cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { cudaGetLastError(); return CTM_ECUDA; }
+    return CTM_OK;
+}
+
+int ctm_get_stats(ctm_ctx *ctx, ctm_stats *out, ctm_stream stream)
+{
+    if (!ctx || !out) return CTM_EINVAL;
+    int st = set_device(ctx);
+    if (st != CTM_OK) return st;
+    Counts c;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(&c, ctx->ws.counts, sizeof(Counts), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return CTM_ECUDA;
+    }
+    out->cost_evals = c.evals;
+    out->n_blocks = c.n_blocks;
+    out->n_boxes = c.n_boxes;
+    return CTM_OK;
+}
+
+int ctm_probe_int_rate(int kind, int iters, double *ops_per_clk_per_sm)
+{
+    if ((kind != 0 && kind != 1) || iters < 1 || !ops_per_clk_per_sm) return CTM_EINVAL;
+    return run_int_probe(kind, iters, ops_per_clk_per_sm) == cudaSuccess ? CTM_OK : CTM_ECUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,188 @@
+// plan.cu -- device-side planning of Algorithm 2's per-box steps.
+//
+// plan_boxes_kernel (one CTA per frame): clip each box to its frame, classify it
+// FAR or CLOSE by its larger side against tau_s (Sec. 4.3.4), map it to its
+// matching grid (full resolution for FAR, the decimated grid for CLOSE), count
+// its blocks, and select its occluders -- overlapping boxes of the same frame
+// with a larger bottom y (Sec. 4.3.5), nearest (largest bottom y) first, at most
+// max_occluders.  Boxes that are empty after clipping get their outputs here.
+//
+// plan_scan_kernel (one CTA): exclusive scan of the block counts, the flat
+// (box, slot) work list the matching kernel drains, and counter reset.  All
+// counts come from device memory so a captured graph replays with new inputs.
+#include <math.h>
+
+#include "ctm_internal.cuh"
+
+namespace ctm {
+namespace {
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+__device__ __forceinline__ int4 clip_box(const ctm_box &b, int W, int H)
+{
+    int4 r;
+    r.x = b.x0 < 0 ? 0 : b.x0;
+    r.y = b.y0 < 0 ? 0 : b.y0;
+    r.z = b.x1 > W ? W : b.x1;
+    r.w = b.y1 > H ? H : b.y1;
+    if (r.z <= r.x || r.w <= r.y) r = make_int4(0, 0, 0, 0);
+    return r;
+}
+
+__device__ __forceinline__ bool overlaps(int4 a, int4 b)
+{
+    const int ix0 = max(a.x, b.x), ix1 = min(a.z, b.z);
+    const int iy0 = max(a.y, b.y), iy1 = min(a.w, b.w);
+    return ix1 > ix0 && iy1 > iy0;
+}
+
+__global__ void stage_frame_kernel(ctm_frame *frames, int *counts_in, ctm_frame f, int n_boxes)
+{
+    frames[0] = f;
+    counts_in[0] = 1;
+    counts_in[1] = n_boxes;
+}
+
+__global__ void __launch_bounds__(kPlanThreads) plan_boxes_kernel(MatchArgs a)
+{
+    const int f = blockIdx.x;
+    const int nf = clampi(a.counts_in[0], 0, a.caps.max_frames);
+    const int nb_total = clampi(a.counts_in[1], 0, a.caps.max_boxes);
+    if (f >= nf) return;
+    const ctm_frame fr = a.frames[f];
+    const bool bad_frame = fr.width < 1 || fr.height < 1 || fr.width > a.caps.max_width ||
+                           fr.height > a.caps.max_height || fr.pitch < fr.width ||
+                           fr.left == nullptr || fr.right == nullptr;
+    const int begin = clampi(fr.box_begin, 0, nb_total);
+    const int end = clampi(fr.box_begin + fr.box_count, begin, nb_total);
+    const ctm_params &p = a.p;
+    const int K = p.max_occluders < kMaxOcc ? p.max_occluders : kMaxOcc;
+
+    for (int i = begin + threadIdx.x; i < end; i += blockDim.x) {
+        const int4 r = clip_box(a.boxes[i], fr.width, fr.height);
+        const int w = r.z - r.x, h = r.w - r.y;
+        const int side = w > h ? w : h;
+        const int far = side < p.far_side_px ? 1 : 0;
+        const int k = far ? 1 : p.close_factor;
+        BoxPlan P;
+        P.cx0 = r.x; P.cy0 = r.y; P.cx1 = r.z; P.cy1 = r.w;
+        // decimated pixel x belongs to the box iff its source pixel k x does
+        P.sx0 = ceil_div_nn(r.x, k); P.sx1 = ceil_div_nn(r.z, k);
+        P.sy0 = ceil_div_nn(r.y, k); P.sy1 = ceil_div_nn(r.w, k);
+        P.frame = f;
+        P.far = far;
+        P.k = k;
+        P.g = far ? 1 : p.grid_g;
+        P.dmin = far ? p.far_dmin : p.close_dmin;
+        P.dmax = far ? p.far_dmax : p.close_dmax;
+        P.Ws = ceil_div_nn(fr.width, k);
+        P.Hs = ceil_div_nn(fr.height, k);
+        P.fb = __fmul_rn(fr.f_px, fr.baseline_m);
+        const bool empty = bad_frame || w <= 0 || h <= 0 || P.sx1 <= P.sx0 || P.sy1 <= P.sy0;
+        P.nblk = empty ? 0 : P.g * P.g;
+
+        // occluders: overlap with positive area and strictly larger bottom y;
+        // keep the K with the largest bottom y (ties: lower index first)
+        int ky[kMaxOcc];
+        int kj[kMaxOcc];
+        int nocc = 0;
+        if (!empty && K > 0) {
+            for (int j = begin; j < end; ++j) {
+                if (j == i) continue;
+                const int4 q = clip_box(a.boxes[j], fr.width, fr.height);
+                if (!(q.w > r.w) || !overlaps(r, q)) continue;
+                // insertion into the descending list (j ascending, so ties keep order)
+                int pos = nocc;
+                while (pos > 0 && ky[pos - 1] < q.w) --pos;
+                if (pos >= K) continue;
+                const int last = nocc < K ? nocc : K - 1;
+                for (int t = last; t > pos; --t) { ky[t] = ky[t - 1]; kj[t] = kj[t - 1]; }
+                ky[pos] = q.w;
+                kj[pos] = j;
+                if (nocc < K) ++nocc;
+            }
+            for (int t = 0; t < nocc; ++t)
+                a.ws.occ[(long long)i * kMaxOcc + t] = clip_box(a.boxes[kj[t]], fr.width, fr.height);
+        }
+        P.nocc = nocc;
+        a.ws.plans[i] = P;
+        a.ws.nblk[i] = P.nblk;
+        if (P.nblk == 0) {
+            a.disp[i] = __int_as_float(0x7fc00000);
+            a.depth[i] = __int_as_float(0x7fc00000);
+            a.flags[i] = (uint8_t)((far ? CTM_BOX_FAR : 0) | CTM_BOX_EMPTY);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) plan_scan_kernel(MatchArgs a)
+{
+    __shared__ int warp_tot[kScanThreads / 32];
+    __shared__ int s_running;
+    const int nb = clampi(a.counts_in[1], 0, a.caps.max_boxes);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_running = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += kScanThreads) {
+        const int i = base + threadIdx.x;
+        const int v = i < nb ? a.ws.nblk[i] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int t = warp_tot[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            warp_tot[lane] = t;  // inclusive over warps
+        }
+        __syncthreads();
+        const int warp_ex = warp > 0 ? warp_tot[warp - 1] : 0;
+        const int ex = s_running + warp_ex + x - v;
+        if (i < nb) {
+            a.ws.blk_base[i] = ex;
+            a.ws.box_done[i] = 0;
+            for (int s = 0; s < v; ++s) a.ws.blocks[ex + s] = make_int2(i, s);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_running += warp_tot[kScanThreads / 32 - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        Counts *c = a.ws.counts;
+        c->n_frames = clampi(a.counts_in[0], 0, a.caps.max_frames);
+        c->n_boxes = nb;
+        c->n_blocks = s_running < a.caps.max_blocks ? s_running : a.caps.max_blocks;
+        c->queue_head = 0;
+        c->evals = 0ull;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_stage_frame(const MatchArgs &a, ctm_frame f, int n_boxes, cudaStream_t s)
+{
+    stage_frame_kernel<<<1, 1, 0, s>>>(a.ws.frames, a.ws.counts_in, f, n_boxes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plan(const MatchArgs &a, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(a.ws.nblk, 0, sizeof(int) * (size_t)a.caps.max_boxes, s);
+    if (e != cudaSuccess) return e;
+    plan_boxes_kernel<<<a.caps.max_frames, kPlanThreads, 0, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    plan_scan_kernel<<<1, kScanThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace ctm

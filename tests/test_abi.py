@@ -1,0 +1,70 @@
+"""CPU-side checks of the C ABI: the library builds for sm_103a, loads without a
+GPU, exports every function include/ctm.h declares, and its ctypes structures
+match the header's layout.  No compute calls here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ctm.h")
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2604_07980_gb300 import build
+    try:
+        build.nvcc()
+    except RuntimeError:
+        pytest.skip("no CUDA toolkit")
+    return build.build()
+
+
+def _declared():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(ctm_\w+)\s*\(", txt, re.M)))
+
+
+def test_header_declares_binding_exports():
+    from paper_2604_07980_gb300 import binding as B
+    assert sorted(B.EXPORTS) == _declared()
+
+
+def test_library_exports_every_declared_symbol(built):
+    lib = ctypes.CDLL(built)
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_struct_layouts():
+    from paper_2604_07980_gb300 import binding as B
+    assert ctypes.sizeof(B.ctm_params) == 20 * 4
+    assert ctypes.sizeof(B.ctm_frame) == 48
+    assert B.BLOCK_DTYPE.itemsize == B.BLOCK_BYTES == 48
+    assert ctypes.sizeof(B.ctm_debug) == 24
+
+
+def test_status_strings_and_defaults(built):
+    from paper_2604_07980_gb300 import binding as B
+    L = B.lib()
+    assert L.ctm_status_str(0) == b"ok"
+    assert b"invalid" in L.ctm_status_str(-1)
+    p = B.make_params()
+    assert (p.win_w, p.win_h, p.sentinel, p.far_side_px, p.close_factor) == (9, 7, 1, 40, 2)
+    # argument checks that need no device
+    assert L.ctm_default_params(None) == B.CTM_EINVAL
+    assert L.ctm_census_build(None, 10, 10, 10, 1, 9, 7, 1, None, 10, None) == B.CTM_EINVAL
+    h = ctypes.c_void_p()
+    bad = B.make_params({"win_w": 8})
+    assert L.ctm_create(ctypes.byref(h), ctypes.byref(bad), 1, 64, 64, 4) == B.CTM_EINVAL
+    assert L.ctm_match_batch(None, None, None, None, None, None, None, None, 0, None) == B.CTM_EINVAL
+
+
+def test_binding_refuses_without_gpu():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    from paper_2604_07980_gb300 import binding as B
+    with pytest.raises(B.CtmError):
+        B.Context({}, 1, 64, 64, 4)
