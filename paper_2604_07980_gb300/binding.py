@@ -257,6 +257,9 @@ class Context:
     def match_batch_profiled(self, batch: "DeviceBatch", events, stream=None):
         """Non-graph batch recording 4 torch.cuda.Event(enable_timing=True) at the phase
         boundaries (before census, before planning, before matching, after matching)."""
+        for e in events:  # torch creates the CUDA event on its first record
+            if not e.cuda_event:
+                e.record()
         arr = (ctypes.c_void_p * 4)(*[e.cuda_event for e in events])
         _check(lib().ctm_match_batch_profiled(self._h, _ptr(batch.frames), _ptr(batch.counts),
                                               _ptr(batch.boxes), _ptr(batch.disp), _ptr(batch.depth),
