@@ -233,7 +233,7 @@ def main():
     for ev in evs:
         phase += [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])]
     phase /= args.steps
-    census_ms, plan_ms, match_ms = (float(x) for x in phase)
+    plan_ms, census_ms, match_ms = (float(x) for x in phase)
 
     # ---- plain one-launch-per-box path, frame by frame
     plain = None
@@ -313,7 +313,7 @@ def main():
                        "l2": "inputs larger than L2 (147 MB images + 1.5 GB census planes per step)",
                        "parallelism": f"frames sharded, {world} rank(s), no collective"},
             "boxes_per_s": w.n_boxes * world / (ms_per_step * 1e-3),
-            "phases_ms": {"census": census_ms, "plan": plan_ms, "match": match_ms},
+            "phases_ms": {"plan_and_mark": plan_ms, "census_roi": census_ms, "match": match_ms},
             "plain_per_box": plain,
             "e2e": {"value": evals_per_step * world / e2e_s / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
@@ -324,7 +324,7 @@ def main():
                          "peak_basis": f"{sms} SMs x {popc_clk:g} popc32/clk/SM (probe {popc_rate:.2f}) / "
                                        f"{POPC_PER_EVAL} per eval x {SM_MAX_MHZ:g} MHz"},
             "cpu_baseline": cpu,
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": 5 * args.steps,
             "clocks": clk,
         }
         print(json.dumps(line))

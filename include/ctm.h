@@ -193,7 +193,7 @@ int ctm_match_batch(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *co
 
 /* ctm_match_batch without a graph, recording four caller-created CUDA events
  * (cudaEvent_t handles, created with timing enabled) on `stream`: events[0]
- * before the census kernel, events[1] before planning, events[2] before the
+ * before planning, events[1] before the census kernel, events[2] before the
  * matching kernel, events[3] after it.  Used to time each phase on the stream
  * the kernels run on.  Errors as ctm_match_batch. */
 int ctm_match_batch_profiled(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *counts_dev,

@@ -7,6 +7,7 @@
 // sequence can be captured once into a CUDA graph and replayed.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -25,6 +26,7 @@ struct ctm_ctx {
     int device = 0;
     int sm_count = 0;
     int ctas_per_sm = 0;
+    int match_threads = 256;
     ctm_params p{};
     Caps caps{};
     Workspace ws{};
@@ -96,13 +98,23 @@ MatchArgs make_args(const ctm_ctx *ctx, const ctm_frame *frames, const int32_t *
     return a;
 }
 
-int enqueue_batch(ctm_ctx *ctx, const MatchArgs &a, int frames_grid, int match_grid, cudaStream_t s)
+// The launch sequence of one match call after the frame descriptors and counts
+// are in device memory: planning, census demand marking, census of the marked
+// tiles, matching.
+int enqueue_match(ctm_ctx *ctx, const MatchArgs &a, int frames_grid, int match_grid, cudaStream_t s,
+                  bool plain, int n_boxes_host)
 {
     MatchArgs b = a;
     b.caps.max_frames = std::min(ctx->caps.max_frames, frames_grid);
-    cudaError_t e = launch_census_batch(b, s);
-    if (e == cudaSuccess) e = launch_plan(b, s);
-    if (e == cudaSuccess) e = launch_match_persistent(b, match_grid, s);
+    cudaError_t e = launch_plan(b, s);
+    if (e == cudaSuccess) e = launch_mark(b, s);
+    if (e == cudaSuccess) e = launch_census_roi(b, ctx->sm_count * 8, s);
+    if (!plain) {
+        if (e == cudaSuccess) e = launch_match_persistent(b, ctx->match_threads, match_grid, s);
+    } else {
+        for (int i = 0; i < n_boxes_host && e == cudaSuccess; ++i)
+            e = launch_match_box(b, ctx->match_threads, i, s);
+    }
     return e == cudaSuccess ? CTM_OK : CTM_ECUDA;
 }
 
@@ -173,6 +185,11 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
     if (!ctx) return CTM_ENOMEM;
     ctx->device = dev;
     ctx->p = *p;
+    // matching CTA size (128 or 256 threads); CTM_MATCH_THREADS overrides for tuning
+    if (const char *env = getenv("CTM_MATCH_THREADS")) {
+        const int t = atoi(env);
+        if (t == 128 || t == 256) ctx->match_threads = t;
+    }
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, dev);
     const int slots = p->grid_g * p->grid_g;
     ctx->caps.max_frames = max_frames;
@@ -184,7 +201,8 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
     const int nd_max = std::max(p->far_dmax - p->far_dmin + 1, p->close_dmax - p->close_dmin + 1);
     ctx->nc_stride = nd_max * ndy;
     ctx->strip_rows = p->pts_side * ndy;
-    int cols = (int)round_up(std::max(nd_max + 128, 256), 32);
+    // strip width: the disparity range plus a 96-column span of points per chunk
+    int cols = (int)round_up(std::max(nd_max + 96, 192), 32);
     while (cols > nd_max && (long long)ctx->strip_rows * cols * 8 > 96 * 1024) cols -= 32;
     cols = std::max(cols, (int)round_up(nd_max, 8));
     if ((long long)ctx->strip_rows * cols * 8 > 180 * 1024) { delete ctx; return CTM_EINVAL; }
@@ -211,6 +229,15 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
     const size_t o_counts = take(sizeof(Counts));
     const size_t o_frames = take(sizeof(ctm_frame) * (size_t)max_frames);
     const size_t o_cin = take(sizeof(int) * 4);
+    // census demand bitmap
+    const int rows_q[4] = {max_height, max_height, k == 1 ? 0 : (int)Hk, k == 1 ? 0 : (int)Hk};
+    const int wq1 = (int)((((long long)max_width + kCensusTilePx - 1) / kCensusTilePx + 31) / 32);
+    const int wqk = (int)(((Wk + kCensusTilePx - 1) / kCensusTilePx + 31) / 32);
+    const int words_q[4] = {wq1, wq1, wqk, wqk};
+    int plane_off[5];
+    plane_off[0] = 0;
+    for (int q = 0; q < 4; ++q) plane_off[q + 1] = plane_off[q] + rows_q[q] * words_q[q];
+    const size_t o_bm = take(sizeof(uint32_t) * (size_t)plane_off[4] * max_frames);
     if (cudaMalloc(&ctx->dev_mem, off) != cudaSuccess) {
         cudaGetLastError();
         delete ctx;
@@ -234,12 +261,16 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
     ws.counts = reinterpret_cast<Counts *>(base + o_counts);
     ws.frames = reinterpret_cast<ctm_frame *>(base + o_frames);
     ws.counts_in = reinterpret_cast<int *>(base + o_cin);
+    ws.bitmap = reinterpret_cast<uint32_t *>(base + o_bm);
+    ws.bm_frame_words = plane_off[4];
+    for (int q = 0; q < 5; ++q) ws.bm_plane_off[q] = plane_off[q];
+    for (int q = 0; q < 4; ++q) ws.bm_row_words[q] = words_q[q];
     if (cudaMemset(ctx->dev_mem, 0, off) != cudaSuccess) {
         ctm_destroy(ctx);
         return CTM_ECUDA;
     }
     MatchArgs a = make_args(ctx, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
-    if (match_configure(a, &ctx->ctas_per_sm) != cudaSuccess || ctx->ctas_per_sm < 1) {
+    if (match_configure(a, ctx->match_threads, &ctx->ctas_per_sm) != cudaSuccess || ctx->ctas_per_sm < 1) {
         cudaGetLastError();
         ctm_destroy(ctx);
         return CTM_ECUDA;
@@ -307,25 +338,11 @@ int ctm_match_boxes(ctm_ctx *ctx, const uint8_t *left_dev, const uint8_t *right_
     ctm_frame fr{left_dev, right_dev, width, height, pitch, 0, n_boxes, f_px, baseline_m};
     MatchArgs a = make_args(ctx, ctx->ws.frames, ctx->ws.counts_in, boxes_dev, disp_dev, depth_dev,
                             flags_dev, dbg);
-    a.caps.max_width = std::min(ctx->caps.max_width, width);
-    a.caps.max_height = std::min(ctx->caps.max_height, height);
     if (launch_stage_frame(a, fr, n_boxes, s) != cudaSuccess) return CTM_ECUDA;
     const int slots = std::max(1, ctx->p.grid_g * ctx->p.grid_g);
     const long long blocks_ub = (long long)std::max(n_boxes, 1) * slots;
     const int grid = (int)std::min<long long>((long long)ctx->sm_count * ctx->ctas_per_sm, blocks_ub);
-    MatchArgs b = a;
-    b.caps.max_width = ctx->caps.max_width;   // plan-time validation uses the capacity
-    b.caps.max_height = ctx->caps.max_height;
-    // census grid for this frame only
-    MatchArgs c = b;
-    c.caps.max_width = width;
-    c.caps.max_height = height;
-    c.caps.max_frames = 1;
-    cudaError_t e = launch_census_batch(c, s);
-    b.caps.max_frames = 1;
-    if (e == cudaSuccess) e = launch_plan(b, s);
-    if (e == cudaSuccess) e = launch_match_persistent(b, grid, s);
-    return e == cudaSuccess ? CTM_OK : CTM_ECUDA;
+    return enqueue_match(ctx, a, 1, grid, s, false, n_boxes);
 }
 
 int ctm_match_boxes_plain(ctm_ctx *ctx, const uint8_t *left_dev, const uint8_t *right_dev,
@@ -342,15 +359,7 @@ int ctm_match_boxes_plain(ctm_ctx *ctx, const uint8_t *left_dev, const uint8_t *
     MatchArgs a = make_args(ctx, ctx->ws.frames, ctx->ws.counts_in, boxes_dev, disp_dev, depth_dev,
                             flags_dev, nullptr);
     if (launch_stage_frame(a, fr, n_boxes, s) != cudaSuccess) return CTM_ECUDA;
-    MatchArgs c = a;
-    c.caps.max_width = width;
-    c.caps.max_height = height;
-    c.caps.max_frames = 1;
-    cudaError_t e = launch_census_batch(c, s);
-    a.caps.max_frames = 1;
-    if (e == cudaSuccess) e = launch_plan(a, s);
-    for (int i = 0; i < n_boxes && e == cudaSuccess; ++i) e = launch_match_box(a, i, s);
-    return e == cudaSuccess ? CTM_OK : CTM_ECUDA;
+    return enqueue_match(ctx, a, 1, 0, s, true, n_boxes);
 }
 
 int ctm_match_batch(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *counts_dev,
@@ -364,7 +373,7 @@ int ctm_match_batch(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *co
     cudaStream_t s = (cudaStream_t)stream;
     MatchArgs a = make_args(ctx, frames_dev, counts_dev, boxes_dev, disp_dev, depth_dev, flags_dev, dbg);
     const int grid = ctx->sm_count * ctx->ctas_per_sm;
-    if (!use_graph) return enqueue_batch(ctx, a, ctx->caps.max_frames, grid, s);
+    if (!use_graph) return enqueue_match(ctx, a, ctx->caps.max_frames, grid, s, false, 0);
 
     GraphKey key{frames_dev, counts_dev, boxes_dev, disp_dev, depth_dev, flags_dev,
                  dbg ? (const void *)dbg->blocks : nullptr, dbg ? (const void *)dbg->cost_f : nullptr,
@@ -377,7 +386,7 @@ int ctm_match_batch(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *co
         cudaGraph_t graph = nullptr;
         if (cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return CTM_ECUDA;
-        const int r = enqueue_batch(ctx, a, ctx->caps.max_frames, grid, ctx->capture_stream);
+        const int r = enqueue_match(ctx, a, ctx->caps.max_frames, grid, ctx->capture_stream, false, 0);
         const cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &graph);
         if (r != CTM_OK || e != cudaSuccess || !graph) {
             if (graph) cudaGraphDestroy(graph);
@@ -410,11 +419,12 @@ int ctm_match_batch_profiled(ctm_ctx *ctx, const ctm_frame *frames_dev, const in
                             nullptr);
     const int grid = ctx->sm_count * ctx->ctas_per_sm;
     cudaError_t e = cudaEventRecord((cudaEvent_t)events[0], s);
-    if (e == cudaSuccess) e = launch_census_batch(a, s);
-    if (e == cudaSuccess) e = cudaEventRecord((cudaEvent_t)events[1], s);
     if (e == cudaSuccess) e = launch_plan(a, s);
+    if (e == cudaSuccess) e = launch_mark(a, s);
+    if (e == cudaSuccess) e = cudaEventRecord((cudaEvent_t)events[1], s);
+    if (e == cudaSuccess) e = launch_census_roi(a, ctx->sm_count * 8, s);
     if (e == cudaSuccess) e = cudaEventRecord((cudaEvent_t)events[2], s);
-    if (e == cudaSuccess) e = launch_match_persistent(a, grid, s);
+    if (e == cudaSuccess) e = launch_match_persistent(a, ctx->match_threads, grid, s);
     if (e == cudaSuccess) e = cudaEventRecord((cudaEvent_t)events[3], s);
     if (e != cudaSuccess) { cudaGetLastError(); return CTM_ECUDA; }
     return CTM_OK;

@@ -8,8 +8,6 @@
 
 namespace ctm {
 
-constexpr int kMatchThreads = 256;               // one CTA matches one block
-constexpr int kMatchWarps = kMatchThreads / 32;
 constexpr int kMaxPtsSide = 16;
 constexpr int kMaxPts = kMaxPtsSide * kMaxPtsSide;
 constexpr int kMaxCand = 256;                    // candidates per pass (8 slices of 32)
@@ -17,8 +15,6 @@ constexpr int kMaxGrid = 8;
 constexpr int kMaxSlots = kMaxGrid * kMaxGrid;
 constexpr int kMaxOcc = 32;
 constexpr int kMaxWin = 15;
-constexpr int kCensusTileW = 32;
-constexpr int kCensusTileH = 16;
 constexpr int kPlanThreads = 128;
 constexpr int kScanThreads = 1024;
 
@@ -64,6 +60,12 @@ struct Workspace {
     Counts *counts;
     ctm_frame *frames;         // staging for single-frame calls [max_frames]
     int *counts_in;            // staging {n_frames, n_boxes}
+    // census demand bitmap: one bit per 64-pixel tile of a plane row, per frame
+    // planes in the order L1, R1, Lk, Rk; words = 32 tiles
+    uint32_t *bitmap;
+    long long bm_frame_words;
+    int bm_plane_off[5];       // word offset of each plane within a frame (+ end)
+    int bm_row_words[4];       // words per row of each plane
 };
 
 struct Caps {
@@ -89,21 +91,52 @@ struct MatchArgs {
 
 __host__ __device__ inline int ceil_div_nn(int a, int b) { return (a + b - 1) / b; }
 
+// Sampled coordinate j of n on [b0, b1): the centre of the j-th of n equal cells
+// (Sec. 4.3.4's regular point grid).
+__device__ __forceinline__ int point_coord(int b0, int b1, int n, int j)
+{
+    return b0 + ((2 * j + 1) * (b1 - b0)) / (2 * n);
+}
+
+// Rectangle of block `slot` (row-major in a g x g grid) of a planned box, on its
+// matching grid, and its point counts per side.
+struct BlockRect {
+    int bx0, by0, bx1, by1, nx, ny;
+};
+
+__device__ __forceinline__ BlockRect block_rect(const BoxPlan &P, int slot, int pts_side)
+{
+    BlockRect r;
+    const int ga = slot % P.g, gb = slot / P.g;
+    const int bw = P.sx1 - P.sx0, bh = P.sy1 - P.sy0;
+    r.bx0 = P.sx0 + (ga * bw) / P.g;
+    r.bx1 = P.sx0 + ((ga + 1) * bw) / P.g;
+    r.by0 = P.sy0 + (gb * bh) / P.g;
+    r.by1 = P.sy0 + ((gb + 1) * bh) / P.g;
+    r.nx = min(r.bx1 - r.bx0, pts_side);
+    r.ny = min(r.by1 - r.by0, pts_side);
+    return r;
+}
+
 // Census launches (census.cu)
+constexpr int kCensusTilePx = 64;   // pixels per bitmap bit (one warp tile)
 cudaError_t launch_census_single(const uint8_t *img, int W, int H, int pitch, int k, int win_w,
                                  int win_h, int sentinel, uint64_t *out, long long out_pitch,
                                  cudaStream_t s);
-cudaError_t launch_census_batch(const MatchArgs &a, cudaStream_t s);
+cudaError_t launch_census_roi(const MatchArgs &a, int grid, cudaStream_t s);
+size_t census_smem_bytes(int win_h);
 
 // Planning (plan.cu)
 cudaError_t launch_stage_frame(const MatchArgs &a, ctm_frame f, int n_boxes, cudaStream_t s);
 cudaError_t launch_plan(const MatchArgs &a, cudaStream_t s);
+cudaError_t launch_mark(const MatchArgs &a, cudaStream_t s);
 
 // Matching (match.cu)
+// threads per matching CTA: 128 or 256
 size_t match_smem_bytes(const MatchArgs &a);
-cudaError_t match_configure(const MatchArgs &a, int *ctas_per_sm);
-cudaError_t launch_match_persistent(const MatchArgs &a, int grid, cudaStream_t s);
-cudaError_t launch_match_box(const MatchArgs &a, int box, cudaStream_t s);
+cudaError_t match_configure(const MatchArgs &a, int threads, int *ctas_per_sm);
+cudaError_t launch_match_persistent(const MatchArgs &a, int threads, int grid, cudaStream_t s);
+cudaError_t launch_match_box(const MatchArgs &a, int threads, int box, cudaStream_t s);
 
 // Probe (probe.cu)
 cudaError_t run_int_probe(int kind, int iters, double *ops_per_clk_per_sm);

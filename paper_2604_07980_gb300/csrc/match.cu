@@ -1,22 +1,26 @@
 // match.cu -- the Hamming-cost search of Algorithm 2 for every planned block.
 //
-// One CTA (256 threads) takes one block end to end:
-//   1. sample the block's point grid (Sec. 4.3.4), drop points whose left census
-//      is undefined or whose full-res position lies in a kept occluder
-//      (Sec. 4.3.5), and compact the survivors column-major in shared memory;
-//   2. forward pass: stage the right-image census strip the block can reach
-//      (sampled rows x [x - dmax, x - dmin]) in shared memory and evaluate
-//      Eq. census_cost, S(dy, d) = sum_p popc(C_L(p) ^ C_R(p.x - d, p.y + dy)),
-//      for every candidate: lanes own consecutive candidates, warps own point
-//      subsets, each thread keeps up to 8 candidate sums in registers;
+// One CTA takes one block end to end:
+//   1. sample the block's point grid (Sec. 4.3.4); copy the left census at every
+//      grid point, the block's occluders and the first forward strip into shared
+//      memory with asynchronous copies issued together (one memory round trip);
+//      drop points whose left census is undefined or whose full-res position
+//      lies in a kept occluder (Sec. 4.3.5) and compact the survivors
+//      column-major;
+//   2. forward pass over the right-image strip the block can reach (sampled rows
+//      x [x - dmax, x - dmin]): Eq. census_cost,
+//      S(dy, d) = sum_p popc(C_L(p) ^ C_R(p.x - d, p.y + dy)), for every
+//      candidate; lanes own consecutive candidates (conflict-free strip reads),
+//      warps own point subsets, each thread keeps up to 8 candidate sums in
+//      registers, and warps combine them with shared-memory atomics;
 //   3. first argmin over (dy, d) by warp min-reductions of (cost << 16 | index)
 //      keys, then Eq. subpixel in fp32 with IEEE division;
-//   4. backward pass (Sec. 4.3.3): queries are the right codes at the matched
-//      positions, the strip is the left census at [q.x + dmin, q.x + dmax];
-//   5. consistency |d_b - d_f| <= fb_tol, block record, and the last CTA to
-//      finish a box (atomic counter after a fence) aggregates its blocks
+//   4. backward pass (Sec. 4.3.3): the right codes at the matched positions and
+//      the left strip [q.x + dmin, q.x + dmax] arrive in one round trip;
+//   5. consistency |d_b - d_f| <= fb_tol, block record; the last CTA to finish a
+//      box (atomic counter after a fence) aggregates its blocks with one warp
 //      (Sec. 4.3.4) and writes disparity, Eq. 1 depth and flags.
-// Wide blocks are split into column chunks whose strip fits; chunk sums add up
+// Blocks wider than the strip are split into column chunks; chunk sums add up
 // because Eq. census_cost is a sum over points.
 #include <math.h>
 
@@ -25,22 +29,53 @@
 namespace ctm {
 namespace {
 
-__device__ __forceinline__ int point_coord(int b0, int b1, int n, int j)
+__device__ __forceinline__ unsigned smem_addr(const void *p)
 {
-    return b0 + ((2 * j + 1) * (b1 - b0)) / (2 * n);
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 struct Smem {
     uint64_t *strip;   // strip_rows * strip_cols
-    uint64_t *pcode;   // kMaxPts (left codes, later right query codes)
-    int *partial;      // kMatchWarps * kMaxCand
+    uint64_t *praw;    // kMaxPts: left code of grid point t = j * ny + m
+    uint64_t *pcode;   // kMaxPts: compacted codes (left, then right queries)
     int *cost;         // kMaxCand
     int *pmj;          // kMaxPts: (m << 8) | j
 };
 
+template <int NW>
+struct Shared {
+    int X[kMaxPtsSide];
+    int Y[kMaxPtsSide];
+    int colstart[kMaxPtsSide + 1];
+    int4 occ[kMaxOcc];
+    int warp_cnt[NW];
+    unsigned warp_min[NW];
+    float agg[kMaxSlots];
+    float agg_sorted[kMaxSlots];
+    int d_f, dy_f, s_m, s_0, s_p;
+    int d_b, dy_b;
+    int last;
+    int next;
+};
+
 struct BlockCtx {
     int box, slot, b;
-    int g, k, far;
+    int k, far;
     int dmin, dmax, nd, ndy, nc;
     int nx, ny, Ws, Hs;
     long long pitch;
@@ -48,33 +83,18 @@ struct BlockCtx {
     const uint64_t *CR;
 };
 
-struct Shared {
-    int X[kMaxPtsSide];
-    int Y[kMaxPtsSide];
-    int colstart[kMaxPtsSide + 1];
-    int4 occ[kMaxOcc];
-    int warp_cnt[kMatchWarps];
-    unsigned warp_min[kMatchWarps];
-    int n_valid;
-    int d_f, dy_f, s_m, s_0, s_p;
-    int d_b, dy_b;
-    int last;
-    int next;
-};
-
-// Sum of popcounts over the points of one chunk; T candidate slices per thread.
-template <int T>
-__device__ __forceinline__ void scan_chunk(const Smem &sm, const Shared &sh, int p0, int p1,
-                                           int ndy, int SWc, int xj0, const int (&coff)[8],
-                                           int (&acc)[8])
+// Sum of popcounts over the points [p0, p1) of one chunk; T candidate slices.
+template <int NW, int T>
+__device__ __forceinline__ void scan_chunk(const Smem &sm, const int *X, int p0, int p1, int ndy,
+                                           int SWc, int xj0, const int (&coff)[8], int (&acc)[8])
 {
     const int warp = threadIdx.x >> 5;
     int p = p0 + warp;
-    for (; p + kMatchWarps < p1; p += 2 * kMatchWarps) {
-        const uint64_t c0 = sm.pcode[p], c1 = sm.pcode[p + kMatchWarps];
-        const int mj0 = sm.pmj[p], mj1 = sm.pmj[p + kMatchWarps];
-        const int base0 = (mj0 >> 8) * ndy * SWc + sh.X[mj0 & 255] - xj0;
-        const int base1 = (mj1 >> 8) * ndy * SWc + sh.X[mj1 & 255] - xj0;
+    for (; p + NW < p1; p += 2 * NW) {
+        const uint64_t c0 = sm.pcode[p], c1 = sm.pcode[p + NW];
+        const int mj0 = sm.pmj[p], mj1 = sm.pmj[p + NW];
+        const int base0 = (mj0 >> 8) * ndy * SWc + X[mj0 & 255] - xj0;
+        const int base1 = (mj1 >> 8) * ndy * SWc + X[mj1 & 255] - xj0;
         const uint32_t l0 = (uint32_t)c0, h0 = (uint32_t)(c0 >> 32);
         const uint32_t l1 = (uint32_t)c1, h1 = (uint32_t)(c1 >> 32);
 #pragma unroll
@@ -88,7 +108,7 @@ __device__ __forceinline__ void scan_chunk(const Smem &sm, const Shared &sh, int
     if (p < p1) {
         const uint64_t c0 = sm.pcode[p];
         const int mj0 = sm.pmj[p];
-        const int base0 = (mj0 >> 8) * ndy * SWc + sh.X[mj0 & 255] - xj0;
+        const int base0 = (mj0 >> 8) * ndy * SWc + X[mj0 & 255] - xj0;
         const uint32_t l0 = (uint32_t)c0, h0 = (uint32_t)(c0 >> 32);
 #pragma unroll
         for (int t = 0; t < T; ++t) {
@@ -98,59 +118,111 @@ __device__ __forceinline__ void scan_chunk(const Smem &sm, const Shared &sh, int
     }
 }
 
-__device__ __forceinline__ void scan_dispatch(int T, const Smem &sm, const Shared &sh, int p0,
-                                              int p1, int ndy, int SWc, int xj0,
-                                              const int (&coff)[8], int (&acc)[8])
+template <int NW>
+__device__ __forceinline__ void scan_dispatch(int T, const Smem &sm, const int *X, int p0, int p1,
+                                              int ndy, int SWc, int xj0, const int (&coff)[8],
+                                              int (&acc)[8])
 {
     switch (T) {
-    case 1: scan_chunk<1>(sm, sh, p0, p1, ndy, SWc, xj0, coff, acc); break;
-    case 2: scan_chunk<2>(sm, sh, p0, p1, ndy, SWc, xj0, coff, acc); break;
-    case 3: scan_chunk<3>(sm, sh, p0, p1, ndy, SWc, xj0, coff, acc); break;
-    case 4: scan_chunk<4>(sm, sh, p0, p1, ndy, SWc, xj0, coff, acc); break;
-    case 5: scan_chunk<5>(sm, sh, p0, p1, ndy, SWc, xj0, coff, acc); break;
-    case 6: scan_chunk<6>(sm, sh, p0, p1, ndy, SWc, xj0, coff, acc); break;
-    case 7: scan_chunk<7>(sm, sh, p0, p1, ndy, SWc, xj0, coff, acc); break;
-    default: scan_chunk<8>(sm, sh, p0, p1, ndy, SWc, xj0, coff, acc); break;
+    case 1: scan_chunk<NW, 1>(sm, X, p0, p1, ndy, SWc, xj0, coff, acc); break;
+    case 2: scan_chunk<NW, 2>(sm, X, p0, p1, ndy, SWc, xj0, coff, acc); break;
+    case 3: scan_chunk<NW, 3>(sm, X, p0, p1, ndy, SWc, xj0, coff, acc); break;
+    case 4: scan_chunk<NW, 4>(sm, X, p0, p1, ndy, SWc, xj0, coff, acc); break;
+    case 5: scan_chunk<NW, 5>(sm, X, p0, p1, ndy, SWc, xj0, coff, acc); break;
+    case 6: scan_chunk<NW, 6>(sm, X, p0, p1, ndy, SWc, xj0, coff, acc); break;
+    case 7: scan_chunk<NW, 7>(sm, X, p0, p1, ndy, SWc, xj0, coff, acc); break;
+    default: scan_chunk<NW, 8>(sm, X, p0, p1, ndy, SWc, xj0, coff, acc); break;
     }
 }
 
-// One search pass; fwd = true: right strip, candidates d in [dmin, dmax] at
-// x - d, y + dy.  fwd = false: left strip around the forward match,
-// candidates at q.x + d', q.y - dy'.  Leaves cost[c] in shared memory and
-// returns the winning key (cost << 16 | c) in sh.warp_min[0].
-__device__ void search_pass(const MatchArgs &a, const BlockCtx &bc, const Smem &sm, Shared &sh,
-                            bool fwd)
+// Last point column of the chunk starting at j0 whose strip fits strip_cols.
+__device__ __forceinline__ int chunk_end(const int *X, int j0, int nx, int nd, int strip_cols)
 {
+    int j1 = j0 + 1;
+    while (j1 < nx && X[j1] - X[j0] + nd <= strip_cols) ++j1;
+    return j1;
+}
+
+// Issue the asynchronous copies of one strip chunk: rows (m, e) of the right
+// plane at Y_m + dy_min + e (forward) or of the left plane at
+// Y_m + dy_f - (dy_min + e) (backward), columns [colbase, colbase + SWc).
+// Positions outside the plane are written as 0.
+template <int NT>
+__device__ __forceinline__ void issue_strip(const BlockCtx &bc, const Smem &sm, const int *Y, bool fwd,
+                                            int dy_min, int dy_f, int colbase, int SWc)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rows = bc.ny * bc.ndy;
+    const uint64_t *plane = fwd ? bc.CR : bc.CL;
+    for (int r = warp; r < rows; r += NT / 32) {
+        const int m = r / bc.ndy;
+        const int e = r - m * bc.ndy;
+        const int y = fwd ? Y[m] + dy_min + e : Y[m] + dy_f - (dy_min + e);
+        uint64_t *dst = sm.strip + r * SWc;
+        const bool row_ok = y >= 0 && y < bc.Hs;
+        const uint64_t *src = plane + (row_ok ? (long long)y * bc.pitch : 0);
+        for (int c = lane; c < SWc; c += 32) {
+            const int x = colbase + c;
+            if (row_ok && x >= 0 && x < bc.Ws)
+                cp_async8(dst + c, src + x);
+            else
+                dst[c] = 0ull;
+        }
+    }
+}
+
+// Warp and CTA minimum of the keys (cost << 16 | c) over the candidates; the
+// result lands in sh.warp_min[0] and the costs stay in shared memory.
+template <int NT>
+__device__ __forceinline__ void argmin_pass(const MatchArgs &a, const BlockCtx &bc, const Smem &sm,
+                                            Shared<NT / 32> &sh, bool fwd)
+{
+    constexpr int NW = NT / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned key = 0xffffffffu;
+    int32_t *dbgc = fwd ? a.dbg.cost_f : a.dbg.cost_b;
+    const int slots = a.p.grid_g * a.p.grid_g;
+    for (int c = tid; c < bc.nc; c += NT) {
+        const int s = sm.cost[c];
+        key = min(key, ((unsigned)s << 16) | (unsigned)c);
+        if (dbgc) dbgc[((long long)bc.box * slots + bc.slot) * a.nc_stride + c] = s;
+    }
+    key = __reduce_min_sync(0xffffffffu, key);
+    if (lane == 0) sh.warp_min[warp] = key;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned m = sh.warp_min[0];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) m = min(m, sh.warp_min[w]);
+        sh.warp_min[0] = m;
+    }
+    __syncthreads();
+}
+
+// One search pass after its first strip chunk has been issued and landed.
+template <int NT>
+__device__ void search_pass(const MatchArgs &a, const BlockCtx &bc, const Smem &sm,
+                            Shared<NT / 32> &sh, bool fwd)
+{
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31;
     const int T = (bc.nc + 31) >> 5;
     int acc[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) acc[t] = 0;
-    const uint64_t *plane = fwd ? bc.CR : bc.CL;
     const int d_f = sh.d_f, dy_f = sh.dy_f;
-    const int dy_min = a.p.dy_min;
-
     int j0 = 0;
+    bool first = true;
     while (j0 < bc.nx) {
-        int j1 = j0 + 1;
-        while (j1 < bc.nx && sh.X[j1] - sh.X[j0] + bc.nd <= a.strip_cols) ++j1;
+        const int j1 = chunk_end(sh.X, j0, bc.nx, bc.nd, a.strip_cols);
         const int xj0 = sh.X[j0];
         const int SWc = sh.X[j1 - 1] - xj0 + bc.nd;
-        const int rows = bc.ny * bc.ndy;
-        const int colbase = fwd ? xj0 - bc.dmax : xj0 - d_f + bc.dmin;
-        const int total = rows * SWc;
-        for (int idx = tid; idx < total; idx += kMatchThreads) {
-            const int r = idx / SWc;
-            const int c = idx - r * SWc;
-            const int m = r / bc.ndy;
-            const int e = r - m * bc.ndy;
-            const int y = fwd ? sh.Y[m] + dy_min + e : sh.Y[m] + dy_f - (dy_min + e);
-            const int x = colbase + c;
-            uint64_t v = 0;
-            if (x >= 0 && x < bc.Ws && y >= 0 && y < bc.Hs) v = plane[(long long)y * bc.pitch + x];
-            sm.strip[idx] = v;
+        if (!first) {  // later chunks: load now (the first chunk was prefetched)
+            const int colbase = fwd ? xj0 - bc.dmax : xj0 - d_f + bc.dmin;
+            issue_strip<NT>(bc, sm, sh.Y, fwd, a.p.dy_min, dy_f, colbase, SWc);
+            cp_async_wait_all();
+            __syncthreads();
         }
-        __syncthreads();
         int coff[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
@@ -163,76 +235,76 @@ __device__ void search_pass(const MatchArgs &a, const BlockCtx &bc, const Smem &
             }
             coff[t] = o;
         }
-        scan_dispatch(T, sm, sh, sh.colstart[j0], sh.colstart[j1], bc.ndy, SWc, xj0, coff, acc);
+        scan_dispatch<NW>(T, sm, sh.X, sh.colstart[j0], sh.colstart[j1], bc.ndy, SWc, xj0, coff, acc);
         __syncthreads();
+        first = false;
         j0 = j1;
     }
-
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
         const int c = t * 32 + lane;
-        if (t < T && c < bc.nc) sm.partial[warp * kMaxCand + c] = acc[t];
+        if (t < T && c < bc.nc) atomicAdd(&sm.cost[c], acc[t]);
     }
     __syncthreads();
-    unsigned key = 0xffffffffu;
-    if (tid < bc.nc) {
-        int s = 0;
-#pragma unroll
-        for (int w = 0; w < kMatchWarps; ++w) s += sm.partial[w * kMaxCand + tid];
-        sm.cost[tid] = s;
-        key = ((unsigned)s << 16) | (unsigned)tid;
-        int32_t *dbgc = fwd ? a.dbg.cost_f : a.dbg.cost_b;
-        if (dbgc) {
-            const int slots = a.p.grid_g * a.p.grid_g;
-            dbgc[((long long)bc.box * slots + bc.slot) * a.nc_stride + tid] = s;
-        }
-    }
-    key = __reduce_min_sync(0xffffffffu, key);
-    if (lane == 0) sh.warp_min[warp] = key;
-    __syncthreads();
-    if (tid == 0) {
-        unsigned m = sh.warp_min[0];
-#pragma unroll
-        for (int w = 1; w < kMatchWarps; ++w) m = min(m, sh.warp_min[w]);
-        sh.warp_min[0] = m;
-    }
-    __syncthreads();
+    argmin_pass<NT>(a, bc, sm, sh, fwd);
 }
 
-__device__ void aggregate_box(const MatchArgs &a, int box)
+// Sec. 4.3.4 on the block records of one box, by warp 0 of the CTA that
+// finished the box last.
+template <int NW>
+__device__ void aggregate_box(const MatchArgs &a, int box, Shared<NW> &sh)
 {
+    const int lane = threadIdx.x & 31;
     const BoxPlan P = a.ws.plans[box];
     const int base = a.ws.blk_base[box];
-    float v[kMaxSlots];
-    int nv = 0;
-    int fb_any = 0, few_any = 0, clamp_any = 0;
-    for (int s = 0; s < P.nblk; ++s) {
-        const int2 raw = __ldcg(reinterpret_cast<const int2 *>(a.ws.blkres + base + s));
-        const float d = __int_as_float(raw.x);
-        const int f = raw.y;
-        if (f & CTM_BLK_FB_REJECT) fb_any = 1;
-        if (f & CTM_BLK_FEW_POINTS) few_any = 1;
-        if (f & CTM_BLK_VALID) {
-            if (f & CTM_BLK_SUBPIX_CLAMPED) clamp_any = 1;
-            v[nv++] = d;
+    float d[2];
+    int f[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int s = lane + 32 * h;
+        f[h] = 0;
+        d[h] = 0.0f;
+        if (s < P.nblk) {
+            const int2 raw = __ldcg(reinterpret_cast<const int2 *>(a.ws.blkres + base + s));
+            d[h] = __int_as_float(raw.x);
+            f[h] = raw.y;
         }
     }
+    const unsigned full = 0xffffffffu;
+    const int fb_any = __any_sync(full, ((f[0] | f[1]) & CTM_BLK_FB_REJECT) != 0);
+    const int few_any = __any_sync(full, ((f[0] | f[1]) & CTM_BLK_FEW_POINTS) != 0);
+    const bool v0 = (f[0] & CTM_BLK_VALID) != 0, v1 = (f[1] & CTM_BLK_VALID) != 0;
+    const int clamp_any = __any_sync(full, (v0 && (f[0] & CTM_BLK_SUBPIX_CLAMPED)) ||
+                                               (v1 && (f[1] & CTM_BLK_SUBPIX_CLAMPED)));
+    const unsigned b0 = __ballot_sync(full, v0), b1 = __ballot_sync(full, v1);
+    const unsigned lt = (1u << lane) - 1u;
+    const int nv = __popc(b0) + __popc(b1);
+    if (v0) sh.agg[__popc(b0 & lt)] = d[0];
+    if (v1) sh.agg[__popc(b0) + __popc(b1 & lt)] = d[1];
+    __syncwarp();
+    // rank sort (ties by position) into agg_sorted
+    for (int e = lane; e < nv; e += 32) {
+        const float x = sh.agg[e];
+        int rank = 0;
+        for (int q = 0; q < nv; ++q) {
+            const float y = sh.agg[q];
+            rank += (y < x) || (y == x && q < e);
+        }
+        sh.agg_sorted[rank] = x;
+    }
+    __syncwarp();
+    if (lane != 0) return;
     int fl = P.far ? CTM_BOX_FAR : 0;
     if (fb_any) fl |= CTM_BOX_FB_REJECT;
     if (few_any) fl |= CTM_BOX_FEW_POINTS;
     if (clamp_any) fl |= CTM_BOX_SUBPIX_CLAMPED;
     bool have = false;
     float d_box = 0.0f;
+    const float *v = sh.agg_sorted;
     if (P.far) {
         if (nv == 1) { have = true; d_box = v[0]; }
     } else if (nv > 0) {
-        // Sec. 4.3.4: sort, longest run with consecutive differences < tau_d
-        for (int i = 1; i < nv; ++i) {
-            const float t = v[i];
-            int j = i - 1;
-            while (j >= 0 && v[j] > t) { v[j + 1] = v[j]; --j; }
-            v[j + 1] = t;
-        }
+        // longest run with consecutive differences < tau_d; first on ties
         int best_start = 0, best_len = 1, cur_start = 0, cur_len = 1;
         for (int i = 1; i < nv; ++i) {
             if (__fsub_rn(v[i], v[i - 1]) < a.p.agg_tau_d) {
@@ -273,8 +345,10 @@ __device__ void aggregate_box(const MatchArgs &a, int box)
     a.flags[box] = (uint8_t)fl;
 }
 
-__device__ void process_block(const MatchArgs &a, int b, const Smem &sm, Shared &sh)
+template <int NT>
+__device__ void process_block(const MatchArgs &a, int b, const Smem &sm, Shared<NT / 32> &sh)
 {
+    constexpr int NW = NT / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int2 bs = a.ws.blocks[b];
     const BoxPlan P = a.ws.plans[bs.x];
@@ -282,7 +356,6 @@ __device__ void process_block(const MatchArgs &a, int b, const Smem &sm, Shared 
     bc.box = bs.x;
     bc.slot = bs.y;
     bc.b = b;
-    bc.g = P.g;
     bc.k = P.k;
     bc.far = P.far;
     bc.dmin = P.dmin;
@@ -299,54 +372,71 @@ __device__ void process_block(const MatchArgs &a, int b, const Smem &sm, Shared 
         bc.CR = full ? base + a.ws.plane1_elems : base + 2 * a.ws.plane1_elems + a.ws.planek_elems;
         bc.pitch = full ? a.ws.pitch1 : a.ws.pitchk;
     }
-    const int ga = bs.y % P.g, gb = bs.y / P.g;
-    const int bw = P.sx1 - P.sx0, bh = P.sy1 - P.sy0;
-    const int bx0 = P.sx0 + (ga * bw) / P.g, bx1 = P.sx0 + ((ga + 1) * bw) / P.g;
-    const int by0 = P.sy0 + (gb * bh) / P.g, by1 = P.sy0 + ((gb + 1) * bh) / P.g;
-    bc.nx = min(bx1 - bx0, a.p.pts_side);
-    bc.ny = min(by1 - by0, a.p.pts_side);
-    if (tid < bc.nx) sh.X[tid] = point_coord(bx0, bx1, bc.nx, tid);
-    if (tid < bc.ny) sh.Y[tid] = point_coord(by0, by1, bc.ny, tid);
-    if (tid < P.nocc) sh.occ[tid] = a.ws.occ[(long long)bc.box * kMaxOcc + tid];
+    const BlockRect br = block_rect(P, bs.y, a.p.pts_side);
+    bc.nx = br.nx;
+    bc.ny = br.ny;
+    const int np_nom = bc.nx * bc.ny;
+
+    // 1a. geometry to shared memory; occluders and grid-point codes in flight
+    if (tid < bc.nx) sh.X[tid] = point_coord(br.bx0, br.bx1, bc.nx, tid);
+    if (tid < bc.ny) sh.Y[tid] = point_coord(br.by0, br.by1, bc.ny, tid);
+    if (tid < P.nocc) cp_async16(&sh.occ[tid], a.ws.occ + (long long)bc.box * kMaxOcc + tid);
+    for (int t = tid; t < np_nom; t += NT) {
+        const int j = t / bc.ny, m = t - (t / bc.ny) * bc.ny;
+        const int x = point_coord(br.bx0, br.bx1, bc.nx, j), y = point_coord(br.by0, br.by1, bc.ny, m);
+        if (x >= 0 && x < bc.Ws && y >= 0 && y < bc.Hs)
+            cp_async8(&sm.praw[t], bc.CL + (long long)y * bc.pitch + x);
+        else
+            sm.praw[t] = 0ull;
+    }
+    for (int c = tid; c < bc.nc; c += NT) sm.cost[c] = 0;
+    __syncthreads();
+    // 1b. first forward strip chunk joins the same round trip
+    const int j1_first = bc.nx > 0 ? chunk_end(sh.X, 0, bc.nx, bc.nd, a.strip_cols) : 0;
+    if (bc.nx > 0 && bc.ny > 0)
+        issue_strip<NT>(bc, sm, sh.Y, true, a.p.dy_min, 0, sh.X[0] - bc.dmax,
+                        sh.X[j1_first - 1] - sh.X[0] + bc.nd);
+    cp_async_wait_all();
     __syncthreads();
 
-    // 1. usable points, compacted column-major (index = j * ny + m)
-    const int np_nom = bc.nx * bc.ny;
+    // 1c. usable points, compacted column-major
     const int sxw = a.p.win_w >> 1, syw = a.p.win_h >> 1;
-    bool valid = false;
-    int m = 0, j = 0, x = 0, y = 0;
-    if (tid < np_nom) {
-        j = tid / bc.ny;
-        m = tid - j * bc.ny;
-        x = sh.X[j];
-        y = sh.Y[m];
-        valid = x - sxw >= 0 && x + sxw < bc.Ws && y - syw >= 0 && y + syw < bc.Hs;
-        const int fx = P.k * x, fy = P.k * y;
-        for (int t = 0; t < P.nocc && valid; ++t) {
-            const int4 o = sh.occ[t];
-            if (fx >= o.x && fx < o.z && fy >= o.y && fy < o.w) valid = false;
+    int total = 0;
+    for (int t0 = 0; t0 < np_nom; t0 += NT) {
+        const int t = t0 + tid;
+        bool valid = false;
+        int m = 0, j = 0;
+        if (t < np_nom) {
+            j = t / bc.ny;
+            m = t - j * bc.ny;
+            const int x = sh.X[j], y = sh.Y[m];
+            valid = x - sxw >= 0 && x + sxw < bc.Ws && y - syw >= 0 && y + syw < bc.Hs;
+            const int fx = P.k * x, fy = P.k * y;
+            for (int q = 0; q < P.nocc && valid; ++q) {
+                const int4 o = sh.occ[q];
+                if (fx >= o.x && fx < o.z && fy >= o.y && fy < o.w) valid = false;
+            }
         }
-    }
-    const unsigned ballot = __ballot_sync(0xffffffffu, valid);
-    if (lane == 0) sh.warp_cnt[warp] = __popc(ballot);
-    __syncthreads();
-    int wpre = 0, total = 0;
+        const unsigned ballot = __ballot_sync(0xffffffffu, valid);
+        if (lane == 0) sh.warp_cnt[warp] = __popc(ballot);
+        __syncthreads();
+        int wpre = 0, sum = 0;
 #pragma unroll
-    for (int w = 0; w < kMatchWarps; ++w) {
-        const int c = sh.warp_cnt[w];
-        if (w < warp) wpre += c;
-        total += c;
+        for (int w = 0; w < NW; ++w) {
+            const int c = sh.warp_cnt[w];
+            if (w < warp) wpre += c;
+            sum += c;
+        }
+        const int idx = total + wpre + __popc(ballot & ((1u << lane) - 1u));
+        if (valid) {
+            sm.pcode[idx] = sm.praw[t];
+            sm.pmj[idx] = (m << 8) | j;
+        }
+        if (t < np_nom && m == 0) sh.colstart[j] = idx;
+        total += sum;
+        __syncthreads();
     }
-    const int idx = wpre + __popc(ballot & ((1u << lane) - 1u));
-    if (valid) {
-        sm.pcode[idx] = bc.CL[(long long)y * bc.pitch + x];
-        sm.pmj[idx] = (m << 8) | j;
-    }
-    if (tid < np_nom && m == 0) sh.colstart[j] = idx;
-    if (tid == 0) {
-        sh.colstart[bc.nx] = total;
-        sh.n_valid = total;
-    }
+    if (tid == 0) sh.colstart[bc.nx] = total;
     __syncthreads();
 
     const int slots = a.p.grid_g * a.p.grid_g;
@@ -363,7 +453,7 @@ __device__ void process_block(const MatchArgs &a, int b, const Smem &sm, Shared 
         rec.flags |= CTM_BLK_FEW_POINTS;
     } else {
         // 2-3. forward pass, argmin, parabola
-        search_pass(a, bc, sm, sh, true);
+        search_pass<NT>(a, bc, sm, sh, true);
         if (tid == 0) {
             const unsigned key = sh.warp_min[0];
             const int c = (int)(key & 0xffffu);
@@ -375,16 +465,22 @@ __device__ void process_block(const MatchArgs &a, int b, const Smem &sm, Shared 
             sh.s_p = di < bc.nd - 1 ? sm.cost[c + 1] : 0;
         }
         __syncthreads();
-        // 4. backward pass: query codes are the right codes at the matched positions
-        for (int t = tid; t < total; t += kMatchThreads) {
+        // 4. backward pass: right codes at the matched positions + first left strip
+        const int d_f = sh.d_f, dy_f = sh.dy_f;
+        for (int t = tid; t < total; t += NT) {
             const int mj = sm.pmj[t];
-            const int qx = sh.X[mj & 255] - sh.d_f, qy = sh.Y[mj >> 8] + sh.dy_f;
-            uint64_t v = 0;
-            if (qx >= 0 && qx < bc.Ws && qy >= 0 && qy < bc.Hs) v = bc.CR[(long long)qy * bc.pitch + qx];
-            sm.pcode[t] = v;
+            const int qx = sh.X[mj & 255] - d_f, qy = sh.Y[mj >> 8] + dy_f;
+            if (qx >= 0 && qx < bc.Ws && qy >= 0 && qy < bc.Hs)
+                cp_async8(&sm.pcode[t], bc.CR + (long long)qy * bc.pitch + qx);
+            else
+                sm.pcode[t] = 0ull;
         }
+        for (int c = tid; c < bc.nc; c += NT) sm.cost[c] = 0;
+        issue_strip<NT>(bc, sm, sh.Y, false, a.p.dy_min, dy_f, sh.X[0] - d_f + bc.dmin,
+                        sh.X[j1_first - 1] - sh.X[0] + bc.nd);
+        cp_async_wait_all();
         __syncthreads();
-        search_pass(a, bc, sm, sh, false);
+        search_pass<NT>(a, bc, sm, sh, false);
         if (tid == 0) {
             const unsigned key = sh.warp_min[0];
             const int c = (int)(key & 0xffffu);
@@ -414,12 +510,12 @@ __device__ void process_block(const MatchArgs &a, int b, const Smem &sm, Shared 
         rec.flags |= dxv <= a.p.fb_tol ? CTM_BLK_VALID : CTM_BLK_FB_REJECT;
     }
 
-    // 5. block record, completion count, last CTA aggregates the box
+    // 5. block record, completion count, the last CTA of the box aggregates
     if (tid == 0) {
-        BlockResult br;
-        br.d_full = rec.d_full;
-        br.flags = rec.flags;
-        a.ws.blkres[b] = br;
+        BlockResult r;
+        r.d_full = rec.d_full;
+        r.flags = rec.flags;
+        a.ws.blkres[b] = r;
         if (a.dbg.blocks) a.dbg.blocks[(long long)bc.box * slots + bc.slot] = rec;
         if (!(rec.flags & CTM_BLK_FEW_POINTS))
             atomicAdd(&a.ws.counts->evals, 2ull * (unsigned long long)total * (unsigned long long)bc.nc);
@@ -428,9 +524,9 @@ __device__ void process_block(const MatchArgs &a, int b, const Smem &sm, Shared 
         sh.last = (prev == P.nblk - 1);
     }
     __syncthreads();
-    if (sh.last && tid == 0) {
+    if (sh.last && warp == 0) {
         __threadfence();
-        aggregate_box(a, bc.box);
+        aggregate_box<NW>(a, bc.box, sh);
     }
     __syncthreads();
 }
@@ -441,20 +537,22 @@ __device__ __forceinline__ Smem carve(const MatchArgs &a, unsigned char *raw)
     size_t off = 0;
     sm.strip = reinterpret_cast<uint64_t *>(raw + off);
     off += sizeof(uint64_t) * (size_t)a.strip_rows * a.strip_cols;
+    sm.praw = reinterpret_cast<uint64_t *>(raw + off);
+    off += sizeof(uint64_t) * kMaxPts;
     sm.pcode = reinterpret_cast<uint64_t *>(raw + off);
     off += sizeof(uint64_t) * kMaxPts;
-    sm.partial = reinterpret_cast<int *>(raw + off);
-    off += sizeof(int) * kMatchWarps * kMaxCand;
     sm.cost = reinterpret_cast<int *>(raw + off);
     off += sizeof(int) * kMaxCand;
     sm.pmj = reinterpret_cast<int *>(raw + off);
     return sm;
 }
 
-__global__ void __launch_bounds__(kMatchThreads) match_persistent_kernel(MatchArgs a)
+template <int NT>
+__global__ void __launch_bounds__(NT, 1536 / NT)
+    match_persistent_kernel(MatchArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ Shared sh;
+    __shared__ Shared<NT / 32> sh;
     const Smem sm = carve(a, smem_raw);
     const int nblocks = a.ws.counts->n_blocks;
     for (;;) {
@@ -463,49 +561,64 @@ __global__ void __launch_bounds__(kMatchThreads) match_persistent_kernel(MatchAr
         const int b = sh.next;
         __syncthreads();
         if (b >= nblocks) break;
-        process_block(a, b, sm, sh);
+        process_block<NT>(a, b, sm, sh);
     }
 }
 
-__global__ void __launch_bounds__(kMatchThreads) match_box_kernel(MatchArgs a, int box)
+template <int NT>
+__global__ void __launch_bounds__(NT) match_box_kernel(MatchArgs a, int box)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ Shared sh;
+    __shared__ Shared<NT / 32> sh;
     if ((int)blockIdx.x >= a.ws.nblk[box]) return;
     const Smem sm = carve(a, smem_raw);
-    process_block(a, a.ws.blk_base[box] + blockIdx.x, sm, sh);
+    process_block<NT>(a, a.ws.blk_base[box] + blockIdx.x, sm, sh);
 }
 
 }  // namespace
 
 size_t match_smem_bytes(const MatchArgs &a)
 {
-    return sizeof(uint64_t) * (size_t)a.strip_rows * a.strip_cols + sizeof(uint64_t) * kMaxPts +
-           sizeof(int) * kMatchWarps * kMaxCand + sizeof(int) * kMaxCand + sizeof(int) * kMaxPts;
+    return sizeof(uint64_t) * (size_t)a.strip_rows * a.strip_cols + 2 * sizeof(uint64_t) * kMaxPts +
+           sizeof(int) * kMaxCand + sizeof(int) * kMaxPts;
 }
 
-cudaError_t match_configure(const MatchArgs &a, int *ctas_per_sm)
+cudaError_t match_configure(const MatchArgs &a, int threads, int *ctas_per_sm)
 {
     const int smem = (int)match_smem_bytes(a);
-    cudaError_t e = cudaFuncSetAttribute(match_persistent_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(match_box_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, match_persistent_kernel,
-                                                         kMatchThreads, smem);
+    cudaError_t e = cudaSuccess;
+    if (threads == 128) {
+        e = cudaFuncSetAttribute(match_persistent_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(match_box_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, match_persistent_kernel<128>, 128, smem);
+    } else {
+        e = cudaFuncSetAttribute(match_persistent_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(match_box_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, match_persistent_kernel<256>, 256, smem);
+    }
+    return e;
 }
 
-cudaError_t launch_match_persistent(const MatchArgs &a, int grid, cudaStream_t s)
+cudaError_t launch_match_persistent(const MatchArgs &a, int threads, int grid, cudaStream_t s)
 {
-    match_persistent_kernel<<<grid, kMatchThreads, match_smem_bytes(a), s>>>(a);
+    if (threads == 128)
+        match_persistent_kernel<128><<<grid, 128, match_smem_bytes(a), s>>>(a);
+    else
+        match_persistent_kernel<256><<<grid, 256, match_smem_bytes(a), s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_match_box(const MatchArgs &a, int box, cudaStream_t s)
+cudaError_t launch_match_box(const MatchArgs &a, int threads, int box, cudaStream_t s)
 {
     const int slots = a.p.grid_g * a.p.grid_g;
-    match_box_kernel<<<slots, kMatchThreads, match_smem_bytes(a), s>>>(a, box);
+    if (threads == 128)
+        match_box_kernel<128><<<slots, 128, match_smem_bytes(a), s>>>(a, box);
+    else
+        match_box_kernel<256><<<slots, 256, match_smem_bytes(a), s>>>(a, box);
     return cudaGetLastError();
 }
 

@@ -166,7 +166,64 @@ __global__ void __launch_bounds__(kScanThreads) plan_scan_kernel(MatchArgs a)
     }
 }
 
+// Mark, for one block, the census row tiles its two passes can read: the left
+// plane at the sampled rows (plus the vertical spread of the backward pass) over
+// [X_0 - (dmax - dmin), X_last + (dmax - dmin)], which holds the points and every
+// backward strip; the right plane at rows Y_m + dy over [X_0 - dmax, X_last - dmin],
+// which holds every forward strip and the backward queries.
+__device__ __forceinline__ void mark_range(const MatchArgs &a, int f, int q, int y, int c0, int c1,
+                                           int Ws, int Hs)
+{
+    if (y < 0 || y >= Hs) return;
+    c0 = max(c0, 0);
+    c1 = min(c1, Ws - 1);
+    if (c1 < c0) return;
+    const int t0 = c0 / kCensusTilePx, t1 = c1 / kCensusTilePx;
+    uint32_t *row = a.ws.bitmap + (long long)f * a.ws.bm_frame_words + a.ws.bm_plane_off[q] +
+                    (long long)y * a.ws.bm_row_words[q];
+    for (int wi = t0 >> 5; wi <= (t1 >> 5); ++wi) {
+        const int lo = max(t0 - wi * 32, 0), hi = min(t1 - wi * 32, 31);
+        const uint32_t upto = hi == 31 ? 0xffffffffu : ((1u << (hi + 1)) - 1u);
+        atomicOr(row + wi, upto & ~((1u << lo) - 1u));
+    }
+}
+
+__global__ void __launch_bounds__(256) mark_kernel(MatchArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int b = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (b >= a.ws.counts->n_blocks) return;
+    const int2 bs = a.ws.blocks[b];
+    const BoxPlan P = a.ws.plans[bs.x];
+    const BlockRect r = block_rect(P, bs.y, a.p.pts_side);
+    if (r.nx <= 0 || r.ny <= 0) return;
+    const int x_first = point_coord(r.bx0, r.bx1, r.nx, 0);
+    const int x_last = point_coord(r.bx0, r.bx1, r.nx, r.nx - 1);
+    const int qL = (P.far || a.p.close_factor == 1) ? 0 : 2;
+    const int span = P.dmax - P.dmin;
+    const int dyr = a.p.dy_max - a.p.dy_min;
+    const int nl = 2 * dyr + 1, nr = dyr + 1;
+    const int items = r.ny * (nl + nr);
+    for (int it = lane; it < items; it += 32) {
+        const int m = it / (nl + nr);
+        const int e = it - m * (nl + nr);
+        const int y = point_coord(r.by0, r.by1, r.ny, m);
+        if (e < nl)
+            mark_range(a, P.frame, qL, y + e - dyr, x_first - span, x_last + span, P.Ws, P.Hs);
+        else
+            mark_range(a, P.frame, qL + 1, y + a.p.dy_min + (e - nl), x_first - P.dmax, x_last - P.dmin,
+                       P.Ws, P.Hs);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_mark(const MatchArgs &a, cudaStream_t s)
+{
+    const int grid = ceil_div_nn(a.caps.max_blocks, 8);
+    mark_kernel<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_stage_frame(const MatchArgs &a, ctm_frame f, int n_boxes, cudaStream_t s)
 {
