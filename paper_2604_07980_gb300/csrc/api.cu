@@ -108,7 +108,7 @@ int enqueue_match(ctm_ctx *ctx, const MatchArgs &a, int frames_grid, int match_g
     b.caps.max_frames = std::min(ctx->caps.max_frames, frames_grid);
     cudaError_t e = launch_plan(b, s);
     if (e == cudaSuccess) e = launch_mark(b, s);
-    if (e == cudaSuccess) e = launch_census_roi(b, ctx->sm_count * 8, s);
+    if (e == cudaSuccess) e = launch_census_roi(b, ctx->sm_count * 4, s);
     if (!plain) {
         if (e == cudaSuccess) e = launch_match_persistent(b, ctx->match_threads, match_grid, s);
     } else {
@@ -201,11 +201,10 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
     const int nd_max = std::max(p->far_dmax - p->far_dmin + 1, p->close_dmax - p->close_dmin + 1);
     ctx->nc_stride = nd_max * ndy;
     ctx->strip_rows = p->pts_side * ndy;
-    // strip width: the disparity range plus a 96-column span of points per chunk
-    int cols = (int)round_up(std::max(nd_max + 96, 192), 32);
-    while (cols > nd_max && (long long)ctx->strip_rows * cols * 8 > 96 * 1024) cols -= 32;
-    cols = std::max(cols, (int)round_up(nd_max, 8));
-    if ((long long)ctx->strip_rows * cols * 8 > 180 * 1024) { delete ctx; return CTM_EINVAL; }
+    // strip piece width (one sampled row per piece, double-buffered per warp): the
+    // disparity range plus a 64-column span of points; wider rows are chunked
+    const int cols = (int)round_up(std::max(nd_max + 64, 128), 32);
+    if ((long long)2 * ndy * cols * 8 * 4 > 160 * 1024) { delete ctx; return CTM_EINVAL; }
     ctx->strip_cols = cols;
 
     // workspace layout (one allocation)
@@ -422,7 +421,7 @@ int ctm_match_batch_profiled(ctm_ctx *ctx, const ctm_frame *frames_dev, const in
     if (e == cudaSuccess) e = launch_plan(a, s);
     if (e == cudaSuccess) e = launch_mark(a, s);
     if (e == cudaSuccess) e = cudaEventRecord((cudaEvent_t)events[1], s);
-    if (e == cudaSuccess) e = launch_census_roi(a, ctx->sm_count * 8, s);
+    if (e == cudaSuccess) e = launch_census_roi(a, ctx->sm_count * 4, s);
     if (e == cudaSuccess) e = cudaEventRecord((cudaEvent_t)events[2], s);
     if (e == cudaSuccess) e = launch_match_persistent(a, ctx->match_threads, grid, s);
     if (e == cudaSuccess) e = cudaEventRecord((cudaEvent_t)events[3], s);

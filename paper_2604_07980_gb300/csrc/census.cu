@@ -50,60 +50,72 @@ struct Plane {
     uint64_t *out;
     long long opitch;
     int vec_ok;           // 16-byte stores allowed (even pitch, 16-byte aligned base)
+    int vec_load;         // word loads allowed: k in {1, 2}, 8-byte aligned base, pitch % 4 == 0
 };
 
 __device__ __forceinline__ __half2 as_h2(uint32_t u) { return *reinterpret_cast<__half2 *>(&u); }
 
-// Stage the WH window rows of tile (x0, y): every load of the tile is issued
-// before any is used, so a warp waits for one memory round trip per tile.
-template <int WW, int WH>
-__device__ __forceinline__ void stage_rows(const Plane &pl, int x0, int y, const WarpStage &st, int lane)
+// Staged row layout: H[b] = 0x6400 | I_k(x0 - 8 + b, row) for b in [0, 80), kept
+// twice as half2 words: even[t] = (H[2t], H[2t+1]) and odd[t] = (H[2t+1], H[2t+2]),
+// so every pair of adjacent pixels is one aligned 32-bit word in one of the two.
+// Lane l < 21 loads H[4l .. 4l+3] with one 32-bit load (k = 1) or one 64-bit
+// load (k = 2) where the four pixels lie inside the image, else byte by byte.
+__device__ __forceinline__ uint32_t load_quad(const Plane &pl, int x0, int ys, int lane)
 {
-    constexpr int sx = WW / 2, sy = WH / 2, ncols = kTile + 2 * sx;
-    constexpr int per_lane = (ncols + 31) / 32;
-    uint16_t v[WH][per_lane];
+    const uint8_t *row = pl.img + (long long)pl.k * ys * pl.pitch;
+    uint32_t v = 0u;
+    if (lane < 21) {
+        const int xs = x0 - 8 + 4 * lane;
+        if (pl.vec_load && pl.k == 1 && xs >= 0 && xs + 3 < pl.W) {
+            v = __ldg(reinterpret_cast<const uint32_t *>(row + xs));
+        } else if (pl.vec_load && pl.k == 2 && xs >= 0 && 2 * xs + 7 < pl.W) {
+            const uint2 w = __ldg(reinterpret_cast<const uint2 *>(row + 2 * xs));
+            v = __byte_perm(w.x, w.y, 0x6420);
+        } else {
 #pragma unroll
-    for (int r = 0; r < WH; ++r) {
-        const uint8_t *src = pl.img + (long long)pl.k * (y - sy + r) * pl.pitch;
-#pragma unroll
-        for (int t = 0; t < per_lane; ++t) {
-            const int c = lane + 32 * t;
-            const int xs = x0 - sx + c;
-            uint16_t val = 0x6400;
-            if (c < ncols && xs >= 0 && xs < pl.Ws) val = (uint16_t)(0x6400 | src[(long long)pl.k * xs]);
-            v[r][t] = val;
-        }
-    }
-    uint16_t *ev = reinterpret_cast<uint16_t *>(st.even);
-    uint16_t *od = reinterpret_cast<uint16_t *>(st.odd);
-#pragma unroll
-    for (int r = 0; r < WH; ++r) {
-#pragma unroll
-        for (int t = 0; t < per_lane; ++t) {
-            const int c = lane + 32 * t;
-            if (c < ncols) {
-                ev[r * 2 * kWordsMax + c] = v[r][t];
-                if (c > 0) od[r * 2 * kWordsMax + c - 1] = v[r][t];
+            for (int q = 0; q < 4; ++q) {
+                const int xq = xs + q;
+                if (xq >= 0 && xq < pl.Ws) v |= (uint32_t)__ldg(row + (long long)pl.k * xq) << (8 * q);
             }
         }
     }
+    return v;
 }
 
-// Any window: staging with runtime sizes.
-__device__ __forceinline__ void stage_rows_any(const Plane &pl, int x0, int y, int sx, int sy,
+// Convert one loaded row (4 pixels per lane) to the two half2 copies.
+__device__ __forceinline__ void store_quad(uint32_t v, uint32_t *even, uint32_t *odd, int lane)
+{
+    const uint32_t nxt = __shfl_down_sync(0xffffffffu, v, 1);
+    if (lane < 20) {
+        const uint32_t C = 0x64646464u;
+        uint2 e, o;
+        e.x = __byte_perm(v, C, 0x4140);                            // H[4l],   H[4l+1]
+        e.y = __byte_perm(v, C, 0x4342);                            // H[4l+2], H[4l+3]
+        o.x = __byte_perm(v, C, 0x4241);                            // H[4l+1], H[4l+2]
+        o.y = __byte_perm(__byte_perm(v, nxt, 0x0043), C, 0x4140);  // H[4l+3], H[4l+4]
+        *reinterpret_cast<uint2 *>(even + 2 * lane) = e;
+        *reinterpret_cast<uint2 *>(odd + 2 * lane) = o;
+    }
+}
+
+// Stage the window rows y - sy .. y + sy of tile x0: all loads first (they are
+// independent and in flight together), then the conversions.
+template <int WH>
+__device__ __forceinline__ void stage_rows(const Plane &pl, int x0, int y, const WarpStage &st, int lane)
+{
+    constexpr int sy = WH / 2;
+    uint32_t v[WH];
+#pragma unroll
+    for (int r = 0; r < WH; ++r) v[r] = load_quad(pl, x0, y - sy + r, lane);
+#pragma unroll
+    for (int r = 0; r < WH; ++r) store_quad(v[r], st.even + r * kWordsMax, st.odd + r * kWordsMax, lane);
+}
+
+__device__ __forceinline__ void stage_rows_any(const Plane &pl, int x0, int y, int sy,
                                                const WarpStage &st, int lane)
 {
-    const int ncols = kTile + 2 * sx;
-    uint16_t *ev = reinterpret_cast<uint16_t *>(st.even);
-    for (int r = 0; r < 2 * sy + 1; ++r) {
-        const uint8_t *src = pl.img + (long long)pl.k * (y - sy + r) * pl.pitch;
-        for (int c = lane; c < ncols; c += 32) {
-            const int xs = x0 - sx + c;
-            uint16_t val = 0x6400;
-            if (xs >= 0 && xs < pl.Ws) val = (uint16_t)(0x6400 | src[(long long)pl.k * xs]);
-            ev[r * 2 * kWordsMax + c] = val;
-        }
-    }
+    for (int r = 0; r < 2 * sy + 1; ++r)
+        store_quad(load_quad(pl, x0, y - sy + r, lane), st.even + r * kWordsMax, st.odd + r * kWordsMax, lane);
 }
 
 // Codes of pixels (x0 + 2 lane, x0 + 2 lane + 1) from the staged rows.
@@ -113,17 +125,16 @@ __device__ __forceinline__ void tile_codes(const WarpStage &st, int lane, int se
 {
     constexpr int sx = WW / 2, sy = WH / 2;
     constexpr int n = WW * WH;
+    constexpr int OFF = 8 - sx;  // H index of the window's left column, relative to 2*lane
     uint32_t acc[4] = {0u, 0u, 0u, 0u};
-    const uint32_t cw = (sx & 1) ? st.odd[sy * kWordsMax + lane + (sx - 1) / 2]
-                                 : st.even[sy * kWordsMax + lane + sx / 2];
-    const __half2 centre = as_h2(cw);
+    const __half2 centre = as_h2(st.even[sy * kWordsMax + lane + 4]);  // H[2*lane + 8]
 #pragma unroll
     for (int j = 0; j < WH; ++j) {
 #pragma unroll
         for (int i = 0; i < WW; ++i) {
-            // staged column of the neighbour, relative to the lane's pair base 2*lane
-            const uint32_t nb = (i & 1) ? st.odd[j * kWordsMax + lane + (i - 1) / 2]
-                                        : st.even[j * kWordsMax + lane + i / 2];
+            const int b = i + OFF;  // H index of the neighbour pair, relative to 2*lane
+            const uint32_t nb = (b & 1) ? st.odd[j * kWordsMax + lane + (b - 1) / 2]
+                                        : st.even[j * kWordsMax + lane + b / 2];
             const uint32_t m = __hgt2_mask(as_h2(nb), centre);
             const int k = j * WW + i;     // raster index of the window offset
             const int p = n - 1 - k;      // its code bit
@@ -148,10 +159,11 @@ __device__ __forceinline__ uint64_t code_any(const WarpStage &st, int px, int wi
     const uint16_t *ev = reinterpret_cast<const uint16_t *>(st.even);
     constexpr int rowh = 2 * kWordsMax;
     const int sx = win_w / 2, sy = win_h / 2;
-    const uint16_t centre = ev[sy * rowh + px + sx];
+    const int off = 8 - sx;
+    const uint16_t centre = ev[sy * rowh + px + 8];
     uint64_t c = sentinel ? 1ull : 0ull;
     for (int j = 0; j < win_h; ++j)
-        for (int i = 0; i < win_w; ++i) c = (c << 1) | (uint64_t)(ev[j * rowh + px + i] > centre);
+        for (int i = 0; i < win_w; ++i) c = (c << 1) | (uint64_t)(ev[j * rowh + px + i + off] > centre);
     return c;
 }
 
@@ -184,11 +196,11 @@ __device__ void census_tile(const Plane &pl, int x0, int y, int win_w, int win_h
     }
     uint64_t c0, c1;
     if constexpr (WW > 0) {
-        stage_rows<WW, WH>(pl, x0, y, st, lane);
+        stage_rows<WH>(pl, x0, y, st, lane);
         __syncwarp();
         tile_codes<WW, WH>(st, lane, sentinel, c0, c1);
     } else {
-        stage_rows_any(pl, x0, y, sx, sy, st, lane);
+        stage_rows_any(pl, x0, y, sy, st, lane);
         __syncwarp();
         c0 = code_any(st, 2 * lane, win_w, win_h, sentinel);
         c1 = code_any(st, 2 * lane + 1, win_w, win_h, sentinel);
@@ -216,7 +228,7 @@ __device__ __forceinline__ void census_tile_any(const Plane &pl, int x0, int y, 
 __global__ void __launch_bounds__(32 * kWarpsPerCta) census_full_kernel(Plane pl, int win_w, int win_h,
                                                                         int sentinel)
 {
-    extern __shared__ uint32_t stage_mem[];
+    extern __shared__ __align__(16) uint32_t stage_mem[];
     const int warp = threadIdx.x >> 5;
     const int y = blockIdx.y * kWarpsPerCta + warp;
     if (y >= pl.Hs) return;
@@ -224,10 +236,118 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) census_full_kernel(Plane pl
     census_tile_any(pl, blockIdx.x * kTile, y, win_w, win_h, sentinel, st);
 }
 
-// Region of interest: warps stride over the bitmap words of all frames' planes.
-__global__ void __launch_bounds__(32 * kWarpsPerCta) census_roi_kernel(MatchArgs a)
+// Region of interest.  Each warp walks the set bits of its bitmap words
+// (grid-stride over the words of all frames' planes) as one stream of tiles and
+// clears every word it consumed.
+struct TileCursor {
+    long long w;       // current word index (grid-stride)
+    uint32_t bits;     // tiles of the current word not yet taken
+    Plane pl;          // plane of the current word
+    int y, wi;         // row and word-in-row of the current word
+};
+
+__device__ __forceinline__ void decode_word(const MatchArgs &a, long long w, TileCursor &c)
 {
-    extern __shared__ uint32_t stage_mem[];
+    const int f = (int)(w / a.ws.bm_frame_words);
+    int r = (int)(w - (long long)f * a.ws.bm_frame_words);
+    int q = 0;
+    while (q < 3 && r >= a.ws.bm_plane_off[q + 1]) ++q;
+    r -= a.ws.bm_plane_off[q];
+    c.y = r / a.ws.bm_row_words[q];
+    c.wi = r - c.y * a.ws.bm_row_words[q];
+    const ctm_frame fr = a.frames[f];
+    Plane &pl = c.pl;
+    pl.img = (q & 1) ? fr.right : fr.left;
+    pl.W = fr.width;
+    pl.H = fr.height;
+    pl.pitch = fr.pitch;
+    pl.k = q < 2 ? 1 : a.p.close_factor;
+    pl.Ws = ceil_div_nn(fr.width, pl.k);
+    pl.Hs = ceil_div_nn(fr.height, pl.k);
+    uint64_t *base = a.ws.census + (long long)f * a.ws.frame_stride;
+    pl.out = q < 2 ? base + q * a.ws.plane1_elems : base + 2 * a.ws.plane1_elems + (q - 2) * a.ws.planek_elems;
+    pl.opitch = q < 2 ? a.ws.pitch1 : a.ws.pitchk;
+    pl.vec_ok = 1;  // workspace planes: 256-byte aligned, pitch a multiple of 32
+    pl.vec_load = (pl.k == 1 || pl.k == 2) && (fr.pitch % 4 == 0) &&
+                  ((reinterpret_cast<uintptr_t>(pl.img) & 7u) == 0);
+}
+
+// Next tile of this warp's stream; false when its words are exhausted.
+__device__ __forceinline__ bool next_tile(const MatchArgs &a, TileCursor &c, long long nwarps,
+                                          long long total, int lane, int &x0, int &y)
+{
+    for (;;) {
+        while (c.bits == 0u) {
+            c.w += nwarps;
+            if (c.w >= total) return false;
+            const uint32_t bits = a.ws.bitmap[c.w];
+            if (bits == 0u) continue;
+            __syncwarp();
+            if (lane == 0) a.ws.bitmap[c.w] = 0u;  // consumed: clear for the next call
+            decode_word(a, c.w, c);
+            c.bits = bits;
+        }
+        const int b = __ffs(c.bits) - 1;
+        c.bits &= c.bits - 1u;
+        x0 = (c.wi * 32 + b) * kTile;
+        y = c.y;
+        if (x0 < c.pl.Ws && y < c.pl.Hs) return true;
+    }
+}
+
+// Fixed windows: the loads of the next tile are issued before the current
+// tile is converted and computed, so memory latency overlaps compute.
+template <int WW, int WH>
+__device__ void roi_stream(const MatchArgs &a, const WarpStage &st, TileCursor &c, long long nwarps,
+                           long long total, int lane)
+{
+    constexpr int sx = WW / 2, sy = WH / 2;
+    int xA = 0, yA = 0;
+    bool okA = next_tile(a, c, nwarps, total, lane, xA, yA);
+    Plane plA = c.pl;
+    uint32_t vA[WH];
+#pragma unroll
+    for (int r = 0; r < WH; ++r) vA[r] = 0u;
+    if (okA && yA - sy >= 0 && yA + sy < plA.Hs) {
+#pragma unroll
+        for (int r = 0; r < WH; ++r) vA[r] = load_quad(plA, xA, yA - sy + r, lane);
+    }
+    while (okA) {
+        int xB = 0, yB = 0;
+        const bool okB = next_tile(a, c, nwarps, total, lane, xB, yB);
+        const Plane plB = c.pl;
+        uint32_t vB[WH];
+#pragma unroll
+        for (int r = 0; r < WH; ++r) vB[r] = 0u;
+        if (okB && yB - sy >= 0 && yB + sy < plB.Hs) {
+#pragma unroll
+            for (int r = 0; r < WH; ++r) vB[r] = load_quad(plB, xB, yB - sy + r, lane);
+        }
+        // compute tile A
+        const int x = xA + 2 * lane;
+        uint64_t c0 = 0ull, c1 = 0ull;
+        if (yA - sy >= 0 && yA + sy < plA.Hs) {
+#pragma unroll
+            for (int r = 0; r < WH; ++r) store_quad(vA[r], st.even + r * kWordsMax, st.odd + r * kWordsMax, lane);
+            __syncwarp();
+            tile_codes<WW, WH>(st, lane, a.p.sentinel, c0, c1);
+            if (x - sx < 0 || x + sx >= plA.Ws) c0 = 0ull;
+            if (x + 1 - sx < 0 || x + 1 + sx >= plA.Ws) c1 = 0ull;
+            __syncwarp();
+        }
+        store_pair(plA, x, yA, c0, c1);
+        plA = plB;
+        xA = xB;
+        yA = yB;
+        okA = okB;
+#pragma unroll
+        for (int r = 0; r < WH; ++r) vA[r] = vB[r];
+    }
+}
+
+__global__ void __launch_bounds__(32 * kWarpsPerCta, 4) census_roi_kernel(MatchArgs a)
+{
+    extern __shared__ __align__(16) uint32_t stage_mem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const WarpStage st = warp_stage(stage_mem, warp, a.p.win_h);
     int nf = a.counts_in[0];
@@ -235,38 +355,20 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) census_roi_kernel(MatchArgs
     const long long total = (long long)nf * a.ws.bm_frame_words;
     const long long gwarp = (long long)blockIdx.x * kWarpsPerCta + warp;
     const long long nwarps = (long long)gridDim.x * kWarpsPerCta;
-    for (long long w = gwarp; w < total; w += nwarps) {
-        uint32_t bits = a.ws.bitmap[w];
-        if (bits == 0u) continue;
-        __syncwarp();
-        if (lane == 0) a.ws.bitmap[w] = 0u;  // consumed: the bitmap is clear for the next call
-        const int f = (int)(w / a.ws.bm_frame_words);
-        int r = (int)(w - (long long)f * a.ws.bm_frame_words);
-        int q = 0;
-        while (q < 3 && r >= a.ws.bm_plane_off[q + 1]) ++q;
-        r -= a.ws.bm_plane_off[q];
-        const int y = r / a.ws.bm_row_words[q];
-        const int wi = r - y * a.ws.bm_row_words[q];
-        const ctm_frame fr = a.frames[f];
-        Plane pl;
-        pl.img = (q & 1) ? fr.right : fr.left;
-        pl.W = fr.width;
-        pl.H = fr.height;
-        pl.pitch = fr.pitch;
-        pl.k = q < 2 ? 1 : a.p.close_factor;
-        pl.Ws = ceil_div_nn(fr.width, pl.k);
-        pl.Hs = ceil_div_nn(fr.height, pl.k);
-        uint64_t *base = a.ws.census + (long long)f * a.ws.frame_stride;
-        pl.out = q < 2 ? base + q * a.ws.plane1_elems : base + 2 * a.ws.plane1_elems + (q - 2) * a.ws.planek_elems;
-        pl.opitch = q < 2 ? a.ws.pitch1 : a.ws.pitchk;
-        pl.vec_ok = 1;  // workspace planes: 256-byte aligned, pitch a multiple of 32
-        while (bits) {
-            const int b = __ffs(bits) - 1;
-            bits &= bits - 1;
-            const int x0 = (wi * 32 + b) * kTile;
-            if (x0 < pl.Ws && y < pl.Hs)
-                census_tile_any(pl, x0, y, a.p.win_w, a.p.win_h, a.p.sentinel, st);
-        }
+    TileCursor c;
+    c.w = gwarp - nwarps;
+    c.bits = 0u;
+    const int ww = a.p.win_w, wh = a.p.win_h;
+    if (ww == 9 && wh == 7) {
+        roi_stream<9, 7>(a, st, c, nwarps, total, lane);
+    } else if (ww == 7 && wh == 7) {
+        roi_stream<7, 7>(a, st, c, nwarps, total, lane);
+    } else if (ww == 5 && wh == 5) {
+        roi_stream<5, 5>(a, st, c, nwarps, total, lane);
+    } else {
+        int x0, y;
+        while (next_tile(a, c, nwarps, total, lane, x0, y))
+            census_tile<0, 0>(c.pl, x0, y, ww, wh, a.p.sentinel, st);
     }
 }
 
@@ -292,6 +394,7 @@ cudaError_t launch_census_single(const uint8_t *img, int W, int H, int pitch, in
     pl.out = out;
     pl.opitch = out_pitch;
     pl.vec_ok = (out_pitch % 2 == 0) && ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
+    pl.vec_load = (k == 1 || k == 2) && (pitch % 4 == 0) && ((reinterpret_cast<uintptr_t>(img) & 7u) == 0);
     dim3 grid(ceil_div_nn(pl.Ws, kTile), ceil_div_nn(pl.Hs, kWarpsPerCta));
     census_full_kernel<<<grid, 32 * kWarpsPerCta, census_smem_bytes(win_h), s>>>(pl, win_w, win_h, sentinel);
     return cudaGetLastError();

@@ -51,10 +51,11 @@ __device__ __forceinline__ void cp_async_wait_all()
 
 struct Smem {
     uint64_t *strip;   // strip_rows * strip_cols
-    uint64_t *praw;    // kMaxPts: left code of grid point t = j * ny + m
+    uint64_t *praw;    // kMaxPts: left code of grid point t = 16 j + m
     uint64_t *pcode;   // kMaxPts: compacted codes (left, then right queries)
     int *cost;         // kMaxCand
     int *pmj;          // kMaxPts: (m << 8) | j
+    int *pbase;        // kMaxPts: byte offset of the point's strip row + column in the chunk
 };
 
 template <int NW>
@@ -83,55 +84,118 @@ struct BlockCtx {
     const uint64_t *CR;
 };
 
-// Sum of popcounts over the points [p0, p1) of one chunk; T candidate slices.
+// Sum of popcounts over the points [p0, p1) of one chunk; T candidate slices,
+// any (dy, d) layout: coff[t] is the element offset of this lane's candidate t.
 template <int NW, int T>
-__device__ __forceinline__ void scan_chunk(const Smem &sm, const int *X, int p0, int p1, int ndy,
-                                           int SWc, int xj0, const int (&coff)[8], int (&acc)[8])
+__device__ __forceinline__ void scan_chunk(const Smem &sm, int p0, int p1, const int (&coff)[8],
+                                           int (&acc)[8])
 {
     const int warp = threadIdx.x >> 5;
+    const char *strip = reinterpret_cast<const char *>(sm.strip);
     int p = p0 + warp;
     for (; p + NW < p1; p += 2 * NW) {
         const uint64_t c0 = sm.pcode[p], c1 = sm.pcode[p + NW];
-        const int mj0 = sm.pmj[p], mj1 = sm.pmj[p + NW];
-        const int base0 = (mj0 >> 8) * ndy * SWc + X[mj0 & 255] - xj0;
-        const int base1 = (mj1 >> 8) * ndy * SWc + X[mj1 & 255] - xj0;
+        const char *b0 = strip + sm.pbase[p], *b1 = strip + sm.pbase[p + NW];
         const uint32_t l0 = (uint32_t)c0, h0 = (uint32_t)(c0 >> 32);
         const uint32_t l1 = (uint32_t)c1, h1 = (uint32_t)(c1 >> 32);
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-            const uint64_t r0 = sm.strip[base0 + coff[t]];
-            const uint64_t r1 = sm.strip[base1 + coff[t]];
+            const uint64_t r0 = *reinterpret_cast<const uint64_t *>(b0 + 8 * coff[t]);
+            const uint64_t r1 = *reinterpret_cast<const uint64_t *>(b1 + 8 * coff[t]);
             acc[t] += __popc(l0 ^ (uint32_t)r0) + __popc(h0 ^ (uint32_t)(r0 >> 32)) +
                       __popc(l1 ^ (uint32_t)r1) + __popc(h1 ^ (uint32_t)(r1 >> 32));
         }
     }
     if (p < p1) {
         const uint64_t c0 = sm.pcode[p];
-        const int mj0 = sm.pmj[p];
-        const int base0 = (mj0 >> 8) * ndy * SWc + X[mj0 & 255] - xj0;
+        const char *b0 = strip + sm.pbase[p];
         const uint32_t l0 = (uint32_t)c0, h0 = (uint32_t)(c0 >> 32);
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-            const uint64_t r0 = sm.strip[base0 + coff[t]];
+            const uint64_t r0 = *reinterpret_cast<const uint64_t *>(b0 + 8 * coff[t]);
+            acc[t] += __popc(l0 ^ (uint32_t)r0) + __popc(h0 ^ (uint32_t)(r0 >> 32));
+        }
+    }
+}
+
+// Fast path for one dy row and N_d a multiple of 32: this lane's candidate t
+// sits at lane_off + DIR * 32 t elements from the point's base, so every strip
+// load has an immediate offset and the inner loop is one load, two xors, two
+// popcounts and one add per evaluation.
+template <int NW, int T, int DIR>
+__device__ __forceinline__ void scan_chunk_fast(const Smem &sm, int p0, int p1, int lane_off,
+                                                int (&acc)[8])
+{
+    const int warp = threadIdx.x >> 5;
+    const char *strip = reinterpret_cast<const char *>(sm.strip) + 8 * lane_off;
+    int p = p0 + warp;
+    for (; p + NW < p1; p += 2 * NW) {
+        const uint64_t c0 = sm.pcode[p], c1 = sm.pcode[p + NW];
+        const uint64_t *b0 = reinterpret_cast<const uint64_t *>(strip + sm.pbase[p]);
+        const uint64_t *b1 = reinterpret_cast<const uint64_t *>(strip + sm.pbase[p + NW]);
+        const uint32_t l0 = (uint32_t)c0, h0 = (uint32_t)(c0 >> 32);
+        const uint32_t l1 = (uint32_t)c1, h1 = (uint32_t)(c1 >> 32);
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const uint64_t r0 = b0[DIR * 32 * t];
+            const uint64_t r1 = b1[DIR * 32 * t];
+            acc[t] += __popc(l0 ^ (uint32_t)r0) + __popc(h0 ^ (uint32_t)(r0 >> 32)) +
+                      __popc(l1 ^ (uint32_t)r1) + __popc(h1 ^ (uint32_t)(r1 >> 32));
+        }
+    }
+    if (p < p1) {
+        const uint64_t c0 = sm.pcode[p];
+        const uint64_t *b0 = reinterpret_cast<const uint64_t *>(strip + sm.pbase[p]);
+        const uint32_t l0 = (uint32_t)c0, h0 = (uint32_t)(c0 >> 32);
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const uint64_t r0 = b0[DIR * 32 * t];
             acc[t] += __popc(l0 ^ (uint32_t)r0) + __popc(h0 ^ (uint32_t)(r0 >> 32));
         }
     }
 }
 
 template <int NW>
-__device__ __forceinline__ void scan_dispatch(int T, const Smem &sm, const int *X, int p0, int p1,
-                                              int ndy, int SWc, int xj0, const int (&coff)[8],
-                                              int (&acc)[8])
+__device__ __forceinline__ void scan_dispatch(int T, const Smem &sm, int p0, int p1,
+                                              const int (&coff)[8], int (&acc)[8])
 {
     switch (T) {
-    case 1: scan_chunk<NW, 1>(sm, X, p0, p1, ndy, SWc, xj0, coff, acc); break;
-    case 2: scan_chunk<NW, 2>(sm, X, p0, p1, ndy, SWc, xj0, coff, acc); break;
-    case 3: scan_chunk<NW, 3>(sm, X, p0, p1, ndy, SWc, xj0, coff, acc); break;
-    case 4: scan_chunk<NW, 4>(sm, X, p0, p1, ndy, SWc, xj0, coff, acc); break;
-    case 5: scan_chunk<NW, 5>(sm, X, p0, p1, ndy, SWc, xj0, coff, acc); break;
-    case 6: scan_chunk<NW, 6>(sm, X, p0, p1, ndy, SWc, xj0, coff, acc); break;
-    case 7: scan_chunk<NW, 7>(sm, X, p0, p1, ndy, SWc, xj0, coff, acc); break;
-    default: scan_chunk<NW, 8>(sm, X, p0, p1, ndy, SWc, xj0, coff, acc); break;
+    case 1: scan_chunk<NW, 1>(sm, p0, p1, coff, acc); break;
+    case 2: scan_chunk<NW, 2>(sm, p0, p1, coff, acc); break;
+    case 3: scan_chunk<NW, 3>(sm, p0, p1, coff, acc); break;
+    case 4: scan_chunk<NW, 4>(sm, p0, p1, coff, acc); break;
+    case 5: scan_chunk<NW, 5>(sm, p0, p1, coff, acc); break;
+    case 6: scan_chunk<NW, 6>(sm, p0, p1, coff, acc); break;
+    case 7: scan_chunk<NW, 7>(sm, p0, p1, coff, acc); break;
+    default: scan_chunk<NW, 8>(sm, p0, p1, coff, acc); break;
+    }
+}
+
+template <int NW, int DIR>
+__device__ __forceinline__ void scan_dispatch_fast(int T, const Smem &sm, int p0, int p1, int lane_off,
+                                                   int (&acc)[8])
+{
+    switch (T) {
+    case 1: scan_chunk_fast<NW, 1, DIR>(sm, p0, p1, lane_off, acc); break;
+    case 2: scan_chunk_fast<NW, 2, DIR>(sm, p0, p1, lane_off, acc); break;
+    case 3: scan_chunk_fast<NW, 3, DIR>(sm, p0, p1, lane_off, acc); break;
+    case 4: scan_chunk_fast<NW, 4, DIR>(sm, p0, p1, lane_off, acc); break;
+    case 5: scan_chunk_fast<NW, 5, DIR>(sm, p0, p1, lane_off, acc); break;
+    case 6: scan_chunk_fast<NW, 6, DIR>(sm, p0, p1, lane_off, acc); break;
+    case 7: scan_chunk_fast<NW, 7, DIR>(sm, p0, p1, lane_off, acc); break;
+    default: scan_chunk_fast<NW, 8, DIR>(sm, p0, p1, lane_off, acc); break;
+    }
+}
+
+// Byte offsets of the compacted points [p0, p1) into a strip chunk of width SWc
+// whose first column is point column xj0: row m * ndy, column X_j - xj0.
+template <int NT>
+__device__ __forceinline__ void set_bases(const Smem &sm, const int *X, int p0, int p1, int ndy,
+                                          int SWc, int xj0)
+{
+    for (int p = p0 + (int)threadIdx.x; p < p1; p += NT) {
+        const int mj = sm.pmj[p];
+        sm.pbase[p] = 8 * ((mj >> 8) * ndy * SWc + X[mj & 255] - xj0);
     }
 }
 
@@ -155,7 +219,7 @@ __device__ __forceinline__ void issue_strip(const BlockCtx &bc, const Smem &sm, 
     const int rows = bc.ny * bc.ndy;
     const uint64_t *plane = fwd ? bc.CR : bc.CL;
     for (int r = warp; r < rows; r += NT / 32) {
-        const int m = r / bc.ndy;
+        const int m = bc.ndy == 1 ? r : r / bc.ndy;
         const int e = r - m * bc.ndy;
         const int y = fwd ? Y[m] + dy_min + e : Y[m] + dy_f - (dy_min + e);
         uint64_t *dst = sm.strip + r * SWc;
@@ -199,7 +263,8 @@ __device__ __forceinline__ void argmin_pass(const MatchArgs &a, const BlockCtx &
     __syncthreads();
 }
 
-// One search pass after its first strip chunk has been issued and landed.
+// One search pass after its first strip chunk has been issued and landed and
+// the point bases of the first chunk are set.
 template <int NT>
 __device__ void search_pass(const MatchArgs &a, const BlockCtx &bc, const Smem &sm,
                             Shared<NT / 32> &sh, bool fwd)
@@ -207,6 +272,7 @@ __device__ void search_pass(const MatchArgs &a, const BlockCtx &bc, const Smem &
     constexpr int NW = NT / 32;
     const int lane = threadIdx.x & 31;
     const int T = (bc.nc + 31) >> 5;
+    const bool fast = bc.ndy == 1 && (bc.nd & 31) == 0;
     int acc[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) acc[t] = 0;
@@ -217,25 +283,34 @@ __device__ void search_pass(const MatchArgs &a, const BlockCtx &bc, const Smem &
         const int j1 = chunk_end(sh.X, j0, bc.nx, bc.nd, a.strip_cols);
         const int xj0 = sh.X[j0];
         const int SWc = sh.X[j1 - 1] - xj0 + bc.nd;
+        const int p0 = sh.colstart[j0], p1 = sh.colstart[j1];
         if (!first) {  // later chunks: load now (the first chunk was prefetched)
             const int colbase = fwd ? xj0 - bc.dmax : xj0 - d_f + bc.dmin;
             issue_strip<NT>(bc, sm, sh.Y, fwd, a.p.dy_min, dy_f, colbase, SWc);
+            set_bases<NT>(sm, sh.X, p0, p1, bc.ndy, SWc, xj0);
             cp_async_wait_all();
             __syncthreads();
         }
-        int coff[8];
+        if (fast) {
+            if (fwd)
+                scan_dispatch_fast<NW, -1>(T, sm, p0, p1, bc.nd - 1 - lane, acc);
+            else
+                scan_dispatch_fast<NW, 1>(T, sm, p0, p1, lane, acc);
+        } else {
+            int coff[8];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const int c = t * 32 + lane;
-            int o = 0;
-            if (c < bc.nc) {
-                const int e = c / bc.nd;
-                const int di = c - e * bc.nd;
-                o = e * SWc + (fwd ? (bc.nd - 1 - di) : di);
+            for (int t = 0; t < 8; ++t) {
+                int c = t * 32 + lane;
+                int o = 0;
+                if (c < bc.nc) {
+                    int e = 0;
+                    while (c >= bc.nd) { c -= bc.nd; ++e; }
+                    o = e * SWc + (fwd ? (bc.nd - 1 - c) : c);
+                }
+                coff[t] = o;
             }
-            coff[t] = o;
+            scan_dispatch<NW>(T, sm, p0, p1, coff, acc);
         }
-        scan_dispatch<NW>(T, sm, sh.X, sh.colstart[j0], sh.colstart[j1], bc.ndy, SWc, xj0, coff, acc);
         __syncthreads();
         first = false;
         j0 = j1;
@@ -377,38 +452,40 @@ __device__ void process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
     bc.ny = br.ny;
     const int np_nom = bc.nx * bc.ny;
 
-    // 1a. geometry to shared memory; occluders and grid-point codes in flight
+    // 1a. geometry to shared memory, occluders in flight
     if (tid < bc.nx) sh.X[tid] = point_coord(br.bx0, br.bx1, bc.nx, tid);
     if (tid < bc.ny) sh.Y[tid] = point_coord(br.by0, br.by1, bc.ny, tid);
     if (tid < P.nocc) cp_async16(&sh.occ[tid], a.ws.occ + (long long)bc.box * kMaxOcc + tid);
-    for (int t = tid; t < np_nom; t += NT) {
-        const int j = t / bc.ny, m = t - (t / bc.ny) * bc.ny;
-        const int x = point_coord(br.bx0, br.bx1, bc.nx, j), y = point_coord(br.by0, br.by1, bc.ny, m);
-        if (x >= 0 && x < bc.Ws && y >= 0 && y < bc.Hs)
-            cp_async8(&sm.praw[t], bc.CL + (long long)y * bc.pitch + x);
-        else
-            sm.praw[t] = 0ull;
-    }
     for (int c = tid; c < bc.nc; c += NT) sm.cost[c] = 0;
     __syncthreads();
-    // 1b. first forward strip chunk joins the same round trip
+    // 1b. grid-point codes (point t = 16 j + m) and the first forward strip chunk
+    // join the same round trip
+    for (int t = tid; t < kMaxPts; t += NT) {
+        const int j = t >> 4, m = t & 15;
+        if (j < bc.nx && m < bc.ny) {
+            const int x = sh.X[j], y = sh.Y[m];
+            if (x >= 0 && x < bc.Ws && y >= 0 && y < bc.Hs)
+                cp_async8(&sm.praw[t], bc.CL + (long long)y * bc.pitch + x);
+            else
+                sm.praw[t] = 0ull;
+        }
+    }
     const int j1_first = bc.nx > 0 ? chunk_end(sh.X, 0, bc.nx, bc.nd, a.strip_cols) : 0;
+    const int SW0 = bc.nx > 0 ? sh.X[j1_first - 1] - sh.X[0] + bc.nd : 0;
     if (bc.nx > 0 && bc.ny > 0)
-        issue_strip<NT>(bc, sm, sh.Y, true, a.p.dy_min, 0, sh.X[0] - bc.dmax,
-                        sh.X[j1_first - 1] - sh.X[0] + bc.nd);
+        issue_strip<NT>(bc, sm, sh.Y, true, a.p.dy_min, 0, sh.X[0] - bc.dmax, SW0);
     cp_async_wait_all();
     __syncthreads();
 
-    // 1c. usable points, compacted column-major
+    // 1c. usable points, compacted column-major, with their first-chunk bases
     const int sxw = a.p.win_w >> 1, syw = a.p.win_h >> 1;
     int total = 0;
-    for (int t0 = 0; t0 < np_nom; t0 += NT) {
+    for (int t0 = 0; t0 < kMaxPts; t0 += NT) {
         const int t = t0 + tid;
+        const int j = t >> 4, m = t & 15;
+        const bool grid_pt = j < bc.nx && m < bc.ny;
         bool valid = false;
-        int m = 0, j = 0;
-        if (t < np_nom) {
-            j = t / bc.ny;
-            m = t - j * bc.ny;
+        if (grid_pt) {
             const int x = sh.X[j], y = sh.Y[m];
             valid = x - sxw >= 0 && x + sxw < bc.Ws && y - syw >= 0 && y + syw < bc.Hs;
             const int fx = P.k * x, fy = P.k * y;
@@ -431,8 +508,9 @@ __device__ void process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
         if (valid) {
             sm.pcode[idx] = sm.praw[t];
             sm.pmj[idx] = (m << 8) | j;
+            if (j < j1_first) sm.pbase[idx] = 8 * (m * bc.ndy * SW0 + sh.X[j] - sh.X[0]);
         }
-        if (t < np_nom && m == 0) sh.colstart[j] = idx;
+        if (grid_pt && m == 0) sh.colstart[j] = idx;
         total += sum;
         __syncthreads();
     }
@@ -476,8 +554,8 @@ __device__ void process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
                 sm.pcode[t] = 0ull;
         }
         for (int c = tid; c < bc.nc; c += NT) sm.cost[c] = 0;
-        issue_strip<NT>(bc, sm, sh.Y, false, a.p.dy_min, dy_f, sh.X[0] - d_f + bc.dmin,
-                        sh.X[j1_first - 1] - sh.X[0] + bc.nd);
+        // chunk 0's point bases are still those of 1c: later chunks own other points
+        issue_strip<NT>(bc, sm, sh.Y, false, a.p.dy_min, dy_f, sh.X[0] - d_f + bc.dmin, SW0);
         cp_async_wait_all();
         __syncthreads();
         search_pass<NT>(a, bc, sm, sh, false);
@@ -515,7 +593,7 @@ __device__ void process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
         BlockResult r;
         r.d_full = rec.d_full;
         r.flags = rec.flags;
-        a.ws.blkres[b] = r;
+        a.ws.blkres[a.ws.blk_base[bc.box] + bc.slot] = r;
         if (a.dbg.blocks) a.dbg.blocks[(long long)bc.box * slots + bc.slot] = rec;
         if (!(rec.flags & CTM_BLK_FEW_POINTS))
             atomicAdd(&a.ws.counts->evals, 2ull * (unsigned long long)total * (unsigned long long)bc.nc);
@@ -544,6 +622,8 @@ __device__ __forceinline__ Smem carve(const MatchArgs &a, unsigned char *raw)
     sm.cost = reinterpret_cast<int *>(raw + off);
     off += sizeof(int) * kMaxCand;
     sm.pmj = reinterpret_cast<int *>(raw + off);
+    off += sizeof(int) * kMaxPts;
+    sm.pbase = reinterpret_cast<int *>(raw + off);
     return sm;
 }
 
@@ -580,7 +660,7 @@ __global__ void __launch_bounds__(NT) match_box_kernel(MatchArgs a, int box)
 size_t match_smem_bytes(const MatchArgs &a)
 {
     return sizeof(uint64_t) * (size_t)a.strip_rows * a.strip_cols + 2 * sizeof(uint64_t) * kMaxPts +
-           sizeof(int) * kMaxCand + sizeof(int) * kMaxPts;
+           sizeof(int) * kMaxCand + 2 * sizeof(int) * kMaxPts;
 }
 
 cudaError_t match_configure(const MatchArgs &a, int threads, int *ctas_per_sm)

@@ -8,7 +8,8 @@
 // max_occluders.  Boxes that are empty after clipping get their outputs here.
 //
 // plan_scan_kernel (one CTA): exclusive scan of the block counts, the flat
-// (box, slot) work list the matching kernel drains, and counter reset.  All
+// (box, slot) work list the matching kernel drains (largest blocks first), and
+// counter reset.  All
 // counts come from device memory so a captured graph replays with new inputs.
 #include <math.h>
 
@@ -116,6 +117,17 @@ __global__ void __launch_bounds__(kPlanThreads) plan_boxes_kernel(MatchArgs a)
     }
 }
 
+constexpr int kWorkBuckets = 64;
+
+// Bucket of a block's nominal work nx * ny * N_d * N_dy (up to 2^16 * 256 / 2^10).
+__device__ __forceinline__ int work_bucket(const BoxPlan &P, int slot, int pts_side, int ndy)
+{
+    const BlockRect r = block_rect(P, slot, pts_side);
+    const int w = r.nx * r.ny * (P.dmax - P.dmin + 1) * ndy;
+    const int b = w >> 10;
+    return b < kWorkBuckets - 1 ? b : kWorkBuckets - 1;
+}
+
 __global__ void __launch_bounds__(kScanThreads) plan_scan_kernel(MatchArgs a)
 {
     __shared__ int warp_tot[kScanThreads / 32];
@@ -150,11 +162,42 @@ __global__ void __launch_bounds__(kScanThreads) plan_scan_kernel(MatchArgs a)
         if (i < nb) {
             a.ws.blk_base[i] = ex;
             a.ws.box_done[i] = 0;
-            for (int s = 0; s < v; ++s) a.ws.blocks[ex + s] = make_int2(i, s);
         }
         __syncthreads();
         if (threadIdx.x == 0) s_running += warp_tot[kScanThreads / 32 - 1];
         __syncthreads();
+    }
+    // Work queue in decreasing order of nominal block work (points x candidates):
+    // the persistent matcher drains it front to back, so the largest blocks start
+    // first and small ones fill in at the end.
+    __shared__ int bucket[kWorkBuckets];
+    for (int b = threadIdx.x; b < kWorkBuckets; b += kScanThreads) bucket[b] = 0;
+    __syncthreads();
+    const int ndy = a.p.dy_max - a.p.dy_min + 1;
+    for (int i = threadIdx.x; i < nb; i += kScanThreads) {
+        const int v = a.ws.nblk[i];
+        if (v == 0) continue;
+        const BoxPlan P = a.ws.plans[i];
+        for (int s = 0; s < v; ++s) atomicAdd(&bucket[work_bucket(P, s, a.p.pts_side, ndy)], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int b = kWorkBuckets - 1; b >= 0; --b) {
+            const int c = bucket[b];
+            bucket[b] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += kScanThreads) {
+        const int v = a.ws.nblk[i];
+        if (v == 0) continue;
+        const BoxPlan P = a.ws.plans[i];
+        for (int s = 0; s < v; ++s) {
+            const int pos = atomicAdd(&bucket[work_bucket(P, s, a.p.pts_side, ndy)], 1);
+            a.ws.blocks[pos] = make_int2(i, s);
+        }
     }
     if (threadIdx.x == 0) {
         Counts *c = a.ws.counts;
