@@ -212,9 +212,10 @@ int ctm_match_batch_host(ctm_ctx *ctx, const ctm_frame *frames_host, int n_frame
 int ctm_get_stats(ctm_ctx *ctx, ctm_stats *out, ctm_stream stream);
 
 /* Integer-pipe probe for roofline denominators (no counterpart in the paper):
- * runs `iters` iterations of independent 32-bit popcount chains (kind 0) or
- * of xor chains (kind 1) on every SM and returns the operations per SM clock
- * per SM.  Synchronizes the device.  Errors: CTM_EINVAL, CTM_ECUDA. */
+ * runs `iters` iterations of independent chains of one instruction on every
+ * SM -- kind 0: 32-bit popcount, 1: 3-input xor, 2: packed fp16 greater-than
+ * mask, 3: 32-bit add, 4: 32-bit multiply-add -- and returns the operations
+ * per SM clock per SM.  Synchronizes the device.  Errors: CTM_EINVAL, CTM_ECUDA. */
 int ctm_probe_int_rate(int kind, int iters, double *ops_per_clk_per_sm);
 
 #ifdef __cplusplus

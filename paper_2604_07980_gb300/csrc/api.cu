@@ -536,7 +536,7 @@ int ctm_get_stats(ctm_ctx *ctx, ctm_stats *out, ctm_stream stream)
 
 int ctm_probe_int_rate(int kind, int iters, double *ops_per_clk_per_sm)
 {
-    if ((kind != 0 && kind != 1) || iters < 1 || !ops_per_clk_per_sm) return CTM_EINVAL;
+    if (kind < 0 || kind > 4 || iters < 1 || !ops_per_clk_per_sm) return CTM_EINVAL;
     return run_int_probe(kind, iters, ops_per_clk_per_sm) == cudaSuccess ? CTM_OK : CTM_ECUDA;
 }
 

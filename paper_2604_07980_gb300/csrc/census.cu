@@ -82,6 +82,40 @@ __device__ __forceinline__ uint32_t load_quad(const Plane &pl, int x0, int ys, i
     return v;
 }
 
+// All WH window rows of tile (x0, y) for this lane, with one uniform decision per
+// tile: interior tiles of a word-aligned image take straight-line word loads,
+// edge tiles take the per-pixel path.  Rows must lie inside the grid.
+template <int WH>
+__device__ __forceinline__ void load_tile(const Plane &pl, int x0, int y, int lane, uint32_t (&v)[WH])
+{
+    constexpr int sy = WH / 2;
+    const int xs = x0 - 8 + 4 * lane;
+    const bool interior = pl.vec_load && x0 - 8 >= 0 &&
+                          (pl.k == 1 ? x0 + 76 <= pl.W : 2 * (x0 + 76) <= pl.W);
+    if (interior) {
+        const long long step = (long long)pl.k * pl.pitch;
+        const uint8_t *row = pl.img + (long long)pl.k * (y - sy) * pl.pitch + (long long)pl.k * xs;
+        if (lane < 21) {
+            if (pl.k == 1) {
+#pragma unroll
+                for (int r = 0; r < WH; ++r) v[r] = __ldg(reinterpret_cast<const uint32_t *>(row + r * step));
+            } else {
+#pragma unroll
+                for (int r = 0; r < WH; ++r) {
+                    const uint2 w = __ldg(reinterpret_cast<const uint2 *>(row + r * step));
+                    v[r] = __byte_perm(w.x, w.y, 0x6420);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < WH; ++r) v[r] = 0u;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < WH; ++r) v[r] = load_quad(pl, x0, y - sy + r, lane);
+    }
+}
+
 // Convert one loaded row (4 pixels per lane) to the two half2 copies.
 __device__ __forceinline__ void store_quad(uint32_t v, uint32_t *even, uint32_t *odd, int lane)
 {
@@ -308,10 +342,7 @@ __device__ void roi_stream(const MatchArgs &a, const WarpStage &st, TileCursor &
     uint32_t vA[WH];
 #pragma unroll
     for (int r = 0; r < WH; ++r) vA[r] = 0u;
-    if (okA && yA - sy >= 0 && yA + sy < plA.Hs) {
-#pragma unroll
-        for (int r = 0; r < WH; ++r) vA[r] = load_quad(plA, xA, yA - sy + r, lane);
-    }
+    if (okA && yA - sy >= 0 && yA + sy < plA.Hs) load_tile<WH>(plA, xA, yA, lane, vA);
     while (okA) {
         int xB = 0, yB = 0;
         const bool okB = next_tile(a, c, nwarps, total, lane, xB, yB);
@@ -319,10 +350,7 @@ __device__ void roi_stream(const MatchArgs &a, const WarpStage &st, TileCursor &
         uint32_t vB[WH];
 #pragma unroll
         for (int r = 0; r < WH; ++r) vB[r] = 0u;
-        if (okB && yB - sy >= 0 && yB + sy < plB.Hs) {
-#pragma unroll
-            for (int r = 0; r < WH; ++r) vB[r] = load_quad(plB, xB, yB - sy + r, lane);
-        }
+        if (okB && yB - sy >= 0 && yB + sy < plB.Hs) load_tile<WH>(plB, xB, yB, lane, vB);
         // compute tile A
         const int x = xA + 2 * lane;
         uint64_t c0 = 0ull, c1 = 0ull;

@@ -1,7 +1,8 @@
 // probe.cu -- integer-pipe throughput probe used for roofline denominators.
 //
 // Every SM runs one CTA of 1024 threads; each thread advances 8 independent
-// chains of the probed instruction (32-bit popcount, or a 3-input xor), and the
+// chains of the probed instruction (0: 32-bit popcount, 1: 3-input xor,
+// 2: packed fp16 greater-than mask, 3: 32-bit add, 4: 32-bit multiply-add), and the
 // CTA's SM-clock cycle count gives operations per clock per SM.  Inline PTX with
 // volatile asm keeps the compiler from folding the chains.
 #include <algorithm>
@@ -19,6 +20,27 @@ __device__ __forceinline__ unsigned popc_op(unsigned x)
 {
     unsigned r;
     asm volatile("popc.b32 %0, %1;" : "=r"(r) : "r"(x));
+    return r;
+}
+
+__device__ __forceinline__ unsigned hgt2_mask_op(unsigned x, unsigned y)
+{
+    unsigned r;
+    asm volatile("set.gt.u32.f16x2 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(y));
+    return r;
+}
+
+__device__ __forceinline__ unsigned iadd_op(unsigned x, unsigned y)
+{
+    unsigned r;
+    asm volatile("add.u32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(y));
+    return r;
+}
+
+__device__ __forceinline__ unsigned imad_op(unsigned x, unsigned y, unsigned z)
+{
+    unsigned r;
+    asm volatile("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(y), "r"(z));
     return r;
 }
 
@@ -44,10 +66,25 @@ __global__ void __launch_bounds__(kProbeThreads) int_probe_kernel(int kind, int 
 #pragma unroll
             for (int c = 0; c < kChains; ++c) v[c] = popc_op(v[c]);
         }
-    } else {
+    } else if (kind == 1) {
         for (int i = 0; i < iters; ++i) {
 #pragma unroll
             for (int c = 0; c < kChains; ++c) v[c] = xor3_op(v[c], y, z);
+        }
+    } else if (kind == 2) {
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) v[c] = hgt2_mask_op(v[c], y);
+        }
+    } else if (kind == 3) {
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) v[c] = iadd_op(v[c], y);
+        }
+    } else {
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) v[c] = imad_op(v[c], y, z);
         }
     }
     __syncthreads();
