@@ -130,6 +130,9 @@ typedef struct {
     uint64_t cost_evals;   /* popcount(C_L xor C_R) evaluations, both passes */
     int32_t n_blocks;      /* blocks planned                                  */
     int32_t n_boxes;       /* boxes planned                                   */
+    int32_t error;         /* nonzero: a bounded device wait expired and some
+                              outputs of the call were not written            */
+    int32_t reserved;
 } ctm_stats;
 
 /* Human-readable name of a status code (static string). */

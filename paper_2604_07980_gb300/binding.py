@@ -55,7 +55,8 @@ class ctm_debug(ctypes.Structure):
 
 
 class ctm_stats(ctypes.Structure):
-    _fields_ = [("cost_evals", ctypes.c_uint64), ("n_blocks", ctypes.c_int32), ("n_boxes", ctypes.c_int32)]
+    _fields_ = [("cost_evals", ctypes.c_uint64), ("n_blocks", ctypes.c_int32), ("n_boxes", ctypes.c_int32),
+                ("error", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 BLOCK_DTYPE = np.dtype([("n_pts", "<i4"), ("n_valid", "<i4"), ("d_f", "<i4"), ("dy_f", "<i4"),
@@ -292,7 +293,8 @@ class Context:
     def stats(self, stream=None) -> dict:
         s = ctm_stats()
         _check(lib().ctm_get_stats(self._h, ctypes.byref(s), _stream(stream)), "ctm_get_stats")
-        return {"cost_evals": int(s.cost_evals), "n_blocks": int(s.n_blocks), "n_boxes": int(s.n_boxes)}
+        return {"cost_evals": int(s.cost_evals), "n_blocks": int(s.n_blocks), "n_boxes": int(s.n_boxes),
+                "error": int(s.error)}
 
 
 class DeviceBatch:

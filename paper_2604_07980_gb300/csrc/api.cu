@@ -26,7 +26,7 @@ struct ctm_ctx {
     int device = 0;
     int sm_count = 0;
     int ctas_per_sm = 0;
-    int match_threads = 256;
+    int match_threads = 128;
     ctm_params p{};
     Caps caps{};
     Workspace ws{};
@@ -107,6 +107,7 @@ int enqueue_match(ctm_ctx *ctx, const MatchArgs &a, int frames_grid, int match_g
     MatchArgs b = a;
     b.caps.max_frames = std::min(ctx->caps.max_frames, frames_grid);
     cudaError_t e = launch_plan(b, s);
+    if (e == cudaSuccess) e = launch_sample(b, s);
     if (e == cudaSuccess) e = launch_mark(b, s);
     if (e == cudaSuccess) e = launch_census_roi(b, ctx->sm_count * 4, s);
     if (!plain) {
@@ -224,6 +225,8 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
     const size_t o_base = take(sizeof(int) * (size_t)max_boxes);
     const size_t o_blocks = take(sizeof(int2) * (size_t)ctx->caps.max_blocks);
     const size_t o_blkres = take(sizeof(BlockResult) * (size_t)ctx->caps.max_blocks);
+    const size_t o_geom = take(sizeof(BlockGeom) * (size_t)ctx->caps.max_blocks);
+    const size_t o_queue = take(sizeof(int) * (size_t)ctx->caps.max_blocks);
     const size_t o_done = take(sizeof(int) * (size_t)max_boxes);
     const size_t o_counts = take(sizeof(Counts));
     const size_t o_frames = take(sizeof(ctm_frame) * (size_t)max_frames);
@@ -256,6 +259,8 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
     ws.blk_base = reinterpret_cast<int *>(base + o_base);
     ws.blocks = reinterpret_cast<int2 *>(base + o_blocks);
     ws.blkres = reinterpret_cast<BlockResult *>(base + o_blkres);
+    ws.geom = reinterpret_cast<BlockGeom *>(base + o_geom);
+    ws.queue = reinterpret_cast<int *>(base + o_queue);
     ws.box_done = reinterpret_cast<int *>(base + o_done);
     ws.counts = reinterpret_cast<Counts *>(base + o_counts);
     ws.frames = reinterpret_cast<ctm_frame *>(base + o_frames);
@@ -419,6 +424,7 @@ int ctm_match_batch_profiled(ctm_ctx *ctx, const ctm_frame *frames_dev, const in
     const int grid = ctx->sm_count * ctx->ctas_per_sm;
     cudaError_t e = cudaEventRecord((cudaEvent_t)events[0], s);
     if (e == cudaSuccess) e = launch_plan(a, s);
+    if (e == cudaSuccess) e = launch_sample(a, s);
     if (e == cudaSuccess) e = launch_mark(a, s);
     if (e == cudaSuccess) e = cudaEventRecord((cudaEvent_t)events[1], s);
     if (e == cudaSuccess) e = launch_census_roi(a, ctx->sm_count * 4, s);
@@ -531,6 +537,8 @@ int ctm_get_stats(ctm_ctx *ctx, ctm_stats *out, ctm_stream stream)
     out->cost_evals = c.evals;
     out->n_blocks = c.n_blocks;
     out->n_boxes = c.n_boxes;
+    out->error = c.error;
+    out->reserved = 0;
     return CTM_OK;
 }
 

@@ -23,8 +23,11 @@ struct Counts {
     int n_frames;    // clamped to capacity
     int n_boxes;     // clamped to capacity
     int n_blocks;    // total planned blocks
-    int queue_head;  // next block index of the persistent queue
+    int queue_head;  // next entry of the persistent work queue
+    int error;       // nonzero: a bounded device wait expired (results incomplete)
     unsigned long long evals;
+    int n_big;       // searchable blocks queued from the front (large work)
+    int n_small;     // searchable blocks queued from the back (small work)
 };
 
 // Planned box (device).
@@ -35,6 +38,18 @@ struct BoxPlan {
     int nblk, nocc, dmin, dmax;
     int Ws, Hs;               // matching-grid size of the frame
     float fb;                 // f_px * baseline_m
+};
+
+// Sampled point grid of one block (Sec. 4.3.4) with its usable points
+// (Sec. 4.3.5), computed once by the sampling kernel.
+struct __align__(16) BlockGeom {
+    int16_t X[kMaxPtsSide];           // sampled columns on the matching grid
+    int16_t Y[kMaxPtsSide];           // sampled rows
+    uint16_t colmask[kMaxPtsSide];    // bit m of colmask[j]: point (X_j, Y_m) usable
+    uint16_t colprefix[kMaxPtsSide];  // usable points in columns < j
+    int32_t n_valid;
+    int32_t nx, ny;
+    uint32_t cstart;                  // bit j: a strip column chunk starts at column j
 };
 
 // Result of one block kept for the aggregation (device).
@@ -54,7 +69,9 @@ struct Workspace {
     int4 *occ;                 // [max_boxes * kMaxOcc]
     int *nblk;                 // [max_boxes]
     int *blk_base;             // [max_boxes]
-    int2 *blocks;              // [max_blocks] (box, slot)
+    int2 *blocks;              // [max_blocks] (box, slot), flat in box order
+    BlockGeom *geom;           // [max_blocks] indexed like blocks
+    int *queue;                // [max_blocks] searchable blocks: large from the front, small from the back
     BlockResult *blkres;       // [max_blocks]
     int *box_done;             // [max_boxes]
     Counts *counts;
@@ -130,6 +147,7 @@ size_t census_smem_bytes(int win_h);
 cudaError_t launch_stage_frame(const MatchArgs &a, ctm_frame f, int n_boxes, cudaStream_t s);
 cudaError_t launch_plan(const MatchArgs &a, cudaStream_t s);
 cudaError_t launch_mark(const MatchArgs &a, cudaStream_t s);
+cudaError_t launch_sample(const MatchArgs &a, cudaStream_t s);
 
 // Matching (match.cu)
 // threads per matching CTA: 128 or 256

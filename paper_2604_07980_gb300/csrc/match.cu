@@ -24,6 +24,7 @@
 // because Eq. census_cost is a sum over points.
 #include <math.h>
 
+#include "aggregate.cuh"
 #include "ctm_internal.cuh"
 
 namespace ctm {
@@ -49,9 +50,50 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// mbarrier + bulk copy (TMA, 1-D) primitives.
+__device__ __forceinline__ void mbar_init(uint64_t *mbar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(mbar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *mbar, unsigned bytes)
+{
+    unsigned long long state;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;\n"
+                 : "=l"(state) : "r"(smem_addr(mbar)), "r"(bytes) : "memory");
+    (void)state;
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(smem_addr(mbar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(mbar)) : "memory");
+}
+
+// Bounded wait for the phase `parity` of mbar.  On expiry the CTA records an
+// error, waits once more (bounded) for its copies in flight and reports false.
+constexpr unsigned kWaitLimit = 1u << 22;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, unsigned parity, int *error_flag)
+{
+    for (unsigned it = 0; it < kWaitLimit; ++it)
+        if (mbar_try_wait(mbar, parity)) return true;
+    atomicOr(error_flag, 1);
+    for (unsigned it = 0; it < kWaitLimit; ++it)
+        if (mbar_try_wait(mbar, parity)) break;
+    return false;
+}
+
 struct Smem {
     uint64_t *strip;   // strip_rows * strip_cols
-    uint64_t *praw;    // kMaxPts: left code of grid point t = 16 j + m
     uint64_t *pcode;   // kMaxPts: compacted codes (left, then right queries)
     int *cost;         // kMaxCand
     int *pmj;          // kMaxPts: (m << 8) | j
@@ -60,11 +102,11 @@ struct Smem {
 
 template <int NW>
 struct Shared {
+    BlockGeom geom;         // the block's sampled grid (copied from global)
+    uint64_t mbar;          // completion of the strip bulk copies
     int X[kMaxPtsSide];
     int Y[kMaxPtsSide];
     int colstart[kMaxPtsSide + 1];
-    int4 occ[kMaxOcc];
-    int warp_cnt[NW];
     unsigned warp_min[NW];
     float agg[kMaxSlots];
     float agg_sorted[kMaxSlots];
@@ -72,6 +114,8 @@ struct Shared {
     int d_b, dy_b;
     int last;
     int next;
+    unsigned cstart;        // bit j set: a strip column chunk starts at point column j
+    int abort;              // a bounded wait expired: stop this CTA
 };
 
 struct BlockCtx {
@@ -187,52 +231,96 @@ __device__ __forceinline__ void scan_dispatch_fast(int T, const Smem &sm, int p0
     }
 }
 
-// Byte offsets of the compacted points [p0, p1) into a strip chunk of width SWc
-// whose first column is point column xj0: row m * ndy, column X_j - xj0.
+// Byte offsets of the compacted points [p0, p1) into a strip chunk with row
+// stride SWa whose element 0 is column xj0 - delta: row m * ndy, column
+// X_j - xj0 + delta.
 template <int NT>
 __device__ __forceinline__ void set_bases(const Smem &sm, const int *X, int p0, int p1, int ndy,
-                                          int SWc, int xj0)
+                                          int SWa, int xj0, int delta)
 {
     for (int p = p0 + (int)threadIdx.x; p < p1; p += NT) {
         const int mj = sm.pmj[p];
-        sm.pbase[p] = 8 * ((mj >> 8) * ndy * SWc + X[mj & 255] - xj0);
+        sm.pbase[p] = 8 * ((mj >> 8) * ndy * SWa + X[mj & 255] - xj0 + delta);
     }
 }
 
-// Last point column of the chunk starting at j0 whose strip fits strip_cols.
-__device__ __forceinline__ int chunk_end(const int *X, int j0, int nx, int nd, int strip_cols)
+// Strip chunk geometry: columns [colbase, colbase + SWc) are stored from the even
+// column colbase & ~1, so rows are 16-byte aligned for bulk copies.
+struct ChunkGeom {
+    int colbase_a;  // first stored column (even)
+    int delta;      // colbase - colbase_a (0 or 1)
+    int SWa;        // row stride in elements (even)
+};
+
+__device__ __forceinline__ ChunkGeom chunk_geom(int colbase, int SWc)
 {
-    int j1 = j0 + 1;
-    while (j1 < nx && X[j1] - X[j0] + nd <= strip_cols) ++j1;
-    return j1;
+    ChunkGeom g;
+    g.colbase_a = colbase & ~1;
+    g.delta = colbase - g.colbase_a;
+    g.SWa = (SWc + g.delta + 1) & ~1;
+    return g;
 }
 
-// Issue the asynchronous copies of one strip chunk: rows (m, e) of the right
-// plane at Y_m + dy_min + e (forward) or of the left plane at
-// Y_m + dy_f - (dy_min + e) (backward), columns [colbase, colbase + SWc).
-// Positions outside the plane are written as 0.
+// Load one strip chunk: rows (m, e) of the right plane at Y_m + dy_min + e
+// (forward) or of the left plane at Y_m + dy_f - (dy_min + e) (backward).
+// Warp 0 issues one bulk copy per row for its in-plane part; lane 0 first
+// registers the total byte count on the CTA's mbarrier.  After the copies land,
+// positions outside the plane are zero-filled (only edge chunks have any).
+// Returns false if the bounded wait expired.
 template <int NT>
-__device__ __forceinline__ void issue_strip(const BlockCtx &bc, const Smem &sm, const int *Y, bool fwd,
-                                            int dy_min, int dy_f, int colbase, int SWc)
+__device__ __forceinline__ bool load_chunk(const MatchArgs &a, const BlockCtx &bc, const Smem &sm,
+                                           Shared<NT / 32> &sh, unsigned &phase, bool fwd, int dy_f,
+                                           const ChunkGeom &g)
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int rows = bc.ny * bc.ndy;
     const uint64_t *plane = fwd ? bc.CR : bc.CL;
-    for (int r = warp; r < rows; r += NT / 32) {
-        const int m = bc.ndy == 1 ? r : r / bc.ndy;
-        const int e = r - m * bc.ndy;
-        const int y = fwd ? Y[m] + dy_min + e : Y[m] + dy_f - (dy_min + e);
-        uint64_t *dst = sm.strip + r * SWc;
-        const bool row_ok = y >= 0 && y < bc.Hs;
-        const uint64_t *src = plane + (row_ok ? (long long)y * bc.pitch : 0);
-        for (int c = lane; c < SWc; c += 32) {
-            const int x = colbase + c;
-            if (row_ok && x >= 0 && x < bc.Ws)
-                cp_async8(dst + c, src + x);
-            else
-                dst[c] = 0ull;
+    const int Ws_even = (bc.Ws + 1) & ~1;   // the padding column after an odd width is readable
+    const int x_lo = max(g.colbase_a, 0);
+    const int x_hi = min(g.colbase_a + g.SWa, Ws_even);
+    const unsigned row_bytes = x_hi > x_lo ? 8u * (unsigned)(x_hi - x_lo) : 0u;
+    if (tid < 32) {
+        unsigned total = 0;
+        for (int r = lane; r < rows; r += 32) {
+            const int m = bc.ndy == 1 ? r : r / bc.ndy;
+            const int e = r - m * bc.ndy;
+            const int y = fwd ? sh.Y[m] + a.p.dy_min + e : sh.Y[m] + dy_f - (a.p.dy_min + e);
+            if (y >= 0 && y < bc.Hs) total += row_bytes;
+        }
+        total = __reduce_add_sync(0xffffffffu, total);
+        // order earlier generic-proxy accesses of the strip before the bulk writes
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        if (lane == 0) mbar_arrive_expect_tx(&sh.mbar, total);
+        __syncwarp();
+        if (row_bytes > 0) {
+            for (int r = lane; r < rows; r += 32) {
+                const int m = bc.ndy == 1 ? r : r / bc.ndy;
+                const int e = r - m * bc.ndy;
+                const int y = fwd ? sh.Y[m] + a.p.dy_min + e : sh.Y[m] + dy_f - (a.p.dy_min + e);
+                if (y >= 0 && y < bc.Hs)
+                    bulk_g2s(sm.strip + r * g.SWa + (x_lo - g.colbase_a), plane + (long long)y * bc.pitch + x_lo,
+                             row_bytes, &sh.mbar);
+            }
         }
     }
+    const bool ok = mbar_wait_bounded(&sh.mbar, phase, &a.ws.counts->error);
+    phase ^= 1u;
+    // zero-fill what lies outside the plane (rows outside it; columns < 0 or >= Ws)
+    const bool edge = g.colbase_a < 0 || g.colbase_a + g.SWa > bc.Ws ||
+                      sh.Y[0] + (fwd ? a.p.dy_min : dy_f - a.p.dy_max) < 0 ||
+                      sh.Y[bc.ny - 1] + (fwd ? a.p.dy_max : dy_f - a.p.dy_min) >= bc.Hs;
+    if (edge) {
+        const int total_el = rows * g.SWa;
+        for (int i = tid; i < total_el; i += NT) {
+            const int r = i / g.SWa, c = i - r * g.SWa;
+            const int m = bc.ndy == 1 ? r : r / bc.ndy;
+            const int e = r - m * bc.ndy;
+            const int y = fwd ? sh.Y[m] + a.p.dy_min + e : sh.Y[m] + dy_f - (a.p.dy_min + e);
+            const int x = g.colbase_a + c;
+            if (y < 0 || y >= bc.Hs || x < 0 || x >= bc.Ws) sm.strip[i] = 0ull;
+        }
+    }
+    return ok;
 }
 
 // Warp and CTA minimum of the keys (cost << 16 | c) over the candidates; the
@@ -263,11 +351,11 @@ __device__ __forceinline__ void argmin_pass(const MatchArgs &a, const BlockCtx &
     __syncthreads();
 }
 
-// One search pass after its first strip chunk has been issued and landed and
-// the point bases of the first chunk are set.
+// One search pass after its first strip chunk has landed and the point bases of
+// the first chunk are set.  Returns false if a bounded wait expired.
 template <int NT>
-__device__ void search_pass(const MatchArgs &a, const BlockCtx &bc, const Smem &sm,
-                            Shared<NT / 32> &sh, bool fwd)
+__device__ bool search_pass(const MatchArgs &a, const BlockCtx &bc, const Smem &sm,
+                            Shared<NT / 32> &sh, unsigned &phase, bool fwd, ChunkGeom g)
 {
     constexpr int NW = NT / 32;
     const int lane = threadIdx.x & 31;
@@ -277,18 +365,19 @@ __device__ void search_pass(const MatchArgs &a, const BlockCtx &bc, const Smem &
 #pragma unroll
     for (int t = 0; t < 8; ++t) acc[t] = 0;
     const int d_f = sh.d_f, dy_f = sh.dy_f;
+    const unsigned cs = sh.cstart;
     int j0 = 0;
-    bool first = true;
+    bool ok = true;
     while (j0 < bc.nx) {
-        const int j1 = chunk_end(sh.X, j0, bc.nx, bc.nd, a.strip_cols);
+        const unsigned later = cs & ~((2u << j0) - 1u);
+        const int j1 = later ? __ffs(later) - 1 : bc.nx;
         const int xj0 = sh.X[j0];
-        const int SWc = sh.X[j1 - 1] - xj0 + bc.nd;
         const int p0 = sh.colstart[j0], p1 = sh.colstart[j1];
-        if (!first) {  // later chunks: load now (the first chunk was prefetched)
-            const int colbase = fwd ? xj0 - bc.dmax : xj0 - d_f + bc.dmin;
-            issue_strip<NT>(bc, sm, sh.Y, fwd, a.p.dy_min, dy_f, colbase, SWc);
-            set_bases<NT>(sm, sh.X, p0, p1, bc.ndy, SWc, xj0);
-            cp_async_wait_all();
+        if (j0 > 0) {  // later chunks: load now (the first chunk was prefetched)
+            const int SWc = sh.X[j1 - 1] - xj0 + bc.nd;
+            g = chunk_geom(fwd ? xj0 - bc.dmax : xj0 - d_f + bc.dmin, SWc);
+            ok = load_chunk<NT>(a, bc, sm, sh, phase, fwd, dy_f, g) && ok;
+            set_bases<NT>(sm, sh.X, p0, p1, bc.ndy, g.SWa, xj0, g.delta);
             __syncthreads();
         }
         if (fast) {
@@ -305,14 +394,13 @@ __device__ void search_pass(const MatchArgs &a, const BlockCtx &bc, const Smem &
                 if (c < bc.nc) {
                     int e = 0;
                     while (c >= bc.nd) { c -= bc.nd; ++e; }
-                    o = e * SWc + (fwd ? (bc.nd - 1 - c) : c);
+                    o = e * g.SWa + (fwd ? (bc.nd - 1 - c) : c);
                 }
                 coff[t] = o;
             }
             scan_dispatch<NW>(T, sm, p0, p1, coff, acc);
         }
         __syncthreads();
-        first = false;
         j0 = j1;
     }
 #pragma unroll
@@ -322,108 +410,13 @@ __device__ void search_pass(const MatchArgs &a, const BlockCtx &bc, const Smem &
     }
     __syncthreads();
     argmin_pass<NT>(a, bc, sm, sh, fwd);
-}
-
-// Sec. 4.3.4 on the block records of one box, by warp 0 of the CTA that
-// finished the box last.
-template <int NW>
-__device__ void aggregate_box(const MatchArgs &a, int box, Shared<NW> &sh)
-{
-    const int lane = threadIdx.x & 31;
-    const BoxPlan P = a.ws.plans[box];
-    const int base = a.ws.blk_base[box];
-    float d[2];
-    int f[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int s = lane + 32 * h;
-        f[h] = 0;
-        d[h] = 0.0f;
-        if (s < P.nblk) {
-            const int2 raw = __ldcg(reinterpret_cast<const int2 *>(a.ws.blkres + base + s));
-            d[h] = __int_as_float(raw.x);
-            f[h] = raw.y;
-        }
-    }
-    const unsigned full = 0xffffffffu;
-    const int fb_any = __any_sync(full, ((f[0] | f[1]) & CTM_BLK_FB_REJECT) != 0);
-    const int few_any = __any_sync(full, ((f[0] | f[1]) & CTM_BLK_FEW_POINTS) != 0);
-    const bool v0 = (f[0] & CTM_BLK_VALID) != 0, v1 = (f[1] & CTM_BLK_VALID) != 0;
-    const int clamp_any = __any_sync(full, (v0 && (f[0] & CTM_BLK_SUBPIX_CLAMPED)) ||
-                                               (v1 && (f[1] & CTM_BLK_SUBPIX_CLAMPED)));
-    const unsigned b0 = __ballot_sync(full, v0), b1 = __ballot_sync(full, v1);
-    const unsigned lt = (1u << lane) - 1u;
-    const int nv = __popc(b0) + __popc(b1);
-    if (v0) sh.agg[__popc(b0 & lt)] = d[0];
-    if (v1) sh.agg[__popc(b0) + __popc(b1 & lt)] = d[1];
-    __syncwarp();
-    // rank sort (ties by position) into agg_sorted
-    for (int e = lane; e < nv; e += 32) {
-        const float x = sh.agg[e];
-        int rank = 0;
-        for (int q = 0; q < nv; ++q) {
-            const float y = sh.agg[q];
-            rank += (y < x) || (y == x && q < e);
-        }
-        sh.agg_sorted[rank] = x;
-    }
-    __syncwarp();
-    if (lane != 0) return;
-    int fl = P.far ? CTM_BOX_FAR : 0;
-    if (fb_any) fl |= CTM_BOX_FB_REJECT;
-    if (few_any) fl |= CTM_BOX_FEW_POINTS;
-    if (clamp_any) fl |= CTM_BOX_SUBPIX_CLAMPED;
-    bool have = false;
-    float d_box = 0.0f;
-    const float *v = sh.agg_sorted;
-    if (P.far) {
-        if (nv == 1) { have = true; d_box = v[0]; }
-    } else if (nv > 0) {
-        // longest run with consecutive differences < tau_d; first on ties
-        int best_start = 0, best_len = 1, cur_start = 0, cur_len = 1;
-        for (int i = 1; i < nv; ++i) {
-            if (__fsub_rn(v[i], v[i - 1]) < a.p.agg_tau_d) {
-                ++cur_len;
-            } else {
-                cur_start = i;
-                cur_len = 1;
-            }
-            if (cur_len > best_len) { best_len = cur_len; best_start = cur_start; }
-        }
-        if (best_len >= a.p.agg_nmin) {
-            have = true;
-            const float *run = v + best_start;
-            const int m = best_len;
-            if (a.p.agg_mode == 0) {
-                d_box = (m & 1) ? run[m / 2] : __fmul_rn(__fadd_rn(run[m / 2 - 1], run[m / 2]), 0.5f);
-            } else {
-                const int t = (int)floorf(__fmul_rn(a.p.trim_frac, (float)m));
-                float s = 0.0f;
-                for (int i = t; i < m - t; ++i) s = __fadd_rn(s, run[i]);
-                d_box = __fdiv_rn(s, (float)(m - 2 * t));
-            }
-        }
-    }
-    if (!P.far && !have) fl |= CTM_BOX_NO_SEGMENT;
-    float disp = __int_as_float(0x7fc00000), dep = __int_as_float(0x7fc00000);
-    if (have) {
-        if (d_box > 0.0f) {
-            fl |= CTM_BOX_VALID;
-            disp = d_box;
-            dep = __fdiv_rn(P.fb, d_box);  // Eq. 1
-        } else {
-            fl |= CTM_BOX_NONPOS_DISP;
-        }
-    }
-    a.disp[box] = disp;
-    a.depth[box] = dep;
-    a.flags[box] = (uint8_t)fl;
+    return ok;
 }
 
 template <int NT>
-__device__ void process_block(const MatchArgs &a, int b, const Smem &sm, Shared<NT / 32> &sh)
+__device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<NT / 32> &sh,
+                              unsigned &phase)
 {
-    constexpr int NW = NT / 32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int2 bs = a.ws.blocks[b];
     const BoxPlan P = a.ws.plans[bs.x];
@@ -447,126 +440,95 @@ __device__ void process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
         bc.CR = full ? base + a.ws.plane1_elems : base + 2 * a.ws.plane1_elems + a.ws.planek_elems;
         bc.pitch = full ? a.ws.pitch1 : a.ws.pitchk;
     }
-    const BlockRect br = block_rect(P, bs.y, a.p.pts_side);
-    bc.nx = br.nx;
-    bc.ny = br.ny;
-    const int np_nom = bc.nx * bc.ny;
 
-    // 1a. geometry to shared memory, occluders in flight
-    if (tid < bc.nx) sh.X[tid] = point_coord(br.bx0, br.bx1, bc.nx, tid);
-    if (tid < bc.ny) sh.Y[tid] = point_coord(br.by0, br.by1, bc.ny, tid);
-    if (tid < P.nocc) cp_async16(&sh.occ[tid], a.ws.occ + (long long)bc.box * kMaxOcc + tid);
+    // 1a. the block's sampled grid and usable points (from the sampling kernel)
+    if (tid < (int)(sizeof(BlockGeom) / 16))
+        cp_async16(reinterpret_cast<char *>(&sh.geom) + 16 * tid,
+                   reinterpret_cast<const char *>(a.ws.geom + b) + 16 * tid);
     for (int c = tid; c < bc.nc; c += NT) sm.cost[c] = 0;
-    __syncthreads();
-    // 1b. grid-point codes (point t = 16 j + m) and the first forward strip chunk
-    // join the same round trip
-    for (int t = tid; t < kMaxPts; t += NT) {
-        const int j = t >> 4, m = t & 15;
-        if (j < bc.nx && m < bc.ny) {
-            const int x = sh.X[j], y = sh.Y[m];
-            if (x >= 0 && x < bc.Ws && y >= 0 && y < bc.Hs)
-                cp_async8(&sm.praw[t], bc.CL + (long long)y * bc.pitch + x);
-            else
-                sm.praw[t] = 0ull;
-        }
-    }
-    const int j1_first = bc.nx > 0 ? chunk_end(sh.X, 0, bc.nx, bc.nd, a.strip_cols) : 0;
-    const int SW0 = bc.nx > 0 ? sh.X[j1_first - 1] - sh.X[0] + bc.nd : 0;
-    if (bc.nx > 0 && bc.ny > 0)
-        issue_strip<NT>(bc, sm, sh.Y, true, a.p.dy_min, 0, sh.X[0] - bc.dmax, SW0);
     cp_async_wait_all();
     __syncthreads();
+    const BlockGeom &g = sh.geom;
+    bc.nx = g.nx;
+    bc.ny = g.ny;
+    const int total = g.n_valid;
+    const unsigned later0 = g.cstart & ~1u;
+    const int j1_first = later0 ? __ffs(later0) - 1 : bc.nx;
+    const int x0 = g.X[0];
+    const int SW0 = g.X[j1_first - 1] - x0 + bc.nd;
+    const ChunkGeom g0 = chunk_geom(x0 - bc.dmax, SW0);
 
-    // 1c. usable points, compacted column-major, with their first-chunk bases
-    const int sxw = a.p.win_w >> 1, syw = a.p.win_h >> 1;
-    int total = 0;
-    for (int t0 = 0; t0 < kMaxPts; t0 += NT) {
-        const int t = t0 + tid;
+    // 1b. usable points at their compacted (column-major) index, left codes in flight
+    for (int t = tid; t < kMaxPts; t += NT) {
         const int j = t >> 4, m = t & 15;
-        const bool grid_pt = j < bc.nx && m < bc.ny;
-        bool valid = false;
-        if (grid_pt) {
-            const int x = sh.X[j], y = sh.Y[m];
-            valid = x - sxw >= 0 && x + sxw < bc.Ws && y - syw >= 0 && y + syw < bc.Hs;
-            const int fx = P.k * x, fy = P.k * y;
-            for (int q = 0; q < P.nocc && valid; ++q) {
-                const int4 o = sh.occ[q];
-                if (fx >= o.x && fx < o.z && fy >= o.y && fy < o.w) valid = false;
-            }
-        }
-        const unsigned ballot = __ballot_sync(0xffffffffu, valid);
-        if (lane == 0) sh.warp_cnt[warp] = __popc(ballot);
-        __syncthreads();
-        int wpre = 0, sum = 0;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            const int c = sh.warp_cnt[w];
-            if (w < warp) wpre += c;
-            sum += c;
-        }
-        const int idx = total + wpre + __popc(ballot & ((1u << lane) - 1u));
-        if (valid) {
-            sm.pcode[idx] = sm.praw[t];
+        if (j < bc.nx && ((g.colmask[j] >> m) & 1u)) {
+            const int idx = g.colprefix[j] + __popc(g.colmask[j] & ((1u << m) - 1u));
+            const int x = g.X[j], y = g.Y[m];
+            cp_async8(&sm.pcode[idx], bc.CL + (long long)y * bc.pitch + x);
             sm.pmj[idx] = (m << 8) | j;
-            if (j < j1_first) sm.pbase[idx] = 8 * (m * bc.ndy * SW0 + sh.X[j] - sh.X[0]);
+            if (j < j1_first) sm.pbase[idx] = 8 * (m * bc.ndy * g0.SWa + x - x0 + g0.delta);
         }
-        if (grid_pt && m == 0) sh.colstart[j] = idx;
-        total += sum;
-        __syncthreads();
     }
-    if (tid == 0) sh.colstart[bc.nx] = total;
+    if (tid < kMaxPtsSide) {
+        sh.X[tid] = g.X[tid];
+        sh.Y[tid] = g.Y[tid];
+    }
+    if (tid <= kMaxPtsSide) sh.colstart[tid] = tid < bc.nx ? g.colprefix[tid] : total;
+    if (tid == 0) sh.cstart = g.cstart;
     __syncthreads();
+    // 1c. the first forward strip chunk
+    bool ok = load_chunk<NT>(a, bc, sm, sh, phase, true, 0, g0);
+    cp_async_wait_all();
+    if (!__syncthreads_and(ok)) return false;
 
-    const int slots = a.p.grid_g * a.p.grid_g;
     ctm_block rec;
-    rec.n_pts = np_nom;
+    rec.n_pts = bc.nx * bc.ny;
     rec.n_valid = total;
-    rec.d_f = rec.dy_f = rec.d_b = rec.dy_b = 0;
-    rec.s_m = rec.s_0 = rec.s_p = 0;
-    rec.d_sub = 0.0f;
-    rec.d_full = 0.0f;
     rec.flags = CTM_BLK_PRESENT;
 
-    if (total < a.p.min_pts) {
-        rec.flags |= CTM_BLK_FEW_POINTS;
-    } else {
-        // 2-3. forward pass, argmin, parabola
-        search_pass<NT>(a, bc, sm, sh, true);
-        if (tid == 0) {
-            const unsigned key = sh.warp_min[0];
-            const int c = (int)(key & 0xffffu);
-            const int e = c / bc.nd, di = c - e * bc.nd;
-            sh.d_f = bc.dmin + di;
-            sh.dy_f = a.p.dy_min + e;
-            sh.s_0 = (int)(key >> 16);
-            sh.s_m = di > 0 ? sm.cost[c - 1] : 0;
-            sh.s_p = di < bc.nd - 1 ? sm.cost[c + 1] : 0;
-        }
-        __syncthreads();
-        // 4. backward pass: right codes at the matched positions + first left strip
-        const int d_f = sh.d_f, dy_f = sh.dy_f;
-        for (int t = tid; t < total; t += NT) {
-            const int mj = sm.pmj[t];
-            const int qx = sh.X[mj & 255] - d_f, qy = sh.Y[mj >> 8] + dy_f;
-            if (qx >= 0 && qx < bc.Ws && qy >= 0 && qy < bc.Hs)
-                cp_async8(&sm.pcode[t], bc.CR + (long long)qy * bc.pitch + qx);
-            else
-                sm.pcode[t] = 0ull;
-        }
-        for (int c = tid; c < bc.nc; c += NT) sm.cost[c] = 0;
-        // chunk 0's point bases are still those of 1c: later chunks own other points
-        issue_strip<NT>(bc, sm, sh.Y, false, a.p.dy_min, dy_f, sh.X[0] - d_f + bc.dmin, SW0);
-        cp_async_wait_all();
-        __syncthreads();
-        search_pass<NT>(a, bc, sm, sh, false);
-        if (tid == 0) {
-            const unsigned key = sh.warp_min[0];
-            const int c = (int)(key & 0xffffu);
-            const int e = c / bc.nd, di = c - e * bc.nd;
-            sh.d_b = bc.dmin + di;
-            sh.dy_b = a.p.dy_min + e;
-        }
-        __syncthreads();
+    // 2-3. forward pass, argmin, parabola
+    ok = search_pass<NT>(a, bc, sm, sh, phase, true, g0);
+    if (!__syncthreads_and(ok)) return false;
+    if (tid == 0) {
+        const unsigned key = sh.warp_min[0];
+        const int c = (int)(key & 0xffffu);
+        const int e = c / bc.nd, di = c - e * bc.nd;
+        sh.d_f = bc.dmin + di;
+        sh.dy_f = a.p.dy_min + e;
+        sh.s_0 = (int)(key >> 16);
+        sh.s_m = di > 0 ? sm.cost[c - 1] : 0;
+        sh.s_p = di < bc.nd - 1 ? sm.cost[c + 1] : 0;
+    }
+    __syncthreads();
+    // 4. backward pass: right codes at the matched positions + first left strip
+    const int d_f = sh.d_f, dy_f = sh.dy_f;
+    for (int t = tid; t < total; t += NT) {
+        const int mj = sm.pmj[t];
+        const int qx = sh.X[mj & 255] - d_f, qy = sh.Y[mj >> 8] + dy_f;
+        if (qx >= 0 && qx < bc.Ws && qy >= 0 && qy < bc.Hs)
+            cp_async8(&sm.pcode[t], bc.CR + (long long)qy * bc.pitch + qx);
+        else
+            sm.pcode[t] = 0ull;
+    }
+    for (int c = tid; c < bc.nc; c += NT) sm.cost[c] = 0;
+    const ChunkGeom gb = chunk_geom(x0 - d_f + bc.dmin, SW0);
+    ok = load_chunk<NT>(a, bc, sm, sh, phase, false, dy_f, gb);
+    set_bases<NT>(sm, sh.X, 0, sh.colstart[j1_first], bc.ndy, gb.SWa, x0, gb.delta);
+    cp_async_wait_all();
+    if (!__syncthreads_and(ok)) return false;
+    ok = search_pass<NT>(a, bc, sm, sh, phase, false, gb);
+    if (!__syncthreads_and(ok)) return false;
+    if (tid == 0) {
+        const unsigned key = sh.warp_min[0];
+        const int c = (int)(key & 0xffffu);
+        const int e = c / bc.nd;
+        sh.d_b = bc.dmin + (c - e * bc.nd);
+        sh.dy_b = a.p.dy_min + e;
+    }
+    __syncthreads();
+
+    // 5. block record (thread 0), completion count; the box's last block aggregates
+    if (tid == 0) {
         rec.d_f = sh.d_f;
         rec.dy_f = sh.dy_f;
         rec.d_b = sh.d_b;
@@ -586,27 +548,15 @@ __device__ void process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
         rec.d_full = __fmul_rn(rec.d_sub, (float)bc.k);
         const int dxv = abs(rec.d_b - rec.d_f);
         rec.flags |= dxv <= a.p.fb_tol ? CTM_BLK_VALID : CTM_BLK_FB_REJECT;
-    }
-
-    // 5. block record, completion count, the last CTA of the box aggregates
-    if (tid == 0) {
-        BlockResult r;
-        r.d_full = rec.d_full;
-        r.flags = rec.flags;
-        a.ws.blkres[a.ws.blk_base[bc.box] + bc.slot] = r;
-        if (a.dbg.blocks) a.dbg.blocks[(long long)bc.box * slots + bc.slot] = rec;
-        if (!(rec.flags & CTM_BLK_FEW_POINTS))
-            atomicAdd(&a.ws.counts->evals, 2ull * (unsigned long long)total * (unsigned long long)bc.nc);
-        __threadfence();
-        const int prev = atomicAdd(&a.ws.box_done[bc.box], 1);
-        sh.last = (prev == P.nblk - 1);
+        sh.last = publish_block(a, bc.box, bc.slot, rec, bc.nc) ? 1 : 0;
     }
     __syncthreads();
     if (sh.last && warp == 0) {
         __threadfence();
-        aggregate_box<NW>(a, bc.box, sh);
+        aggregate_box(a, bc.box, sh.agg, lane);
     }
     __syncthreads();
+    return true;
 }
 
 __device__ __forceinline__ Smem carve(const MatchArgs &a, unsigned char *raw)
@@ -615,8 +565,6 @@ __device__ __forceinline__ Smem carve(const MatchArgs &a, unsigned char *raw)
     size_t off = 0;
     sm.strip = reinterpret_cast<uint64_t *>(raw + off);
     off += sizeof(uint64_t) * (size_t)a.strip_rows * a.strip_cols;
-    sm.praw = reinterpret_cast<uint64_t *>(raw + off);
-    off += sizeof(uint64_t) * kMaxPts;
     sm.pcode = reinterpret_cast<uint64_t *>(raw + off);
     off += sizeof(uint64_t) * kMaxPts;
     sm.cost = reinterpret_cast<int *>(raw + off);
@@ -631,35 +579,45 @@ template <int NT>
 __global__ void __launch_bounds__(NT, 1536 / NT)
     match_persistent_kernel(MatchArgs a)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ Shared<NT / 32> sh;
     const Smem sm = carve(a, smem_raw);
-    const int nblocks = a.ws.counts->n_blocks;
+    if (threadIdx.x == 0) mbar_init(&sh.mbar, 1);
+    __syncthreads();
+    unsigned phase = 0;
+    const int n_big = a.ws.counts->n_big;
+    const int nq = n_big + a.ws.counts->n_small;
     for (;;) {
         if (threadIdx.x == 0) sh.next = atomicAdd(&a.ws.counts->queue_head, 1);
         __syncthreads();
-        const int b = sh.next;
+        const int i = sh.next;
         __syncthreads();
-        if (b >= nblocks) break;
-        process_block<NT>(a, b, sm, sh);
+        if (i >= nq) break;
+        const int b = i < n_big ? a.ws.queue[i] : a.ws.queue[a.caps.max_blocks - 1 - (i - n_big)];
+        if (!process_block<NT>(a, b, sm, sh, phase)) break;  // a bounded wait expired
     }
 }
 
 template <int NT>
 __global__ void __launch_bounds__(NT) match_box_kernel(MatchArgs a, int box)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ Shared<NT / 32> sh;
     if ((int)blockIdx.x >= a.ws.nblk[box]) return;
+    const int b = a.ws.blk_base[box] + blockIdx.x;
+    if (a.ws.geom[b].n_valid < a.p.min_pts) return;  // finished by the sampling kernel
     const Smem sm = carve(a, smem_raw);
-    process_block<NT>(a, a.ws.blk_base[box] + blockIdx.x, sm, sh);
+    if (threadIdx.x == 0) mbar_init(&sh.mbar, 1);
+    __syncthreads();
+    unsigned phase = 0;
+    process_block<NT>(a, b, sm, sh, phase);
 }
 
 }  // namespace
 
 size_t match_smem_bytes(const MatchArgs &a)
 {
-    return sizeof(uint64_t) * (size_t)a.strip_rows * a.strip_cols + 2 * sizeof(uint64_t) * kMaxPts +
+    return sizeof(uint64_t) * (size_t)a.strip_rows * a.strip_cols + sizeof(uint64_t) * kMaxPts +
            sizeof(int) * kMaxCand + 2 * sizeof(int) * kMaxPts;
 }
 

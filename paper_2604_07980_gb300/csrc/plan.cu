@@ -8,11 +8,17 @@
 // max_occluders.  Boxes that are empty after clipping get their outputs here.
 //
 // plan_scan_kernel (one CTA): exclusive scan of the block counts, the flat
-// (box, slot) work list the matching kernel drains (largest blocks first), and
-// counter reset.  All
+// (box, slot) block list, and counter reset.
+//
+// sample_kernel (one warp per block): the block's point grid and its usable
+// points; blocks with fewer than min_pts usable points are finished here, the
+// others go to the work queue (large work first).
+//
+// mark_kernel (one warp per queued block): census tiles the search can read.  All
 // counts come from device memory so a captured graph replays with new inputs.
 #include <math.h>
 
+#include "aggregate.cuh"
 #include "ctm_internal.cuh"
 
 namespace ctm {
@@ -117,17 +123,6 @@ __global__ void __launch_bounds__(kPlanThreads) plan_boxes_kernel(MatchArgs a)
     }
 }
 
-constexpr int kWorkBuckets = 64;
-
-// Bucket of a block's nominal work nx * ny * N_d * N_dy (up to 2^16 * 256 / 2^10).
-__device__ __forceinline__ int work_bucket(const BoxPlan &P, int slot, int pts_side, int ndy)
-{
-    const BlockRect r = block_rect(P, slot, pts_side);
-    const int w = r.nx * r.ny * (P.dmax - P.dmin + 1) * ndy;
-    const int b = w >> 10;
-    return b < kWorkBuckets - 1 ? b : kWorkBuckets - 1;
-}
-
 __global__ void __launch_bounds__(kScanThreads) plan_scan_kernel(MatchArgs a)
 {
     __shared__ int warp_tot[kScanThreads / 32];
@@ -162,42 +157,11 @@ __global__ void __launch_bounds__(kScanThreads) plan_scan_kernel(MatchArgs a)
         if (i < nb) {
             a.ws.blk_base[i] = ex;
             a.ws.box_done[i] = 0;
+            for (int s = 0; s < v; ++s) a.ws.blocks[ex + s] = make_int2(i, s);
         }
         __syncthreads();
         if (threadIdx.x == 0) s_running += warp_tot[kScanThreads / 32 - 1];
         __syncthreads();
-    }
-    // Work queue in decreasing order of nominal block work (points x candidates):
-    // the persistent matcher drains it front to back, so the largest blocks start
-    // first and small ones fill in at the end.
-    __shared__ int bucket[kWorkBuckets];
-    for (int b = threadIdx.x; b < kWorkBuckets; b += kScanThreads) bucket[b] = 0;
-    __syncthreads();
-    const int ndy = a.p.dy_max - a.p.dy_min + 1;
-    for (int i = threadIdx.x; i < nb; i += kScanThreads) {
-        const int v = a.ws.nblk[i];
-        if (v == 0) continue;
-        const BoxPlan P = a.ws.plans[i];
-        for (int s = 0; s < v; ++s) atomicAdd(&bucket[work_bucket(P, s, a.p.pts_side, ndy)], 1);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int run = 0;
-        for (int b = kWorkBuckets - 1; b >= 0; --b) {
-            const int c = bucket[b];
-            bucket[b] = run;
-            run += c;
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < nb; i += kScanThreads) {
-        const int v = a.ws.nblk[i];
-        if (v == 0) continue;
-        const BoxPlan P = a.ws.plans[i];
-        for (int s = 0; s < v; ++s) {
-            const int pos = atomicAdd(&bucket[work_bucket(P, s, a.p.pts_side, ndy)], 1);
-            a.ws.blocks[pos] = make_int2(i, s);
-        }
     }
     if (threadIdx.x == 0) {
         Counts *c = a.ws.counts;
@@ -205,7 +169,10 @@ __global__ void __launch_bounds__(kScanThreads) plan_scan_kernel(MatchArgs a)
         c->n_boxes = nb;
         c->n_blocks = s_running < a.caps.max_blocks ? s_running : a.caps.max_blocks;
         c->queue_head = 0;
+        c->error = 0;
         c->evals = 0ull;
+        c->n_big = 0;
+        c->n_small = 0;
     }
 }
 
@@ -231,26 +198,131 @@ __device__ __forceinline__ void mark_range(const MatchArgs &a, int f, int q, int
     }
 }
 
+// Work threshold (usable points x candidates) of the large-work queue.
+constexpr int kBigWork = 4096;
+
+__global__ void __launch_bounds__(256) sample_kernel(MatchArgs a)
+{
+    __shared__ float agg_scratch[8][2 * kMaxSlots];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int b = blockIdx.x * 8 + warp;
+    if (b >= a.ws.counts->n_blocks) return;
+    const int2 bs = a.ws.blocks[b];
+    const int box = bs.x, slot = bs.y;
+    const BoxPlan P = a.ws.plans[box];
+    const BlockRect r = block_rect(P, slot, a.p.pts_side);
+    const int nx = r.nx, ny = r.ny;
+    const int Xl = lane < nx ? point_coord(r.bx0, r.bx1, nx, lane) : 0;
+    const int Yl = lane < ny ? point_coord(r.by0, r.by1, ny, lane) : 0;
+    int4 occ = make_int4(0, 0, 0, 0);
+    if (lane < P.nocc) occ = a.ws.occ[(long long)box * kMaxOcc + lane];
+    // usable: left census defined (window inside the grid) and full-res position
+    // k (x, y) in no kept occluder
+    const int sxw = a.p.win_w >> 1, syw = a.p.win_h >> 1;
+    const bool col_ok = lane < nx && Xl - sxw >= 0 && Xl + sxw < P.Ws;
+    unsigned colmask = 0u;
+    for (int m = 0; m < ny; ++m) {
+        const int y = __shfl_sync(full, Yl, m);
+        bool valid = col_ok && y - syw >= 0 && y + syw < P.Hs;
+        const int fx = P.k * Xl, fy = P.k * y;
+        for (int q = 0; q < P.nocc; ++q) {
+            const int ox0 = __shfl_sync(full, occ.x, q), oy0 = __shfl_sync(full, occ.y, q);
+            const int ox1 = __shfl_sync(full, occ.z, q), oy1 = __shfl_sync(full, occ.w, q);
+            if (fx >= ox0 && fx < ox1 && fy >= oy0 && fy < oy1) valid = false;
+        }
+        if (valid) colmask |= 1u << m;
+    }
+    const int cnt = __popc(colmask);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(full, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int n_valid = __shfl_sync(full, incl, 31);
+    // column chunks whose strip (plus alignment) fits the shared-memory strip
+    const int nd = P.dmax - P.dmin + 1;
+    unsigned cstart = 1u;
+    {
+        int x0 = __shfl_sync(full, Xl, 0);
+        for (int j = 1; j < nx; ++j) {
+            const int xj = __shfl_sync(full, Xl, j);
+            if (xj - x0 + nd + 2 > a.strip_cols) {
+                cstart |= 1u << j;
+                x0 = xj;
+            }
+        }
+    }
+    BlockGeom *g = a.ws.geom + b;
+    if (lane < kMaxPtsSide) {
+        g->X[lane] = (int16_t)Xl;
+        g->Y[lane] = (int16_t)Yl;
+        g->colmask[lane] = (uint16_t)colmask;
+        g->colprefix[lane] = (uint16_t)(incl - cnt);
+    }
+    if (lane == 0) {
+        g->n_valid = n_valid;
+        g->nx = nx;
+        g->ny = ny;
+        g->cstart = cstart;
+    }
+    const int ndy = a.p.dy_max - a.p.dy_min + 1;
+    if (n_valid < a.p.min_pts) {
+        int last = 0;
+        if (lane == 0) {
+            ctm_block rec;
+            rec.n_pts = nx * ny;
+            rec.n_valid = n_valid;
+            rec.d_f = rec.dy_f = rec.d_b = rec.dy_b = 0;
+            rec.s_m = rec.s_0 = rec.s_p = 0;
+            rec.d_sub = 0.0f;
+            rec.d_full = 0.0f;
+            rec.flags = CTM_BLK_PRESENT | CTM_BLK_FEW_POINTS;
+            last = publish_block(a, box, slot, rec, nd * ndy) ? 1 : 0;
+        }
+        last = __shfl_sync(full, last, 0);
+        if (last) {
+            __threadfence();
+            aggregate_box(a, box, agg_scratch[warp], lane);
+        }
+    } else if (lane == 0) {
+        if (n_valid * nd * ndy >= kBigWork) {
+            const int q = atomicAdd(&a.ws.counts->n_big, 1);
+            a.ws.queue[q] = b;
+        } else {
+            const int q = atomicAdd(&a.ws.counts->n_small, 1);
+            a.ws.queue[a.caps.max_blocks - 1 - q] = b;
+        }
+    }
+}
+
+__device__ __forceinline__ int queue_entry(const MatchArgs &a, int i, int n_big)
+{
+    return i < n_big ? a.ws.queue[i] : a.ws.queue[a.caps.max_blocks - 1 - (i - n_big)];
+}
+
 __global__ void __launch_bounds__(256) mark_kernel(MatchArgs a)
 {
     const int lane = threadIdx.x & 31;
-    const int b = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (b >= a.ws.counts->n_blocks) return;
+    const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int n_big = a.ws.counts->n_big;
+    if (i >= n_big + a.ws.counts->n_small) return;
+    const int b = queue_entry(a, i, n_big);
     const int2 bs = a.ws.blocks[b];
     const BoxPlan P = a.ws.plans[bs.x];
-    const BlockRect r = block_rect(P, bs.y, a.p.pts_side);
-    if (r.nx <= 0 || r.ny <= 0) return;
-    const int x_first = point_coord(r.bx0, r.bx1, r.nx, 0);
-    const int x_last = point_coord(r.bx0, r.bx1, r.nx, r.nx - 1);
+    const BlockGeom &g = a.ws.geom[b];
+    const int nx = g.nx, ny = g.ny;
+    const int x_first = g.X[0], x_last = g.X[nx - 1];
     const int qL = (P.far || a.p.close_factor == 1) ? 0 : 2;
     const int span = P.dmax - P.dmin;
     const int dyr = a.p.dy_max - a.p.dy_min;
     const int nl = 2 * dyr + 1, nr = dyr + 1;
-    const int items = r.ny * (nl + nr);
+    const int items = ny * (nl + nr);
     for (int it = lane; it < items; it += 32) {
         const int m = it / (nl + nr);
         const int e = it - m * (nl + nr);
-        const int y = point_coord(r.by0, r.by1, r.ny, m);
+        const int y = g.Y[m];
         if (e < nl)
             mark_range(a, P.frame, qL, y + e - dyr, x_first - span, x_last + span, P.Ws, P.Hs);
         else
@@ -260,6 +332,13 @@ __global__ void __launch_bounds__(256) mark_kernel(MatchArgs a)
 }
 
 }  // namespace
+
+cudaError_t launch_sample(const MatchArgs &a, cudaStream_t s)
+{
+    const int grid = ceil_div_nn(a.caps.max_blocks, 8);
+    sample_kernel<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_mark(const MatchArgs &a, cudaStream_t s)
 {
