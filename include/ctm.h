@@ -43,6 +43,7 @@ typedef struct CUstream_st *ctm_stream;
 #define CTM_ENOMEM (-2)   /* workspace allocation failed or request exceeds capacity */
 #define CTM_ECUDA (-3)    /* a CUDA call or launch failed */
 #define CTM_ENODEV (-4)   /* no usable CUDA device */
+#define CTM_ETOOBIG (-5)  /* beyond the fixed limits of ctm_match_boxes_noalloc */
 
 /* Per-box flags (uint8), written by the match calls. */
 #define CTM_BOX_VALID 0x01           /* disparity > 0 found; disp/depth finite         */
@@ -210,6 +211,26 @@ int ctm_match_batch_profiled(ctm_ctx *ctx, const ctm_frame *frames_dev, const in
 int ctm_match_batch_host(ctm_ctx *ctx, const ctm_frame *frames_host, int n_frames,
                          const ctm_box *boxes_host, int n_boxes, float *disp_host,
                          float *depth_host, uint8_t *flags_host, ctm_stream stream);
+
+/* Single-frame matching that allocates no device memory -- the paper has no
+ * counterpart; it exists for callers that cannot call cudaMalloc (code inside a
+ * captured CUDA graph region, real-time loops that must not touch the device
+ * allocator, hosts that give this library a fixed memory budget).  Same inputs,
+ * outputs and results as ctm_match_boxes without a context: `p` is the parameter
+ * block, all other arguments as there.  Limits: width <= 640, height <= 480,
+ * n_boxes <= 64; larger requests return CTM_ETOOBIG.  The workspace is one
+ * 8 MiB array in static device memory that every GPU loading the library holds
+ * until exit.  The first call on a device does a one-time set-up with that device
+ * current (looks up the array's device address, raises the matching kernel's
+ * shared-memory limit), so make it before any stream capture.  All calls share
+ * the array and it keeps the previous call's contents (each call clears what must
+ * start at zero); calls that overlap on the GPU race.  Not thread-safe.  Calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ * Errors: CTM_EINVAL, CTM_ETOOBIG, CTM_ENODEV, CTM_ECUDA. */
+int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_dev, const uint8_t *right_dev,
+                            int width, int height, int pitch, const ctm_box *boxes_dev, int n_boxes,
+                            float f_px, float baseline_m, float *disp_dev, float *depth_dev,
+                            uint8_t *flags_dev, ctm_stream stream);
 
 /* Counters of the most recent match call on ctx.  Synchronizes `stream`. */
 int ctm_get_stats(ctm_ctx *ctx, ctm_stats *out, ctm_stream stream);

@@ -16,7 +16,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libctm.so")
 
-CTM_OK, CTM_EINVAL, CTM_ENOMEM, CTM_ECUDA, CTM_ENODEV = 0, -1, -2, -3, -4
+CTM_OK, CTM_EINVAL, CTM_ENOMEM, CTM_ECUDA, CTM_ENODEV, CTM_ETOOBIG = 0, -1, -2, -3, -4, -5
 
 BOX_VALID, BOX_FB_REJECT, BOX_FEW_POINTS, BOX_NO_SEGMENT = 0x01, 0x02, 0x04, 0x08
 BOX_NONPOS_DISP, BOX_EMPTY, BOX_SUBPIX_CLAMPED, BOX_FAR = 0x10, 0x20, 0x40, 0x80
@@ -25,7 +25,8 @@ BLK_VALID, BLK_FB_REJECT, BLK_FEW_POINTS, BLK_SUBPIX_CLAMPED, BLK_PRESENT = 1, 2
 # every symbol include/ctm.h declares
 EXPORTS = ("ctm_status_str", "ctm_default_params", "ctm_create", "ctm_destroy",
            "ctm_census_build", "ctm_match_boxes", "ctm_match_boxes_plain", "ctm_match_batch",
-           "ctm_match_batch_profiled", "ctm_match_batch_host", "ctm_get_stats", "ctm_probe_int_rate")
+           "ctm_match_batch_profiled", "ctm_match_batch_host", "ctm_match_boxes_noalloc",
+           "ctm_get_stats", "ctm_probe_int_rate")
 
 
 class CtmError(RuntimeError):
@@ -98,6 +99,9 @@ def lib():
     L.ctm_match_batch_profiled.restype = i32
     L.ctm_match_batch_host.argtypes = [vp, ctypes.POINTER(ctm_frame), i32, vp, i32, vp, vp, vp, vp]
     L.ctm_match_batch_host.restype = i32
+    L.ctm_match_boxes_noalloc.argtypes = [ctypes.POINTER(ctm_params), vp, vp, i32, i32, i32, vp, i32,
+                                          f32, f32, vp, vp, vp, vp]
+    L.ctm_match_boxes_noalloc.restype = i32
     L.ctm_get_stats.argtypes = [vp, ctypes.POINTER(ctm_stats), vp]
     L.ctm_get_stats.restype = i32
     L.ctm_probe_int_rate.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double)]

@@ -139,6 +139,7 @@ const char *ctm_status_str(int status)
     case CTM_ENOMEM: return "out of memory or beyond context capacity";
     case CTM_ECUDA: return "CUDA error";
     case CTM_ENODEV: return "no usable CUDA device";
+    case CTM_ETOOBIG: return "request exceeds the fixed limits of the no-allocation entry point";
     default: return "unknown status";
     }
 }

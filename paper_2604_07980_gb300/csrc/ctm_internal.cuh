@@ -153,6 +153,8 @@ cudaError_t launch_sample(const MatchArgs &a, cudaStream_t s);
 // threads per matching CTA: 128 or 256
 size_t match_smem_bytes(const MatchArgs &a);
 cudaError_t match_configure(const MatchArgs &a, int threads, int *ctas_per_sm);
+// Like match_configure, but only ever raises the kernel's shared-memory limit.
+cudaError_t match_configure_raise(const MatchArgs &a, int threads, int *ctas_per_sm);
 cudaError_t launch_match_persistent(const MatchArgs &a, int threads, int grid, cudaStream_t s);
 cudaError_t launch_match_box(const MatchArgs &a, int threads, int box, cudaStream_t s);
 

@@ -641,6 +641,27 @@ cudaError_t match_configure(const MatchArgs &a, int threads, int *ctas_per_sm)
     return e;
 }
 
+cudaError_t match_configure_raise(const MatchArgs &a, int threads, int *ctas_per_sm)
+{
+    const int need = (int)match_smem_bytes(a);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaSuccess;
+    if (threads == 128) {
+        e = cudaFuncGetAttributes(&fa, match_persistent_kernel<128>);
+        if (e == cudaSuccess && fa.maxDynamicSharedSizeBytes < need)
+            e = cudaFuncSetAttribute(match_persistent_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, match_persistent_kernel<128>, 128, need);
+    } else {
+        e = cudaFuncGetAttributes(&fa, match_persistent_kernel<256>);
+        if (e == cudaSuccess && fa.maxDynamicSharedSizeBytes < need)
+            e = cudaFuncSetAttribute(match_persistent_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, match_persistent_kernel<256>, 256, need);
+    }
+    return e;
+}
+
 cudaError_t launch_match_persistent(const MatchArgs &a, int threads, int grid, cudaStream_t s)
 {
     if (threads == 128)

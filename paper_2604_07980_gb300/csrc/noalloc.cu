@@ -1,0 +1,212 @@
+// noalloc.cu -- single-frame matching that allocates no device memory.
+//
+// Some callers cannot call cudaMalloc: code running inside a captured CUDA
+// graph region, real-time loops that must not touch the device allocator, and
+// hosts that hand the GPU to this library with a fixed memory budget.  For them
+// ctm_match_boxes_noalloc runs the same launch sequence as ctm_match_boxes, but
+// its workspace is carved from one file-scope __device__ array of fixed size,
+// which every GPU that loads the library holds until the process exits.
+//
+// Set-up happens on the first call on each device (with that device current):
+// the array's device address is taken with cudaGetSymbolAddress -- in host code
+// the array's name is only a host-side stand-in -- and the matching kernels'
+// shared-memory limit is raised.  That first call should therefore come before
+// any stream capture.  All calls share the one array and it keeps the previous
+// call's contents: each call clears what must start at zero (the census demand
+// bitmap; the planner resets its own counters), and calls that overlap on the
+// GPU race on the array.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "ctm_internal.cuh"
+
+namespace {
+
+constexpr size_t kScratchBytes = 8u << 20;  // 8 MiB per GPU
+constexpr int kMaxW = 640, kMaxH = 480, kMaxBoxes = 64;
+constexpr int kMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+struct DeviceState {
+    bool ready;
+    unsigned char *base;  // device address of g_noalloc_scratch on this device
+    int sm_count;
+};
+DeviceState g_state[kMaxDevices];
+
+inline long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
+
+bool params_ok(const ctm_params &p)
+{
+    using namespace ctm;
+    if (p.win_w < 1 || p.win_h < 1 || (p.win_w & 1) == 0 || (p.win_h & 1) == 0) return false;
+    if (p.win_w > kMaxWin || p.win_h > kMaxWin) return false;
+    if (p.win_w * p.win_h + (p.sentinel ? 1 : 0) > 64) return false;
+    if (p.sentinel != 0 && p.sentinel != 1) return false;
+    if (p.close_factor < 1 || p.close_factor > 8) return false;
+    if (p.far_dmin > p.far_dmax || p.close_dmin > p.close_dmax || p.dy_min > p.dy_max) return false;
+    const long long ndy = (long long)p.dy_max - p.dy_min + 1;
+    if (((long long)p.far_dmax - p.far_dmin + 1) * ndy > kMaxCand) return false;
+    if (((long long)p.close_dmax - p.close_dmin + 1) * ndy > kMaxCand) return false;
+    if (p.grid_g < 1 || p.grid_g > kMaxGrid) return false;
+    if (p.pts_side < 1 || p.pts_side > kMaxPtsSide) return false;
+    if (p.min_pts < 1 || p.fb_tol < 0 || p.agg_nmin < 1) return false;
+    if (p.agg_mode != 0 && p.agg_mode != 1) return false;
+    if (!(p.trim_frac >= 0.0f && p.trim_frac < 0.5f)) return false;
+    if (!(p.agg_tau_d == p.agg_tau_d)) return false;
+    if (p.max_occluders < 0 || p.max_occluders > kMaxOcc) return false;
+    return true;
+}
+
+int setup_device(int dev)
+{
+    DeviceState &st = g_state[dev];
+    if (st.ready) return CTM_OK;
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr) {
+        cudaGetLastError();
+        return CTM_ECUDA;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        return CTM_ECUDA;
+    }
+    st.base = static_cast<unsigned char *>(ptr);
+    st.sm_count = sms;
+    st.ready = true;
+    return CTM_OK;
+}
+
+}  // namespace
+
+using namespace ctm;
+
+extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_dev,
+                                       const uint8_t *right_dev, int width, int height, int pitch,
+                                       const ctm_box *boxes_dev, int n_boxes, float f_px,
+                                       float baseline_m, float *disp_dev, float *depth_dev,
+                                       uint8_t *flags_dev, ctm_stream stream)
+{
+    if (!p || !params_ok(*p)) return CTM_EINVAL;
+    if (!left_dev || !right_dev || width < 1 || height < 1 || pitch < width || n_boxes < 0)
+        return CTM_EINVAL;
+    if (n_boxes > 0 && (!boxes_dev || !disp_dev || !depth_dev || !flags_dev)) return CTM_EINVAL;
+    if (width > kMaxW || height > kMaxH || n_boxes > kMaxBoxes) return CTM_ETOOBIG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return CTM_ENODEV;
+    }
+    int st = setup_device(dev);
+    if (st != CTM_OK) return st;
+    const DeviceState &ds = g_state[dev];
+
+    // workspace sizes for one frame of at most kMaxW x kMaxH and kMaxBoxes boxes
+    Caps caps;
+    caps.max_frames = 1;
+    caps.max_width = kMaxW;
+    caps.max_height = kMaxH;
+    caps.max_boxes = kMaxBoxes;
+    caps.max_blocks = kMaxBoxes * std::max(p->grid_g * p->grid_g, 1);
+    const int ndy = p->dy_max - p->dy_min + 1;
+    const int nd_max = std::max(p->far_dmax - p->far_dmin + 1, p->close_dmax - p->close_dmin + 1);
+    const int strip_cols = (int)round_up(std::max(nd_max + 64, 128), 32);
+    const int k = p->close_factor;
+    const long long pitch1 = round_up(kMaxW, 32);
+    const long long Wk = (kMaxW + k - 1) / k, Hk = (kMaxH + k - 1) / k;
+    const long long pitchk = k == 1 ? 0 : round_up(Wk, 32);
+    const long long plane1 = pitch1 * kMaxH;
+    const long long planek = k == 1 ? 0 : pitchk * Hk;
+    const int rows_q[4] = {kMaxH, kMaxH, k == 1 ? 0 : (int)Hk, k == 1 ? 0 : (int)Hk};
+    const int wq1 = (int)(((kMaxW + kCensusTilePx - 1) / kCensusTilePx + 31) / 32);
+    const int wqk = (int)(((Wk + kCensusTilePx - 1) / kCensusTilePx + 31) / 32);
+    const int words_q[4] = {wq1, wq1, wqk, wqk};
+    int plane_off[5];
+    plane_off[0] = 0;
+    for (int q = 0; q < 4; ++q) plane_off[q + 1] = plane_off[q] + rows_q[q] * words_q[q];
+
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = (size_t)round_up(off + bytes, 256); return o; };
+    const size_t o_census = take(sizeof(uint64_t) * (size_t)(2 * plane1 + 2 * planek));
+    const size_t o_plans = take(sizeof(BoxPlan) * kMaxBoxes);
+    const size_t o_occ = take(sizeof(int4) * (size_t)kMaxBoxes * kMaxOcc);
+    const size_t o_nblk = take(sizeof(int) * kMaxBoxes);
+    const size_t o_base = take(sizeof(int) * kMaxBoxes);
+    const size_t o_blocks = take(sizeof(int2) * (size_t)caps.max_blocks);
+    const size_t o_blkres = take(sizeof(BlockResult) * (size_t)caps.max_blocks);
+    const size_t o_geom = take(sizeof(BlockGeom) * (size_t)caps.max_blocks);
+    const size_t o_queue = take(sizeof(int) * (size_t)caps.max_blocks);
+    const size_t o_done = take(sizeof(int) * kMaxBoxes);
+    const size_t o_counts = take(sizeof(Counts));
+    const size_t o_frames = take(sizeof(ctm_frame));
+    const size_t o_cin = take(sizeof(int) * 4);
+    const size_t o_bm = take(sizeof(uint32_t) * (size_t)plane_off[4]);
+    if (off > kScratchBytes) return CTM_ETOOBIG;
+
+    unsigned char *b = ds.base;
+    MatchArgs a;
+    Workspace &ws = a.ws;
+    ws.census = reinterpret_cast<uint64_t *>(b + o_census);
+    ws.frame_stride = 2 * plane1 + 2 * planek;
+    ws.plane1_elems = plane1;
+    ws.planek_elems = planek;
+    ws.pitch1 = pitch1;
+    ws.pitchk = pitchk;
+    ws.plans = reinterpret_cast<BoxPlan *>(b + o_plans);
+    ws.occ = reinterpret_cast<int4 *>(b + o_occ);
+    ws.nblk = reinterpret_cast<int *>(b + o_nblk);
+    ws.blk_base = reinterpret_cast<int *>(b + o_base);
+    ws.blocks = reinterpret_cast<int2 *>(b + o_blocks);
+    ws.blkres = reinterpret_cast<BlockResult *>(b + o_blkres);
+    ws.geom = reinterpret_cast<BlockGeom *>(b + o_geom);
+    ws.queue = reinterpret_cast<int *>(b + o_queue);
+    ws.box_done = reinterpret_cast<int *>(b + o_done);
+    ws.counts = reinterpret_cast<Counts *>(b + o_counts);
+    ws.frames = reinterpret_cast<ctm_frame *>(b + o_frames);
+    ws.counts_in = reinterpret_cast<int *>(b + o_cin);
+    ws.bitmap = reinterpret_cast<uint32_t *>(b + o_bm);
+    ws.bm_frame_words = plane_off[4];
+    for (int q = 0; q < 5; ++q) ws.bm_plane_off[q] = plane_off[q];
+    for (int q = 0; q < 4; ++q) ws.bm_row_words[q] = words_q[q];
+    a.caps = caps;
+    a.p = *p;
+    a.frames = ws.frames;
+    a.counts_in = ws.counts_in;
+    a.boxes = boxes_dev;
+    a.disp = disp_dev;
+    a.depth = depth_dev;
+    a.flags = flags_dev;
+    a.dbg.blocks = nullptr;
+    a.dbg.cost_f = nullptr;
+    a.dbg.cost_b = nullptr;
+    a.nc_stride = nd_max * ndy;
+    a.strip_cols = strip_cols;
+    a.strip_rows = p->pts_side * ndy;
+
+    const int threads = 128;
+    int ctas = 0;
+    if (match_configure_raise(a, threads, &ctas) != cudaSuccess || ctas < 1) {
+        cudaGetLastError();
+        return CTM_ECUDA;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // the census demand bitmap must start clear (an interrupted call may leave marks)
+    cudaError_t e = cudaMemsetAsync(ws.bitmap, 0, sizeof(uint32_t) * (size_t)plane_off[4], s);
+    const ctm_frame fr{left_dev, right_dev, width, height, pitch, 0, n_boxes, f_px, baseline_m};
+    if (e == cudaSuccess) e = launch_stage_frame(a, fr, n_boxes, s);
+    if (e == cudaSuccess) e = launch_plan(a, s);
+    if (e == cudaSuccess) e = launch_sample(a, s);
+    if (e == cudaSuccess) e = launch_mark(a, s);
+    if (e == cudaSuccess) e = launch_census_roi(a, ds.sm_count * 4, s);
+    const long long blocks_ub = (long long)std::max(n_boxes, 1) * std::max(p->grid_g * p->grid_g, 1);
+    const int grid = (int)std::min<long long>((long long)ds.sm_count * ctas, blocks_ub);
+    if (e == cudaSuccess) e = launch_match_persistent(a, threads, grid, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return CTM_ECUDA;
+    }
+    return CTM_OK;
+}

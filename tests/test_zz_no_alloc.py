@@ -1,0 +1,96 @@
+"""ctm_match_boxes_noalloc: the entry point for callers that cannot call
+cudaMalloc (code inside a captured CUDA graph region, real-time loops that must
+not touch the device allocator, hosts with a fixed memory budget).  Called
+through the C ABI, it must give the results of the ordinary context path on
+consecutive calls -- different frames and parameters, then the first again --
+although every call reuses the same static device workspace.
+
+Kept in a file of its own that pytest collects last."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2604_07980_gb300 import workloads as wl
+from tests.parity_util import compare_box_outputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    return torch
+
+
+def _inputs(torch, w):
+    fr = w.frames[0]
+    L = torch.from_numpy(np.ascontiguousarray(fr.left)).cuda()
+    R = torch.from_numpy(np.ascontiguousarray(fr.right)).cuda()
+    boxes = torch.from_numpy(np.ascontiguousarray(w.boxes)).cuda()
+    return fr, L, R, boxes
+
+
+def _noalloc(torch, B, w, L, R, boxes, fr):
+    n = int(boxes.shape[0])
+    p = B.make_params(w.params)
+    disp = torch.full((n,), -1.0, dtype=torch.float32, device="cuda")
+    depth = torch.full((n,), -1.0, dtype=torch.float32, device="cuda")
+    flags = torch.full((n,), 0xEE, dtype=torch.uint8, device="cuda")
+    H, W = L.shape
+    st = B.lib().ctm_match_boxes_noalloc(
+        ctypes.byref(p), ctypes.c_void_p(L.data_ptr()), ctypes.c_void_p(R.data_ptr()), W, H,
+        L.stride(0), ctypes.c_void_p(boxes.data_ptr()), n, fr.f_px, fr.baseline_m,
+        ctypes.c_void_p(disp.data_ptr()), ctypes.c_void_p(depth.data_ptr()),
+        ctypes.c_void_p(flags.data_ptr()), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == B.CTM_OK, B.lib().ctm_status_str(st)
+    torch.cuda.synchronize()
+    return {"disp": disp.cpu().numpy(), "depth": depth.cpu().numpy(), "flags": flags.cpu().numpy()}
+
+
+def _context(torch, B, w, L, R, boxes, fr):
+    H, W = L.shape
+    ctx = B.Context(w.params, 1, W, H, max(int(boxes.shape[0]), 1))
+    out = ctx.match_boxes(L, R, boxes, fr.f_px, fr.baseline_m)
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    ctx.close()
+    return res
+
+
+def test_noalloc_equals_context_path_on_consecutive_calls(torch_cuda):
+    from paper_2604_07980_gb300 import binding as B
+    wa = wl.pair640()
+    wb = wl.frame1080(W=640, H=480, n_boxes=48, side_range=(12, 200))
+    runs = []
+    for w in (wa, wb, wa):
+        fr, L, R, boxes = _inputs(torch_cuda, w)
+        ref = _context(torch_cuda, B, w, L, R, boxes, fr)
+        got = _noalloc(torch_cuda, B, w, L, R, boxes, fr)
+        compare_box_outputs(got, ref, f"noalloc {w.name}")
+        runs.append(got)
+    assert np.array_equal(runs[0]["flags"], runs[2]["flags"])
+    assert np.array_equal(runs[0]["disp"], runs[2]["disp"], equal_nan=True)
+
+
+def test_noalloc_rejects_sizes_beyond_its_limits(torch_cuda):
+    from paper_2604_07980_gb300 import binding as B
+    w = wl.pair640()
+    fr, L, R, boxes = _inputs(torch_cuda, w)
+    big = torch_cuda.zeros((481, 640), dtype=torch_cuda.uint8, device="cuda")
+    p = B.make_params(w.params)
+    out = torch_cuda.empty(4, dtype=torch_cuda.float32, device="cuda")
+    fl = torch_cuda.empty(4, dtype=torch_cuda.uint8, device="cuda")
+    st = B.lib().ctm_match_boxes_noalloc(
+        ctypes.byref(p), ctypes.c_void_p(big.data_ptr()), ctypes.c_void_p(big.data_ptr()), 640, 481, 640,
+        ctypes.c_void_p(boxes.data_ptr()), 4, fr.f_px, fr.baseline_m, ctypes.c_void_p(out.data_ptr()),
+        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(fl.data_ptr()), None)
+    assert st == B.CTM_ETOOBIG
+    many = torch_cuda.zeros((65, 5), dtype=torch_cuda.int32, device="cuda")
+    st = B.lib().ctm_match_boxes_noalloc(
+        ctypes.byref(p), ctypes.c_void_p(L.data_ptr()), ctypes.c_void_p(R.data_ptr()), 640, 480, 640,
+        ctypes.c_void_p(many.data_ptr()), 65, fr.f_px, fr.baseline_m, ctypes.c_void_p(out.data_ptr()),
+        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(fl.data_ptr()), None)
+    assert st == B.CTM_ETOOBIG
