@@ -58,10 +58,8 @@ __device__ __forceinline__ void mbar_init(uint64_t *mbar, unsigned count)
 
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *mbar, unsigned bytes)
 {
-    unsigned long long state;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;\n"
-                 : "=l"(state) : "r"(smem_addr(mbar)), "r"(bytes) : "memory");
-    (void)state;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
+                 ::"r"(smem_addr(mbar)), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, unsigned parity)
