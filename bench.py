@@ -38,6 +38,10 @@ UNIT = "Gevals/s"
 SM_COUNT_NOMINAL = 152
 SM_MAX_MHZ = 2070.0
 POPC_PER_EVAL = 2          # one u64 code pair = two 32-bit popcounts
+# DRAM bytes (read + write) of one match_persistent_kernel launch on this workload, from the
+# ncu capture summarised in profiles/match_persistent_kernel_batch32x1200.md; None once the
+# kernel changes after that capture.
+MATCH_DRAM_BYTES = (101.938432 + 2.879232) * 1e6
 
 
 def parse():
@@ -319,12 +323,13 @@ def main():
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "ms_per_step": e2e_s * 1e3},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT,
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": MATCH_DRAM_BYTES if len(w.frames) == 32 else None,
                          "kernel": "match_persistent_kernel",
                          "peak_basis": f"{sms} SMs x {popc_clk:g} popc32/clk/SM (probe {popc_rate:.2f}) / "
                                        f"{POPC_PER_EVAL} per eval x {SM_MAX_MHZ:g} MHz"},
             "cpu_baseline": cpu,
-            "gpu_launches": 5 * args.steps,
+            "gpu_launches": 6 * args.steps,
             "clocks": clk,
         }
         print(json.dumps(line))
