@@ -185,7 +185,9 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
 
     from paper_2604_07980_gb300 import binding as B
-    w = wl.batch32x1200(n_frames=args.frames, seed=1002 + 7919 * rank)
+    from paper_2604_07980_gb300 import dist as D
+
+    w = wl.batch32x1200(n_frames=args.frames, seed=D.rank_seed(1002, rank))
     frames_dev = B.frames_to_device(w.frames)
     calib = [(f.f_px, f.baseline_m) for f in w.frames]
     ctx = B.Context(w.params, len(w.frames), 1920, 1200, w.n_boxes)
@@ -218,12 +220,8 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    ms = e0.elapsed_time(e1)
+    ms = D.max_over_ranks(e0.elapsed_time(e1), dist)
     clk = clocks.stop()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     ms_per_step = ms / args.steps
     value = evals_per_step * world * args.steps / (ms * 1e-3) / 1e9
 
@@ -286,10 +284,7 @@ def main():
         ctx.match_batch_host(pinned, w.boxes, fpx, bml, out=out_h)
     e2e_s = (time.perf_counter() - t0) / k_e2e
     barrier()
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = D.max_over_ranks(e2e_s, dist)
     h2d = sum(f.left.nbytes + f.right.nbytes for f in w.frames) + w.boxes.nbytes + 48 * len(w.frames) + 8
     d2h = w.n_boxes * 9
 

@@ -34,7 +34,11 @@ def compare_box_outputs(got, ref, where=""):
 
 
 def compare_debug(dbg, ref, nc_gpu, where=""):
-    gb = dbg.blocks_np()
+    compare_debug_arrays(dbg.blocks_np(), dbg.cost_f.cpu().numpy(), dbg.cost_b.cpu().numpy(), ref,
+                         nc_gpu, where)
+
+
+def compare_debug_arrays(gb, gcf, gcb, ref, nc_gpu, where=""):
     rb = ref["blocks"]
     assert gb.shape == rb.shape, (gb.shape, rb.shape)
     for f in INT_BLOCK_FIELDS:
@@ -43,8 +47,6 @@ def compare_debug(dbg, ref, nc_gpu, where=""):
                               f"gpu {gb[f][tuple(bad[0])]} oracle {rb[f][tuple(bad[0])]}"
     for f in ("d_sub", "d_full"):
         np.testing.assert_allclose(gb[f], rb[f], rtol=0, atol=DISP_ATOL, err_msg=f"{where} {f}")
-    gcf = dbg.cost_f.cpu().numpy()
-    gcb = dbg.cost_b.cpu().numpy()
     nc = min(nc_gpu, ref["cost_f"].shape[2])
     assert np.array_equal(gcf[..., :nc], ref["cost_f"][..., :nc]), f"{where} forward costs differ"
     assert np.array_equal(gcb[..., :nc], ref["cost_b"][..., :nc]), f"{where} backward costs differ"
