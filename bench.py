@@ -42,6 +42,8 @@ POPC_PER_EVAL = 2          # one u64 code pair = two 32-bit popcounts
 # ncu capture summarised in profiles/match_persistent_kernel_batch32x1200.md; None once the
 # kernel changes after that capture.
 MATCH_DRAM_BYTES = (101.938432 + 2.879232) * 1e6
+# kernels of one step of the batched path: plan, sample, mark, census_roi, match
+KERNELS_PER_STEP = 5
 
 
 def parse():
@@ -324,7 +326,7 @@ def main():
                          "peak_basis": f"{sms} SMs x {popc_clk:g} popc32/clk/SM (probe {popc_rate:.2f}) / "
                                        f"{POPC_PER_EVAL} per eval x {SM_MAX_MHZ:g} MHz"},
             "cpu_baseline": cpu,
-            "gpu_launches": 6 * args.steps,
+            "gpu_launches": KERNELS_PER_STEP * args.steps,
             "clocks": clk,
         }
         print(json.dumps(line))

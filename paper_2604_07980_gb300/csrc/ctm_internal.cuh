@@ -15,7 +15,7 @@ constexpr int kMaxGrid = 8;
 constexpr int kMaxSlots = kMaxGrid * kMaxGrid;
 constexpr int kMaxOcc = 32;
 constexpr int kMaxWin = 15;
-constexpr int kPlanThreads = 128;
+constexpr int kPlanThreads = 256;
 constexpr int kScanThreads = 1024;
 
 // Device-side counters of one call.

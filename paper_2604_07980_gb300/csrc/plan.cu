@@ -1,14 +1,12 @@
 // plan.cu -- device-side planning of Algorithm 2's per-box steps.
 //
-// plan_boxes_kernel (one CTA per frame): clip each box to its frame, classify it
-// FAR or CLOSE by its larger side against tau_s (Sec. 4.3.4), map it to its
-// matching grid (full resolution for FAR, the decimated grid for CLOSE), count
-// its blocks, and select its occluders -- overlapping boxes of the same frame
-// with a larger bottom y (Sec. 4.3.5), nearest (largest bottom y) first, at most
+// plan_kernel (one CTA per frame): clip each box to its frame, classify it FAR
+// or CLOSE by its larger side against tau_s (Sec. 4.3.4), map it to its matching
+// grid (full resolution for FAR, the decimated grid for CLOSE), count its
+// blocks, and select its occluders -- overlapping boxes of the same frame with a
+// larger bottom y (Sec. 4.3.5), nearest (largest bottom y) first, at most
 // max_occluders.  Boxes that are empty after clipping get their outputs here.
-//
-// plan_scan_kernel (one CTA): exclusive scan of the block counts, the flat
-// (box, slot) block list, and counter reset.
+// The frame's blocks get a contiguous range of the flat (box, slot) block list.
 //
 // sample_kernel (one warp per block): the block's point grid and its usable
 // points; blocks with fewer than min_pts usable points are finished here, the
@@ -51,11 +49,25 @@ __global__ void stage_frame_kernel(ctm_frame *frames, int *counts_in, ctm_frame 
     counts_in[1] = n_boxes;
 }
 
-__global__ void __launch_bounds__(kPlanThreads) plan_boxes_kernel(MatchArgs a)
+constexpr int kStageBoxes = 1024;  // boxes of one frame staged in shared memory
+
+// One CTA per frame: clip, classify, map to the matching grid and select the
+// occluders of every box of the frame (the frame's clipped boxes are staged in
+// shared memory for the pairwise test), then the frame's block counts are
+// scanned and one atomic reserves the frame's range of the flat block list.
+__global__ void __launch_bounds__(kPlanThreads) plan_kernel(MatchArgs a)
 {
+    __shared__ int4 sbox[kStageBoxes];
+    __shared__ int warp_tot[kPlanThreads / 32];
+    __shared__ int s_run, s_base;
     const int f = blockIdx.x;
     const int nf = clampi(a.counts_in[0], 0, a.caps.max_frames);
     const int nb_total = clampi(a.counts_in[1], 0, a.caps.max_boxes);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (f == 0 && tid == 0) {
+        a.ws.counts->n_frames = nf;
+        a.ws.counts->n_boxes = nb_total;
+    }
     if (f >= nf) return;
     const ctm_frame fr = a.frames[f];
     const bool bad_frame = fr.width < 1 || fr.height < 1 || fr.width > a.caps.max_width ||
@@ -63,11 +75,16 @@ __global__ void __launch_bounds__(kPlanThreads) plan_boxes_kernel(MatchArgs a)
                            fr.left == nullptr || fr.right == nullptr;
     const int begin = clampi(fr.box_begin, 0, nb_total);
     const int end = clampi(fr.box_begin + fr.box_count, begin, nb_total);
+    const int nloc = end - begin;
+    const bool staged = nloc <= kStageBoxes;
+    if (staged)
+        for (int t = tid; t < nloc; t += blockDim.x) sbox[t] = clip_box(a.boxes[begin + t], fr.width, fr.height);
+    __syncthreads();
     const ctm_params &p = a.p;
     const int K = p.max_occluders < kMaxOcc ? p.max_occluders : kMaxOcc;
 
-    for (int i = begin + threadIdx.x; i < end; i += blockDim.x) {
-        const int4 r = clip_box(a.boxes[i], fr.width, fr.height);
+    for (int i = begin + tid; i < end; i += blockDim.x) {
+        const int4 r = staged ? sbox[i - begin] : clip_box(a.boxes[i], fr.width, fr.height);
         const int w = r.z - r.x, h = r.w - r.y;
         const int side = w > h ? w : h;
         const int far = side < p.far_side_px ? 1 : 0;
@@ -97,7 +114,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_boxes_kernel(MatchArgs a)
         if (!empty && K > 0) {
             for (int j = begin; j < end; ++j) {
                 if (j == i) continue;
-                const int4 q = clip_box(a.boxes[j], fr.width, fr.height);
+                const int4 q = staged ? sbox[j - begin] : clip_box(a.boxes[j], fr.width, fr.height);
                 if (!(q.w > r.w) || !overlaps(r, q)) continue;
                 // insertion into the descending list (j ascending, so ties keep order)
                 int pos = nocc;
@@ -110,30 +127,27 @@ __global__ void __launch_bounds__(kPlanThreads) plan_boxes_kernel(MatchArgs a)
                 if (nocc < K) ++nocc;
             }
             for (int t = 0; t < nocc; ++t)
-                a.ws.occ[(long long)i * kMaxOcc + t] = clip_box(a.boxes[kj[t]], fr.width, fr.height);
+                a.ws.occ[(long long)i * kMaxOcc + t] =
+                    staged ? sbox[kj[t] - begin] : clip_box(a.boxes[kj[t]], fr.width, fr.height);
         }
         P.nocc = nocc;
         a.ws.plans[i] = P;
         a.ws.nblk[i] = P.nblk;
+        a.ws.box_done[i] = 0;
         if (P.nblk == 0) {
             a.disp[i] = __int_as_float(0x7fc00000);
             a.depth[i] = __int_as_float(0x7fc00000);
             a.flags[i] = (uint8_t)((far ? CTM_BOX_FAR : 0) | CTM_BOX_EMPTY);
         }
     }
-}
-
-__global__ void __launch_bounds__(kScanThreads) plan_scan_kernel(MatchArgs a)
-{
-    __shared__ int warp_tot[kScanThreads / 32];
-    __shared__ int s_running;
-    const int nb = clampi(a.counts_in[1], 0, a.caps.max_boxes);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_running = 0;
     __syncthreads();
-    for (int base = 0; base < nb; base += kScanThreads) {
-        const int i = base + threadIdx.x;
-        const int v = i < nb ? a.ws.nblk[i] : 0;
+
+    // frame-local exclusive scan of the block counts, one reservation per frame
+    if (tid == 0) s_run = 0;
+    __syncthreads();
+    for (int c0 = begin; c0 < end; c0 += blockDim.x) {
+        const int i = c0 + tid;
+        const int v = i < end ? a.ws.nblk[i] : 0;
         int x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -142,37 +156,26 @@ __global__ void __launch_bounds__(kScanThreads) plan_scan_kernel(MatchArgs a)
         }
         if (lane == 31) warp_tot[warp] = x;
         __syncthreads();
-        if (warp == 0) {
-            int t = warp_tot[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, t, o);
-                if (lane >= o) t += y;
-            }
-            warp_tot[lane] = t;  // inclusive over warps
+        int wpre = 0, tot = 0;
+        for (int wi = 0; wi < kPlanThreads / 32; ++wi) {
+            if (wi < warp) wpre += warp_tot[wi];
+            tot += warp_tot[wi];
         }
+        if (i < end) a.ws.blk_base[i] = s_run + wpre + x - v;  // frame-local for now
         __syncthreads();
-        const int warp_ex = warp > 0 ? warp_tot[warp - 1] : 0;
-        const int ex = s_running + warp_ex + x - v;
-        if (i < nb) {
-            a.ws.blk_base[i] = ex;
-            a.ws.box_done[i] = 0;
-            for (int s = 0; s < v; ++s) a.ws.blocks[ex + s] = make_int2(i, s);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) s_running += warp_tot[kScanThreads / 32 - 1];
+        if (tid == 0) s_run += tot;
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        Counts *c = a.ws.counts;
-        c->n_frames = clampi(a.counts_in[0], 0, a.caps.max_frames);
-        c->n_boxes = nb;
-        c->n_blocks = s_running < a.caps.max_blocks ? s_running : a.caps.max_blocks;
-        c->queue_head = 0;
-        c->error = 0;
-        c->evals = 0ull;
-        c->n_big = 0;
-        c->n_small = 0;
+    if (tid == 0) s_base = atomicAdd(&a.ws.counts->n_blocks, s_run);
+    __syncthreads();
+    const int base = s_base;
+    // a warp per box writes the box's entries of the flat block list
+    for (int i = begin + warp; i < end; i += kPlanThreads / 32) {
+        const int bb = base + a.ws.blk_base[i];
+        const int v = a.ws.nblk[i];
+        __syncwarp();
+        if (lane == 0) a.ws.blk_base[i] = bb;
+        for (int s2 = lane; s2 < v; s2 += 32) a.ws.blocks[bb + s2] = make_int2(i, s2);
     }
 }
 
@@ -221,17 +224,22 @@ __global__ void __launch_bounds__(256) sample_kernel(MatchArgs a)
     // k (x, y) in no kept occluder
     const int sxw = a.p.win_w >> 1, syw = a.p.win_h >> 1;
     const bool col_ok = lane < nx && Xl - sxw >= 0 && Xl + sxw < P.Ws;
-    unsigned colmask = 0u;
+    // Each occluder covers a column range x a row range of the point grid: lane q
+    // forms the row mask of occluder q, then every column lane removes the rows
+    // of the occluders whose x range holds it.
+    unsigned rowok = 0u, occrows = 0u;
     for (int m = 0; m < ny; ++m) {
         const int y = __shfl_sync(full, Yl, m);
-        bool valid = col_ok && y - syw >= 0 && y + syw < P.Hs;
-        const int fx = P.k * Xl, fy = P.k * y;
-        for (int q = 0; q < P.nocc; ++q) {
-            const int ox0 = __shfl_sync(full, occ.x, q), oy0 = __shfl_sync(full, occ.y, q);
-            const int ox1 = __shfl_sync(full, occ.z, q), oy1 = __shfl_sync(full, occ.w, q);
-            if (fx >= ox0 && fx < ox1 && fy >= oy0 && fy < oy1) valid = false;
-        }
-        if (valid) colmask |= 1u << m;
+        if (y - syw >= 0 && y + syw < P.Hs) rowok |= 1u << m;
+        const int fy = P.k * y;
+        if (lane < P.nocc && fy >= occ.y && fy < occ.w) occrows |= 1u << m;
+    }
+    unsigned colmask = col_ok ? rowok : 0u;
+    const int fx = P.k * Xl;
+    for (int q = 0; q < P.nocc; ++q) {
+        const int ox0 = __shfl_sync(full, occ.x, q), ox1 = __shfl_sync(full, occ.z, q);
+        const unsigned rows = __shfl_sync(full, occrows, q);
+        if (fx >= ox0 && fx < ox1) colmask &= ~rows;
     }
     const int cnt = __popc(colmask);
     int incl = cnt;
@@ -356,11 +364,9 @@ cudaError_t launch_stage_frame(const MatchArgs &a, ctm_frame f, int n_boxes, cud
 cudaError_t launch_plan(const MatchArgs &a, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(a.ws.nblk, 0, sizeof(int) * (size_t)a.caps.max_boxes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.ws.counts, 0, sizeof(Counts), s);  // all counters
     if (e != cudaSuccess) return e;
-    plan_boxes_kernel<<<a.caps.max_frames, kPlanThreads, 0, s>>>(a);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    plan_scan_kernel<<<1, kScanThreads, 0, s>>>(a);
+    plan_kernel<<<a.caps.max_frames, kPlanThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
