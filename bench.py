@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--frames", type=int, default=32)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="length of the served 4-stream 30 Hz trace (0: skip the serving leg)")
     return ap.parse_args()
 
 
@@ -139,6 +141,76 @@ def cpu_oracle(w, budget_s: float = 12.0) -> dict:
     return {"value": evals / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {frames} of {len(w.frames)} frames ({boxes} boxes, {evals} evals), "
                       f"{dt:.1f} s single-threaded", "seconds": dt, "evals": evals}
+
+
+# ----------------------------------------------------------------------------- serving
+
+def _pct(x, q):
+    return float(np.percentile(np.asarray(x, dtype=np.float64), q)) if len(x) else None
+
+
+def serve_trace(B, torch, tr, plain: bool) -> dict:
+    """Replay a camera trace through the serving loop: every frame is submitted at
+    its arrival time (pinned host images, host boxes); latency is submit to the
+    outputs written in host memory, from the server's own timestamps.  Then the
+    same frames are offered all at once to measure the server's saturated boxes/s."""
+    pinned = [[(torch.from_numpy(f.left).pin_memory(), torch.from_numpy(f.right).pin_memory())
+               for f in st.frames] for st in tr.streams]
+    W = max(st.width for st in tr.streams)
+    H = max(st.height for st in tr.streams)
+    srv = B.Server(tr.params, lanes=1 if plain else 2, frames_per_batch=1 if plain else 8,
+                   plain=int(plain), max_width=W, max_height=H, max_boxes_per_frame=256,
+                   max_queue=1024, image_budget_bytes=1 << 30)
+
+    def submit(s, k):
+        st = tr.streams[s]
+        fr = st.frames[k]
+        while srv.submit(*pinned[s][k], st.boxes[k], fr.f_px, fr.baseline_m) is None:
+            time.sleep(50e-6)  # admission queue full: retry
+
+    for s, st in enumerate(tr.streams):  # warm-up: each rendered frame once
+        for k in range(len(st.frames)):
+            submit(s, k)
+    srv.wait_all()
+    st0 = srv.stats()
+    done = []
+    t0 = time.perf_counter() + 0.05
+    for t, s, k in tr.arrivals:
+        target = t0 + t
+        while True:
+            now = time.perf_counter()
+            if now >= target:
+                break
+            if target - now > 2e-3:
+                time.sleep(target - now - 1e-3)
+        submit(s, k)
+        done += srv.poll(256, 0)
+    done += srv.wait_all()
+    st1 = srv.stats()
+    lat = [(r["t_done_ns"] - r["t_submit_ns"]) * 1e-6 for r in done]
+    boxes = sum(r["n_boxes"] for r in done)
+    span = (max(r["t_done_ns"] for r in done) - min(r["t_submit_ns"] for r in done)) * 1e-9
+    batches = st1["batches"] - st0["batches"]
+    paced = {"frames": len(done), "boxes": boxes, "failed": sum(r["status"] != 0 for r in done),
+             "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99), "max_ms": max(lat),
+             "boxes_per_s": boxes / span, "frames_per_s": len(done) / span,
+             "mean_batch_frames": (st1["batched_frames"] - st0["batched_frames"]) / max(batches, 1)}
+    # saturated: the whole trace offered at once
+    t_b = time.perf_counter()
+    for _, s, k in tr.arrivals:
+        submit(s, k)
+    burst = srv.wait_all()
+    dt = time.perf_counter() - t_b
+    st2 = srv.stats()
+    out = {"lanes": srv.config.lanes, "frames_per_batch": srv.config.frames_per_batch,
+           "paced": paced,
+           "saturated": {"frames": len(burst), "boxes_per_s": sum(r["n_boxes"] for r in burst) / dt,
+                         "frames_per_s": len(burst) / dt, "seconds": dt},
+           "max_lanes_busy": st2["max_lanes_busy"], "max_admitted": st2["max_admitted"],
+           "arena_peak_mb": st2["arena_peak_bytes"] / 2**20,
+           "workspace_mb": st2["workspace_bytes"] / 2**20}
+    srv.close()
+    return out
 
 
 # ----------------------------------------------------------------------------- main
@@ -297,6 +369,15 @@ def main():
     peak = sms * popc_clk / POPC_PER_EVAL * SM_MAX_MHZ * 1e6 / 1e9
     achieved = evals_per_step / (match_ms * 1e-3) / 1e9
 
+    # ---- serving: 4 stereo streams at 30 Hz (batched lanes, then the plain per-box path)
+    serving = serving_plain = None
+    if args.serve_seconds > 0:
+        tr = wl.serving(seed=D.rank_seed(1004, rank), duration_s=args.serve_seconds)
+        serving = serve_trace(B, torch, tr, plain=False)
+        serving_plain = serve_trace(B, torch, tr, plain=True)
+        serving["streams"] = [f"{st.width}x{st.height}" for st in tr.streams]
+        serving["p99_ms_max_over_ranks"] = D.max_over_ranks(serving["paced"]["p99_ms"], dist)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_oracle(w)
@@ -316,6 +397,8 @@ def main():
             "boxes_per_s": w.n_boxes * world / (ms_per_step * 1e-3),
             "phases_ms": {"plan_and_mark": plan_ms, "census_roi": census_ms, "match": match_ms},
             "plain_per_box": plain,
+            "serving": serving,
+            "serving_plain_path": serving_plain,
             "e2e": {"value": evals_per_step * world / e2e_s / 1e9, "unit": UNIT,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "ms_per_step": e2e_s * 1e3},

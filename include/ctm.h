@@ -43,7 +43,8 @@ typedef struct CUstream_st *ctm_stream;
 #define CTM_ENOMEM (-2)   /* workspace allocation failed or request exceeds capacity */
 #define CTM_ECUDA (-3)    /* a CUDA call or launch failed */
 #define CTM_ENODEV (-4)   /* no usable CUDA device */
-#define CTM_ETOOBIG (-5)  /* beyond the fixed limits of ctm_match_boxes_noalloc */
+#define CTM_ETOOBIG (-5)  /* beyond a fixed limit: ctm_match_boxes_noalloc's maxima, a server's frame size or arena */
+#define CTM_EAGAIN (-6)   /* a server's admission queue is full; nothing was queued */
 
 /* Per-box flags (uint8), written by the match calls. */
 #define CTM_BOX_VALID 0x01           /* disparity > 0 found; disp/depth finite         */

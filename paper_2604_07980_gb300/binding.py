@@ -16,7 +16,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libctm.so")
 
-CTM_OK, CTM_EINVAL, CTM_ENOMEM, CTM_ECUDA, CTM_ENODEV, CTM_ETOOBIG = 0, -1, -2, -3, -4, -5
+CTM_OK, CTM_EINVAL, CTM_ENOMEM, CTM_ECUDA, CTM_ENODEV, CTM_ETOOBIG, CTM_EAGAIN = 0, -1, -2, -3, -4, -5, -6
 
 BOX_VALID, BOX_FB_REJECT, BOX_FEW_POINTS, BOX_NO_SEGMENT = 0x01, 0x02, 0x04, 0x08
 BOX_NONPOS_DISP, BOX_EMPTY, BOX_SUBPIX_CLAMPED, BOX_FAR = 0x10, 0x20, 0x40, 0x80
@@ -26,7 +26,9 @@ BLK_VALID, BLK_FB_REJECT, BLK_FEW_POINTS, BLK_SUBPIX_CLAMPED, BLK_PRESENT = 1, 2
 EXPORTS = ("ctm_status_str", "ctm_default_params", "ctm_create", "ctm_destroy",
            "ctm_census_build", "ctm_match_boxes", "ctm_match_boxes_plain", "ctm_match_batch",
            "ctm_match_batch_profiled", "ctm_match_batch_host", "ctm_match_boxes_noalloc",
-           "ctm_get_stats", "ctm_probe_int_rate")
+           "ctm_get_stats", "ctm_probe_int_rate",
+           "ctm_server_default_config", "ctm_server_create", "ctm_server_submit", "ctm_server_poll",
+           "ctm_server_outstanding", "ctm_server_get_stats", "ctm_server_destroy", "ctm_server_now_ns")
 
 
 class CtmError(RuntimeError):
@@ -58,6 +60,38 @@ class ctm_debug(ctypes.Structure):
 class ctm_stats(ctypes.Structure):
     _fields_ = [("cost_evals", ctypes.c_uint64), ("n_blocks", ctypes.c_int32), ("n_boxes", ctypes.c_int32),
                 ("error", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class ctm_server_config(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_int32), ("frames_per_batch", ctypes.c_int32),
+                ("max_width", ctypes.c_int32), ("max_height", ctypes.c_int32),
+                ("max_boxes_per_frame", ctypes.c_int32), ("max_queue", ctypes.c_int32),
+                ("image_budget_bytes", ctypes.c_int64), ("plain", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class ctm_request(ctypes.Structure):
+    _fields_ = [("left_host", ctypes.c_void_p), ("right_host", ctypes.c_void_p),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32), ("pitch", ctypes.c_int32),
+                ("n_boxes", ctypes.c_int32), ("boxes_host", ctypes.c_void_p),
+                ("f_px", ctypes.c_float), ("baseline_m", ctypes.c_float),
+                ("disp_host", ctypes.c_void_p), ("depth_host", ctypes.c_void_p),
+                ("flags_host", ctypes.c_void_p), ("tag", ctypes.c_uint64)]
+
+
+class ctm_completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int32), ("n_boxes", ctypes.c_int32),
+                ("t_submit_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64),
+                ("t_launch_ns", ctypes.c_int64), ("t_done_ns", ctypes.c_int64),
+                ("lane", ctypes.c_int32), ("batch_frames", ctypes.c_int32)]
+
+
+class ctm_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("rejected", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("batched_frames", ctypes.c_int64), ("arena_bytes", ctypes.c_int64),
+                ("arena_peak_bytes", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
+                ("max_admitted", ctypes.c_int32), ("max_lanes_busy", ctypes.c_int32)]
 
 
 BLOCK_DTYPE = np.dtype([("n_pts", "<i4"), ("n_valid", "<i4"), ("d_f", "<i4"), ("dy_f", "<i4"),
@@ -106,6 +140,25 @@ def lib():
     L.ctm_get_stats.restype = i32
     L.ctm_probe_int_rate.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double)]
     L.ctm_probe_int_rate.restype = i32
+    i64 = ctypes.c_int64
+    L.ctm_server_default_config.argtypes = [ctypes.POINTER(ctm_server_config)]
+    L.ctm_server_default_config.restype = i32
+    L.ctm_server_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ctm_params),
+                                    ctypes.POINTER(ctm_server_config)]
+    L.ctm_server_create.restype = i32
+    L.ctm_server_submit.argtypes = [vp, ctypes.POINTER(ctm_request)]
+    L.ctm_server_submit.restype = i32
+    L.ctm_server_poll.argtypes = [vp, ctypes.POINTER(ctm_completion), ctypes.c_int32, i64,
+                                  ctypes.POINTER(ctypes.c_int32)]
+    L.ctm_server_poll.restype = i32
+    L.ctm_server_outstanding.argtypes = [vp]
+    L.ctm_server_outstanding.restype = i64
+    L.ctm_server_get_stats.argtypes = [vp, ctypes.POINTER(ctm_server_stats)]
+    L.ctm_server_get_stats.restype = i32
+    L.ctm_server_destroy.argtypes = [vp]
+    L.ctm_server_destroy.restype = i32
+    L.ctm_server_now_ns.argtypes = []
+    L.ctm_server_now_ns.restype = i64
     _lib = L
     return L
 
@@ -328,6 +381,117 @@ class DeviceBatch:
         self.disp = torch.empty(max(n, 1), dtype=torch.float32, device=device)
         self.depth = torch.empty(max(n, 1), dtype=torch.float32, device=device)
         self.flags = torch.empty(max(n, 1), dtype=torch.uint8, device=device)
+
+
+def _host_ptr(a):
+    """Address and row pitch of a 2-D uint8 host array (numpy or CPU torch tensor)."""
+    if hasattr(a, "data_ptr"):
+        assert a.dtype.itemsize == 1 and not a.is_cuda and a.dim() == 2 and a.stride(1) == 1
+        return a.data_ptr(), a.stride(0), a.shape[0], a.shape[1]
+    assert a.dtype == np.uint8 and a.ndim == 2 and a.strides[1] == 1
+    return a.ctypes.data, a.strides[0], a.shape[0], a.shape[1]
+
+
+class Server:
+    """The serving loop (ctm_server_*) on the current CUDA device.
+
+    submit() queues one frame (host images, host boxes) and returns its tag;
+    poll() returns finished frames with their outputs and timestamps.  The
+    arrays passed to submit() are kept alive here until their frame completes;
+    page-locked images (pinned torch tensors) let the uploads run async."""
+
+    def __init__(self, params: dict | None = None, **config):
+        _torch()
+        self.params = make_params(params)
+        cfg = ctm_server_config()
+        _check(lib().ctm_server_default_config(ctypes.byref(cfg)), "ctm_server_default_config")
+        for k, v in config.items():
+            setattr(cfg, k, v)
+        self.config = cfg
+        h = ctypes.c_void_p()
+        _check(lib().ctm_server_create(ctypes.byref(h), ctypes.byref(self.params), ctypes.byref(cfg)),
+               "ctm_server_create")
+        self._h = h
+        self._live = {}
+        self._next_tag = 1
+
+    def submit(self, left, right, boxes, f_px: float, baseline_m: float, tag: int | None = None):
+        """Queue a frame; returns its tag, or None when the admission queue is full."""
+        lp, pitch, H, W = _host_ptr(left)
+        rp, rpitch, H2, W2 = _host_ptr(right)
+        assert (H, W) == (H2, W2) and rpitch == pitch
+        bx = np.ascontiguousarray(np.asarray(boxes, dtype=np.int32).reshape(-1, 5)
+                                  if np.asarray(boxes).size else np.zeros((0, 5), np.int32))
+        n = int(bx.shape[0])
+        out = (np.empty(max(n, 1), np.float32), np.empty(max(n, 1), np.float32),
+               np.empty(max(n, 1), np.uint8))
+        if tag is None:
+            tag = self._next_tag
+            self._next_tag += 1
+        req = ctm_request(lp, rp, W, H, pitch, n, bx.ctypes.data, float(f_px), float(baseline_m),
+                          out[0].ctypes.data, out[1].ctypes.data, out[2].ctypes.data, int(tag))
+        self._live[int(tag)] = (left, right, bx, out)
+        st = lib().ctm_server_submit(self._h, ctypes.byref(req))
+        if st == CTM_EAGAIN:
+            del self._live[int(tag)]
+            return None
+        if st != CTM_OK:
+            del self._live[int(tag)]
+            _check(st, "ctm_server_submit")
+        return int(tag)
+
+    def poll(self, max_n: int = 256, timeout_us: int = 0) -> list:
+        """Finished frames: dicts with tag, status, disp/depth/flags, timestamps (ns), lane."""
+        arr = (ctm_completion * max_n)()
+        n = ctypes.c_int32(0)
+        _check(lib().ctm_server_poll(self._h, arr, max_n, int(timeout_us), ctypes.byref(n)),
+               "ctm_server_poll")
+        res = []
+        for i in range(n.value):
+            c = arr[i]
+            _, _, _, out = self._live.pop(int(c.tag))
+            k = int(c.n_boxes)
+            res.append({"tag": int(c.tag), "status": int(c.status), "n_boxes": k,
+                        "disp": out[0][:k], "depth": out[1][:k], "flags": out[2][:k],
+                        "t_submit_ns": int(c.t_submit_ns), "t_admit_ns": int(c.t_admit_ns),
+                        "t_launch_ns": int(c.t_launch_ns), "t_done_ns": int(c.t_done_ns),
+                        "lane": int(c.lane), "batch_frames": int(c.batch_frames)})
+        return res
+
+    def wait_all(self, timeout_s: float = 120.0) -> list:
+        """Poll until every submitted frame has completed."""
+        import time
+        out = []
+        t_end = time.monotonic() + timeout_s
+        while self._live:
+            if time.monotonic() > t_end:
+                raise CtmError(f"server: {len(self._live)} frames still outstanding after {timeout_s} s")
+            out += self.poll(256, 20000)
+        return out
+
+    def outstanding(self) -> int:
+        return int(lib().ctm_server_outstanding(self._h))
+
+    def stats(self) -> dict:
+        s = ctm_server_stats()
+        _check(lib().ctm_server_get_stats(self._h, ctypes.byref(s)), "ctm_server_get_stats")
+        return {f: int(getattr(s, f)) for f, _ in ctm_server_stats._fields_}
+
+    @staticmethod
+    def now_ns() -> int:
+        return int(lib().ctm_server_now_ns())
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().ctm_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def frames_to_device(frames, device="cuda"):

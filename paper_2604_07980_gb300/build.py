@@ -21,7 +21,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libctm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-              "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
+              "--expt-relaxed-constexpr", "-Xcompiler", "-pthread", "-I", os.path.join(ROOT, "include")]
 
 
 def nvcc() -> str:
@@ -32,7 +32,8 @@ def nvcc() -> str:
 
 
 def _headers():
-    return glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
+    return (glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) +
+            glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 def _compile(src: str, extra) -> str:
@@ -63,7 +64,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     if (not os.path.exists(LIB) or force or
             any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs)):
         tmp = LIB + f".{os.getpid()}.tmp"
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
+        cmd = [nvcc()] + ARCH + ["-shared", "-Xcompiler", "-pthread", "-o", tmp] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -1,10 +1,11 @@
 // api.cu -- the C ABI (include/ctm.h): context, workspace and launch sequences.
 //
-// A match call is four launches on one stream: census of both images at both
-// resolutions (one kernel), device planning (two kernels), and the matching
-// kernel whose last CTA per box aggregates and writes the outputs.  The batch
-// entry point reads its frame and box counts from device memory, so the whole
-// sequence can be captured once into a CUDA graph and replayed.
+// A match call is five launches on one stream: device planning, point sampling,
+// census demand marking, census of the marked tiles (both images, both
+// resolutions) and the matching kernel whose last CTA per box aggregates and
+// writes the outputs.  The batch entry point reads its frame and box counts
+// from device memory, so the whole sequence can be captured once into a CUDA
+// graph and replayed.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdlib.h>
@@ -34,6 +35,7 @@ struct ctm_ctx {
     int strip_cols = 0;
     int strip_rows = 0;
     void *dev_mem = nullptr;
+    size_t dev_bytes = 0;
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
     GraphKey gkey{};
@@ -129,6 +131,8 @@ int set_device(const ctm_ctx *ctx)
 
 }  // namespace
 
+size_t ctm::context_device_bytes(const ctm_ctx *ctx) { return ctx ? ctx->dev_bytes : 0; }
+
 extern "C" {
 
 const char *ctm_status_str(int status)
@@ -139,7 +143,8 @@ const char *ctm_status_str(int status)
     case CTM_ENOMEM: return "out of memory or beyond context capacity";
     case CTM_ECUDA: return "CUDA error";
     case CTM_ENODEV: return "no usable CUDA device";
-    case CTM_ETOOBIG: return "request exceeds the fixed limits of the no-allocation entry point";
+    case CTM_ETOOBIG: return "request exceeds a fixed limit (no-allocation maxima, server frame size or arena)";
+    case CTM_EAGAIN: return "admission queue full, try again";
     default: return "unknown status";
     }
 }
@@ -246,6 +251,7 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
         delete ctx;
         return CTM_ENOMEM;
     }
+    ctx->dev_bytes = off;
     char *base = static_cast<char *>(ctx->dev_mem);
     Workspace &ws = ctx->ws;
     ws.census = reinterpret_cast<uint64_t *>(base + o_census);

@@ -16,7 +16,6 @@ constexpr int kMaxSlots = kMaxGrid * kMaxGrid;
 constexpr int kMaxOcc = 32;
 constexpr int kMaxWin = 15;
 constexpr int kPlanThreads = 256;
-constexpr int kScanThreads = 1024;
 
 // Device-side counters of one call.
 struct Counts {
@@ -160,5 +159,8 @@ cudaError_t launch_match_box(const MatchArgs &a, int threads, int box, cudaStrea
 
 // Probe (probe.cu)
 cudaError_t run_int_probe(int kind, int iters, double *ops_per_clk_per_sm);
+
+// Bytes of device workspace a context holds (its one allocation at creation).
+size_t context_device_bytes(const ctm_ctx *ctx);
 
 }  // namespace ctm

@@ -271,3 +271,64 @@ def batch8x2160(seed: int = 1003, n_frames: int = 8, W: int = 3840, H: int = 216
 def by_name(name: str, **kw) -> Workload:
     return {"pair640": pair640, "frame1080": frame1080, "batch32x1200": batch32x1200,
             "batch8x2160": batch8x2160}[name](**kw)
+
+
+# --------------------------------------------------------------------------- serving
+
+SERVING_SIZES = ((1280, 720), (1920, 1080), (3840, 2160))
+
+
+@dataclass
+class ServingStream:
+    width: int
+    height: int
+    frames: list     # Frame objects cycled through by the stream
+    boxes: list      # int32 [n_i, 5] per frame (column 4 = 0)
+    d_true: list
+
+
+@dataclass
+class ServingTrace:
+    streams: list    # ServingStream per camera stream
+    arrivals: list   # (t_s, stream, frame index within the stream's list), sorted by time
+    params: dict
+
+
+def serving(seed: int = 1004, n_streams: int = 4, rate_hz: float = 30.0, duration_s: float = 10.0,
+            unique_frames: int = 3, jitter_ms: float = 5.0, mean_boxes: float = 60.0,
+            max_boxes: int = 200, side_range=(12.0, 400.0), sizes=SERVING_SIZES,
+            stream_sizes=None) -> ServingTrace:
+    """Several stereo streams at a fixed rate: each stream's frame size is drawn
+    once from `sizes`; each frame has min(max_boxes, Poisson(mean_boxes)) boxes
+    (far d U[0.5,30], close U[2,250], gain/offset/noise as the 1080p frame);
+    frame k of a stream arrives at k / rate + U[-jitter, +jitter] ms.  A stream
+    cycles through `unique_frames` rendered frames.  `stream_sizes` fixes each
+    stream's (width, height) instead of drawing it."""
+    params = dict(PARAMS["serving"])
+    top = np.random.Generator(np.random.PCG64([seed, 0xFFFF]))
+    streams = []
+    for s in range(n_streams):
+        W, H = sizes[int(top.integers(0, len(sizes)))]
+        if stream_sizes is not None:
+            W, H = stream_sizes[s]
+        frames, boxes, dts = [], [], []
+        for k in range(unique_frames):
+            rng = np.random.Generator(np.random.PCG64([seed, s, k]))
+            n_obj = min(int(rng.poisson(mean_boxes)), max_boxes)
+            bx, d = _random_frame(rng, W, H, n_obj, side_range, params["far_side_px"],
+                                  (0.5, 30.0), (2.0, 250.0), 0.0)
+            gain = rng.uniform(0.8, 1.2)
+            offset = rng.uniform(-20.0, 20.0)
+            L, R = _render(rng, W, H, bx, d, gain, offset, 2.0)
+            frames.append(Frame(L, R))
+            boxes.append(np.array([b + [0] for b in bx], dtype=np.int32).reshape(-1, 5))
+            dts.append(np.array(d, np.float32))
+        streams.append(ServingStream(W, H, frames, boxes, dts))
+    arrivals = []
+    n_per = int(round(rate_hz * duration_s))
+    for s in range(n_streams):
+        for k in range(n_per):
+            t = k / rate_hz + top.uniform(-jitter_ms, jitter_ms) * 1e-3
+            arrivals.append((max(t, 0.0), s, k % unique_frames))
+    arrivals.sort()
+    return ServingTrace(streams, arrivals, params)

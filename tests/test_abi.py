@@ -8,7 +8,7 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "ctm.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("ctm.h", "ctm_server.h")]
 
 
 @pytest.fixture(scope="module")
@@ -22,7 +22,7 @@ def built():
 
 
 def _declared():
-    txt = open(HEADER).read()
+    txt = "".join(open(h).read() for h in HEADERS)
     return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(ctm_\w+)\s*\(", txt, re.M)))
 
 
@@ -43,6 +43,10 @@ def test_struct_layouts():
     assert ctypes.sizeof(B.ctm_frame) == 48
     assert B.BLOCK_DTYPE.itemsize == B.BLOCK_BYTES == 48
     assert ctypes.sizeof(B.ctm_debug) == 24
+    assert ctypes.sizeof(B.ctm_server_config) == 40
+    assert ctypes.sizeof(B.ctm_request) == 80
+    assert ctypes.sizeof(B.ctm_completion) == 56
+    assert ctypes.sizeof(B.ctm_server_stats) == 72
 
 
 def test_status_strings_and_defaults(built):
@@ -68,3 +72,28 @@ def test_binding_refuses_without_gpu():
     from paper_2604_07980_gb300 import binding as B
     with pytest.raises(B.CtmError):
         B.Context({}, 1, 64, 64, 4)
+
+
+def test_server_argument_checks(built):
+    """Server entry points reject bad arguments before touching a device."""
+    from paper_2604_07980_gb300 import binding as B
+    L = B.lib()
+    cfg = B.ctm_server_config()
+    assert L.ctm_server_default_config(ctypes.byref(cfg)) == B.CTM_OK
+    assert (cfg.lanes, cfg.frames_per_batch, cfg.max_width, cfg.max_height) == (2, 8, 3840, 2160)
+    assert L.ctm_server_default_config(None) == B.CTM_EINVAL
+    p = B.make_params()
+    h = ctypes.c_void_p()
+    assert L.ctm_server_create(None, ctypes.byref(p), ctypes.byref(cfg)) == B.CTM_EINVAL
+    for field, bad in (("lanes", 0), ("lanes", 9), ("frames_per_batch", 0), ("max_queue", 0),
+                       ("image_budget_bytes", 0), ("plain", 2)):
+        c = B.ctm_server_config.from_buffer_copy(cfg)
+        setattr(c, field, bad)
+        assert L.ctm_server_create(ctypes.byref(h), ctypes.byref(p), ctypes.byref(c)) == B.CTM_EINVAL
+        assert not h.value
+    req = B.ctm_request()
+    assert L.ctm_server_submit(None, ctypes.byref(req)) == B.CTM_EINVAL
+    n = ctypes.c_int32(7)
+    assert L.ctm_server_poll(None, None, 0, 0, ctypes.byref(n)) == B.CTM_EINVAL
+    assert L.ctm_server_destroy(None) == B.CTM_EINVAL
+    assert L.ctm_server_now_ns() > 0
