@@ -42,8 +42,8 @@ POPC_PER_EVAL = 2          # one u64 code pair = two 32-bit popcounts
 # ncu capture summarised in profiles/match_persistent_kernel_batch32x1200.md; None once the
 # kernel changes after that capture.
 MATCH_DRAM_BYTES = (101.938432 + 2.879232) * 1e6
-# kernels of one step of the batched path: plan, sample, mark, census_roi, match
-KERNELS_PER_STEP = 5
+# kernels of one step of the batched path: plan, sample, mark, tile_list, census_roi, match
+KERNELS_PER_STEP = 6
 
 
 def parse():

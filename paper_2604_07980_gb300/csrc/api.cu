@@ -111,7 +111,7 @@ int enqueue_match(ctm_ctx *ctx, const MatchArgs &a, int frames_grid, int match_g
     cudaError_t e = launch_plan(b, s);
     if (e == cudaSuccess) e = launch_sample(b, s);
     if (e == cudaSuccess) e = launch_mark(b, s);
-    if (e == cudaSuccess) e = launch_census_roi(b, ctx->sm_count * 4, s);
+    if (e == cudaSuccess) e = launch_census_roi(b, ctx->sm_count, s);
     if (!plain) {
         if (e == cudaSuccess) e = launch_match_persistent(b, ctx->match_threads, match_grid, s);
     } else {
@@ -246,6 +246,7 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
     plane_off[0] = 0;
     for (int q = 0; q < 4; ++q) plane_off[q + 1] = plane_off[q] + rows_q[q] * words_q[q];
     const size_t o_bm = take(sizeof(uint32_t) * (size_t)plane_off[4] * max_frames);
+    const size_t o_tiles = take(sizeof(unsigned long long) * 32 * (size_t)plane_off[4] * max_frames);
     if (cudaMalloc(&ctx->dev_mem, off) != cudaSuccess) {
         cudaGetLastError();
         delete ctx;
@@ -273,6 +274,7 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
     ws.frames = reinterpret_cast<ctm_frame *>(base + o_frames);
     ws.counts_in = reinterpret_cast<int *>(base + o_cin);
     ws.bitmap = reinterpret_cast<uint32_t *>(base + o_bm);
+    ws.tiles = reinterpret_cast<unsigned long long *>(base + o_tiles);
     ws.bm_frame_words = plane_off[4];
     for (int q = 0; q < 5; ++q) ws.bm_plane_off[q] = plane_off[q];
     for (int q = 0; q < 4; ++q) ws.bm_row_words[q] = words_q[q];
@@ -290,6 +292,7 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
         ctm_destroy(ctx);
         return CTM_ECUDA;
     }
+    census_roi_ctas_per_sm(p->win_w, p->win_h);  // occupancy query outside any capture
     *out = ctx;
     return CTM_OK;
 }
@@ -434,7 +437,7 @@ int ctm_match_batch_profiled(ctm_ctx *ctx, const ctm_frame *frames_dev, const in
     if (e == cudaSuccess) e = launch_sample(a, s);
     if (e == cudaSuccess) e = launch_mark(a, s);
     if (e == cudaSuccess) e = cudaEventRecord((cudaEvent_t)events[1], s);
-    if (e == cudaSuccess) e = launch_census_roi(a, ctx->sm_count * 4, s);
+    if (e == cudaSuccess) e = launch_census_roi(a, ctx->sm_count, s);
     if (e == cudaSuccess) e = cudaEventRecord((cudaEvent_t)events[2], s);
     if (e == cudaSuccess) e = launch_match_persistent(a, ctx->match_threads, grid, s);
     if (e == cudaSuccess) e = cudaEventRecord((cudaEvent_t)events[3], s);

@@ -17,6 +17,7 @@
 // tiles the planner marked in a per-plane bitmap (one bit per 64-pixel tile of
 // a row) and clears the marks it consumed.
 #include <cuda_fp16.h>
+#include <stdlib.h>
 
 #include "ctm_internal.cuh"
 
@@ -216,6 +217,194 @@ __device__ __forceinline__ void store_pair(const Plane &pl, int x, int y, uint64
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Fixed windows (5x5, 7x7, 9x7): four pixels per lane, a half-warp per tile.
+//
+// Lane l of a half-warp owns pixels x .. x+3 of its tile (x = x0 + 4 l).  It
+// loads the twelve pixels I_k(x-4 .. x+7) of every window row straight into
+// registers (three 32-bit loads at k = 1, three 64-bit loads compacted with
+// PRMT at k = 2; adjacent lanes share bytes through L1) and forms the eleven
+// words (b[t], b[t+1]) of pixel pairs in registers, so no shared
+// memory is involved.  Pixel pairs (x, x+1) and (x+2, x+3) are compared two at
+// a time in the 16-bit halves of a word (codes4).
+
+// Raw window-row bytes of one lane: v[r][q] holds I_k(x - 4 + 4q .. x - 1 + 4q)
+// of window row r, little-endian; out-of-grid pixels read as 0 (they only
+// feed pixels whose codes are zeroed).  Lanes whose twelve pixels lie inside
+// a word-aligned image take word loads, the others (image borders, other
+// decimations or alignments) byte loads.
+template <int WH>
+__device__ __forceinline__ void load_rows4(const Plane &pl, int x0, int y, int hl, uint32_t (&v)[WH][3])
+{
+    constexpr int sy = WH / 2;
+    const int x = x0 + 4 * hl;
+    // word loads where this lane's twelve pixels lie inside the row
+    const bool inside = pl.vec_load && x >= 4 && (pl.k == 1 ? x + 8 <= pl.W : 2 * x + 16 <= pl.W);
+    if (inside && pl.k == 1) {
+        const uint8_t *p = pl.img + (long long)(y - sy) * pl.pitch + (x - 4);
+#pragma unroll
+        for (int r = 0; r < WH; ++r) {
+            const uint32_t *q = reinterpret_cast<const uint32_t *>(p + (long long)r * pl.pitch);
+            v[r][0] = __ldg(q);
+            v[r][1] = __ldg(q + 1);
+            v[r][2] = __ldg(q + 2);
+        }
+    } else if (inside) {  // k == 2: every other source byte
+        const uint8_t *p = pl.img + 2LL * (y - sy) * pl.pitch + 2 * (x - 4);
+#pragma unroll
+        for (int r = 0; r < WH; ++r) {
+            const uint2 *q = reinterpret_cast<const uint2 *>(p + 2LL * r * pl.pitch);
+            const uint2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+            v[r][0] = __byte_perm(a.x, a.y, 0x6420);
+            v[r][1] = __byte_perm(b.x, b.y, 0x6420);
+            v[r][2] = __byte_perm(c.x, c.y, 0x6420);
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < WH; ++r) {
+            const uint8_t *row = pl.img + (long long)pl.k * (y - sy + r) * pl.pitch;
+            uint32_t w[3] = {0u, 0u, 0u};
+#pragma unroll
+            for (int t = 0; t < 12; ++t) {
+                const int xs = x - 4 + t;
+                const uint32_t b = (xs >= 0 && xs < pl.Ws) ? (uint32_t)__ldg(row + (long long)pl.k * xs) : 0u;
+                w[t >> 2] |= b << (8 * (t & 3));
+            }
+            v[r][0] = w[0];
+            v[r][1] = w[1];
+            v[r][2] = w[2];
+        }
+    }
+}
+
+// Codes of pixels x .. x+3 from the raw rows (bit layout as tile_codes).
+//
+// The compares run on the integer multiply-add pipe: with both pixels of a
+// pair in the two 16-bit halves of a word w (plain values, upper bytes zero),
+// e = w * 2^s + K_s, K_s = (2^16 - 2^(8+s) - 1 - c 2^s) per half, is per half
+// the complement of 2^(8+s) + (c - nb) 2^s, which lies in [1, 2^16) for
+// s <= 7; so no carry crosses the halves and bit 8 + s of each half is
+// [nb > c].  Code bit p = 8 a + s is taken from bit 8 + s (and 24 + s) of e
+// into accumulator a with one LOP3; accumulator a ends up holding code byte a
+// of the low pixel in its byte 1 and of the high pixel in its byte 3.
+template <int WW, int WH>
+__device__ __forceinline__ void codes4(const uint32_t (&v)[WH][3], int sentinel, uint64_t (&c)[4])
+{
+    constexpr int sx = WW / 2, sy = WH / 2;
+    constexpr int n = WW * WH;
+    constexpr int OFF = 4 - sx;  // byte index of the window's left column for pixel x
+    uint32_t accA[8], accB[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) accA[q] = accB[q] = 0u;
+    if (sentinel) {
+        accA[n >> 3] = (0x100u << (n & 7)) | (0x1000000u << (n & 7));
+        accB[n >> 3] = accA[n >> 3];
+    }
+    const uint32_t cA = __byte_perm(v[sy][1], 0u, 0x4140);  // pixels x, x+1
+    const uint32_t cB = __byte_perm(v[sy][1], 0u, 0x4342);  // pixels x+2, x+3
+    uint32_t KA[8], KB[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const uint32_t h = 0x10000u - (0x100u << q) - 1u;
+        KA[q] = (h | (h << 16)) - (cA << q);
+        KB[q] = (h | (h << 16)) - (cB << q);
+    }
+#pragma unroll
+    for (int j = 0; j < WH; ++j) {
+        // w[t] = (b[t], b[t+1]) in the two halves, t = 0 .. 10
+        uint32_t w[11];
+        const uint32_t s1 = __funnelshift_r(v[j][0], v[j][1], 8);  // b1 .. b4
+        const uint32_t s2 = __funnelshift_r(v[j][1], v[j][2], 8);  // b5 .. b8
+        w[0] = __byte_perm(v[j][0], 0u, 0x4140);
+        w[1] = __byte_perm(s1, 0u, 0x4140);
+        w[2] = __byte_perm(v[j][0], 0u, 0x4342);
+        w[3] = __byte_perm(s1, 0u, 0x4342);
+        w[4] = __byte_perm(v[j][1], 0u, 0x4140);
+        w[5] = __byte_perm(s2, 0u, 0x4140);
+        w[6] = __byte_perm(v[j][1], 0u, 0x4342);
+        w[7] = __byte_perm(s2, 0u, 0x4342);
+        w[8] = __byte_perm(v[j][2], 0u, 0x4140);
+        w[9] = __byte_perm(v[j][2], 0u, 0x4241);
+        w[10] = __byte_perm(v[j][2], 0u, 0x4342);
+#pragma unroll
+        for (int i = 0; i < WW; ++i) {
+            const int p = n - 1 - (j * WW + i);  // code bit of this window offset
+            const int q = p & 7;
+            const uint32_t pos = (0x100u << q) | (0x1000000u << q);
+            accA[p >> 3] |= (w[OFF + i] * (1u << q) + KA[q]) & pos;
+            accB[p >> 3] |= (w[OFF + i + 2] * (1u << q) + KB[q]) & pos;
+        }
+    }
+    uint32_t tA[4], tB[4];  // code bytes (2q, 2q+1) of the low pixel, then of the high pixel
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        tA[q] = __byte_perm(accA[2 * q], accA[2 * q + 1], 0x7351);
+        tB[q] = __byte_perm(accB[2 * q], accB[2 * q + 1], 0x7351);
+    }
+    c[0] = ((uint64_t)__byte_perm(tA[2], tA[3], 0x5410) << 32) | __byte_perm(tA[0], tA[1], 0x5410);
+    c[1] = ((uint64_t)__byte_perm(tA[2], tA[3], 0x7632) << 32) | __byte_perm(tA[0], tA[1], 0x7632);
+    c[2] = ((uint64_t)__byte_perm(tB[2], tB[3], 0x5410) << 32) | __byte_perm(tB[0], tB[1], 0x5410);
+    c[3] = ((uint64_t)__byte_perm(tB[2], tB[3], 0x7632) << 32) | __byte_perm(tB[0], tB[1], 0x7632);
+}
+
+// One lane's part of a tile between its loads and its stores.
+struct Job4 {
+    uint64_t *dst;  // code of pixel x
+    int x, Ws;
+    bool row_ok, vec_ok;
+};
+
+template <int WW, int WH>
+__device__ __forceinline__ void start_tile4(const Plane &pl, int x0, int y, int hl, bool ok, uint32_t (&v)[WH][3],
+                                            Job4 &j)
+{
+    constexpr int sy = WH / 2;
+    j.x = x0 + 4 * hl;
+    j.Ws = ok ? pl.Ws : 0;  // no tile: nothing is stored
+    j.row_ok = ok && y - sy >= 0 && y + sy < pl.Hs;
+    j.vec_ok = pl.vec_ok != 0;
+    j.dst = pl.out + (long long)y * pl.opitch + j.x;
+    if (j.row_ok) {
+        load_rows4<WH>(pl, x0, y, hl, v);
+    } else {
+#pragma unroll
+        for (int r = 0; r < WH; ++r) v[r][0] = v[r][1] = v[r][2] = 0u;
+    }
+}
+
+template <int WW, int WH>
+__device__ __forceinline__ void finish_tile4(const uint32_t (&v)[WH][3], const Job4 &j, int sentinel)
+{
+    constexpr int sx = WW / 2;
+    uint64_t c[4] = {0ull, 0ull, 0ull, 0ull};
+    if (j.row_ok) codes4<WW, WH>(v, sentinel, c);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (!(j.row_ok && j.x + q - sx >= 0 && j.x + q + sx < j.Ws)) c[q] = 0ull;
+    if (j.vec_ok && j.x + 3 < j.Ws) {
+        reinterpret_cast<ulonglong2 *>(j.dst)[0] = make_ulonglong2(c[0], c[1]);
+        reinterpret_cast<ulonglong2 *>(j.dst)[1] = make_ulonglong2(c[2], c[3]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (j.x + q < j.Ws) j.dst[q] = c[q];
+    }
+}
+
+// Full image, fixed window: half-warp h of CTA (bx, by) takes tile bx of row by * 16 + h.
+template <int WW, int WH>
+__global__ void __launch_bounds__(256) census_full4_kernel(Plane pl, int sentinel)
+{
+    const int hl = threadIdx.x & 15;
+    const int y = blockIdx.y * 16 + (threadIdx.x >> 4);
+    if (y >= pl.Hs) return;
+    uint32_t v[WH][3];
+    Job4 j;
+    start_tile4<WW, WH>(pl, blockIdx.x * kTile, y, hl, true, v, j);
+    finish_tile4<WW, WH>(v, j, sentinel);
+}
+
 // One 64-pixel tile of row y starting at x0 (x0 a multiple of 64).
 template <int WW, int WH>
 __device__ void census_tile(const Plane &pl, int x0, int y, int win_w, int win_h, int sentinel,
@@ -270,27 +459,23 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) census_full_kernel(Plane pl
     census_tile_any(pl, blockIdx.x * kTile, y, win_w, win_h, sentinel, st);
 }
 
-// Region of interest.  Each warp walks the set bits of its bitmap words
-// (grid-stride over the words of all frames' planes) as one stream of tiles and
-// clears every word it consumed.
-struct TileCursor {
-    long long w;       // current word index (grid-stride)
-    uint32_t bits;     // tiles of the current word not yet taken
-    Plane pl;          // plane of the current word
-    int y, wi;         // row and word-in-row of the current word
-};
-
-__device__ __forceinline__ void decode_word(const MatchArgs &a, long long w, TileCursor &c)
+// Region of interest.  The planner marks, per plane row, the 64-pixel tiles the
+// search reads (bitmap, one bit per tile).  tile_list_kernel compacts the
+// marks into a dense list (one packed entry per tile, row-major within each
+// 256-word chunk of the bitmap) and clears the bitmap for the next call; the
+// census kernels then take tiles from the list, so every warp gets the same
+// share of work and no warp scans empty bitmap words.
+//
+// Entry: bits 0-9 tile (x0 / 64), 10-25 row, 26-27 plane (L1, R1, Lk, Rk), 28- frame.
+__device__ __forceinline__ unsigned long long tile_entry(int f, int q, int y, int tile)
 {
-    const int f = (int)(w / a.ws.bm_frame_words);
-    int r = (int)(w - (long long)f * a.ws.bm_frame_words);
-    int q = 0;
-    while (q < 3 && r >= a.ws.bm_plane_off[q + 1]) ++q;
-    r -= a.ws.bm_plane_off[q];
-    c.y = r / a.ws.bm_row_words[q];
-    c.wi = r - c.y * a.ws.bm_row_words[q];
+    return ((unsigned long long)f << 28) | ((unsigned long long)q << 26) | ((unsigned long long)y << 10) |
+           (unsigned long long)tile;
+}
+
+__device__ __forceinline__ void plane_of(const MatchArgs &a, int f, int q, Plane &pl)
+{
     const ctm_frame fr = a.frames[f];
-    Plane &pl = c.pl;
     pl.img = (q & 1) ? fr.right : fr.left;
     pl.W = fr.width;
     pl.H = fr.height;
@@ -306,98 +491,116 @@ __device__ __forceinline__ void decode_word(const MatchArgs &a, long long w, Til
                   ((reinterpret_cast<uintptr_t>(pl.img) & 7u) == 0);
 }
 
-// Next tile of this warp's stream; false when its words are exhausted.
-__device__ __forceinline__ bool next_tile(const MatchArgs &a, TileCursor &c, long long nwarps,
-                                          long long total, int lane, int &x0, int &y)
+// Plane, tile origin and row of a list entry; false if the tile lies outside its plane.
+__device__ __forceinline__ bool tile_of(const MatchArgs &a, unsigned long long e, Plane &pl, int &x0, int &y)
 {
-    for (;;) {
-        while (c.bits == 0u) {
-            c.w += nwarps;
-            if (c.w >= total) return false;
-            const uint32_t bits = a.ws.bitmap[c.w];
-            if (bits == 0u) continue;
-            __syncwarp();
-            if (lane == 0) a.ws.bitmap[c.w] = 0u;  // consumed: clear for the next call
-            decode_word(a, c.w, c);
-            c.bits = bits;
-        }
-        const int b = __ffs(c.bits) - 1;
-        c.bits &= c.bits - 1u;
-        x0 = (c.wi * 32 + b) * kTile;
-        y = c.y;
-        if (x0 < c.pl.Ws && y < c.pl.Hs) return true;
-    }
+    const int tile = (int)(e & 1023u);
+    y = (int)((e >> 10) & 0xffffu);
+    const int q = (int)((e >> 26) & 3u);
+    const int f = (int)(e >> 28);
+    plane_of(a, f, q, pl);
+    x0 = tile * kTile;
+    return x0 < pl.Ws && y < pl.Hs;
 }
 
-// Fixed windows: the loads of the next tile are issued before the current
-// tile is converted and computed, so memory latency overlaps compute.
-template <int WW, int WH>
-__device__ void roi_stream(const MatchArgs &a, const WarpStage &st, TileCursor &c, long long nwarps,
-                           long long total, int lane)
+__global__ void __launch_bounds__(256) tile_list_kernel(MatchArgs a)
 {
-    constexpr int sx = WW / 2, sy = WH / 2;
-    int xA = 0, yA = 0;
-    bool okA = next_tile(a, c, nwarps, total, lane, xA, yA);
-    Plane plA = c.pl;
-    uint32_t vA[WH];
-#pragma unroll
-    for (int r = 0; r < WH; ++r) vA[r] = 0u;
-    if (okA && yA - sy >= 0 && yA + sy < plA.Hs) load_tile<WH>(plA, xA, yA, lane, vA);
-    while (okA) {
-        int xB = 0, yB = 0;
-        const bool okB = next_tile(a, c, nwarps, total, lane, xB, yB);
-        const Plane plB = c.pl;
-        uint32_t vB[WH];
-#pragma unroll
-        for (int r = 0; r < WH; ++r) vB[r] = 0u;
-        if (okB && yB - sy >= 0 && yB + sy < plB.Hs) load_tile<WH>(plB, xB, yB, lane, vB);
-        // compute tile A
-        const int x = xA + 2 * lane;
-        uint64_t c0 = 0ull, c1 = 0ull;
-        if (yA - sy >= 0 && yA + sy < plA.Hs) {
-#pragma unroll
-            for (int r = 0; r < WH; ++r) store_quad(vA[r], st.even + r * kWordsMax, st.odd + r * kWordsMax, lane);
-            __syncwarp();
-            tile_codes<WW, WH>(st, lane, a.p.sentinel, c0, c1);
-            if (x - sx < 0 || x + sx >= plA.Ws) c0 = 0ull;
-            if (x + 1 - sx < 0 || x + 1 + sx >= plA.Ws) c1 = 0ull;
-            __syncwarp();
-        }
-        store_pair(plA, x, yA, c0, c1);
-        plA = plB;
-        xA = xB;
-        yA = yB;
-        okA = okB;
-#pragma unroll
-        for (int r = 0; r < WH; ++r) vA[r] = vB[r];
-    }
-}
-
-__global__ void __launch_bounds__(32 * kWarpsPerCta, 4) census_roi_kernel(MatchArgs a)
-{
-    extern __shared__ __align__(16) uint32_t stage_mem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const WarpStage st = warp_stage(stage_mem, warp, a.p.win_h);
+    __shared__ int warp_tot[8];
+    __shared__ int s_base;
     int nf = a.counts_in[0];
     nf = nf < 0 ? 0 : (nf > a.caps.max_frames ? a.caps.max_frames : nf);
     const long long total = (long long)nf * a.ws.bm_frame_words;
-    const long long gwarp = (long long)blockIdx.x * kWarpsPerCta + warp;
-    const long long nwarps = (long long)gridDim.x * kWarpsPerCta;
-    TileCursor c;
-    c.w = gwarp - nwarps;
-    c.bits = 0u;
-    const int ww = a.p.win_w, wh = a.p.win_h;
-    if (ww == 9 && wh == 7) {
-        roi_stream<9, 7>(a, st, c, nwarps, total, lane);
-    } else if (ww == 7 && wh == 7) {
-        roi_stream<7, 7>(a, st, c, nwarps, total, lane);
-    } else if (ww == 5 && wh == 5) {
-        roi_stream<5, 5>(a, st, c, nwarps, total, lane);
-    } else {
-        int x0, y;
-        while (next_tile(a, c, nwarps, total, lane, x0, y))
-            census_tile<0, 0>(c.pl, x0, y, ww, wh, a.p.sentinel, st);
+    const long long w0 = (long long)blockIdx.x * blockDim.x;
+    if (w0 >= total) return;  // uniform per CTA
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long w = w0 + tid;
+    uint32_t bits = 0u;
+    if (w < total) {
+        bits = a.ws.bitmap[w];
+        if (bits) a.ws.bitmap[w] = 0u;  // consumed: clear for the next call
     }
+    const int cnt = __popc(bits);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    int wpre = 0, tot = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        wpre += i < warp ? warp_tot[i] : 0;
+        tot += warp_tot[i];
+    }
+    if (tid == 0) s_base = tot ? atomicAdd(&a.ws.counts->n_tiles, tot) : 0;
+    __syncthreads();
+    if (bits == 0u) return;
+    const int f = (int)(w / a.ws.bm_frame_words);
+    int r = (int)(w - (long long)f * a.ws.bm_frame_words);
+    int q = 0;
+    while (q < 3 && r >= a.ws.bm_plane_off[q + 1]) ++q;
+    r -= a.ws.bm_plane_off[q];
+    const int y = r / a.ws.bm_row_words[q];
+    const int wi = r - y * a.ws.bm_row_words[q];
+    int pos = s_base + wpre + incl - cnt;
+    while (bits) {
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1u;
+        a.ws.tiles[pos++] = tile_entry(f, q, y, wi * 32 + b);
+    }
+}
+
+// Fixed windows: warp w takes list entries 2p and 2p + 1 (p = w, w + warps, ...),
+// the first for lanes 0-15 and the second for lanes 16-31, so both halves run
+// the same instructions in lockstep.  MODE: 0 = 4 CTAs per SM (64 registers),
+// otherwise 3 CTAs per SM.
+template <int WW, int WH, int MODE>
+__global__ void __launch_bounds__(256, MODE == 0 ? 4 : 3) census_roi4_kernel(MatchArgs a)
+{
+    const int lane = threadIdx.x & 31, hl = lane & 15;
+    const int n = a.ws.counts->n_tiles;
+    const int npairs = (n + 1) >> 1;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int sentinel = a.p.sentinel;
+    for (int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < npairs; p += nw) {
+        const int t = 2 * p + (lane >> 4);
+        Plane pl;
+        int x0, y;
+        const bool ok = tile_of(a, a.ws.tiles[t < n ? t : 2 * p], pl, x0, y) && t < n;
+        uint32_t v[WH][3];
+        Job4 j;
+        start_tile4<WW, WH>(pl, x0, y, hl, ok, v, j);
+        finish_tile4<WW, WH>(v, j, sentinel);
+    }
+}
+
+// Any other window: a warp per listed tile, rows staged in shared memory.
+__global__ void __launch_bounds__(32 * kWarpsPerCta) census_roi_kernel(MatchArgs a)
+{
+    extern __shared__ __align__(16) uint32_t stage_mem[];
+    const int warp = threadIdx.x >> 5;
+    const WarpStage st = warp_stage(stage_mem, warp, a.p.win_h);
+    const int n = a.ws.counts->n_tiles;
+    const int nw = gridDim.x * kWarpsPerCta;
+    for (int t = blockIdx.x * kWarpsPerCta + warp; t < n; t += nw) {
+        Plane pl;
+        int x0, y;
+        if (tile_of(a, a.ws.tiles[t], pl, x0, y))
+            census_tile<0, 0>(pl, x0, y, a.p.win_w, a.p.win_h, a.p.sentinel, st);
+    }
+}
+
+template <typename K>
+int resident_ctas(K kernel, int threads, size_t smem)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        n = 1;
+    }
+    return n;
 }
 
 }  // namespace
@@ -423,14 +626,74 @@ cudaError_t launch_census_single(const uint8_t *img, int W, int H, int pitch, in
     pl.opitch = out_pitch;
     pl.vec_ok = (out_pitch % 2 == 0) && ((reinterpret_cast<uintptr_t>(out) & 15u) == 0);
     pl.vec_load = (k == 1 || k == 2) && (pitch % 4 == 0) && ((reinterpret_cast<uintptr_t>(img) & 7u) == 0);
-    dim3 grid(ceil_div_nn(pl.Ws, kTile), ceil_div_nn(pl.Hs, kWarpsPerCta));
-    census_full_kernel<<<grid, 32 * kWarpsPerCta, census_smem_bytes(win_h), s>>>(pl, win_w, win_h, sentinel);
+    const dim3 grid4(ceil_div_nn(pl.Ws, kTile), ceil_div_nn(pl.Hs, 16));
+    if (win_w == 9 && win_h == 7) {
+        census_full4_kernel<9, 7><<<grid4, 256, 0, s>>>(pl, sentinel);
+    } else if (win_w == 7 && win_h == 7) {
+        census_full4_kernel<7, 7><<<grid4, 256, 0, s>>>(pl, sentinel);
+    } else if (win_w == 5 && win_h == 5) {
+        census_full4_kernel<5, 5><<<grid4, 256, 0, s>>>(pl, sentinel);
+    } else {
+        dim3 grid(ceil_div_nn(pl.Ws, kTile), ceil_div_nn(pl.Hs, kWarpsPerCta));
+        census_full_kernel<<<grid, 32 * kWarpsPerCta, census_smem_bytes(win_h), s>>>(pl, win_w, win_h, sentinel);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_census_roi(const MatchArgs &a, int grid, cudaStream_t s)
+// Variant of the fixed-window ROI kernel (census_roi4_kernel MODE); the
+// default is 0, CTM_CENSUS_MODE (0 or 1) overrides it for tuning.
+static int roi_mode()
 {
-    census_roi_kernel<<<grid, 32 * kWarpsPerCta, census_smem_bytes(a.p.win_h), s>>>(a);
+    static const int v = [] {
+        const char *e = getenv("CTM_CENSUS_MODE");
+        return (e && e[0] == '1' && e[1] == 0) ? 1 : 0;
+    }();
+    return v;
+}
+
+template <int WW, int WH>
+static int roi4_ctas(int mode)
+{
+    static const int n0 = resident_ctas(census_roi4_kernel<WW, WH, 0>, 256, 0);
+    static const int n1 = resident_ctas(census_roi4_kernel<WW, WH, 1>, 256, 0);
+    return mode == 0 ? n0 : n1;
+}
+
+int census_roi_ctas_per_sm(int win_w, int win_h)
+{
+    const int mode = roi_mode();
+    if (win_w == 9 && win_h == 7) return roi4_ctas<9, 7>(mode);
+    if (win_w == 7 && win_h == 7) return roi4_ctas<7, 7>(mode);
+    if (win_w == 5 && win_h == 5) return roi4_ctas<5, 5>(mode);
+    static const int ng = resident_ctas(census_roi_kernel, 32 * kWarpsPerCta, census_smem_bytes(kMaxWin));
+    return ng;
+}
+
+template <int WW, int WH>
+static void launch_roi4(const MatchArgs &a, int grid, cudaStream_t s)
+{
+    if (roi_mode() == 0)
+        census_roi4_kernel<WW, WH, 0><<<grid, 256, 0, s>>>(a);
+    else
+        census_roi4_kernel<WW, WH, 1><<<grid, 256, 0, s>>>(a);
+}
+
+cudaError_t launch_census_roi(const MatchArgs &a, int sm_count, cudaStream_t s)
+{
+    const long long words = (long long)a.caps.max_frames * a.ws.bm_frame_words;
+    const int list_grid = (int)((words + 255) / 256);
+    if (list_grid > 0) tile_list_kernel<<<list_grid, 256, 0, s>>>(a);
+    const int ww = a.p.win_w, wh = a.p.win_h;
+    const int grid = sm_count * census_roi_ctas_per_sm(ww, wh);
+    if (ww == 9 && wh == 7) {
+        launch_roi4<9, 7>(a, grid, s);
+    } else if (ww == 7 && wh == 7) {
+        launch_roi4<7, 7>(a, grid, s);
+    } else if (ww == 5 && wh == 5) {
+        launch_roi4<5, 5>(a, grid, s);
+    } else {
+        census_roi_kernel<<<grid, 32 * kWarpsPerCta, census_smem_bytes(wh), s>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -27,6 +27,7 @@ struct Counts {
     unsigned long long evals;
     int n_big;       // searchable blocks queued from the front (large work)
     int n_small;     // searchable blocks queued from the back (small work)
+    int n_tiles;     // census tiles listed for the region-of-interest census
 };
 
 // Planned box (device).
@@ -79,6 +80,7 @@ struct Workspace {
     // census demand bitmap: one bit per 64-pixel tile of a plane row, per frame
     // planes in the order L1, R1, Lk, Rk; words = 32 tiles
     uint32_t *bitmap;
+    unsigned long long *tiles;  // [max_frames * bm_frame_words * 32] marked tiles, packed (census.cu)
     long long bm_frame_words;
     int bm_plane_off[5];       // word offset of each plane within a frame (+ end)
     int bm_row_words[4];       // words per row of each plane
@@ -139,7 +141,11 @@ constexpr int kCensusTilePx = 64;   // pixels per bitmap bit (one warp tile)
 cudaError_t launch_census_single(const uint8_t *img, int W, int H, int pitch, int k, int win_w,
                                  int win_h, int sentinel, uint64_t *out, long long out_pitch,
                                  cudaStream_t s);
-cudaError_t launch_census_roi(const MatchArgs &a, int grid, cudaStream_t s);
+// Region-of-interest census over the marked tiles, `ctas_per_sm` resident CTAs
+// per SM (census_roi_ctas_per_sm; the first call queries the occupancy, so make
+// it before any stream capture).
+int census_roi_ctas_per_sm(int win_w, int win_h);
+cudaError_t launch_census_roi(const MatchArgs &a, int sm_count, cudaStream_t s);
 size_t census_smem_bytes(int win_h);
 
 // Planning (plan.cu)

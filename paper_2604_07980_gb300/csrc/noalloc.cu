@@ -76,6 +76,9 @@ int setup_device(int dev)
     }
     st.base = static_cast<unsigned char *>(ptr);
     st.sm_count = sms;
+    ctm::census_roi_ctas_per_sm(9, 7);  // occupancy queries outside any capture
+    ctm::census_roi_ctas_per_sm(7, 7);
+    ctm::census_roi_ctas_per_sm(5, 5);
     st.ready = true;
     return CTM_OK;
 }
@@ -144,6 +147,7 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
     const size_t o_frames = take(sizeof(ctm_frame));
     const size_t o_cin = take(sizeof(int) * 4);
     const size_t o_bm = take(sizeof(uint32_t) * (size_t)plane_off[4]);
+    const size_t o_tiles = take(sizeof(unsigned long long) * 32 * (size_t)plane_off[4]);
     if (off > kScratchBytes) return CTM_ETOOBIG;
 
     unsigned char *b = ds.base;
@@ -168,6 +172,7 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
     ws.frames = reinterpret_cast<ctm_frame *>(b + o_frames);
     ws.counts_in = reinterpret_cast<int *>(b + o_cin);
     ws.bitmap = reinterpret_cast<uint32_t *>(b + o_bm);
+    ws.tiles = reinterpret_cast<unsigned long long *>(b + o_tiles);
     ws.bm_frame_words = plane_off[4];
     for (int q = 0; q < 5; ++q) ws.bm_plane_off[q] = plane_off[q];
     for (int q = 0; q < 4; ++q) ws.bm_row_words[q] = words_q[q];
@@ -200,7 +205,7 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
     if (e == cudaSuccess) e = launch_plan(a, s);
     if (e == cudaSuccess) e = launch_sample(a, s);
     if (e == cudaSuccess) e = launch_mark(a, s);
-    if (e == cudaSuccess) e = launch_census_roi(a, ds.sm_count * 4, s);
+    if (e == cudaSuccess) e = launch_census_roi(a, ds.sm_count, s);
     const long long blocks_ub = (long long)std::max(n_boxes, 1) * std::max(p->grid_g * p->grid_g, 1);
     const int grid = (int)std::min<long long>((long long)ds.sm_count * ctas, blocks_ub);
     if (e == cudaSuccess) e = launch_match_persistent(a, threads, grid, s);
