@@ -275,6 +275,7 @@ def main():
     st = ctx.stats()
     evals_per_step = st["cost_evals"]
     n_blocks = st["n_blocks"]
+    census_tiles = st["census_tiles"]
 
     def barrier():
         if dist is not None:
@@ -391,6 +392,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "frames": len(w.frames), "width": 1920, "height": 1200,
                        "boxes": w.n_boxes, "blocks": n_blocks, "evals_per_step": evals_per_step,
+                       "census_tiles": census_tiles,
                        "census": "9x7 u64 + sentinel", "graph": True,
                        "l2": "inputs larger than L2 (147 MB images + 1.5 GB census planes per step)",
                        "parallelism": f"frames sharded, {world} rank(s), no collective"},

@@ -59,7 +59,7 @@ class ctm_debug(ctypes.Structure):
 
 class ctm_stats(ctypes.Structure):
     _fields_ = [("cost_evals", ctypes.c_uint64), ("n_blocks", ctypes.c_int32), ("n_boxes", ctypes.c_int32),
-                ("error", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("error", ctypes.c_int32), ("census_tiles", ctypes.c_int32)]
 
 
 class ctm_server_config(ctypes.Structure):
@@ -351,7 +351,7 @@ class Context:
         s = ctm_stats()
         _check(lib().ctm_get_stats(self._h, ctypes.byref(s), _stream(stream)), "ctm_get_stats")
         return {"cost_evals": int(s.cost_evals), "n_blocks": int(s.n_blocks), "n_boxes": int(s.n_boxes),
-                "error": int(s.error)}
+                "error": int(s.error), "census_tiles": int(s.census_tiles)}
 
 
 class DeviceBatch:

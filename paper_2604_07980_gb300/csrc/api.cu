@@ -247,6 +247,7 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
     for (int q = 0; q < 4; ++q) plane_off[q + 1] = plane_off[q] + rows_q[q] * words_q[q];
     const size_t o_bm = take(sizeof(uint32_t) * (size_t)plane_off[4] * max_frames);
     const size_t o_tiles = take(sizeof(unsigned long long) * 32 * (size_t)plane_off[4] * max_frames);
+    const size_t o_planes = take(sizeof(PlaneDesc) * 4 * (size_t)max_frames);
     if (cudaMalloc(&ctx->dev_mem, off) != cudaSuccess) {
         cudaGetLastError();
         delete ctx;
@@ -275,6 +276,7 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
     ws.counts_in = reinterpret_cast<int *>(base + o_cin);
     ws.bitmap = reinterpret_cast<uint32_t *>(base + o_bm);
     ws.tiles = reinterpret_cast<unsigned long long *>(base + o_tiles);
+    ws.planes = reinterpret_cast<PlaneDesc *>(base + o_planes);
     ws.bm_frame_words = plane_off[4];
     for (int q = 0; q < 5; ++q) ws.bm_plane_off[q] = plane_off[q];
     for (int q = 0; q < 4; ++q) ws.bm_row_words[q] = words_q[q];
@@ -548,7 +550,7 @@ int ctm_get_stats(ctm_ctx *ctx, ctm_stats *out, ctm_stream stream)
     out->n_blocks = c.n_blocks;
     out->n_boxes = c.n_boxes;
     out->error = c.error;
-    out->reserved = 0;
+    out->census_tiles = c.n_tiles;
     return CTM_OK;
 }
 

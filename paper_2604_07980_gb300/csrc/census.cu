@@ -229,56 +229,42 @@ __device__ __forceinline__ void store_pair(const Plane &pl, int x, int y, uint64
 // memory is involved.  Pixel pairs (x, x+1) and (x+2, x+3) are compared two at
 // a time in the 16-bit halves of a word (codes4).
 
-// Raw window-row bytes of one lane: v[r][q] holds I_k(x - 4 + 4q .. x - 1 + 4q)
-// of window row r, little-endian; out-of-grid pixels read as 0 (they only
-// feed pixels whose codes are zeroed).  Lanes whose twelve pixels lie inside
-// a word-aligned image take word loads, the others (image borders, other
+// Twelve pixels I_k(x - 4 .. x + 7) of grid row `yr` for this lane, as three
+// little-endian words; pixels outside the grid read as 0 (they only feed
+// pixels whose codes are zeroed).  Lanes whose twelve pixels lie inside a
+// word-aligned image take word loads, the others (image borders, other
 // decimations or alignments) byte loads.
-template <int WH>
-__device__ __forceinline__ void load_rows4(const Plane &pl, int x0, int y, int hl, uint32_t (&v)[WH][3])
+__device__ __forceinline__ void load_row12(const PlaneDesc &d, bool inside, int x, int yr, uint32_t (&v)[3])
 {
-    constexpr int sy = WH / 2;
-    const int x = x0 + 4 * hl;
-    // word loads where this lane's twelve pixels lie inside the row
-    const bool inside = pl.vec_load && x >= 4 && (pl.k == 1 ? x + 8 <= pl.W : 2 * x + 16 <= pl.W);
-    if (inside && pl.k == 1) {
-        const uint8_t *p = pl.img + (long long)(y - sy) * pl.pitch + (x - 4);
-#pragma unroll
-        for (int r = 0; r < WH; ++r) {
-            const uint32_t *q = reinterpret_cast<const uint32_t *>(p + (long long)r * pl.pitch);
-            v[r][0] = __ldg(q);
-            v[r][1] = __ldg(q + 1);
-            v[r][2] = __ldg(q + 2);
-        }
+    if (inside && d.k == 1) {
+        const uint32_t *q = reinterpret_cast<const uint32_t *>(d.img + (long long)yr * d.pitch + (x - 4));
+        v[0] = __ldg(q);
+        v[1] = __ldg(q + 1);
+        v[2] = __ldg(q + 2);
     } else if (inside) {  // k == 2: every other source byte
-        const uint8_t *p = pl.img + 2LL * (y - sy) * pl.pitch + 2 * (x - 4);
-#pragma unroll
-        for (int r = 0; r < WH; ++r) {
-            const uint2 *q = reinterpret_cast<const uint2 *>(p + 2LL * r * pl.pitch);
-            const uint2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
-            v[r][0] = __byte_perm(a.x, a.y, 0x6420);
-            v[r][1] = __byte_perm(b.x, b.y, 0x6420);
-            v[r][2] = __byte_perm(c.x, c.y, 0x6420);
-        }
+        const uint2 *q = reinterpret_cast<const uint2 *>(d.img + 2LL * yr * d.pitch + 2 * (x - 4));
+        const uint2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+        v[0] = __byte_perm(a.x, a.y, 0x6420);
+        v[1] = __byte_perm(b.x, b.y, 0x6420);
+        v[2] = __byte_perm(c.x, c.y, 0x6420);
     } else {
+        const uint8_t *row = d.img + (long long)d.k * yr * d.pitch;
+        uint32_t w[3] = {0u, 0u, 0u};
 #pragma unroll
-        for (int r = 0; r < WH; ++r) {
-            const uint8_t *row = pl.img + (long long)pl.k * (y - sy + r) * pl.pitch;
-            uint32_t w[3] = {0u, 0u, 0u};
-#pragma unroll
-            for (int t = 0; t < 12; ++t) {
-                const int xs = x - 4 + t;
-                const uint32_t b = (xs >= 0 && xs < pl.Ws) ? (uint32_t)__ldg(row + (long long)pl.k * xs) : 0u;
-                w[t >> 2] |= b << (8 * (t & 3));
-            }
-            v[r][0] = w[0];
-            v[r][1] = w[1];
-            v[r][2] = w[2];
+        for (int t = 0; t < 12; ++t) {
+            const int xs = x - 4 + t;
+            const uint32_t b = (xs >= 0 && xs < d.Ws) ? (uint32_t)__ldg(row + (long long)d.k * xs) : 0u;
+            w[t >> 2] |= b << (8 * (t & 3));
         }
+        v[0] = w[0];
+        v[1] = w[1];
+        v[2] = w[2];
     }
 }
 
-// Codes of pixels x .. x+3 from the raw rows (bit layout as tile_codes).
+// Codes of pixels x .. x+3 of row y of plane d (4 consecutive pixels per lane;
+// bit layout as tile_codes), stored to the plane; `ok` false: this lane has
+// no tile and stores nothing.  All 32 lanes of the warp must call it together.
 //
 // The compares run on the integer multiply-add pipe: with both pixels of a
 // pair in the two 16-bit halves of a word w (plain values, upper bytes zero),
@@ -287,122 +273,143 @@ __device__ __forceinline__ void load_rows4(const Plane &pl, int x0, int y, int h
 // s <= 7; so no carry crosses the halves and bit 8 + s of each half is
 // [nb > c].  Code bit p = 8 a + s is taken from bit 8 + s (and 24 + s) of e
 // into accumulator a with one LOP3; accumulator a ends up holding code byte a
-// of the low pixel in its byte 1 and of the high pixel in its byte 3.
+// of the low pixel in its byte 1 and of the high pixel in its byte 3.  All
+// window rows are loaded before the first is used.
 template <int WW, int WH>
-__device__ __forceinline__ void codes4(const uint32_t (&v)[WH][3], int sentinel, uint64_t (&c)[4])
+__device__ __forceinline__ void census4(const PlaneDesc &d, int x0, int y, int hl, bool ok, int sentinel)
 {
     constexpr int sx = WW / 2, sy = WH / 2;
     constexpr int n = WW * WH;
     constexpr int OFF = 4 - sx;  // byte index of the window's left column for pixel x
-    uint32_t accA[8], accB[8];
+    const unsigned full = 0xffffffffu;
+    const int x = x0 + 4 * hl;
+    const bool active = ok && y - sy >= 0 && y + sy < d.Hs;
+    const bool inside = d.vec_load && x >= 4 && (d.k == 1 ? x + 8 <= d.W : 2 * x + 16 <= d.W);
+    // one load scheme for the whole warp where possible (a uniform branch, so
+    // the other schemes are not executed predicated off)
+    uint32_t rows[WH][3];
+    if (__all_sync(full, !active || (inside && d.k == 1))) {
+        if (active) {
+            const uint8_t *p = d.img + (long long)(y - sy) * d.pitch + (x - 4);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) accA[q] = accB[q] = 0u;
-    if (sentinel) {
-        accA[n >> 3] = (0x100u << (n & 7)) | (0x1000000u << (n & 7));
-        accB[n >> 3] = accA[n >> 3];
-    }
-    const uint32_t cA = __byte_perm(v[sy][1], 0u, 0x4140);  // pixels x, x+1
-    const uint32_t cB = __byte_perm(v[sy][1], 0u, 0x4342);  // pixels x+2, x+3
-    uint32_t KA[8], KB[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const uint32_t h = 0x10000u - (0x100u << q) - 1u;
-        KA[q] = (h | (h << 16)) - (cA << q);
-        KB[q] = (h | (h << 16)) - (cB << q);
-    }
-#pragma unroll
-    for (int j = 0; j < WH; ++j) {
-        // w[t] = (b[t], b[t+1]) in the two halves, t = 0 .. 10
-        uint32_t w[11];
-        const uint32_t s1 = __funnelshift_r(v[j][0], v[j][1], 8);  // b1 .. b4
-        const uint32_t s2 = __funnelshift_r(v[j][1], v[j][2], 8);  // b5 .. b8
-        w[0] = __byte_perm(v[j][0], 0u, 0x4140);
-        w[1] = __byte_perm(s1, 0u, 0x4140);
-        w[2] = __byte_perm(v[j][0], 0u, 0x4342);
-        w[3] = __byte_perm(s1, 0u, 0x4342);
-        w[4] = __byte_perm(v[j][1], 0u, 0x4140);
-        w[5] = __byte_perm(s2, 0u, 0x4140);
-        w[6] = __byte_perm(v[j][1], 0u, 0x4342);
-        w[7] = __byte_perm(s2, 0u, 0x4342);
-        w[8] = __byte_perm(v[j][2], 0u, 0x4140);
-        w[9] = __byte_perm(v[j][2], 0u, 0x4241);
-        w[10] = __byte_perm(v[j][2], 0u, 0x4342);
-#pragma unroll
-        for (int i = 0; i < WW; ++i) {
-            const int p = n - 1 - (j * WW + i);  // code bit of this window offset
-            const int q = p & 7;
-            const uint32_t pos = (0x100u << q) | (0x1000000u << q);
-            accA[p >> 3] |= (w[OFF + i] * (1u << q) + KA[q]) & pos;
-            accB[p >> 3] |= (w[OFF + i + 2] * (1u << q) + KB[q]) & pos;
+            for (int r = 0; r < WH; ++r) {
+                const uint32_t *q = reinterpret_cast<const uint32_t *>(p + (long long)r * d.pitch);
+                rows[r][0] = __ldg(q);
+                rows[r][1] = __ldg(q + 1);
+                rows[r][2] = __ldg(q + 2);
+            }
         }
-    }
-    uint32_t tA[4], tB[4];  // code bytes (2q, 2q+1) of the low pixel, then of the high pixel
+    } else if (__all_sync(full, !active || (inside && d.k == 2))) {
+        if (active) {
+            const uint8_t *p = d.img + 2LL * (y - sy) * d.pitch + 2 * (x - 4);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        tA[q] = __byte_perm(accA[2 * q], accA[2 * q + 1], 0x7351);
-        tB[q] = __byte_perm(accB[2 * q], accB[2 * q + 1], 0x7351);
-    }
-    c[0] = ((uint64_t)__byte_perm(tA[2], tA[3], 0x5410) << 32) | __byte_perm(tA[0], tA[1], 0x5410);
-    c[1] = ((uint64_t)__byte_perm(tA[2], tA[3], 0x7632) << 32) | __byte_perm(tA[0], tA[1], 0x7632);
-    c[2] = ((uint64_t)__byte_perm(tB[2], tB[3], 0x5410) << 32) | __byte_perm(tB[0], tB[1], 0x5410);
-    c[3] = ((uint64_t)__byte_perm(tB[2], tB[3], 0x7632) << 32) | __byte_perm(tB[0], tB[1], 0x7632);
-}
-
-// One lane's part of a tile between its loads and its stores.
-struct Job4 {
-    uint64_t *dst;  // code of pixel x
-    int x, Ws;
-    bool row_ok, vec_ok;
-};
-
-template <int WW, int WH>
-__device__ __forceinline__ void start_tile4(const Plane &pl, int x0, int y, int hl, bool ok, uint32_t (&v)[WH][3],
-                                            Job4 &j)
-{
-    constexpr int sy = WH / 2;
-    j.x = x0 + 4 * hl;
-    j.Ws = ok ? pl.Ws : 0;  // no tile: nothing is stored
-    j.row_ok = ok && y - sy >= 0 && y + sy < pl.Hs;
-    j.vec_ok = pl.vec_ok != 0;
-    j.dst = pl.out + (long long)y * pl.opitch + j.x;
-    if (j.row_ok) {
-        load_rows4<WH>(pl, x0, y, hl, v);
-    } else {
+            for (int r = 0; r < WH; ++r) {
+                const uint2 *q = reinterpret_cast<const uint2 *>(p + 2LL * r * d.pitch);
+                const uint2 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+                rows[r][0] = __byte_perm(a.x, a.y, 0x6420);
+                rows[r][1] = __byte_perm(b.x, b.y, 0x6420);
+                rows[r][2] = __byte_perm(c.x, c.y, 0x6420);
+            }
+        }
+    } else if (active) {
 #pragma unroll
-        for (int r = 0; r < WH; ++r) v[r][0] = v[r][1] = v[r][2] = 0u;
+        for (int r = 0; r < WH; ++r) load_row12(d, inside, x, y - sy + r, rows[r]);
     }
-}
-
-template <int WW, int WH>
-__device__ __forceinline__ void finish_tile4(const uint32_t (&v)[WH][3], const Job4 &j, int sentinel)
-{
-    constexpr int sx = WW / 2;
     uint64_t c[4] = {0ull, 0ull, 0ull, 0ull};
-    if (j.row_ok) codes4<WW, WH>(v, sentinel, c);
+    if (active) {
+        const uint32_t *vc = rows[sy];
+        uint32_t accA[8], accB[8];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-        if (!(j.row_ok && j.x + q - sx >= 0 && j.x + q + sx < j.Ws)) c[q] = 0ull;
-    if (j.vec_ok && j.x + 3 < j.Ws) {
-        reinterpret_cast<ulonglong2 *>(j.dst)[0] = make_ulonglong2(c[0], c[1]);
-        reinterpret_cast<ulonglong2 *>(j.dst)[1] = make_ulonglong2(c[2], c[3]);
+        for (int q = 0; q < 8; ++q) accA[q] = accB[q] = 0u;
+        if (sentinel) {
+            accA[n >> 3] = (0x100u << (n & 7)) | (0x1000000u << (n & 7));
+            accB[n >> 3] = accA[n >> 3];
+        }
+        const uint32_t cA = __byte_perm(vc[1], 0u, 0x4140);  // pixels x, x+1
+        const uint32_t cB = __byte_perm(vc[1], 0u, 0x4342);  // pixels x+2, x+3
+        uint32_t KA[8], KB[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const uint32_t h = 0x10000u - (0x100u << q) - 1u;
+            KA[q] = (h | (h << 16)) - (cA << q);
+            KB[q] = (h | (h << 16)) - (cB << q);
+        }
+#pragma unroll
+        for (int j = 0; j < WH; ++j) {
+            const uint32_t *v = rows[j];
+            // w[t] = (b[t], b[t+1]) in the two halves, t = 0 .. 10
+            uint32_t w[11];
+            const uint32_t s1 = __funnelshift_r(v[0], v[1], 8);  // b1 .. b4
+            const uint32_t s2 = __funnelshift_r(v[1], v[2], 8);  // b5 .. b8
+            w[0] = __byte_perm(v[0], 0u, 0x4140);
+            w[1] = __byte_perm(s1, 0u, 0x4140);
+            w[2] = __byte_perm(v[0], 0u, 0x4342);
+            w[3] = __byte_perm(s1, 0u, 0x4342);
+            w[4] = __byte_perm(v[1], 0u, 0x4140);
+            w[5] = __byte_perm(s2, 0u, 0x4140);
+            w[6] = __byte_perm(v[1], 0u, 0x4342);
+            w[7] = __byte_perm(s2, 0u, 0x4342);
+            w[8] = __byte_perm(v[2], 0u, 0x4140);
+            w[9] = __byte_perm(v[2], 0u, 0x4241);
+            w[10] = __byte_perm(v[2], 0u, 0x4342);
+#pragma unroll
+            for (int i = 0; i < WW; ++i) {
+                const int p = n - 1 - (j * WW + i);  // code bit of this window offset
+                const int q = p & 7;
+                const uint32_t pos = (0x100u << q) | (0x1000000u << q);
+                accA[p >> 3] |= (w[OFF + i] * (1u << q) + KA[q]) & pos;
+                accB[p >> 3] |= (w[OFF + i + 2] * (1u << q) + KB[q]) & pos;
+            }
+        }
+        uint32_t tA[4], tB[4];  // code bytes (2q, 2q+1) of the low pixel, then of the high pixel
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            tA[q] = __byte_perm(accA[2 * q], accA[2 * q + 1], 0x7351);
+            tB[q] = __byte_perm(accB[2 * q], accB[2 * q + 1], 0x7351);
+        }
+        c[0] = ((uint64_t)__byte_perm(tA[2], tA[3], 0x5410) << 32) | __byte_perm(tA[0], tA[1], 0x5410);
+        c[1] = ((uint64_t)__byte_perm(tA[2], tA[3], 0x7632) << 32) | __byte_perm(tA[0], tA[1], 0x7632);
+        c[2] = ((uint64_t)__byte_perm(tB[2], tB[3], 0x5410) << 32) | __byte_perm(tB[0], tB[1], 0x5410);
+        c[3] = ((uint64_t)__byte_perm(tB[2], tB[3], 0x7632) << 32) | __byte_perm(tB[0], tB[1], 0x7632);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (x + q - sx < 0 || x + q + sx >= d.Ws) c[q] = 0ull;
+    }
+    if (!ok) return;
+    uint64_t *dst = d.out + (long long)y * d.opitch + x;
+    if (x + 3 < d.Ws && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
+        reinterpret_cast<ulonglong2 *>(dst)[0] = make_ulonglong2(c[0], c[1]);
+        reinterpret_cast<ulonglong2 *>(dst)[1] = make_ulonglong2(c[2], c[3]);
     } else {
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            if (j.x + q < j.Ws) j.dst[q] = c[q];
+            if (x + q < d.Ws) dst[q] = c[q];
     }
+}
+
+__device__ __forceinline__ PlaneDesc desc_of(const Plane &pl)
+{
+    PlaneDesc d;
+    d.img = pl.img;
+    d.out = pl.out;
+    d.W = pl.W;
+    d.pitch = pl.pitch;
+    d.k = pl.k;
+    d.Ws = pl.Ws;
+    d.Hs = pl.Hs;
+    d.opitch = (int)pl.opitch;
+    d.vec_load = pl.vec_load;
+    d.pad = 0;
+    return d;
 }
 
 // Full image, fixed window: half-warp h of CTA (bx, by) takes tile bx of row by * 16 + h.
 template <int WW, int WH>
 __global__ void __launch_bounds__(256) census_full4_kernel(Plane pl, int sentinel)
 {
-    const int hl = threadIdx.x & 15;
     const int y = blockIdx.y * 16 + (threadIdx.x >> 4);
-    if (y >= pl.Hs) return;
-    uint32_t v[WH][3];
-    Job4 j;
-    start_tile4<WW, WH>(pl, blockIdx.x * kTile, y, hl, true, v, j);
-    finish_tile4<WW, WH>(v, j, sentinel);
+    // every lane reaches census4 (its load scheme is chosen warp-wide)
+    census4<WW, WH>(desc_of(pl), blockIdx.x * kTile, y, threadIdx.x & 15, y < pl.Hs, sentinel);
 }
 
 // One 64-pixel tile of row y starting at x0 (x0 a multiple of 64).
@@ -473,34 +480,15 @@ __device__ __forceinline__ unsigned long long tile_entry(int f, int q, int y, in
            (unsigned long long)tile;
 }
 
-__device__ __forceinline__ void plane_of(const MatchArgs &a, int f, int q, Plane &pl)
-{
-    const ctm_frame fr = a.frames[f];
-    pl.img = (q & 1) ? fr.right : fr.left;
-    pl.W = fr.width;
-    pl.H = fr.height;
-    pl.pitch = fr.pitch;
-    pl.k = q < 2 ? 1 : a.p.close_factor;
-    pl.Ws = ceil_div_nn(fr.width, pl.k);
-    pl.Hs = ceil_div_nn(fr.height, pl.k);
-    uint64_t *base = a.ws.census + (long long)f * a.ws.frame_stride;
-    pl.out = q < 2 ? base + q * a.ws.plane1_elems : base + 2 * a.ws.plane1_elems + (q - 2) * a.ws.planek_elems;
-    pl.opitch = q < 2 ? a.ws.pitch1 : a.ws.pitchk;
-    pl.vec_ok = 1;  // workspace planes: 256-byte aligned, pitch a multiple of 32
-    pl.vec_load = (pl.k == 1 || pl.k == 2) && (fr.pitch % 4 == 0) &&
-                  ((reinterpret_cast<uintptr_t>(pl.img) & 7u) == 0);
-}
-
-// Plane, tile origin and row of a list entry; false if the tile lies outside its plane.
-__device__ __forceinline__ bool tile_of(const MatchArgs &a, unsigned long long e, Plane &pl, int &x0, int &y)
+// Plane descriptor, tile origin and row of a list entry; false if the tile lies
+// outside its plane.
+__device__ __forceinline__ bool tile_of(const MatchArgs &a, unsigned long long e, PlaneDesc &d, int &x0, int &y)
 {
     const int tile = (int)(e & 1023u);
     y = (int)((e >> 10) & 0xffffu);
-    const int q = (int)((e >> 26) & 3u);
-    const int f = (int)(e >> 28);
-    plane_of(a, f, q, pl);
+    d = a.ws.planes[e >> 26];  // frame * 4 + plane
     x0 = tile * kTile;
-    return x0 < pl.Ws && y < pl.Hs;
+    return x0 < d.Ws && y < d.Hs;
 }
 
 __global__ void __launch_bounds__(256) tile_list_kernel(MatchArgs a)
@@ -566,13 +554,10 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 3) census_roi4_kernel(Mat
     const int sentinel = a.p.sentinel;
     for (int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < npairs; p += nw) {
         const int t = 2 * p + (lane >> 4);
-        Plane pl;
+        PlaneDesc d;
         int x0, y;
-        const bool ok = tile_of(a, a.ws.tiles[t < n ? t : 2 * p], pl, x0, y) && t < n;
-        uint32_t v[WH][3];
-        Job4 j;
-        start_tile4<WW, WH>(pl, x0, y, hl, ok, v, j);
-        finish_tile4<WW, WH>(v, j, sentinel);
+        const bool ok = tile_of(a, a.ws.tiles[t < n ? t : 2 * p], d, x0, y) && t < n;
+        census4<WW, WH>(d, x0, y, hl, ok, sentinel);
     }
 }
 
@@ -585,10 +570,22 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) census_roi_kernel(MatchArgs
     const int n = a.ws.counts->n_tiles;
     const int nw = gridDim.x * kWarpsPerCta;
     for (int t = blockIdx.x * kWarpsPerCta + warp; t < n; t += nw) {
-        Plane pl;
+        PlaneDesc d;
         int x0, y;
-        if (tile_of(a, a.ws.tiles[t], pl, x0, y))
-            census_tile<0, 0>(pl, x0, y, a.p.win_w, a.p.win_h, a.p.sentinel, st);
+        if (!tile_of(a, a.ws.tiles[t], d, x0, y)) continue;
+        Plane pl;
+        pl.img = d.img;
+        pl.W = d.W;
+        pl.H = 0;
+        pl.pitch = d.pitch;
+        pl.k = d.k;
+        pl.Ws = d.Ws;
+        pl.Hs = d.Hs;
+        pl.out = d.out;
+        pl.opitch = d.opitch;
+        pl.vec_ok = 1;  // workspace planes: 256-byte aligned, pitch a multiple of 32
+        pl.vec_load = d.vec_load;
+        census_tile<0, 0>(pl, x0, y, a.p.win_w, a.p.win_h, a.p.sentinel, st);
     }
 }
 

@@ -59,6 +59,18 @@ struct BlockResult {
 };
 
 // Device workspace of a context.
+// One census plane of one frame (L1, R1, Lk, Rk), written by the planner so the
+// census kernels need no per-tile divisions or address arithmetic.
+struct PlaneDesc {
+    const uint8_t *img;  // source image (full resolution)
+    uint64_t *out;       // census plane
+    int W, pitch, k;     // source width, row pitch (bytes), decimation
+    int Ws, Hs;          // census grid
+    int opitch;          // census row pitch (elements)
+    int vec_load;        // word loads allowed (k in {1, 2}, aligned base and pitch)
+    int pad;
+};
+
 struct Workspace {
     uint64_t *census;          // per frame: L1, R1, Lk, Rk planes
     long long frame_stride;    // elements per frame
@@ -81,6 +93,7 @@ struct Workspace {
     // planes in the order L1, R1, Lk, Rk; words = 32 tiles
     uint32_t *bitmap;
     unsigned long long *tiles;  // [max_frames * bm_frame_words * 32] marked tiles, packed (census.cu)
+    PlaneDesc *planes;          // [max_frames * 4]
     long long bm_frame_words;
     int bm_plane_off[5];       // word offset of each plane within a frame (+ end)
     int bm_row_words[4];       // words per row of each plane

@@ -148,6 +148,7 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
     const size_t o_cin = take(sizeof(int) * 4);
     const size_t o_bm = take(sizeof(uint32_t) * (size_t)plane_off[4]);
     const size_t o_tiles = take(sizeof(unsigned long long) * 32 * (size_t)plane_off[4]);
+    const size_t o_planes = take(sizeof(PlaneDesc) * 4);
     if (off > kScratchBytes) return CTM_ETOOBIG;
 
     unsigned char *b = ds.base;
@@ -173,6 +174,7 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
     ws.counts_in = reinterpret_cast<int *>(b + o_cin);
     ws.bitmap = reinterpret_cast<uint32_t *>(b + o_bm);
     ws.tiles = reinterpret_cast<unsigned long long *>(b + o_tiles);
+    ws.planes = reinterpret_cast<PlaneDesc *>(b + o_planes);
     ws.bm_frame_words = plane_off[4];
     for (int q = 0; q < 5; ++q) ws.bm_plane_off[q] = plane_off[q];
     for (int q = 0; q < 4; ++q) ws.bm_row_words[q] = words_q[q];

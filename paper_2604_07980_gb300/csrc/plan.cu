@@ -73,6 +73,23 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(MatchArgs a)
     const bool bad_frame = fr.width < 1 || fr.height < 1 || fr.width > a.caps.max_width ||
                            fr.height > a.caps.max_height || fr.pitch < fr.width ||
                            fr.left == nullptr || fr.right == nullptr;
+    if (tid < 4) {  // census plane descriptors of this frame: L1, R1, Lk, Rk
+        PlaneDesc d;
+        const int q = tid;
+        d.img = (q & 1) ? fr.right : fr.left;
+        d.W = fr.width;
+        d.pitch = fr.pitch;
+        d.k = q < 2 ? 1 : a.p.close_factor;
+        d.Ws = ceil_div_nn(fr.width, d.k);
+        d.Hs = ceil_div_nn(fr.height, d.k);
+        uint64_t *cb = a.ws.census + (long long)f * a.ws.frame_stride;
+        d.out = q < 2 ? cb + q * a.ws.plane1_elems : cb + 2 * a.ws.plane1_elems + (q - 2) * a.ws.planek_elems;
+        d.opitch = (int)(q < 2 ? a.ws.pitch1 : a.ws.pitchk);
+        d.vec_load = (d.k == 1 || d.k == 2) && (fr.pitch % 4 == 0) &&
+                     ((reinterpret_cast<uintptr_t>(d.img) & 7u) == 0);
+        d.pad = 0;
+        a.ws.planes[f * 4 + q] = d;
+    }
     const int begin = clampi(fr.box_begin, 0, nb_total);
     const int end = clampi(fr.box_begin + fr.box_count, begin, nb_total);
     const int nloc = end - begin;
