@@ -127,6 +127,19 @@ typedef struct {
     int32_t *cost_b;
 } ctm_debug;
 
+/* Launch-shape tuning of a context (no effect on results).  Not described
+ * by the paper: these are choices of this implementation's kernels. */
+typedef struct {
+    int32_t match_threads;  /* matching CTA size: 128 or 256 threads                    */
+    int32_t strip_cols;     /* width, in codes, of the staged strip of one column chunk
+                               of a block: a multiple of 32, at least the larger
+                               disparity range + 2; larger values mean fewer chunks
+                               and more shared memory per CTA                         */
+    int32_t census_mode;    /* region-of-interest census: 0 = 4 CTAs per SM, 1 = 3    */
+    int32_t big_work;       /* blocks with usable points x candidates >= big_work are
+                               queued first (largest work first)                      */
+} ctm_tuning;
+
 /* Counters of the last match call (ctm_get_stats). */
 typedef struct {
     uint64_t cost_evals;   /* popcount(C_L xor C_R) evaluations, both passes */
@@ -236,6 +249,27 @@ int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_dev, const 
 
 /* Counters of the most recent match call on ctx.  Synchronizes `stream`. */
 int ctm_get_stats(ctm_ctx *ctx, ctm_stats *out, ctm_stream stream);
+
+/* Current tuning of a context. */
+int ctm_get_tuning(const ctm_ctx *ctx, ctm_tuning *out);
+
+/* Set the tuning (CTM_EINVAL if a field is out of range or the strip does not
+ * fit in shared memory; the context keeps its previous tuning then).  A
+ * captured batch graph is dropped and recaptured by the next graph call.
+ * Synchronous; do not call while a stream capture is active. */
+int ctm_set_tuning(ctm_ctx *ctx, const ctm_tuning *t);
+
+/* Autotuner: runs the batch of ctm_match_batch (same arguments, no debug
+ * output) under candidate tunings -- every matching CTA size x strip width,
+ * then each census variant and each queue split around the best so far --
+ * timing `reps` calls of each with CUDA events after one warm-up call, keeps
+ * the fastest in the context and returns it in *best (and its time per call,
+ * in ms, in *best_ms; either may be NULL).  The outputs are written by every
+ * call and do not depend on the tuning.  Synchronizes `stream`; not
+ * capturable.  On error the previous tuning is restored. */
+int ctm_autotune(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *counts_dev,
+                 const ctm_box *boxes_dev, float *disp_dev, float *depth_dev, uint8_t *flags_dev,
+                 int reps, ctm_tuning *best, float *best_ms, ctm_stream stream);
 
 /* Integer-pipe probe for roofline denominators (no counterpart in the paper):
  * runs `iters` iterations of independent chains of one instruction on every

@@ -26,7 +26,7 @@ BLK_VALID, BLK_FB_REJECT, BLK_FEW_POINTS, BLK_SUBPIX_CLAMPED, BLK_PRESENT = 1, 2
 EXPORTS = ("ctm_status_str", "ctm_default_params", "ctm_create", "ctm_destroy",
            "ctm_census_build", "ctm_match_boxes", "ctm_match_boxes_plain", "ctm_match_batch",
            "ctm_match_batch_profiled", "ctm_match_batch_host", "ctm_match_boxes_noalloc",
-           "ctm_get_stats", "ctm_probe_int_rate",
+           "ctm_get_stats", "ctm_probe_int_rate", "ctm_get_tuning", "ctm_set_tuning", "ctm_autotune",
            "ctm_server_default_config", "ctm_server_create", "ctm_server_submit", "ctm_server_poll",
            "ctm_server_outstanding", "ctm_server_get_stats", "ctm_server_destroy", "ctm_server_now_ns")
 
@@ -60,6 +60,14 @@ class ctm_debug(ctypes.Structure):
 class ctm_stats(ctypes.Structure):
     _fields_ = [("cost_evals", ctypes.c_uint64), ("n_blocks", ctypes.c_int32), ("n_boxes", ctypes.c_int32),
                 ("error", ctypes.c_int32), ("census_tiles", ctypes.c_int32)]
+
+
+class ctm_tuning(ctypes.Structure):
+    _fields_ = [("match_threads", ctypes.c_int32), ("strip_cols", ctypes.c_int32),
+                ("census_mode", ctypes.c_int32), ("big_work", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
 
 class ctm_server_config(ctypes.Structure):
@@ -140,6 +148,13 @@ def lib():
     L.ctm_get_stats.restype = i32
     L.ctm_probe_int_rate.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double)]
     L.ctm_probe_int_rate.restype = i32
+    L.ctm_get_tuning.argtypes = [vp, ctypes.POINTER(ctm_tuning)]
+    L.ctm_get_tuning.restype = i32
+    L.ctm_set_tuning.argtypes = [vp, ctypes.POINTER(ctm_tuning)]
+    L.ctm_set_tuning.restype = i32
+    L.ctm_autotune.argtypes = [vp, vp, vp, vp, vp, vp, vp, i32, ctypes.POINTER(ctm_tuning),
+                               ctypes.POINTER(ctypes.c_float), vp]
+    L.ctm_autotune.restype = i32
     i64 = ctypes.c_int64
     L.ctm_server_default_config.argtypes = [ctypes.POINTER(ctm_server_config)]
     L.ctm_server_default_config.restype = i32
@@ -346,6 +361,24 @@ class Context:
                                           disp.ctypes.data, depth.ctypes.data, flags.ctypes.data,
                                           _stream(stream)), "ctm_match_batch_host")
         return {"disp": disp[:n], "depth": depth[:n], "flags": flags[:n]}
+
+    def get_tuning(self) -> dict:
+        t = ctm_tuning()
+        _check(lib().ctm_get_tuning(self._h, ctypes.byref(t)), "ctm_get_tuning")
+        return t.as_dict()
+
+    def set_tuning(self, **fields):
+        t = ctm_tuning(**{**self.get_tuning(), **fields})
+        _check(lib().ctm_set_tuning(self._h, ctypes.byref(t)), "ctm_set_tuning")
+
+    def autotune(self, batch: "DeviceBatch", reps: int = 3, stream=None) -> tuple[dict, float]:
+        """Time candidate launch shapes on this batch, keep the fastest; returns it and ms per call."""
+        t = ctm_tuning()
+        ms = ctypes.c_float(0.0)
+        _check(lib().ctm_autotune(self._h, _ptr(batch.frames), _ptr(batch.counts), _ptr(batch.boxes),
+                                  _ptr(batch.disp), _ptr(batch.depth), _ptr(batch.flags), int(reps),
+                                  ctypes.byref(t), ctypes.byref(ms), _stream(stream)), "ctm_autotune")
+        return t.as_dict(), float(ms.value)
 
     def stats(self, stream=None) -> dict:
         s = ctm_stats()

@@ -34,6 +34,9 @@ struct ctm_ctx {
     int nc_stride = 0;
     int strip_cols = 0;
     int strip_rows = 0;
+    int census_mode = 0;
+    int big_work = 4096;
+    int nd_max = 0;
     void *dev_mem = nullptr;
     size_t dev_bytes = 0;
     cudaStream_t capture_stream = nullptr;
@@ -97,6 +100,8 @@ MatchArgs make_args(const ctm_ctx *ctx, const ctm_frame *frames, const int32_t *
     a.nc_stride = ctx->nc_stride;
     a.strip_cols = ctx->strip_cols;
     a.strip_rows = ctx->strip_rows;
+    a.big_work = ctx->big_work;
+    a.census_mode = ctx->census_mode;
     return a;
 }
 
@@ -192,11 +197,6 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
     if (!ctx) return CTM_ENOMEM;
     ctx->device = dev;
     ctx->p = *p;
-    // matching CTA size (128 or 256 threads); CTM_MATCH_THREADS overrides for tuning
-    if (const char *env = getenv("CTM_MATCH_THREADS")) {
-        const int t = atoi(env);
-        if (t == 128 || t == 256) ctx->match_threads = t;
-    }
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, dev);
     const int slots = p->grid_g * p->grid_g;
     ctx->caps.max_frames = max_frames;
@@ -207,6 +207,7 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
     const int ndy = p->dy_max - p->dy_min + 1;
     const int nd_max = std::max(p->far_dmax - p->far_dmin + 1, p->close_dmax - p->close_dmin + 1);
     ctx->nc_stride = nd_max * ndy;
+    ctx->nd_max = nd_max;
     ctx->strip_rows = p->pts_side * ndy;
     // strip piece width (one sampled row per piece, double-buffered per warp): the
     // disparity range plus a 64-column span of points; wider rows are chunked
@@ -294,7 +295,7 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
         ctm_destroy(ctx);
         return CTM_ECUDA;
     }
-    census_roi_ctas_per_sm(p->win_w, p->win_h);  // occupancy query outside any capture
+    for (int m = 0; m < 2; ++m) census_roi_ctas_per_sm(p->win_w, p->win_h, m);  // outside any capture
     *out = ctx;
     return CTM_OK;
 }
@@ -531,6 +532,131 @@ int ctm_match_batch_host(ctm_ctx *ctx, const ctm_frame *frames_host, int n_frame
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { cudaGetLastError(); return CTM_ECUDA; }
+    return CTM_OK;
+}
+
+int ctm_get_tuning(const ctm_ctx *ctx, ctm_tuning *out)
+{
+    if (!ctx || !out) return CTM_EINVAL;
+    out->match_threads = ctx->match_threads;
+    out->strip_cols = ctx->strip_cols;
+    out->census_mode = ctx->census_mode;
+    out->big_work = ctx->big_work;
+    return CTM_OK;
+}
+
+int ctm_set_tuning(ctm_ctx *ctx, const ctm_tuning *t)
+{
+    if (!ctx || !t) return CTM_EINVAL;
+    if (t->match_threads != 128 && t->match_threads != 256) return CTM_EINVAL;
+    if (t->strip_cols < ctx->nd_max + 2 || (t->strip_cols & 31) != 0 || t->strip_cols > 4096) return CTM_EINVAL;
+    if (t->census_mode != 0 && t->census_mode != 1) return CTM_EINVAL;
+    if (t->big_work < 0) return CTM_EINVAL;
+    int st = set_device(ctx);
+    if (st != CTM_OK) return st;
+    ctm_ctx trial = *ctx;  // shallow: only the tuning fields are read below
+    trial.match_threads = t->match_threads;
+    trial.strip_cols = t->strip_cols;
+    MatchArgs a = make_args(&trial, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    int ctas = 0;
+    if (match_smem_bytes(a) > 227 * 1024) return CTM_EINVAL;
+    if (match_configure(a, t->match_threads, &ctas) != cudaSuccess || ctas < 1) {
+        cudaGetLastError();
+        return CTM_EINVAL;
+    }
+    const bool changed = t->match_threads != ctx->match_threads || t->strip_cols != ctx->strip_cols ||
+                         t->census_mode != ctx->census_mode || t->big_work != ctx->big_work;
+    ctx->match_threads = t->match_threads;
+    ctx->strip_cols = t->strip_cols;
+    ctx->census_mode = t->census_mode;
+    ctx->big_work = t->big_work;
+    ctx->ctas_per_sm = ctas;
+    if (changed && ctx->gexec) {  // the captured graph holds the old launch shapes
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+    }
+    return CTM_OK;
+}
+
+int ctm_autotune(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *counts_dev,
+                 const ctm_box *boxes_dev, float *disp_dev, float *depth_dev, uint8_t *flags_dev, int reps,
+                 ctm_tuning *best, float *best_ms, ctm_stream stream)
+{
+    if (!ctx || !frames_dev || !counts_dev || !boxes_dev || !disp_dev || !depth_dev || !flags_dev || reps < 1)
+        return CTM_EINVAL;
+    int st = set_device(ctx);
+    if (st != CTM_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    ctm_tuning cur;
+    ctm_get_tuning(ctx, &cur);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaGetLastError();
+        return CTM_ECUDA;
+    }
+    // time one configuration: one warm-up call, then `reps` calls between events
+    auto measure = [&](const ctm_tuning &t, float *ms) -> int {
+        int r = ctm_set_tuning(ctx, &t);
+        if (r != CTM_OK) return r;
+        MatchArgs a = make_args(ctx, frames_dev, counts_dev, boxes_dev, disp_dev, depth_dev, flags_dev, nullptr);
+        const int grid = ctx->sm_count * ctx->ctas_per_sm;
+        r = enqueue_match(ctx, a, ctx->caps.max_frames, grid, s, false, 0);
+        if (r == CTM_OK && cudaEventRecord(e0, s) != cudaSuccess) r = CTM_ECUDA;
+        for (int i = 0; i < reps && r == CTM_OK; ++i) r = enqueue_match(ctx, a, ctx->caps.max_frames, grid, s, false, 0);
+        if (r == CTM_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+            r = CTM_ECUDA;
+        float t_ms = 0.0f;
+        if (r == CTM_OK && cudaEventElapsedTime(&t_ms, e0, e1) != cudaSuccess) r = CTM_ECUDA;
+        *ms = t_ms / (float)reps;
+        return r;
+    };
+    ctm_tuning bt = cur;
+    float bms = 3.4e38f;
+    int status = CTM_OK;
+    // 1. matching CTA size x strip chunk width (joint), at the current census mode and split
+    const int base = (int)round_up(ctx->nd_max + 34, 32);
+    for (int th = 128; th <= 256 && status == CTM_OK; th *= 2) {
+        for (int extra = 0; extra <= 192; extra += 32) {
+            ctm_tuning t = bt;
+            t.match_threads = th;
+            t.strip_cols = base + extra;
+            float ms = 0.0f;
+            const int r = measure(t, &ms);
+            if (r == CTM_EINVAL) continue;  // does not fit shared memory
+            if (r != CTM_OK) { status = r; break; }
+            if (ms < bms) { bms = ms; bt = t; }
+        }
+    }
+    // 2. census variant, 3. queue split, one at a time around the best so far
+    const int modes[2] = {0, 1};
+    for (int i = 0; i < 2 && status == CTM_OK; ++i) {
+        ctm_tuning t = bt;
+        t.census_mode = modes[i];
+        float ms = 0.0f;
+        const int r = measure(t, &ms);
+        if (r != CTM_OK) { status = r; break; }
+        if (ms < bms) { bms = ms; bt = t; }
+    }
+    const int splits[5] = {1024, 2048, 4096, 8192, 1 << 30};
+    for (int i = 0; i < 5 && status == CTM_OK; ++i) {
+        ctm_tuning t = bt;
+        t.big_work = splits[i];
+        float ms = 0.0f;
+        const int r = measure(t, &ms);
+        if (r != CTM_OK) { status = r; break; }
+        if (ms < bms) { bms = ms; bt = t; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (status != CTM_OK) {
+        ctm_set_tuning(ctx, &cur);
+        return status;
+    }
+    st = ctm_set_tuning(ctx, &bt);
+    if (st != CTM_OK) return st;
+    if (best) *best = bt;
+    if (best_ms) *best_ms = bms;
     return CTM_OK;
 }
 

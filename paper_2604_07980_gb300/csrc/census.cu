@@ -17,7 +17,6 @@
 // tiles the planner marked in a per-plane bitmap (one bit per 64-pixel tile of
 // a row) and clears the marks it consumed.
 #include <cuda_fp16.h>
-#include <stdlib.h>
 
 #include "ctm_internal.cuh"
 
@@ -637,17 +636,6 @@ cudaError_t launch_census_single(const uint8_t *img, int W, int H, int pitch, in
     return cudaGetLastError();
 }
 
-// Variant of the fixed-window ROI kernel (census_roi4_kernel MODE); the
-// default is 0, CTM_CENSUS_MODE (0 or 1) overrides it for tuning.
-static int roi_mode()
-{
-    static const int v = [] {
-        const char *e = getenv("CTM_CENSUS_MODE");
-        return (e && e[0] == '1' && e[1] == 0) ? 1 : 0;
-    }();
-    return v;
-}
-
 template <int WW, int WH>
 static int roi4_ctas(int mode)
 {
@@ -656,9 +644,8 @@ static int roi4_ctas(int mode)
     return mode == 0 ? n0 : n1;
 }
 
-int census_roi_ctas_per_sm(int win_w, int win_h)
+int census_roi_ctas_per_sm(int win_w, int win_h, int mode)
 {
-    const int mode = roi_mode();
     if (win_w == 9 && win_h == 7) return roi4_ctas<9, 7>(mode);
     if (win_w == 7 && win_h == 7) return roi4_ctas<7, 7>(mode);
     if (win_w == 5 && win_h == 5) return roi4_ctas<5, 5>(mode);
@@ -669,7 +656,7 @@ int census_roi_ctas_per_sm(int win_w, int win_h)
 template <int WW, int WH>
 static void launch_roi4(const MatchArgs &a, int grid, cudaStream_t s)
 {
-    if (roi_mode() == 0)
+    if (a.census_mode == 0)
         census_roi4_kernel<WW, WH, 0><<<grid, 256, 0, s>>>(a);
     else
         census_roi4_kernel<WW, WH, 1><<<grid, 256, 0, s>>>(a);
@@ -681,7 +668,7 @@ cudaError_t launch_census_roi(const MatchArgs &a, int sm_count, cudaStream_t s)
     const int list_grid = (int)((words + 255) / 256);
     if (list_grid > 0) tile_list_kernel<<<list_grid, 256, 0, s>>>(a);
     const int ww = a.p.win_w, wh = a.p.win_h;
-    const int grid = sm_count * census_roi_ctas_per_sm(ww, wh);
+    const int grid = sm_count * census_roi_ctas_per_sm(ww, wh, a.census_mode);
     if (ww == 9 && wh == 7) {
         launch_roi4<9, 7>(a, grid, s);
     } else if (ww == 7 && wh == 7) {

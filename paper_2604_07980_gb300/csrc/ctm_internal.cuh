@@ -117,6 +117,8 @@ struct MatchArgs {
     ctm_debug dbg;
     int nc_stride;
     int strip_cols;            // columns of the shared-memory strip
+    int big_work;              // queue split: usable points x candidates of a large block
+    int census_mode;           // region-of-interest census variant (census.cu)
     int strip_rows;            // rows of the shared-memory strip (pts_side * ndy)
 };
 
@@ -157,7 +159,7 @@ cudaError_t launch_census_single(const uint8_t *img, int W, int H, int pitch, in
 // Region-of-interest census over the marked tiles, `ctas_per_sm` resident CTAs
 // per SM (census_roi_ctas_per_sm; the first call queries the occupancy, so make
 // it before any stream capture).
-int census_roi_ctas_per_sm(int win_w, int win_h);
+int census_roi_ctas_per_sm(int win_w, int win_h, int mode);
 cudaError_t launch_census_roi(const MatchArgs &a, int sm_count, cudaStream_t s);
 size_t census_smem_bytes(int win_h);
 

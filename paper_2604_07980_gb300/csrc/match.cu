@@ -619,24 +619,24 @@ size_t match_smem_bytes(const MatchArgs &a)
            sizeof(int) * kMaxCand + 2 * sizeof(int) * kMaxPts;
 }
 
+// The dynamic shared-memory limit is a per-kernel, process-wide setting: it is
+// only ever raised, so contexts with different strip sizes can coexist.
 cudaError_t match_configure(const MatchArgs &a, int threads, int *ctas_per_sm)
 {
-    const int smem = (int)match_smem_bytes(a);
+    const int need = (int)match_smem_bytes(a);
+    cudaFuncAttributes fa;
     cudaError_t e = cudaSuccess;
     if (threads == 128) {
-        e = cudaFuncSetAttribute(match_persistent_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(match_box_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, match_persistent_kernel<128>, 128, smem);
+        e = cudaFuncGetAttributes(&fa, match_box_kernel<128>);
+        if (e == cudaSuccess && fa.maxDynamicSharedSizeBytes < need)
+            e = cudaFuncSetAttribute(match_box_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
     } else {
-        e = cudaFuncSetAttribute(match_persistent_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(match_box_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, match_persistent_kernel<256>, 256, smem);
+        e = cudaFuncGetAttributes(&fa, match_box_kernel<256>);
+        if (e == cudaSuccess && fa.maxDynamicSharedSizeBytes < need)
+            e = cudaFuncSetAttribute(match_box_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
     }
-    return e;
+    if (e != cudaSuccess) return e;
+    return match_configure_raise(a, threads, ctas_per_sm);
 }
 
 cudaError_t match_configure_raise(const MatchArgs &a, int threads, int *ctas_per_sm)

@@ -76,9 +76,11 @@ int setup_device(int dev)
     }
     st.base = static_cast<unsigned char *>(ptr);
     st.sm_count = sms;
-    ctm::census_roi_ctas_per_sm(9, 7);  // occupancy queries outside any capture
-    ctm::census_roi_ctas_per_sm(7, 7);
-    ctm::census_roi_ctas_per_sm(5, 5);
+    for (int m = 0; m < 2; ++m) {  // occupancy queries outside any capture
+        ctm::census_roi_ctas_per_sm(9, 7, m);
+        ctm::census_roi_ctas_per_sm(7, 7, m);
+        ctm::census_roi_ctas_per_sm(5, 5, m);
+    }
     st.ready = true;
     return CTM_OK;
 }
@@ -191,6 +193,8 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
     a.dbg.cost_b = nullptr;
     a.nc_stride = nd_max * ndy;
     a.strip_cols = strip_cols;
+    a.big_work = 4096;
+    a.census_mode = 0;
     a.strip_rows = p->pts_side * ndy;
 
     const int threads = 128;

@@ -218,9 +218,6 @@ __device__ __forceinline__ void mark_range(const MatchArgs &a, int f, int q, int
     }
 }
 
-// Work threshold (usable points x candidates) of the large-work queue.
-constexpr int kBigWork = 4096;
-
 __global__ void __launch_bounds__(256) sample_kernel(MatchArgs a)
 {
     __shared__ float agg_scratch[8][2 * kMaxSlots];
@@ -312,7 +309,7 @@ __global__ void __launch_bounds__(256) sample_kernel(MatchArgs a)
             aggregate_box(a, box, agg_scratch[warp], lane);
         }
     } else if (lane == 0) {
-        if (n_valid * nd * ndy >= kBigWork) {
+        if (n_valid * nd * ndy >= a.big_work) {
             const int q = atomicAdd(&a.ws.counts->n_big, 1);
             a.ws.queue[q] = b;
         } else {
