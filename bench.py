@@ -41,9 +41,10 @@ POPC_PER_EVAL = 2          # one u64 code pair = two 32-bit popcounts
 # DRAM bytes (read + write) of one match_persistent_kernel launch on this workload, from the
 # ncu capture summarised in profiles/match_persistent_kernel_batch32x1200.md; None once the
 # kernel changes after that capture.
-MATCH_DRAM_BYTES = (101.938432 + 2.879232) * 1e6
-# kernels of one step of the batched path: plan, sample, mark, tile_list, census_roi, match
-KERNELS_PER_STEP = 6
+MATCH_DRAM_BYTES = None
+# kernels of one step of the batched path: plan, sample, mark, tile_list, census_roi, match,
+# aggregate
+KERNELS_PER_STEP = 7
 
 
 def parse():

@@ -212,8 +212,8 @@ int ctm_match_batch(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *co
 
 /* ctm_match_batch without a graph, recording four caller-created CUDA events
  * (cudaEvent_t handles, created with timing enabled) on `stream`: events[0]
- * before planning, events[1] before the census kernel, events[2] before the
- * matching kernel, events[3] after it.  Used to time each phase on the stream
+ * before planning, events[1] before the census kernels, events[2] before the
+ * matching kernel, events[3] after the per-box aggregation that follows it.  Used to time each phase on the stream
  * the kernels run on.  Errors as ctm_match_batch. */
 int ctm_match_batch_profiled(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *counts_dev,
                              const ctm_box *boxes_dev, float *disp_dev, float *depth_dev,

@@ -1,6 +1,7 @@
-// aggregate.cuh -- block completion and per-box aggregation (Sec. 4.3.4),
-// shared by the sampling kernel (blocks with too few points) and the matching
-// kernel (searched blocks).
+// aggregate.cuh -- block records and per-box aggregation (Sec. 4.3.4).  The
+// sampling kernel (blocks with too few points) and the matching kernels
+// (searched blocks) write block records; aggregate_kernel (plan.cu) then
+// aggregates every box with one warp.
 #pragma once
 
 #include <math.h>
@@ -9,8 +10,7 @@
 
 namespace ctm {
 
-// Sec. 4.3.4 on the block records of one box, by one full warp (the warp that
-// completed the box): FAR boxes take their single block; CLOSE boxes sort the
+// Sec. 4.3.4 on the block records of one box, by one full warp: FAR boxes take their single block; CLOSE boxes sort the
 // valid block disparities, take the longest run whose consecutive differences
 // are below tau_d (first run on ties), require N_min members and return its
 // median (even length: mean of the middle two) or trimmed mean (floor(trim m)
@@ -110,24 +110,15 @@ __device__ __forceinline__ void aggregate_box(const MatchArgs &a, int box, float
     __syncwarp();
 }
 
-// Publish a finished block: its aggregation record, the optional diagnostic
-// record, and the box completion count.  Called by lane 0 of a warp; returns
-// true on that lane when this block completed its box (the caller's warp then
-// aggregates).  The fence orders the record before the count.
-__device__ __forceinline__ bool publish_block(const MatchArgs &a, int box, int slot, const ctm_block &rec,
-                                              int nc)
+// Record a finished block: its aggregation record and the optional diagnostic
+// record.  Boxes are aggregated after all blocks are written (aggregate_kernel).
+__device__ __forceinline__ void write_block(const MatchArgs &a, int box, int slot, const ctm_block &rec)
 {
-    const BoxPlan &P = a.ws.plans[box];
     BlockResult r;
     r.d_full = rec.d_full;
     r.flags = rec.flags;
     a.ws.blkres[a.ws.blk_base[box] + slot] = r;
     if (a.dbg.blocks) a.dbg.blocks[(long long)box * (a.p.grid_g * a.p.grid_g) + slot] = rec;
-    if (!(rec.flags & CTM_BLK_FEW_POINTS))
-        atomicAdd(&a.ws.counts->evals, 2ull * (unsigned long long)rec.n_valid * (unsigned long long)nc);
-    __threadfence();
-    const int prev = atomicAdd(&a.ws.box_done[box], 1);
-    return prev == P.nblk - 1;
 }
 
 }  // namespace ctm

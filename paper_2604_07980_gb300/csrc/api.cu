@@ -1,9 +1,9 @@
 // api.cu -- the C ABI (include/ctm.h): context, workspace and launch sequences.
 //
-// A match call is five launches on one stream: device planning, point sampling,
-// census demand marking, census of the marked tiles (both images, both
-// resolutions) and the matching kernel whose last CTA per box aggregates and
-// writes the outputs.  The batch entry point reads its frame and box counts
+// A match call is seven launches on one stream: device planning, point
+// sampling, census demand marking, the census tile list, census of the listed
+// tiles (both images, both resolutions), the matching kernel, and the per-box
+// aggregation that writes the outputs.  The batch entry point reads its frame and box counts
 // from device memory, so the whole sequence can be captured once into a CUDA
 // graph and replayed.
 #include <cuda_runtime.h>
@@ -123,6 +123,7 @@ int enqueue_match(ctm_ctx *ctx, const MatchArgs &a, int frames_grid, int match_g
         for (int i = 0; i < n_boxes_host && e == cudaSuccess; ++i)
             e = launch_match_box(b, ctx->match_threads, i, s);
     }
+    if (e == cudaSuccess) e = launch_aggregate(b, s);
     return e == cudaSuccess ? CTM_OK : CTM_ECUDA;
 }
 
@@ -234,7 +235,6 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
     const size_t o_blkres = take(sizeof(BlockResult) * (size_t)ctx->caps.max_blocks);
     const size_t o_geom = take(sizeof(BlockGeom) * (size_t)ctx->caps.max_blocks);
     const size_t o_queue = take(sizeof(int) * (size_t)ctx->caps.max_blocks);
-    const size_t o_done = take(sizeof(int) * (size_t)max_boxes);
     const size_t o_counts = take(sizeof(Counts));
     const size_t o_frames = take(sizeof(ctm_frame) * (size_t)max_frames);
     const size_t o_cin = take(sizeof(int) * 4);
@@ -271,7 +271,6 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
     ws.blkres = reinterpret_cast<BlockResult *>(base + o_blkres);
     ws.geom = reinterpret_cast<BlockGeom *>(base + o_geom);
     ws.queue = reinterpret_cast<int *>(base + o_queue);
-    ws.box_done = reinterpret_cast<int *>(base + o_done);
     ws.counts = reinterpret_cast<Counts *>(base + o_counts);
     ws.frames = reinterpret_cast<ctm_frame *>(base + o_frames);
     ws.counts_in = reinterpret_cast<int *>(base + o_cin);
@@ -443,6 +442,7 @@ int ctm_match_batch_profiled(ctm_ctx *ctx, const ctm_frame *frames_dev, const in
     if (e == cudaSuccess) e = launch_census_roi(a, ctx->sm_count, s);
     if (e == cudaSuccess) e = cudaEventRecord((cudaEvent_t)events[2], s);
     if (e == cudaSuccess) e = launch_match_persistent(a, ctx->match_threads, grid, s);
+    if (e == cudaSuccess) e = launch_aggregate(a, s);
     if (e == cudaSuccess) e = cudaEventRecord((cudaEvent_t)events[3], s);
     if (e != cudaSuccess) { cudaGetLastError(); return CTM_ECUDA; }
     return CTM_OK;

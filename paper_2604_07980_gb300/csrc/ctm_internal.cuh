@@ -85,7 +85,6 @@ struct Workspace {
     BlockGeom *geom;           // [max_blocks] indexed like blocks
     int *queue;                // [max_blocks] searchable blocks: large from the front, small from the back
     BlockResult *blkres;       // [max_blocks]
-    int *box_done;             // [max_boxes]
     Counts *counts;
     ctm_frame *frames;         // staging for single-frame calls [max_frames]
     int *counts_in;            // staging {n_frames, n_boxes}
@@ -167,6 +166,7 @@ size_t census_smem_bytes(int win_h);
 cudaError_t launch_stage_frame(const MatchArgs &a, ctm_frame f, int n_boxes, cudaStream_t s);
 cudaError_t launch_plan(const MatchArgs &a, cudaStream_t s);
 cudaError_t launch_mark(const MatchArgs &a, cudaStream_t s);
+cudaError_t launch_aggregate(const MatchArgs &a, cudaStream_t s);
 cudaError_t launch_sample(const MatchArgs &a, cudaStream_t s);
 
 // Matching (match.cu)

@@ -77,16 +77,35 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
                  ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(mbar)) : "memory");
 }
 
-// Bounded wait for the phase `parity` of mbar.  On expiry the CTA records an
-// error, waits once more (bounded) for its copies in flight and reports false.
-constexpr unsigned kWaitLimit = 1u << 22;
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for the phase `parity` of mbar: about one second of try_waits
+// (global timer; an iteration cap as a backstop).  On expiry the CTA
+// records an error, waits once more (bounded) for its copies in flight and
+// reports false.
+constexpr unsigned long long kWaitNs = 1000000000ull;
+constexpr unsigned kWaitIters = 1u << 26;
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *mbar, unsigned parity)
+{
+    if (mbar_try_wait(mbar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 1; it < kWaitIters; ++it) {
+        if (mbar_try_wait(mbar, parity)) return true;
+        if ((it & 15u) == 0 && global_ns() - t0 > kWaitNs) break;
+    }
+    return false;
+}
+
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, unsigned parity, int *error_flag)
 {
-    for (unsigned it = 0; it < kWaitLimit; ++it)
-        if (mbar_try_wait(mbar, parity)) return true;
+    if (mbar_wait_for(mbar, parity)) return true;
     atomicOr(error_flag, 1);
-    for (unsigned it = 0; it < kWaitLimit; ++it)
-        if (mbar_try_wait(mbar, parity)) break;
+    mbar_wait_for(mbar, parity);
     return false;
 }
 
@@ -100,8 +119,9 @@ struct Smem {
 
 template <int NW>
 struct Shared {
-    BlockGeom geom;         // the block's sampled grid (copied from global)
+    BlockGeom geom[2];      // sampled grids: the current block's and the prefetched next one's
     uint64_t mbar;          // completion of the strip bulk copies
+    uint64_t mbar_g;        // completion of the geometry prefetch
     int X[kMaxPtsSide];
     int Y[kMaxPtsSide];
     int colstart[kMaxPtsSide + 1];
@@ -110,8 +130,9 @@ struct Shared {
     float agg_sorted[kMaxSlots];
     int d_f, dy_f, s_m, s_0, s_p;
     int d_b, dy_b;
-    int last;
-    int next;
+    int next;               // queue index of the next block
+    int next_b;             // its block
+    int gpend;              // a geometry copy is in flight on mbar_g
     unsigned cstart;        // bit j set: a strip column chunk starts at point column j
     int abort;              // a bounded wait expired: stop this CTA
 };
@@ -307,15 +328,21 @@ __device__ __forceinline__ bool load_chunk(const MatchArgs &a, const BlockCtx &b
     const bool edge = g.colbase_a < 0 || g.colbase_a + g.SWa > bc.Ws ||
                       sh.Y[0] + (fwd ? a.p.dy_min : dy_f - a.p.dy_max) < 0 ||
                       sh.Y[bc.ny - 1] + (fwd ? a.p.dy_max : dy_f - a.p.dy_min) >= bc.Hs;
-    if (edge) {
-        const int total_el = rows * g.SWa;
-        for (int i = tid; i < total_el; i += NT) {
-            const int r = i / g.SWa, c = i - r * g.SWa;
+    if (edge) {  // a warp per row: whole rows outside the plane, else the columns outside it
+        const int warp = tid >> 5;
+        const int c_lo = min(max(-g.colbase_a, 0), g.SWa);             // [0, c_lo): x < 0
+        const int c_hi = max(min(bc.Ws - g.colbase_a, g.SWa), c_lo);   // [c_hi, SWa): x >= Ws
+        for (int r = warp; r < rows; r += NT / 32) {
             const int m = bc.ndy == 1 ? r : r / bc.ndy;
             const int e = r - m * bc.ndy;
             const int y = fwd ? sh.Y[m] + a.p.dy_min + e : sh.Y[m] + dy_f - (a.p.dy_min + e);
-            const int x = g.colbase_a + c;
-            if (y < 0 || y >= bc.Hs || x < 0 || x >= bc.Ws) sm.strip[i] = 0ull;
+            uint64_t *row = sm.strip + r * g.SWa;
+            if (y < 0 || y >= bc.Hs) {
+                for (int c = lane; c < g.SWa; c += 32) row[c] = 0ull;
+            } else {
+                for (int c = lane; c < c_lo; c += 32) row[c] = 0ull;
+                for (int c = c_hi + lane; c < g.SWa; c += 32) row[c] = 0ull;
+            }
         }
     }
     return ok;
@@ -411,11 +438,33 @@ __device__ bool search_pass(const MatchArgs &a, const BlockCtx &bc, const Smem &
     return ok;
 }
 
+// Queue entry i: large work from the front, small work from the back.
+__device__ __forceinline__ int queue_block(const MatchArgs &a, int i, int n_big)
+{
+    return i < n_big ? a.ws.queue[i] : a.ws.queue[a.caps.max_blocks - 1 - (i - n_big)];
+}
+
+// Prefetch state of the persistent kernel: the queue index taken for the next
+// block and the geometry buffer it goes to.  A single-block launch has none.
+struct Prefetch {
+    bool on;
+    int n_big, nq;
+    int buf;  // geometry buffer of the next block
+};
+
+// One block end to end.  Its geometry is in sh.geom[gbuf] (landed).  With
+// pf.on, thread 0 takes the next queue index at the start, and once the
+// forward pass is done issues the next block's geometry copy into the other
+// buffer (completion on sh.mbar_g), so that round trip overlaps this block.
+// Returns false if a bounded wait expired.  evals: thread 0 adds this block's
+// evaluation count.
 template <int NT>
 __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<NT / 32> &sh,
-                              unsigned &phase)
+                              unsigned &phase, int gbuf, const Prefetch &pf, unsigned long long &evals)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int next_i = 0;
+    if (pf.on && threadIdx.x == 0) next_i = atomicAdd(&a.ws.counts->queue_head, 1);
+    const int tid = threadIdx.x;
     const int2 bs = a.ws.blocks[b];
     const BoxPlan P = a.ws.plans[bs.x];
     BlockCtx bc;
@@ -440,13 +489,8 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
     }
 
     // 1a. the block's sampled grid and usable points (from the sampling kernel)
-    if (tid < (int)(sizeof(BlockGeom) / 16))
-        cp_async16(reinterpret_cast<char *>(&sh.geom) + 16 * tid,
-                   reinterpret_cast<const char *>(a.ws.geom + b) + 16 * tid);
     for (int c = tid; c < bc.nc; c += NT) sm.cost[c] = 0;
-    cp_async_wait_all();
-    __syncthreads();
-    const BlockGeom &g = sh.geom;
+    const BlockGeom &g = sh.geom[gbuf];
     bc.nx = g.nx;
     bc.ny = g.ny;
     const int total = g.n_valid;
@@ -477,6 +521,8 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
     // 1c. the first forward strip chunk
     bool ok = load_chunk<NT>(a, bc, sm, sh, phase, true, 0, g0);
     cp_async_wait_all();
+    int next_b = 0;
+    if (pf.on && tid == 0 && next_i < pf.nq) next_b = queue_block(a, next_i, pf.n_big);
     if (!__syncthreads_and(ok)) return false;
 
     ctm_block rec;
@@ -496,6 +542,16 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
         sh.s_0 = (int)(key >> 16);
         sh.s_m = di > 0 ? sm.cost[c - 1] : 0;
         sh.s_p = di < bc.nd - 1 ? sm.cost[c + 1] : 0;
+        if (pf.on) {
+            sh.next = next_i;
+            sh.next_b = next_b;
+            if (next_i < pf.nq) {  // the next block's geometry, in flight during this backward pass
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                mbar_arrive_expect_tx(&sh.mbar_g, (unsigned)sizeof(BlockGeom));
+                bulk_g2s(&sh.geom[pf.buf], a.ws.geom + next_b, (unsigned)sizeof(BlockGeom), &sh.mbar_g);
+                sh.gpend = 1;
+            }
+        }
     }
     __syncthreads();
     // 4. backward pass: right codes at the matched positions + first left strip
@@ -525,7 +581,7 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
     }
     __syncthreads();
 
-    // 5. block record (thread 0), completion count; the box's last block aggregates
+    // 5. block record (thread 0); boxes are aggregated by aggregate_kernel
     if (tid == 0) {
         rec.d_f = sh.d_f;
         rec.dy_f = sh.dy_f;
@@ -546,12 +602,8 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
         rec.d_full = __fmul_rn(rec.d_sub, (float)bc.k);
         const int dxv = abs(rec.d_b - rec.d_f);
         rec.flags |= dxv <= a.p.fb_tol ? CTM_BLK_VALID : CTM_BLK_FB_REJECT;
-        sh.last = publish_block(a, bc.box, bc.slot, rec, bc.nc) ? 1 : 0;
-    }
-    __syncthreads();
-    if (sh.last && warp == 0) {
-        __threadfence();
-        aggregate_box(a, bc.box, sh.agg, lane);
+        write_block(a, bc.box, bc.slot, rec);
+        evals += 2ull * (unsigned long long)total * (unsigned long long)bc.nc;
     }
     __syncthreads();
     return true;
@@ -574,26 +626,51 @@ __device__ __forceinline__ Smem carve(const MatchArgs &a, unsigned char *raw)
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT, 1536 / NT)
+__global__ void __launch_bounds__(NT, 1024 / NT)
     match_persistent_kernel(MatchArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ Shared<NT / 32> sh;
     const Smem sm = carve(a, smem_raw);
-    if (threadIdx.x == 0) mbar_init(&sh.mbar, 1);
-    __syncthreads();
-    unsigned phase = 0;
-    const int n_big = a.ws.counts->n_big;
-    const int nq = n_big + a.ws.counts->n_small;
-    for (;;) {
-        if (threadIdx.x == 0) sh.next = atomicAdd(&a.ws.counts->queue_head, 1);
-        __syncthreads();
-        const int i = sh.next;
-        __syncthreads();
-        if (i >= nq) break;
-        const int b = i < n_big ? a.ws.queue[i] : a.ws.queue[a.caps.max_blocks - 1 - (i - n_big)];
-        if (!process_block<NT>(a, b, sm, sh, phase)) break;  // a bounded wait expired
+    Prefetch pf;
+    pf.on = true;
+    pf.n_big = a.ws.counts->n_big;
+    pf.nq = pf.n_big + a.ws.counts->n_small;
+    if (threadIdx.x == 0) {
+        mbar_init(&sh.mbar, 1);
+        mbar_init(&sh.mbar_g, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        const int i = atomicAdd(&a.ws.counts->queue_head, 1);
+        sh.next = i;
+        sh.gpend = 0;
+        if (i < pf.nq) {
+            sh.next_b = queue_block(a, i, pf.n_big);
+            mbar_arrive_expect_tx(&sh.mbar_g, (unsigned)sizeof(BlockGeom));
+            bulk_g2s(&sh.geom[0], a.ws.geom + sh.next_b, (unsigned)sizeof(BlockGeom), &sh.mbar_g);
+            sh.gpend = 1;
+        }
     }
+    __syncthreads();
+    unsigned phase = 0, gphase = 0;
+    unsigned long long evals = 0ull;
+    int buf = 0;
+    while (sh.gpend) {
+        const int b = sh.next_b;
+        const bool landed = mbar_wait_bounded(&sh.mbar_g, gphase, &a.ws.counts->error);
+        gphase ^= 1u;
+        if (!__syncthreads_and(landed)) break;  // (its copy landed or the wait gave up twice)
+        if (threadIdx.x == 0) sh.gpend = 0;     // read by all threads before the barrier above
+        pf.buf = buf ^ 1;
+        if (!process_block<NT>(a, b, sm, sh, phase, buf, pf, evals)) {
+            // a bounded wait expired: let a geometry copy in flight land before leaving
+            __syncthreads();
+            if (sh.gpend) mbar_wait_bounded(&sh.mbar_g, gphase, &a.ws.counts->error);
+            break;
+        }
+        buf ^= 1;
+    }
+    if (threadIdx.x == 0 && evals) atomicAdd(&a.ws.counts->evals, evals);
 }
 
 template <int NT>
@@ -605,10 +682,20 @@ __global__ void __launch_bounds__(NT) match_box_kernel(MatchArgs a, int box)
     const int b = a.ws.blk_base[box] + blockIdx.x;
     if (a.ws.geom[b].n_valid < a.p.min_pts) return;  // finished by the sampling kernel
     const Smem sm = carve(a, smem_raw);
+    if (threadIdx.x < (int)(sizeof(BlockGeom) / 16))
+        cp_async16(reinterpret_cast<char *>(&sh.geom[0]) + 16 * threadIdx.x,
+                   reinterpret_cast<const char *>(a.ws.geom + b) + 16 * threadIdx.x);
     if (threadIdx.x == 0) mbar_init(&sh.mbar, 1);
+    cp_async_wait_all();
     __syncthreads();
     unsigned phase = 0;
-    process_block<NT>(a, b, sm, sh, phase);
+    unsigned long long evals = 0ull;
+    Prefetch pf;
+    pf.on = false;
+    pf.n_big = pf.nq = 0;
+    pf.buf = 1;
+    process_block<NT>(a, b, sm, sh, phase, 0, pf, evals);
+    if (threadIdx.x == 0 && evals) atomicAdd(&a.ws.counts->evals, evals);
 }
 
 }  // namespace

@@ -144,7 +144,6 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
     const size_t o_blkres = take(sizeof(BlockResult) * (size_t)caps.max_blocks);
     const size_t o_geom = take(sizeof(BlockGeom) * (size_t)caps.max_blocks);
     const size_t o_queue = take(sizeof(int) * (size_t)caps.max_blocks);
-    const size_t o_done = take(sizeof(int) * kMaxBoxes);
     const size_t o_counts = take(sizeof(Counts));
     const size_t o_frames = take(sizeof(ctm_frame));
     const size_t o_cin = take(sizeof(int) * 4);
@@ -170,7 +169,6 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
     ws.blkres = reinterpret_cast<BlockResult *>(b + o_blkres);
     ws.geom = reinterpret_cast<BlockGeom *>(b + o_geom);
     ws.queue = reinterpret_cast<int *>(b + o_queue);
-    ws.box_done = reinterpret_cast<int *>(b + o_done);
     ws.counts = reinterpret_cast<Counts *>(b + o_counts);
     ws.frames = reinterpret_cast<ctm_frame *>(b + o_frames);
     ws.counts_in = reinterpret_cast<int *>(b + o_cin);
@@ -215,6 +213,7 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
     const long long blocks_ub = (long long)std::max(n_boxes, 1) * std::max(p->grid_g * p->grid_g, 1);
     const int grid = (int)std::min<long long>((long long)ds.sm_count * ctas, blocks_ub);
     if (e == cudaSuccess) e = launch_match_persistent(a, threads, grid, s);
+    if (e == cudaSuccess) e = launch_aggregate(a, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return CTM_ECUDA;

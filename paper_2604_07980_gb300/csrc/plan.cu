@@ -150,7 +150,6 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(MatchArgs a)
         P.nocc = nocc;
         a.ws.plans[i] = P;
         a.ws.nblk[i] = P.nblk;
-        a.ws.box_done[i] = 0;
         if (P.nblk == 0) {
             a.disp[i] = __int_as_float(0x7fc00000);
             a.depth[i] = __int_as_float(0x7fc00000);
@@ -220,7 +219,6 @@ __device__ __forceinline__ void mark_range(const MatchArgs &a, int f, int q, int
 
 __global__ void __launch_bounds__(256) sample_kernel(MatchArgs a)
 {
-    __shared__ float agg_scratch[8][2 * kMaxSlots];
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int b = blockIdx.x * 8 + warp;
@@ -291,7 +289,6 @@ __global__ void __launch_bounds__(256) sample_kernel(MatchArgs a)
     }
     const int ndy = a.p.dy_max - a.p.dy_min + 1;
     if (n_valid < a.p.min_pts) {
-        int last = 0;
         if (lane == 0) {
             ctm_block rec;
             rec.n_pts = nx * ny;
@@ -301,12 +298,7 @@ __global__ void __launch_bounds__(256) sample_kernel(MatchArgs a)
             rec.d_sub = 0.0f;
             rec.d_full = 0.0f;
             rec.flags = CTM_BLK_PRESENT | CTM_BLK_FEW_POINTS;
-            last = publish_block(a, box, slot, rec, nd * ndy) ? 1 : 0;
-        }
-        last = __shfl_sync(full, last, 0);
-        if (last) {
-            __threadfence();
-            aggregate_box(a, box, agg_scratch[warp], lane);
+            write_block(a, box, slot, rec);
         }
     } else if (lane == 0) {
         if (n_valid * nd * ndy >= a.big_work) {
@@ -366,6 +358,24 @@ cudaError_t launch_mark(const MatchArgs &a, cudaStream_t s)
 {
     const int grid = ceil_div_nn(a.caps.max_blocks, 8);
     mark_kernel<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// One warp per planned box with blocks: Sec. 4.3.4 over its block records and
+// Eq. 1 (boxes without blocks got their outputs from the planner).
+__global__ void __launch_bounds__(256) aggregate_kernel(MatchArgs a)
+{
+    __shared__ float scratch[8][2 * kMaxSlots];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int box = blockIdx.x * 8 + warp;
+    if (box >= a.ws.counts->n_boxes) return;
+    if (a.ws.nblk[box] == 0) return;
+    aggregate_box(a, box, scratch[warp], lane);
+}
+
+cudaError_t launch_aggregate(const MatchArgs &a, cudaStream_t s)
+{
+    aggregate_kernel<<<ceil_div_nn(a.caps.max_boxes, 8), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
