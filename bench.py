@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--frames", type=int, default=32)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the context's default tuning (deterministic launches for profiling)")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the served 4-stream 30 Hz trace (0: skip the serving leg)")
     return ap.parse_args()
@@ -271,7 +273,10 @@ def main():
 
     # autotuner: launch shapes timed on this batch (results do not depend on them)
     t_tune = time.perf_counter()
-    tuning, tuned_ms = ctx.autotune(batch, reps=3)
+    if args.no_autotune:
+        tuning = ctx.get_tuning()
+    else:
+        tuning, _ = ctx.autotune(batch, reps=3)
     tune_s = time.perf_counter() - t_tune
 
     # warm-up (captures the graph)
@@ -307,16 +312,20 @@ def main():
     value = evals_per_step * world * args.steps / (ms * 1e-3) / 1e9
 
     # ---- per-phase kernel times, same steps, events on the launching stream
-    phase = np.zeros(3)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    names = ("plan", "sample", "mark", "census", "match", "aggregate")
+    phase = np.zeros(len(names))
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(args.steps)]
     torch.cuda.synchronize()
     for i in range(args.steps):
         ctx.match_batch_profiled(batch, evs[i])
     torch.cuda.synchronize()
     for ev in evs:
-        phase += [ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])]
+        phase += [ev[k].elapsed_time(ev[k + 1]) for k in range(len(names))]
     phase /= args.steps
-    plan_ms, census_ms, match_ms = (float(x) for x in phase)
+    kernels_ms = {n: float(v) for n, v in zip(names, phase)}
+    plan_ms = kernels_ms["plan"] + kernels_ms["sample"] + kernels_ms["mark"]
+    census_ms = kernels_ms["census"]
+    match_ms = kernels_ms["match"]
 
     # ---- plain one-launch-per-box path, frame by frame
     plain = None
@@ -405,6 +414,7 @@ def main():
                        "parallelism": f"frames sharded, {world} rank(s), no collective"},
             "boxes_per_s": w.n_boxes * world / (ms_per_step * 1e-3),
             "phases_ms": {"plan_and_mark": plan_ms, "census_roi": census_ms, "match": match_ms},
+            "kernels_ms": kernels_ms,
             "plain_per_box": plain,
             "serving": serving,
             "serving_plain_path": serving_plain,

@@ -18,7 +18,8 @@
  *    must not run two calls concurrently on different streams.
  *  - Return value: CTM_OK (0) or a negative CTM_E* status.  Per-box outcomes
  *    are flags (CTM_BOX_*), never errors.  On error nothing has been enqueued
- *    unless the status is CTM_ECUDA.
+ *    unless the status is CTM_ECUDA; after CTM_ECUDA from a match call the
+ *    context's device state is undefined and the context should be destroyed.
  *  - Disparities are in full-resolution pixels; the right-image match of a left
  *    pixel x is at x - d (d >= 0 for objects in front of the cameras).
  *  - No entry point falls back to a CPU implementation.
@@ -210,14 +211,16 @@ int ctm_match_batch(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *co
                     const ctm_box *boxes_dev, float *disp_dev, float *depth_dev,
                     uint8_t *flags_dev, const ctm_debug *dbg, int use_graph, ctm_stream stream);
 
-/* ctm_match_batch without a graph, recording four caller-created CUDA events
- * (cudaEvent_t handles, created with timing enabled) on `stream`: events[0]
- * before planning, events[1] before the census kernels, events[2] before the
- * matching kernel, events[3] after the per-box aggregation that follows it.  Used to time each phase on the stream
- * the kernels run on.  Errors as ctm_match_batch. */
+/* ctm_match_batch without a graph, recording eight caller-created CUDA events
+ * (cudaEvent_t handles, created with timing enabled) on `stream` around its
+ * launches: events[0] before planning (counter reset and plan_kernel),
+ * [1] before point sampling, [2] before census demand marking, [3] before the
+ * census (tile list and region-of-interest kernel), [4] before matching,
+ * [5] before the per-box aggregation, [6] and [7] after it.  Used to time each
+ * phase on the stream the kernels run on.  Errors as ctm_match_batch. */
 int ctm_match_batch_profiled(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *counts_dev,
                              const ctm_box *boxes_dev, float *disp_dev, float *depth_dev,
-                             uint8_t *flags_dev, void *const events[4], ctm_stream stream);
+                             uint8_t *flags_dev, void *const events[8], ctm_stream stream);
 
 /* End-to-end batch from host memory: frames_host[i].left/right are HOST images
  * (page-locked for asynchronous copies), boxes_host and the outputs are host

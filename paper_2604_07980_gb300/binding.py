@@ -328,12 +328,13 @@ class Context:
         return res
 
     def match_batch_profiled(self, batch: "DeviceBatch", events, stream=None):
-        """Non-graph batch recording 4 torch.cuda.Event(enable_timing=True) at the phase
-        boundaries (before census, before planning, before matching, after matching)."""
+        """Non-graph batch recording 8 torch.cuda.Event(enable_timing=True) around its launches
+        (before plan, sample, mark, census, match, aggregate; after aggregate, twice)."""
+        assert len(events) == 8
         for e in events:  # torch creates the CUDA event on its first record
             if not e.cuda_event:
                 e.record()
-        arr = (ctypes.c_void_p * 4)(*[e.cuda_event for e in events])
+        arr = (ctypes.c_void_p * 8)(*[e.cuda_event for e in events])
         _check(lib().ctm_match_batch_profiled(self._h, _ptr(batch.frames), _ptr(batch.counts),
                                               _ptr(batch.boxes), _ptr(batch.disp), _ptr(batch.depth),
                                               _ptr(batch.flags), arr, _stream(stream)),

@@ -236,6 +236,7 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
     const size_t o_geom = take(sizeof(BlockGeom) * (size_t)ctx->caps.max_blocks);
     const size_t o_queue = take(sizeof(int) * (size_t)ctx->caps.max_blocks);
     const size_t o_counts = take(sizeof(Counts));
+    const size_t o_stats = take(sizeof(Counts));
     const size_t o_frames = take(sizeof(ctm_frame) * (size_t)max_frames);
     const size_t o_cin = take(sizeof(int) * 4);
     // census demand bitmap
@@ -272,6 +273,7 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
     ws.geom = reinterpret_cast<BlockGeom *>(base + o_geom);
     ws.queue = reinterpret_cast<int *>(base + o_queue);
     ws.counts = reinterpret_cast<Counts *>(base + o_counts);
+    ws.stats = reinterpret_cast<Counts *>(base + o_stats);
     ws.frames = reinterpret_cast<ctm_frame *>(base + o_frames);
     ws.counts_in = reinterpret_cast<int *>(base + o_cin);
     ws.bitmap = reinterpret_cast<uint32_t *>(base + o_bm);
@@ -423,27 +425,33 @@ int ctm_match_batch(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *co
 
 int ctm_match_batch_profiled(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *counts_dev,
                              const ctm_box *boxes_dev, float *disp_dev, float *depth_dev,
-                             uint8_t *flags_dev, void *const events[4], ctm_stream stream)
+                             uint8_t *flags_dev, void *const events[8], ctm_stream stream)
 {
-    if (!ctx || !frames_dev || !counts_dev || !boxes_dev || !disp_dev || !depth_dev || !flags_dev ||
-        !events || !events[0] || !events[1] || !events[2] || !events[3])
+    if (!ctx || !frames_dev || !counts_dev || !boxes_dev || !disp_dev || !depth_dev || !flags_dev || !events)
         return CTM_EINVAL;
+    for (int i = 0; i < 8; ++i)
+        if (!events[i]) return CTM_EINVAL;
     int st = set_device(ctx);
     if (st != CTM_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     MatchArgs a = make_args(ctx, frames_dev, counts_dev, boxes_dev, disp_dev, depth_dev, flags_dev,
                             nullptr);
     const int grid = ctx->sm_count * ctx->ctas_per_sm;
-    cudaError_t e = cudaEventRecord((cudaEvent_t)events[0], s);
+    cudaEvent_t const *ev = reinterpret_cast<cudaEvent_t const *>(events);
+    cudaError_t e = cudaEventRecord(ev[0], s);
     if (e == cudaSuccess) e = launch_plan(a, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
     if (e == cudaSuccess) e = launch_sample(a, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2], s);
     if (e == cudaSuccess) e = launch_mark(a, s);
-    if (e == cudaSuccess) e = cudaEventRecord((cudaEvent_t)events[1], s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[3], s);
     if (e == cudaSuccess) e = launch_census_roi(a, ctx->sm_count, s);
-    if (e == cudaSuccess) e = cudaEventRecord((cudaEvent_t)events[2], s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[4], s);
     if (e == cudaSuccess) e = launch_match_persistent(a, ctx->match_threads, grid, s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[5], s);
     if (e == cudaSuccess) e = launch_aggregate(a, s);
-    if (e == cudaSuccess) e = cudaEventRecord((cudaEvent_t)events[3], s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[6], s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[7], s);
     if (e != cudaSuccess) { cudaGetLastError(); return CTM_ECUDA; }
     return CTM_OK;
 }
@@ -667,7 +675,7 @@ int ctm_get_stats(ctm_ctx *ctx, ctm_stats *out, ctm_stream stream)
     if (st != CTM_OK) return st;
     Counts c;
     cudaStream_t s = (cudaStream_t)stream;
-    if (cudaMemcpyAsync(&c, ctx->ws.counts, sizeof(Counts), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+    if (cudaMemcpyAsync(&c, ctx->ws.stats, sizeof(Counts), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         cudaGetLastError();
         return CTM_ECUDA;

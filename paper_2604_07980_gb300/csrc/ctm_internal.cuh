@@ -85,7 +85,8 @@ struct Workspace {
     BlockGeom *geom;           // [max_blocks] indexed like blocks
     int *queue;                // [max_blocks] searchable blocks: large from the front, small from the back
     BlockResult *blkres;       // [max_blocks]
-    Counts *counts;
+    Counts *counts;            // counters of the call in progress (zero between calls)
+    Counts *stats;             // the last finished call's counters
     ctm_frame *frames;         // staging for single-frame calls [max_frames]
     int *counts_in;            // staging {n_frames, n_boxes}
     // census demand bitmap: one bit per 64-pixel tile of a plane row, per frame

@@ -145,6 +145,7 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
     const size_t o_geom = take(sizeof(BlockGeom) * (size_t)caps.max_blocks);
     const size_t o_queue = take(sizeof(int) * (size_t)caps.max_blocks);
     const size_t o_counts = take(sizeof(Counts));
+    const size_t o_stats = take(sizeof(Counts));
     const size_t o_frames = take(sizeof(ctm_frame));
     const size_t o_cin = take(sizeof(int) * 4);
     const size_t o_bm = take(sizeof(uint32_t) * (size_t)plane_off[4]);
@@ -170,6 +171,7 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
     ws.geom = reinterpret_cast<BlockGeom *>(b + o_geom);
     ws.queue = reinterpret_cast<int *>(b + o_queue);
     ws.counts = reinterpret_cast<Counts *>(b + o_counts);
+    ws.stats = reinterpret_cast<Counts *>(b + o_stats);
     ws.frames = reinterpret_cast<ctm_frame *>(b + o_frames);
     ws.counts_in = reinterpret_cast<int *>(b + o_cin);
     ws.bitmap = reinterpret_cast<uint32_t *>(b + o_bm);
@@ -202,8 +204,11 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
         return CTM_ECUDA;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    // the census demand bitmap must start clear (an interrupted call may leave marks)
+    // the census demand bitmap, the counters and the block counts must start at
+    // zero (a call interrupted on the device may leave them set)
     cudaError_t e = cudaMemsetAsync(ws.bitmap, 0, sizeof(uint32_t) * (size_t)plane_off[4], s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.counts, 0, sizeof(Counts), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws.nblk, 0, sizeof(int) * kMaxBoxes, s);
     const ctm_frame fr{left_dev, right_dev, width, height, pitch, 0, n_boxes, f_px, baseline_m};
     if (e == cudaSuccess) e = launch_stage_frame(a, fr, n_boxes, s);
     if (e == cudaSuccess) e = launch_plan(a, s);

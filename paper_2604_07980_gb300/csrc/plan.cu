@@ -1,12 +1,13 @@
 // plan.cu -- device-side planning of Algorithm 2's per-box steps.
 //
-// plan_kernel (one CTA per frame): clip each box to its frame, classify it FAR
+// plan_kernel (kPlanSlices CTAs per frame, each a slice of the frame's boxes,
+// a warp per box): clip each box to its frame, classify it FAR
 // or CLOSE by its larger side against tau_s (Sec. 4.3.4), map it to its matching
 // grid (full resolution for FAR, the decimated grid for CLOSE), count its
 // blocks, and select its occluders -- overlapping boxes of the same frame with a
 // larger bottom y (Sec. 4.3.5), nearest (largest bottom y) first, at most
 // max_occluders.  Boxes that are empty after clipping get their outputs here.
-// The frame's blocks get a contiguous range of the flat (box, slot) block list.
+// Each slice's blocks get a contiguous range of the flat (box, slot) block list.
 //
 // sample_kernel (one warp per block): the block's point grid and its usable
 // points; blocks with fewer than min_pts usable points are finished here, the
@@ -50,6 +51,7 @@ __global__ void stage_frame_kernel(ctm_frame *frames, int *counts_in, ctm_frame 
 }
 
 constexpr int kStageBoxes = 1024;  // boxes of one frame staged in shared memory
+constexpr int kPlanSlices = 4;     // CTAs per frame, each planning a slice of its boxes
 
 // One CTA per frame: clip, classify, map to the matching grid and select the
 // occluders of every box of the frame (the frame's clipped boxes are staged in
@@ -60,11 +62,11 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(MatchArgs a)
     __shared__ int4 sbox[kStageBoxes];
     __shared__ int warp_tot[kPlanThreads / 32];
     __shared__ int s_run, s_base;
-    const int f = blockIdx.x;
+    const int f = blockIdx.x / kPlanSlices, slice = blockIdx.x % kPlanSlices;
     const int nf = clampi(a.counts_in[0], 0, a.caps.max_frames);
     const int nb_total = clampi(a.counts_in[1], 0, a.caps.max_boxes);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (f == 0 && tid == 0) {
+    if (blockIdx.x == 0 && tid == 0) {
         a.ws.counts->n_frames = nf;
         a.ws.counts->n_boxes = nb_total;
     }
@@ -73,7 +75,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(MatchArgs a)
     const bool bad_frame = fr.width < 1 || fr.height < 1 || fr.width > a.caps.max_width ||
                            fr.height > a.caps.max_height || fr.pitch < fr.width ||
                            fr.left == nullptr || fr.right == nullptr;
-    if (tid < 4) {  // census plane descriptors of this frame: L1, R1, Lk, Rk
+    if (slice == 0 && tid < 4) {  // census plane descriptors of this frame: L1, R1, Lk, Rk
         PlaneDesc d;
         const int q = tid;
         d.img = (q & 1) ? fr.right : fr.left;
@@ -99,8 +101,12 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(MatchArgs a)
     __syncthreads();
     const ctm_params &p = a.p;
     const int K = p.max_occluders < kMaxOcc ? p.max_occluders : kMaxOcc;
+    // this CTA's slice of the frame's boxes
+    const int per = (nloc + kPlanSlices - 1) / kPlanSlices;
+    const int sb = begin + min(slice * per, nloc), se = begin + min((slice + 1) * per, nloc);
 
-    for (int i = begin + tid; i < end; i += blockDim.x) {
+    // a warp per box
+    for (int i = sb + warp; i < se; i += kPlanThreads / 32) {
         const int4 r = staged ? sbox[i - begin] : clip_box(a.boxes[i], fr.width, fr.height);
         const int w = r.z - r.x, h = r.w - r.y;
         const int side = w > h ? w : h;
@@ -123,37 +129,45 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(MatchArgs a)
         const bool empty = bad_frame || w <= 0 || h <= 0 || P.sx1 <= P.sx0 || P.sy1 <= P.sy0;
         P.nblk = empty ? 0 : P.g * P.g;
 
-        // occluders: overlap with positive area and strictly larger bottom y;
-        // keep the K with the largest bottom y (ties: lower index first)
-        int ky[kMaxOcc];
-        int kj[kMaxOcc];
+        // occluders: overlap with positive area and strictly larger bottom y; keep
+        // the K with the largest bottom y, ties to the lower index.  Key
+        // (bottom y, -index) is unique per box, so round t takes the largest key
+        // below round t-1's: each lane scans its share of the frame's boxes.
         int nocc = 0;
         if (!empty && K > 0) {
-            for (int j = begin; j < end; ++j) {
-                if (j == i) continue;
-                const int4 q = staged ? sbox[j - begin] : clip_box(a.boxes[j], fr.width, fr.height);
-                if (!(q.w > r.w) || !overlaps(r, q)) continue;
-                // insertion into the descending list (j ascending, so ties keep order)
-                int pos = nocc;
-                while (pos > 0 && ky[pos - 1] < q.w) --pos;
-                if (pos >= K) continue;
-                const int last = nocc < K ? nocc : K - 1;
-                for (int t = last; t > pos; --t) { ky[t] = ky[t - 1]; kj[t] = kj[t - 1]; }
-                ky[pos] = q.w;
-                kj[pos] = j;
-                if (nocc < K) ++nocc;
+            unsigned long long prev = ~0ull;
+            for (; nocc < K; ++nocc) {
+                unsigned long long best = 0ull;
+                for (int j = begin + lane; j < end; j += 32) {
+                    if (j == i) continue;
+                    const int4 q = staged ? sbox[j - begin] : clip_box(a.boxes[j], fr.width, fr.height);
+                    if (!(q.w > r.w) || !overlaps(r, q)) continue;
+                    const unsigned long long key =
+                        ((unsigned long long)(unsigned)q.w << 32) | (unsigned)(0x7fffffff - (j - begin));
+                    if (key < prev && key > best) best = key;
+                }
+                // warp maximum of the 64-bit keys (two 32-bit reductions)
+                const unsigned hi = __reduce_max_sync(0xffffffffu, (unsigned)(best >> 32));
+                const unsigned lo = __reduce_max_sync(0xffffffffu, (unsigned)(best >> 32) == hi ? (unsigned)best : 0u);
+                best = ((unsigned long long)hi << 32) | lo;
+                if (best == 0ull) break;
+                prev = best;
+                if (lane == 0) {
+                    const int j = begin + (0x7fffffff - (int)lo);
+                    a.ws.occ[(long long)i * kMaxOcc + nocc] =
+                        staged ? sbox[j - begin] : clip_box(a.boxes[j], fr.width, fr.height);
+                }
             }
-            for (int t = 0; t < nocc; ++t)
-                a.ws.occ[(long long)i * kMaxOcc + t] =
-                    staged ? sbox[kj[t] - begin] : clip_box(a.boxes[kj[t]], fr.width, fr.height);
         }
         P.nocc = nocc;
-        a.ws.plans[i] = P;
-        a.ws.nblk[i] = P.nblk;
-        if (P.nblk == 0) {
-            a.disp[i] = __int_as_float(0x7fc00000);
-            a.depth[i] = __int_as_float(0x7fc00000);
-            a.flags[i] = (uint8_t)((far ? CTM_BOX_FAR : 0) | CTM_BOX_EMPTY);
+        if (lane == 0) {
+            a.ws.plans[i] = P;
+            a.ws.nblk[i] = P.nblk;
+            if (P.nblk == 0) {
+                a.disp[i] = __int_as_float(0x7fc00000);
+                a.depth[i] = __int_as_float(0x7fc00000);
+                a.flags[i] = (uint8_t)((far ? CTM_BOX_FAR : 0) | CTM_BOX_EMPTY);
+            }
         }
     }
     __syncthreads();
@@ -161,9 +175,9 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(MatchArgs a)
     // frame-local exclusive scan of the block counts, one reservation per frame
     if (tid == 0) s_run = 0;
     __syncthreads();
-    for (int c0 = begin; c0 < end; c0 += blockDim.x) {
+    for (int c0 = sb; c0 < se; c0 += blockDim.x) {
         const int i = c0 + tid;
-        const int v = i < end ? a.ws.nblk[i] : 0;
+        const int v = i < se ? a.ws.nblk[i] : 0;
         int x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -177,7 +191,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(MatchArgs a)
             if (wi < warp) wpre += warp_tot[wi];
             tot += warp_tot[wi];
         }
-        if (i < end) a.ws.blk_base[i] = s_run + wpre + x - v;  // frame-local for now
+        if (i < se) a.ws.blk_base[i] = s_run + wpre + x - v;  // slice-local for now
         __syncthreads();
         if (tid == 0) s_run += tot;
         __syncthreads();
@@ -186,7 +200,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(MatchArgs a)
     __syncthreads();
     const int base = s_base;
     // a warp per box writes the box's entries of the flat block list
-    for (int i = begin + warp; i < end; i += kPlanThreads / 32) {
+    for (int i = sb + warp; i < se; i += kPlanThreads / 32) {
         const int bb = base + a.ws.blk_base[i];
         const int v = a.ws.nblk[i];
         __syncwarp();
@@ -363,14 +377,25 @@ cudaError_t launch_mark(const MatchArgs &a, cudaStream_t s)
 
 // One warp per planned box with blocks: Sec. 4.3.4 over its block records and
 // Eq. 1 (boxes without blocks got their outputs from the planner).
+//
+// It is the last kernel of a call, so it also leaves the workspace ready for
+// the next one: block 0 moves the counters to the stats record and zeroes
+// them, and every box's block count goes back to zero (no memset nodes at the
+// start of a call).
 __global__ void __launch_bounds__(256) aggregate_kernel(MatchArgs a)
 {
     __shared__ float scratch[8][2 * kMaxSlots];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *a.ws.stats = *a.ws.counts;
+        *a.ws.counts = Counts{};
+    }
     const int box = blockIdx.x * 8 + warp;
-    if (box >= a.ws.counts->n_boxes) return;
+    if (box >= clampi(a.counts_in[1], 0, a.caps.max_boxes)) return;
     if (a.ws.nblk[box] == 0) return;
     aggregate_box(a, box, scratch[warp], lane);
+    __syncwarp();
+    if (lane == 0) a.ws.nblk[box] = 0;
 }
 
 cudaError_t launch_aggregate(const MatchArgs &a, cudaStream_t s)
@@ -385,12 +410,11 @@ cudaError_t launch_stage_frame(const MatchArgs &a, ctm_frame f, int n_boxes, cud
     return cudaGetLastError();
 }
 
+// The counters and block counts start at zero: the workspace is created zeroed
+// and every call's aggregate_kernel zeroes them again.
 cudaError_t launch_plan(const MatchArgs &a, cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(a.ws.nblk, 0, sizeof(int) * (size_t)a.caps.max_boxes, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(a.ws.counts, 0, sizeof(Counts), s);  // all counters
-    if (e != cudaSuccess) return e;
-    plan_kernel<<<a.caps.max_frames, kPlanThreads, 0, s>>>(a);
+    plan_kernel<<<a.caps.max_frames * kPlanSlices, kPlanThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
