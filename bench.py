@@ -41,7 +41,7 @@ POPC_PER_EVAL = 2          # one u64 code pair = two 32-bit popcounts
 # DRAM bytes (read + write) of one match_persistent_kernel launch on this workload, from the
 # ncu capture summarised in profiles/match_persistent_kernel_batch32x1200.md; None once the
 # kernel changes after that capture.
-MATCH_DRAM_BYTES = None
+MATCH_DRAM_BYTES = (102.542 + 4.018) * 1e6
 # kernels of one step of the batched path: plan, sample, mark, tile_list, census_roi, match,
 # aggregate
 KERNELS_PER_STEP = 7
