@@ -447,3 +447,42 @@ int orc_match_frame(const uint8_t *L, const uint8_t *R, int W, int H, int pitch,
     free(bres); free(dvals);
     return 0;
 }
+
+/* Sec. 4.3.6 (Q reprojection, transform to the vehicle frame) and the
+ * covariance estimation equation, written out in double. */
+void orc_box_points(const int32_t *boxes, const float *disp, const uint8_t *flags, int n,
+                    const orc_geometry *geo, int n_geo, double *out)
+{
+    for (int i = 0; i < n; ++i) {
+        double *o = out + 8 * (size_t)i;
+        for (int k = 0; k < 8; ++k) o[k] = NAN;
+        const int32_t *b = boxes + 5 * (size_t)i;
+        const int fi = b[4];
+        if (fi < 0 || fi >= n_geo || !(flags[i] & ORC_BOX_VALID)) continue;
+        const orc_geometry *g = geo + fi;
+        const int x0 = b[0] > 0 ? b[0] : 0, y0 = b[1] > 0 ? b[1] : 0;
+        const int x1 = b[2] < g->width ? b[2] : g->width, y1 = b[3] < g->height ? b[3] : g->height;
+        if (x1 <= x0 || y1 <= y0) continue;
+        const double in[4] = {(x0 + x1 - 1) / 2.0, (y0 + y1 - 1) / 2.0, (double)disp[i], 1.0};
+        double h[4];
+        for (int r = 0; r < 4; ++r) {
+            h[r] = 0.0;
+            for (int c = 0; c < 4; ++c) h[r] += g->Q[4 * r + c] * in[c];
+        }
+        if (h[3] == 0.0) continue;
+        const double p[3] = {h[0] / h[3], h[1] / h[3], h[2] / h[3]};
+        double pv[3];
+        for (int r = 0; r < 3; ++r)
+            pv[r] = g->T[4 * r] * p[0] + g->T[4 * r + 1] * p[1] + g->T[4 * r + 2] * p[2] + g->T[4 * r + 3];
+        const double Z = p[2];
+        const double fb = g->f_px * g->baseline_m;
+        o[0] = p[0];
+        o[1] = p[1];
+        o[2] = p[2];
+        o[3] = pv[0];
+        o[4] = pv[1];
+        o[5] = pv[2];
+        o[6] = Z * Z * Z * Z * g->disp_var / (fb * fb);
+        o[7] = h[3];
+    }
+}

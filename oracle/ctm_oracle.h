@@ -102,6 +102,27 @@ int orc_match_frame(const uint8_t *L, const uint8_t *R, int W, int H, int pitch,
                     const orc_params *p, float *disp, float *depth, uint8_t *flags,
                     orc_block *blk, int32_t *cost_f, int32_t *cost_b);
 
+/* Camera geometry of one frame for orc_box_points. */
+typedef struct {
+    double Q[16];        /* 4x4 row-major reprojection matrix: [X Y Z W]^T = Q [u v d 1]^T */
+    double T[12];        /* 3x4 row-major camera-to-vehicle transform [R | t]               */
+    double disp_var;     /* sigma_d^2 (px^2), the configured disparity variance            */
+    double f_px, baseline_m;
+    int32_t width, height;   /* image size: boxes are clipped to it                        */
+} orc_geometry;
+
+/* Sec. 4.3.6 disparity-to-depth conversion and covariance estimation, in
+ * double, for n boxes after matching.  Box i uses geo[boxes[i].frame].  For a
+ * VALID box: (u, v) = centre of the clipped box in pixel coordinates (pixel c
+ * spans [c, c+1), its centre is c; so u = (x0 + x1 - 1) / 2), d = disp[i];
+ * [X Y Z W] = Q [u v d 1]; p = (X, Y, Z) / W; p_v = R p + t;
+ * sigma_Z^2 = Z^4 sigma_d^2 / (f^2 b^2) with Z = p.z.  out[8 i ..]: p.x, p.y,
+ * p.z, p_v.x, p_v.y, p_v.z, sigma_Z^2, W; all NaN when the box is not VALID,
+ * its frame index is outside [0, n_geo) or W == 0.  The paper prints no
+ * worked example; the tests pin this against closed forms. */
+void orc_box_points(const int32_t *boxes, const float *disp, const uint8_t *flags, int n,
+                    const orc_geometry *geo, int n_geo, double *out);
+
 #ifdef __cplusplus
 }
 #endif

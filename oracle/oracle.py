@@ -57,6 +57,9 @@ def lib():
         L.orc_aggregate.restype = ctypes.c_int
         L.orc_depth.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_float]
         L.orc_depth.restype = ctypes.c_float
+        L.orc_box_points.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+        L.orc_box_points.restype = None
         L.orc_match_frame.argtypes = [u8p, u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       i32p, ctypes.c_int, ctypes.c_float, ctypes.c_float,
                                       ctypes.c_void_p, f32p, f32p, u8p, ctypes.c_void_p,
@@ -196,3 +199,32 @@ def match_batch(frames, boxes: np.ndarray, p: Params, debug: bool = False):
         outs.append(match_frame(L, R, boxes[sel], f_px, b_m, p, debug=debug))
     res = {key: np.concatenate([o[key] for o in outs]) for key in outs[0]} if outs else {}
     return res
+
+
+class _CGeometry(ctypes.Structure):
+    _fields_ = [("Q", ctypes.c_double * 16), ("T", ctypes.c_double * 12), ("disp_var", ctypes.c_double),
+                ("f_px", ctypes.c_double), ("baseline_m", ctypes.c_double),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+def box_points(boxes: np.ndarray, disp: np.ndarray, flags: np.ndarray, geometries) -> np.ndarray:
+    """Sec. 4.3.6 reprojection + vehicle transform + depth variance per box (float64 [n, 8]:
+    camera x y z, vehicle x y z, sigma_Z^2, W).  geometries: list of dicts with Q (4x4),
+    T (3x4), disp_var, f_px, baseline_m, width, height; box i uses geometries[boxes[i, 4]]."""
+    boxes = np.ascontiguousarray(boxes, dtype=np.int32).reshape(-1, 5)
+    n = boxes.shape[0]
+    disp = np.ascontiguousarray(disp, dtype=np.float32)
+    flags = np.ascontiguousarray(flags, dtype=np.uint8)
+    arr = (_CGeometry * max(len(geometries), 1))()
+    for i, g in enumerate(geometries):
+        arr[i].Q[:] = [float(x) for x in np.asarray(g["Q"], np.float64).ravel()]
+        arr[i].T[:] = [float(x) for x in np.asarray(g["T"], np.float64).ravel()]
+        arr[i].disp_var = float(g["disp_var"])
+        arr[i].f_px = float(g["f_px"])
+        arr[i].baseline_m = float(g["baseline_m"])
+        arr[i].width = int(g["width"])
+        arr[i].height = int(g["height"])
+    out = np.empty((max(n, 1), 8), np.float64)
+    lib().orc_box_points(boxes.ctypes.data, disp.ctypes.data, flags.ctypes.data, n,
+                         ctypes.addressof(arr), len(geometries), out.ctypes.data)
+    return out[:n]
