@@ -43,7 +43,8 @@ POPC_PER_EVAL = 2          # one u64 code pair = two 32-bit popcounts
 # ncu capture summarised in profiles/match_persistent_kernel_batch32x1200.md; None once the
 # kernel changes after that capture.
 MATCH_DRAM_BYTES = (102.542 + 4.018) * 1e6
-# kernels of one step of the batched path: plan, sample, mark, tile_list, census_roi, match,
+# kernels of one step of the batched path (ctm_box_points, timed apart, is not in it): plan,
+# sample, mark, tile_list, census_roi, match,
 # aggregate
 KERNELS_PER_STEP = 7
 
@@ -409,6 +410,27 @@ def main():
     h2d = sum(f.left.nbytes + f.right.nbytes for f in w.frames) + w.boxes.nbytes + 48 * len(w.frames) + 8
     d2h = w.n_boxes * 9
 
+    # ---- Sec. 4.3.6 step after matching: 3-D points in camera and vehicle frames + depth variance
+    cx, cy = 1920 / 2.0, 1200 / 2.0
+    Qm = np.array([[1, 0, 0, -cx], [0, 1, 0, -cy], [0, 0, 0, wl.F_PX], [0, 0, 1 / wl.BASELINE_M, 0]])
+    Tm = np.hstack([np.eye(3), np.array([[0.0], [1.2], [-1.5]])])
+    geo_dev, n_geo = B.geometries_to_device(
+        [dict(Q=Qm, T=Tm, disp_var=0.25, f_px=wl.F_PX, baseline_m=wl.BASELINE_M, width=1920, height=1200)]
+        * len(w.frames))
+    pts = torch.empty((w.n_boxes, 8), dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        B.box_points(batch.boxes, batch.disp, batch.flags, geo_dev, n_geo, out=pts)
+    q0 = torch.cuda.Event(enable_timing=True)
+    q1 = torch.cuda.Event(enable_timing=True)
+    q0.record(stream)
+    for _ in range(args.steps):
+        B.box_points(batch.boxes, batch.disp, batch.flags, geo_dev, n_geo, out=pts)
+    q1.record(stream)
+    torch.cuda.synchronize()
+    pts_ms = q0.elapsed_time(q1) / args.steps
+    box_points = {"ms": pts_ms, "boxes_per_s": w.n_boxes / (pts_ms * 1e-3),
+                  "valid_boxes": int(torch.isfinite(pts[:, 2]).sum().item())}
+
     # ---- roofline of the matching kernel (integer popcount pipe)
     sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
     popc_rate = B.probe_int_rate(0, 4096)
@@ -450,6 +472,7 @@ def main():
             "phases_ms": {"plan_and_mark": plan_ms, "census_roi": census_ms, "match": match_ms},
             "kernels_ms": kernels_ms,
             "plain_per_box": plain,
+            "box_points": box_points,
             "serving": serving,
             "serving_plain_path": serving_plain,
             "e2e": {"value": evals_per_step * world / e2e_s / 1e9, "unit": UNIT,

@@ -253,6 +253,31 @@ int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_dev, const 
 /* Counters of the most recent match call on ctx.  Synchronizes `stream`. */
 int ctm_get_stats(ctm_ctx *ctx, ctm_stats *out, ctm_stream stream);
 
+/* Camera geometry of one frame for ctm_box_points (Sec. 4.3.6). */
+typedef struct {
+    float Q[16];          /* 4x4 row-major reprojection matrix: [X Y Z W]^T = Q [u v d 1]^T  */
+    float T[12];          /* 3x4 row-major camera-to-vehicle transform [R | t]                */
+    float disp_var;       /* sigma_d^2 (px^2): the configured disparity variance              */
+    float f_px, baseline_m;
+    int32_t width, height;    /* image size: boxes are clipped to it                          */
+    int32_t reserved;
+} ctm_geometry;
+
+/* Sec. 4.3.6 disparity-to-depth conversion and the covariance estimation, per
+ * box, after a match call: box i uses geo_dev[boxes_dev[i].frame].  For a box
+ * whose flags have CTM_BOX_VALID: (u, v) = centre of the box clipped to the
+ * image, in pixel coordinates (pixel c spans [c, c+1), so u = (x0 + x1 - 1) / 2),
+ * d = disp_dev[i]; [X Y Z W] = Q [u v d 1]; p = (X, Y, Z) / W in the camera
+ * frame; p_v = R p + t in the vehicle frame; sigma_Z^2 = Z^4 sigma_d^2 / (f b)^2
+ * with Z = p.z.  out_dev (float, n_boxes x 8, row-major): p.x, p.y, p.z, p_v.x,
+ * p_v.y, p_v.z, sigma_Z^2, W; all NaN for boxes that are not VALID, whose frame
+ * index is outside [0, n_geo), or whose W is 0.  fp32 arithmetic in a fixed
+ * order (no contraction).  out_dev must be 16-byte aligned.  Errors: CTM_EINVAL
+ * (null pointer, n < 0, unaligned out_dev), CTM_ECUDA. */
+int ctm_box_points(const ctm_box *boxes_dev, const float *disp_dev, const uint8_t *flags_dev,
+                   int n_boxes, const ctm_geometry *geo_dev, int n_geo, float *out_dev,
+                   ctm_stream stream);
+
 /* Current tuning of a context. */
 int ctm_get_tuning(const ctm_ctx *ctx, ctm_tuning *out);
 

@@ -27,6 +27,7 @@ EXPORTS = ("ctm_status_str", "ctm_default_params", "ctm_create", "ctm_destroy",
            "ctm_census_build", "ctm_match_boxes", "ctm_match_boxes_plain", "ctm_match_batch",
            "ctm_match_batch_profiled", "ctm_match_batch_host", "ctm_match_boxes_noalloc",
            "ctm_get_stats", "ctm_probe_int_rate", "ctm_get_tuning", "ctm_set_tuning", "ctm_autotune",
+           "ctm_box_points",
            "ctm_server_default_config", "ctm_server_create", "ctm_server_submit", "ctm_server_poll",
            "ctm_server_outstanding", "ctm_server_get_stats", "ctm_server_destroy", "ctm_server_now_ns")
 
@@ -60,6 +61,12 @@ class ctm_debug(ctypes.Structure):
 class ctm_stats(ctypes.Structure):
     _fields_ = [("cost_evals", ctypes.c_uint64), ("n_blocks", ctypes.c_int32), ("n_boxes", ctypes.c_int32),
                 ("error", ctypes.c_int32), ("census_tiles", ctypes.c_int32)]
+
+
+class ctm_geometry(ctypes.Structure):
+    _fields_ = [("Q", ctypes.c_float * 16), ("T", ctypes.c_float * 12), ("disp_var", ctypes.c_float),
+                ("f_px", ctypes.c_float), ("baseline_m", ctypes.c_float), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class ctm_tuning(ctypes.Structure):
@@ -148,6 +155,8 @@ def lib():
     L.ctm_get_stats.restype = i32
     L.ctm_probe_int_rate.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double)]
     L.ctm_probe_int_rate.restype = i32
+    L.ctm_box_points.argtypes = [vp, vp, vp, i32, vp, i32, vp, vp]
+    L.ctm_box_points.restype = i32
     L.ctm_get_tuning.argtypes = [vp, ctypes.POINTER(ctm_tuning)]
     L.ctm_get_tuning.restype = i32
     L.ctm_set_tuning.argtypes = [vp, ctypes.POINTER(ctm_tuning)]
@@ -415,6 +424,36 @@ class DeviceBatch:
         self.disp = torch.empty(max(n, 1), dtype=torch.float32, device=device)
         self.depth = torch.empty(max(n, 1), dtype=torch.float32, device=device)
         self.flags = torch.empty(max(n, 1), dtype=torch.uint8, device=device)
+
+
+def geometries_to_device(geometries, device="cuda"):
+    """ctm_geometry array in device memory from dicts with Q (4x4), T (3x4), disp_var,
+    f_px, baseline_m, width, height."""
+    torch = _torch()
+    arr = (ctm_geometry * max(len(geometries), 1))()
+    for i, g in enumerate(geometries):
+        arr[i].Q[:] = [float(x) for x in np.asarray(g["Q"], np.float64).ravel()]
+        arr[i].T[:] = [float(x) for x in np.asarray(g["T"], np.float64).ravel()]
+        arr[i].disp_var = float(g["disp_var"])
+        arr[i].f_px = float(g["f_px"])
+        arr[i].baseline_m = float(g["baseline_m"])
+        arr[i].width = int(g["width"])
+        arr[i].height = int(g["height"])
+    raw = np.frombuffer(bytes(arr), dtype=np.uint8)
+    return torch.from_numpy(raw.copy()).to(device), len(geometries)
+
+
+def box_points(boxes, disp, flags, geo, n_geo: int, out=None, stream=None):
+    """Sec. 4.3.6 per box on the device: float32 [n, 8] (camera x y z, vehicle x y z,
+    sigma_Z^2, W).  boxes int32 [n, 5] (column 4 = frame index into geo), disp float32 [n],
+    flags uint8 [n], geo from geometries_to_device."""
+    torch = _torch()
+    n = int(boxes.shape[0])
+    if out is None:
+        out = torch.empty((max(n, 1), 8), dtype=torch.float32, device=boxes.device)
+    _check(lib().ctm_box_points(_ptr(boxes), _ptr(disp), _ptr(flags), n, _ptr(geo), int(n_geo), _ptr(out),
+                                _stream(stream)), "ctm_box_points")
+    return out[:n]
 
 
 def _host_ptr(a):

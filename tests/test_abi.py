@@ -44,6 +44,7 @@ def test_struct_layouts():
     assert B.BLOCK_DTYPE.itemsize == B.BLOCK_BYTES == 48
     assert ctypes.sizeof(B.ctm_debug) == 24
     assert ctypes.sizeof(B.ctm_tuning) == 16
+    assert ctypes.sizeof(B.ctm_geometry) == 136
     assert ctypes.sizeof(B.ctm_server_config) == 40
     assert ctypes.sizeof(B.ctm_request) == 80
     assert ctypes.sizeof(B.ctm_completion) == 56
@@ -107,3 +108,11 @@ def test_tuning_argument_checks(built):
     assert L.ctm_get_tuning(None, ctypes.byref(t)) == B.CTM_EINVAL
     assert L.ctm_set_tuning(None, ctypes.byref(t)) == B.CTM_EINVAL
     assert L.ctm_autotune(None, None, None, None, None, None, None, 3, None, None, None) == B.CTM_EINVAL
+
+
+def test_box_points_argument_checks(built):
+    from paper_2604_07980_gb300 import binding as B
+    L = B.lib()
+    assert L.ctm_box_points(None, None, None, 0, None, 0, None, None) == B.CTM_OK  # nothing to do
+    assert L.ctm_box_points(None, None, None, 4, None, 1, None, None) == B.CTM_EINVAL
+    assert L.ctm_box_points(None, None, None, -1, None, 0, None, None) == B.CTM_EINVAL
