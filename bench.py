@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--frames", type=int, default=32)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tuning", type=str, default=None,
+                    help="JSON object of ctm_tuning fields to set instead of autotuning")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the context's default tuning (deterministic launches for profiling)")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
@@ -305,7 +307,10 @@ def main():
 
     # autotuner: launch shapes timed on this batch (results do not depend on them)
     t_tune = time.perf_counter()
-    if args.no_autotune:
+    if args.tuning:
+        ctx.set_tuning(**json.loads(args.tuning))
+        tuning = ctx.get_tuning()
+    elif args.no_autotune:
         tuning = ctx.get_tuning()
     else:
         tuning, _ = ctx.autotune(batch, reps=3)

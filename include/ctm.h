@@ -139,6 +139,10 @@ typedef struct {
     int32_t census_mode;    /* region-of-interest census: 0 = 4 CTAs per SM, 1 = 3    */
     int32_t big_work;       /* blocks with usable points x candidates >= big_work are
                                queued first (largest work first)                      */
+    int32_t match_mode;     /* 0: fused matcher (one CTA runs both passes of a block);
+                               1: two-pass pipelined matcher (a forward kernel, then a
+                               backward kernel; each CTA loads its next block while it
+                               scans the current one)                                 */
 } ctm_tuning;
 
 /* Counters of the last match call (ctm_get_stats). */
@@ -289,7 +293,8 @@ int ctm_set_tuning(ctm_ctx *ctx, const ctm_tuning *t);
 
 /* Autotuner: runs the batch of ctm_match_batch (same arguments, no debug
  * output) under candidate tunings -- every matching CTA size x strip width,
- * then each census variant and each queue split around the best so far --
+ * for each matcher, then each census variant and each queue split around the
+ * best so far --
  * timing `reps` calls of each with CUDA events after one warm-up call, keeps
  * the fastest in the context and returns it in *best (and its time per call,
  * in ms, in *best_ms; either may be NULL).  The outputs are written by every

@@ -71,7 +71,8 @@ class ctm_geometry(ctypes.Structure):
 
 class ctm_tuning(ctypes.Structure):
     _fields_ = [("match_threads", ctypes.c_int32), ("strip_cols", ctypes.c_int32),
-                ("census_mode", ctypes.c_int32), ("big_work", ctypes.c_int32)]
+                ("census_mode", ctypes.c_int32), ("big_work", ctypes.c_int32),
+                ("match_mode", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}

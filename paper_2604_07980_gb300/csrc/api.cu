@@ -36,6 +36,7 @@ struct ctm_ctx {
     int strip_rows = 0;
     int census_mode = 0;
     int big_work = 4096;
+    int match_mode = 0;
     int nd_max = 0;
     void *dev_mem = nullptr;
     size_t dev_bytes = 0;
@@ -102,6 +103,7 @@ MatchArgs make_args(const ctm_ctx *ctx, const ctm_frame *frames, const int32_t *
     a.strip_rows = ctx->strip_rows;
     a.big_work = ctx->big_work;
     a.census_mode = ctx->census_mode;
+    a.match_mode = ctx->match_mode;
     return a;
 }
 
@@ -118,7 +120,9 @@ int enqueue_match(ctm_ctx *ctx, const MatchArgs &a, int frames_grid, int match_g
     if (e == cudaSuccess) e = launch_mark(b, s);
     if (e == cudaSuccess) e = launch_census_roi(b, ctx->sm_count, s);
     if (!plain) {
-        if (e == cudaSuccess) e = launch_match_persistent(b, ctx->match_threads, match_grid, s);
+        if (e == cudaSuccess)
+            e = ctx->match_mode == 1 ? launch_match_pipe(b, ctx->match_threads, match_grid, s)
+                                     : launch_match_persistent(b, ctx->match_threads, match_grid, s);
     } else {
         for (int i = 0; i < n_boxes_host && e == cudaSuccess; ++i)
             e = launch_match_box(b, ctx->match_threads, i, s);
@@ -447,7 +451,9 @@ int ctm_match_batch_profiled(ctm_ctx *ctx, const ctm_frame *frames_dev, const in
     if (e == cudaSuccess) e = cudaEventRecord(ev[3], s);
     if (e == cudaSuccess) e = launch_census_roi(a, ctx->sm_count, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev[4], s);
-    if (e == cudaSuccess) e = launch_match_persistent(a, ctx->match_threads, grid, s);
+    if (e == cudaSuccess)
+        e = ctx->match_mode == 1 ? launch_match_pipe(a, ctx->match_threads, grid, s)
+                                 : launch_match_persistent(a, ctx->match_threads, grid, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev[5], s);
     if (e == cudaSuccess) e = launch_aggregate(a, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev[6], s);
@@ -550,6 +556,7 @@ int ctm_get_tuning(const ctm_ctx *ctx, ctm_tuning *out)
     out->strip_cols = ctx->strip_cols;
     out->census_mode = ctx->census_mode;
     out->big_work = ctx->big_work;
+    out->match_mode = ctx->match_mode;
     return CTM_OK;
 }
 
@@ -560,6 +567,7 @@ int ctm_set_tuning(ctm_ctx *ctx, const ctm_tuning *t)
     if (t->strip_cols < ctx->nd_max + 2 || (t->strip_cols & 31) != 0 || t->strip_cols > 4096) return CTM_EINVAL;
     if (t->census_mode != 0 && t->census_mode != 1) return CTM_EINVAL;
     if (t->big_work < 0) return CTM_EINVAL;
+    if (t->match_mode != 0 && t->match_mode != 1) return CTM_EINVAL;
     int st = set_device(ctx);
     if (st != CTM_OK) return st;
     ctm_ctx trial = *ctx;  // shallow: only the tuning fields are read below
@@ -567,17 +575,27 @@ int ctm_set_tuning(ctm_ctx *ctx, const ctm_tuning *t)
     trial.strip_cols = t->strip_cols;
     MatchArgs a = make_args(&trial, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
     int ctas = 0;
+    // the fused kernels stay configured either way (the per-box path uses them)
     if (match_smem_bytes(a) > 227 * 1024) return CTM_EINVAL;
     if (match_configure(a, t->match_threads, &ctas) != cudaSuccess || ctas < 1) {
         cudaGetLastError();
         return CTM_EINVAL;
     }
+    if (t->match_mode == 1) {
+        if (match_pipe_smem_bytes(a) > 227 * 1024) return CTM_EINVAL;
+        if (match_pipe_configure(a, t->match_threads, &ctas) != cudaSuccess || ctas < 1) {
+            cudaGetLastError();
+            return CTM_EINVAL;
+        }
+    }
     const bool changed = t->match_threads != ctx->match_threads || t->strip_cols != ctx->strip_cols ||
-                         t->census_mode != ctx->census_mode || t->big_work != ctx->big_work;
+                         t->census_mode != ctx->census_mode || t->big_work != ctx->big_work ||
+                         t->match_mode != ctx->match_mode;
     ctx->match_threads = t->match_threads;
     ctx->strip_cols = t->strip_cols;
     ctx->census_mode = t->census_mode;
     ctx->big_work = t->big_work;
+    ctx->match_mode = t->match_mode;
     ctx->ctas_per_sm = ctas;
     if (changed && ctx->gexec) {  // the captured graph holds the old launch shapes
         cudaGraphExecDestroy(ctx->gexec);
@@ -622,11 +640,13 @@ int ctm_autotune(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *count
     ctm_tuning bt = cur;
     float bms = 3.4e38f;
     int status = CTM_OK;
-    // 1. matching CTA size x strip chunk width (joint), at the current census mode and split
+    // 1. matcher x CTA size x strip chunk width (joint), at the current census mode and split
     const int base = (int)round_up(ctx->nd_max + 34, 32);
-    for (int th = 128; th <= 256 && status == CTM_OK; th *= 2) {
+    for (int mode = 0; mode <= 1 && status == CTM_OK; ++mode) {
+      for (int th = 128; th <= 256 && status == CTM_OK; th *= 2) {
         for (int extra = 0; extra <= 192; extra += 32) {
             ctm_tuning t = bt;
+            t.match_mode = mode;
             t.match_threads = th;
             t.strip_cols = base + extra;
             float ms = 0.0f;
@@ -635,6 +655,7 @@ int ctm_autotune(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *count
             if (r != CTM_OK) { status = r; break; }
             if (ms < bms) { bms = ms; bt = t; }
         }
+      }
     }
     // 2. census variant, 3. queue split, one at a time around the best so far
     const int modes[2] = {0, 1};

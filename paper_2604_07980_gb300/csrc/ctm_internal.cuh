@@ -50,7 +50,14 @@ struct __align__(16) BlockGeom {
     int32_t n_valid;
     int32_t nx, ny;
     uint32_t cstart;                  // bit j: a strip column chunk starts at column j
+    // the block's box plan, copied so that a matcher needs only this record
+    int32_t box, slot, frame, k, far, dmin, dmax, Ws, Hs;
+    // forward-pass result, written by the two-pass matcher's forward kernel
+    int32_t d_f, dy_f;                // first argmin of the forward costs
+    int32_t s_m, s_0, s_p;            // costs at d_f - 1, d_f, d_f + 1 (0 where outside)
+    int32_t pad[2];
 };
+static_assert(sizeof(BlockGeom) % 16 == 0, "BlockGeom is moved by 16-byte copies");
 
 // Result of one block kept for the aggregation (device).
 struct BlockResult {
@@ -118,6 +125,7 @@ struct MatchArgs {
     int nc_stride;
     int strip_cols;            // columns of the shared-memory strip
     int big_work;              // queue split: usable points x candidates of a large block
+    int match_mode;            // 0: fused single-kernel matcher, 1: two-pass pipelined matcher
     int census_mode;           // region-of-interest census variant (census.cu)
     int strip_rows;            // rows of the shared-memory strip (pts_side * ndy)
 };
@@ -178,6 +186,12 @@ cudaError_t match_configure(const MatchArgs &a, int threads, int *ctas_per_sm);
 cudaError_t match_configure_raise(const MatchArgs &a, int threads, int *ctas_per_sm);
 cudaError_t launch_match_persistent(const MatchArgs &a, int threads, int grid, cudaStream_t s);
 cudaError_t launch_match_box(const MatchArgs &a, int threads, int box, cudaStream_t s);
+
+// Two-pass pipelined matcher (match_pipe.cu): forward kernel then backward
+// kernel over the same queue, `grid` persistent CTAs each.
+size_t match_pipe_smem_bytes(const MatchArgs &a);
+cudaError_t match_pipe_configure(const MatchArgs &a, int threads, int *ctas_per_sm);
+cudaError_t launch_match_pipe(const MatchArgs &a, int threads, int grid, cudaStream_t s);
 
 // Probe (probe.cu)
 cudaError_t run_int_probe(int kind, int iters, double *ops_per_clk_per_sm);

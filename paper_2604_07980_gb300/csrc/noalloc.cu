@@ -195,6 +195,7 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
     a.strip_cols = strip_cols;
     a.big_work = 4096;
     a.census_mode = 0;
+    a.match_mode = 0;
     a.strip_rows = p->pts_side * ndy;
 
     const int threads = 128;

@@ -300,6 +300,15 @@ __global__ void __launch_bounds__(256) sample_kernel(MatchArgs a)
         g->nx = nx;
         g->ny = ny;
         g->cstart = cstart;
+        g->box = box;
+        g->slot = slot;
+        g->frame = P.frame;
+        g->k = P.k;
+        g->far = P.far;
+        g->dmin = P.dmin;
+        g->dmax = P.dmax;
+        g->Ws = P.Ws;
+        g->Hs = P.Hs;
     }
     const int ndy = a.p.dy_max - a.p.dy_min + 1;
     if (n_valid < a.p.min_pts) {

@@ -43,7 +43,7 @@ def test_struct_layouts():
     assert ctypes.sizeof(B.ctm_frame) == 48
     assert B.BLOCK_DTYPE.itemsize == B.BLOCK_BYTES == 48
     assert ctypes.sizeof(B.ctm_debug) == 24
-    assert ctypes.sizeof(B.ctm_tuning) == 16
+    assert ctypes.sizeof(B.ctm_tuning) == 20
     assert ctypes.sizeof(B.ctm_geometry) == 136
     assert ctypes.sizeof(B.ctm_server_config) == 40
     assert ctypes.sizeof(B.ctm_request) == 80
@@ -104,7 +104,7 @@ def test_server_argument_checks(built):
 def test_tuning_argument_checks(built):
     from paper_2604_07980_gb300 import binding as B
     L = B.lib()
-    t = B.ctm_tuning(128, 192, 0, 4096)
+    t = B.ctm_tuning(128, 192, 0, 4096, 0)
     assert L.ctm_get_tuning(None, ctypes.byref(t)) == B.CTM_EINVAL
     assert L.ctm_set_tuning(None, ctypes.byref(t)) == B.CTM_EINVAL
     assert L.ctm_autotune(None, None, None, None, None, None, None, 3, None, None, None) == B.CTM_EINVAL
