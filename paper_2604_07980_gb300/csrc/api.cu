@@ -641,10 +641,10 @@ int ctm_autotune(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *count
     float bms = 3.4e38f;
     int status = CTM_OK;
     // 1. matcher x CTA size x strip chunk width (joint), at the current census mode and split
-    const int base = (int)round_up(ctx->nd_max + 34, 32);
+    const int base = (int)round_up(ctx->nd_max + 2, 32);  // the narrowest strip a point column fits
     for (int mode = 0; mode <= 1 && status == CTM_OK; ++mode) {
       for (int th = 128; th <= 256 && status == CTM_OK; th *= 2) {
-        for (int extra = 0; extra <= 192; extra += 32) {
+        for (int extra = 0; extra <= 224; extra += 32) {
             ctm_tuning t = bt;
             t.match_mode = mode;
             t.match_threads = th;

@@ -36,8 +36,6 @@ struct Shared {
     int Y[kMaxPtsSide];
     int colstart[kMaxPtsSide + 1];
     unsigned warp_min[NW];
-    float agg[kMaxSlots];
-    float agg_sorted[kMaxSlots];
     int d_f, dy_f, s_m, s_0, s_p;
     int d_b, dy_b;
     int next;               // queue index of the next block
