@@ -133,7 +133,7 @@ typedef struct {
 typedef struct {
     int32_t match_threads;  /* matching CTA size: 128 or 256 threads                    */
     int32_t strip_cols;     /* width, in codes, of the staged strip of one column chunk
-                               of a block: a multiple of 32, at least the larger
+                               of a block: a multiple of 8, at least the larger
                                disparity range + 2; larger values mean fewer chunks
                                and more shared memory per CTA                         */
     int32_t census_mode;    /* region-of-interest census: 0 = 4 CTAs per SM, 1 = 3    */

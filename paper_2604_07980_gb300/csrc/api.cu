@@ -564,7 +564,7 @@ int ctm_set_tuning(ctm_ctx *ctx, const ctm_tuning *t)
 {
     if (!ctx || !t) return CTM_EINVAL;
     if (t->match_threads != 128 && t->match_threads != 256) return CTM_EINVAL;
-    if (t->strip_cols < ctx->nd_max + 2 || (t->strip_cols & 31) != 0 || t->strip_cols > 4096) return CTM_EINVAL;
+    if (t->strip_cols < ctx->nd_max + 2 || (t->strip_cols & 7) != 0 || t->strip_cols > 4096) return CTM_EINVAL;
     if (t->census_mode != 0 && t->census_mode != 1) return CTM_EINVAL;
     if (t->big_work < 0) return CTM_EINVAL;
     if (t->match_mode != 0 && t->match_mode != 1) return CTM_EINVAL;
@@ -641,14 +641,20 @@ int ctm_autotune(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *count
     float bms = 3.4e38f;
     int status = CTM_OK;
     // 1. matcher x CTA size x strip chunk width (joint), at the current census mode and split
-    const int base = (int)round_up(ctx->nd_max + 2, 32);  // the narrowest strip a point column fits
+    // strip widths: the narrowest a point column fits (N_d + 2, rounded up to 8),
+    // then multiples of 32 above it
+    int widths[10];
+    int nw = 0;
+    widths[nw++] = (int)round_up(ctx->nd_max + 2, 8);
+    for (int w = (int)round_up(ctx->nd_max + 2, 32); nw < 10; w += 32)
+        if (w > widths[0]) widths[nw++] = w;
     for (int mode = 0; mode <= 1 && status == CTM_OK; ++mode) {
       for (int th = 128; th <= 256 && status == CTM_OK; th *= 2) {
-        for (int extra = 0; extra <= 224; extra += 32) {
+        for (int wi = 0; wi < nw; ++wi) {
             ctm_tuning t = bt;
             t.match_mode = mode;
             t.match_threads = th;
-            t.strip_cols = base + extra;
+            t.strip_cols = widths[wi];
             float ms = 0.0f;
             const int r = measure(t, &ms);
             if (r == CTM_EINVAL) continue;  // does not fit shared memory
