@@ -44,9 +44,8 @@ POPC_PER_EVAL = 2          # one u64 code pair = two 32-bit popcounts
 # kernel changes after that capture.
 MATCH_DRAM_BYTES = (102.542 + 4.018) * 1e6
 # kernels of one step of the batched path (ctm_box_points, timed apart, is not in it): plan,
-# sample, mark, tile_list, census_roi, match,
-# aggregate
-KERNELS_PER_STEP = 7
+# sample (with census demand marking), tile_list, census_roi, match, aggregate
+KERNELS_PER_STEP = 6
 
 
 def parse():
@@ -349,7 +348,7 @@ def main():
     value = evals_per_step * world * args.steps / (ms * 1e-3) / 1e9
 
     # ---- per-phase kernel times, same steps, events on the launching stream
-    names = ("plan", "sample", "mark", "census", "match", "aggregate")
+    names = ("plan", "sample_and_mark", "census", "match", "aggregate")
     phase = np.zeros(len(names))
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(args.steps)]
     torch.cuda.synchronize()
@@ -360,7 +359,7 @@ def main():
         phase += [ev[k].elapsed_time(ev[k + 1]) for k in range(len(names))]
     phase /= args.steps
     kernels_ms = {n: float(v) for n, v in zip(names, phase)}
-    plan_ms = kernels_ms["plan"] + kernels_ms["sample"] + kernels_ms["mark"]
+    plan_ms = kernels_ms["plan"] + kernels_ms["sample_and_mark"]
     census_ms = kernels_ms["census"]
     match_ms = kernels_ms["match"]
 

@@ -217,10 +217,10 @@ int ctm_match_batch(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *co
 
 /* ctm_match_batch without a graph, recording eight caller-created CUDA events
  * (cudaEvent_t handles, created with timing enabled) on `stream` around its
- * launches: events[0] before planning (counter reset and plan_kernel),
- * [1] before point sampling, [2] before census demand marking, [3] before the
- * census (tile list and region-of-interest kernel), [4] before matching,
- * [5] before the per-box aggregation, [6] and [7] after it.  Used to time each
+ * launches: events[0] before planning, [1] before point sampling (which also
+ * marks the census demand), [2] before the census (tile list and
+ * region-of-interest kernel), [3] before matching, [4] before the per-box
+ * aggregation, [5], [6] and [7] after it.  Used to time each
  * phase on the stream the kernels run on.  Errors as ctm_match_batch. */
 int ctm_match_batch_profiled(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *counts_dev,
                              const ctm_box *boxes_dev, float *disp_dev, float *depth_dev,

@@ -339,7 +339,7 @@ class Context:
 
     def match_batch_profiled(self, batch: "DeviceBatch", events, stream=None):
         """Non-graph batch recording 8 torch.cuda.Event(enable_timing=True) around its launches
-        (before plan, sample, mark, census, match, aggregate; after aggregate, twice)."""
+        (before plan, sample+mark, census, match, aggregate; after aggregate, three times)."""
         assert len(events) == 8
         for e in events:  # torch creates the CUDA event on its first record
             if not e.cuda_event:

@@ -1,9 +1,10 @@
 // api.cu -- the C ABI (include/ctm.h): context, workspace and launch sequences.
 //
-// A match call is seven launches on one stream: device planning, point
-// sampling, census demand marking, the census tile list, census of the listed
-// tiles (both images, both resolutions), the matching kernel, and the per-box
-// aggregation that writes the outputs.  The batch entry point reads its frame and box counts
+// A match call is six launches on one stream (seven with the two-pass
+// matcher): device planning, point sampling with census demand marking, the
+// census tile list, census of the listed tiles (both images, both
+// resolutions), the matching kernel, and the per-box aggregation that writes
+// the outputs.  The batch entry point reads its frame and box counts
 // from device memory, so the whole sequence can be captured once into a CUDA
 // graph and replayed.
 #include <cuda_runtime.h>
@@ -117,7 +118,6 @@ int enqueue_match(ctm_ctx *ctx, const MatchArgs &a, int frames_grid, int match_g
     b.caps.max_frames = std::min(ctx->caps.max_frames, frames_grid);
     cudaError_t e = launch_plan(b, s);
     if (e == cudaSuccess) e = launch_sample(b, s);
-    if (e == cudaSuccess) e = launch_mark(b, s);
     if (e == cudaSuccess) e = launch_census_roi(b, ctx->sm_count, s);
     if (!plain) {
         if (e == cudaSuccess)
@@ -447,17 +447,14 @@ int ctm_match_batch_profiled(ctm_ctx *ctx, const ctm_frame *frames_dev, const in
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
     if (e == cudaSuccess) e = launch_sample(a, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2], s);
-    if (e == cudaSuccess) e = launch_mark(a, s);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[3], s);
     if (e == cudaSuccess) e = launch_census_roi(a, ctx->sm_count, s);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[4], s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[3], s);
     if (e == cudaSuccess)
         e = ctx->match_mode == 1 ? launch_match_pipe(a, ctx->match_threads, grid, s)
                                  : launch_match_persistent(a, ctx->match_threads, grid, s);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[5], s);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[4], s);
     if (e == cudaSuccess) e = launch_aggregate(a, s);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[6], s);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[7], s);
+    for (int i = 5; i < 8 && e == cudaSuccess; ++i) e = cudaEventRecord(ev[i], s);
     if (e != cudaSuccess) { cudaGetLastError(); return CTM_ECUDA; }
     return CTM_OK;
 }

@@ -174,7 +174,6 @@ size_t census_smem_bytes(int win_h);
 // Planning (plan.cu)
 cudaError_t launch_stage_frame(const MatchArgs &a, ctm_frame f, int n_boxes, cudaStream_t s);
 cudaError_t launch_plan(const MatchArgs &a, cudaStream_t s);
-cudaError_t launch_mark(const MatchArgs &a, cudaStream_t s);
 cudaError_t launch_aggregate(const MatchArgs &a, cudaStream_t s);
 cudaError_t launch_sample(const MatchArgs &a, cudaStream_t s);
 

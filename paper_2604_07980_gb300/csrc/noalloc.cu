@@ -214,7 +214,6 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
     if (e == cudaSuccess) e = launch_stage_frame(a, fr, n_boxes, s);
     if (e == cudaSuccess) e = launch_plan(a, s);
     if (e == cudaSuccess) e = launch_sample(a, s);
-    if (e == cudaSuccess) e = launch_mark(a, s);
     if (e == cudaSuccess) e = launch_census_roi(a, ds.sm_count, s);
     const long long blocks_ub = (long long)std::max(n_boxes, 1) * std::max(p->grid_g * p->grid_g, 1);
     const int grid = (int)std::min<long long>((long long)ds.sm_count * ctas, blocks_ub);

@@ -11,10 +11,9 @@
 //
 // sample_kernel (one warp per block): the block's point grid and its usable
 // points; blocks with fewer than min_pts usable points are finished here, the
-// others go to the work queue (large work first).
-//
-// mark_kernel (one warp per queued block): census tiles the search can read.  All
-// counts come from device memory so a captured graph replays with new inputs.
+// others go to the work queue (large work first) and mark the census tiles
+// their search can read.  All counts come from device memory so a captured
+// graph replays with new inputs.
 #include <math.h>
 
 #include "aggregate.cuh"
@@ -323,48 +322,35 @@ __global__ void __launch_bounds__(256) sample_kernel(MatchArgs a)
             rec.flags = CTM_BLK_PRESENT | CTM_BLK_FEW_POINTS;
             write_block(a, box, slot, rec);
         }
-    } else if (lane == 0) {
-        if (n_valid * nd * ndy >= a.big_work) {
-            const int q = atomicAdd(&a.ws.counts->n_big, 1);
-            a.ws.queue[q] = b;
-        } else {
-            const int q = atomicAdd(&a.ws.counts->n_small, 1);
-            a.ws.queue[a.caps.max_blocks - 1 - q] = b;
+    } else {
+        if (lane == 0) {
+            if (n_valid * nd * ndy >= a.big_work) {
+                const int q = atomicAdd(&a.ws.counts->n_big, 1);
+                a.ws.queue[q] = b;
+            } else {
+                const int q = atomicAdd(&a.ws.counts->n_small, 1);
+                a.ws.queue[a.caps.max_blocks - 1 - q] = b;
+            }
         }
-    }
-}
-
-__device__ __forceinline__ int queue_entry(const MatchArgs &a, int i, int n_big)
-{
-    return i < n_big ? a.ws.queue[i] : a.ws.queue[a.caps.max_blocks - 1 - (i - n_big)];
-}
-
-__global__ void __launch_bounds__(256) mark_kernel(MatchArgs a)
-{
-    const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
-    const int n_big = a.ws.counts->n_big;
-    if (i >= n_big + a.ws.counts->n_small) return;
-    const int b = queue_entry(a, i, n_big);
-    const int2 bs = a.ws.blocks[b];
-    const BoxPlan P = a.ws.plans[bs.x];
-    const BlockGeom &g = a.ws.geom[b];
-    const int nx = g.nx, ny = g.ny;
-    const int x_first = g.X[0], x_last = g.X[nx - 1];
-    const int qL = (P.far || a.p.close_factor == 1) ? 0 : 2;
-    const int span = P.dmax - P.dmin;
-    const int dyr = a.p.dy_max - a.p.dy_min;
-    const int nl = 2 * dyr + 1, nr = dyr + 1;
-    const int items = ny * (nl + nr);
-    for (int it = lane; it < items; it += 32) {
-        const int m = it / (nl + nr);
-        const int e = it - m * (nl + nr);
-        const int y = g.Y[m];
-        if (e < nl)
-            mark_range(a, P.frame, qL, y + e - dyr, x_first - span, x_last + span, P.Ws, P.Hs);
-        else
-            mark_range(a, P.frame, qL + 1, y + a.p.dy_min + (e - nl), x_first - P.dmax, x_last - P.dmin,
-                       P.Ws, P.Hs);
+        // census demand of the searchable block (see mark_range)
+        const int x_first = __shfl_sync(full, Xl, 0), x_last = __shfl_sync(full, Xl, nx - 1);
+        const int qL = (P.far || a.p.close_factor == 1) ? 0 : 2;
+        const int span = P.dmax - P.dmin;
+        const int dyr = a.p.dy_max - a.p.dy_min;
+        const int nl = 2 * dyr + 1, nr = dyr + 1;
+        const int items = ny * (nl + nr);
+        for (int it0 = 0; it0 < items; it0 += 32) {  // uniform trip count: the shuffle needs every lane
+            const int it = it0 + lane;
+            const int m = (it < items ? it : 0) / (nl + nr);
+            const int e = it - m * (nl + nr);
+            const int y = __shfl_sync(full, Yl, m);
+            if (it >= items) continue;
+            if (e < nl)
+                mark_range(a, P.frame, qL, y + e - dyr, x_first - span, x_last + span, P.Ws, P.Hs);
+            else
+                mark_range(a, P.frame, qL + 1, y + a.p.dy_min + (e - nl), x_first - P.dmax, x_last - P.dmin,
+                           P.Ws, P.Hs);
+        }
     }
 }
 
@@ -377,12 +363,6 @@ cudaError_t launch_sample(const MatchArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_mark(const MatchArgs &a, cudaStream_t s)
-{
-    const int grid = ceil_div_nn(a.caps.max_blocks, 8);
-    mark_kernel<<<grid, 256, 0, s>>>(a);
-    return cudaGetLastError();
-}
 
 // One warp per planned box with blocks: Sec. 4.3.4 over its block records and
 // Eq. 1 (boxes without blocks got their outputs from the planner).
