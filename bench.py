@@ -390,11 +390,13 @@ def main():
         ctx1.close()
 
     # ---- e2e through the host-memory entry point (pinned host images)
+    # one page-locked buffer holding L0 R0 L1 R1 ... (a frame-grabber ring buffer layout)
+    host_all = torch.empty((len(w.frames), 2, 1200, 1920), dtype=torch.uint8).pin_memory()
     pinned = []
-    for f in w.frames:
-        L = torch.from_numpy(f.left).pin_memory()
-        R = torch.from_numpy(f.right).pin_memory()
-        pinned.append((L.numpy(), R.numpy()))
+    for i, f in enumerate(w.frames):
+        host_all[i, 0].copy_(torch.from_numpy(f.left))
+        host_all[i, 1].copy_(torch.from_numpy(f.right))
+        pinned.append((host_all[i, 0].numpy(), host_all[i, 1].numpy()))
     out_h = (torch.empty(w.n_boxes, dtype=torch.float32).pin_memory().numpy(),
              torch.empty(w.n_boxes, dtype=torch.float32).pin_memory().numpy(),
              torch.empty(w.n_boxes, dtype=torch.uint8).pin_memory().numpy())

@@ -192,3 +192,26 @@ def test_batch_replay_with_fewer_frames(torch_cuda):
     compare_box_outputs({k: v.cpu().numpy()[:n0] for k, v in got.items()}, ref, "replay")
     assert np.all(batch.disp.cpu().numpy()[n0:len(w.boxes)] == -7.0)
     ctx.close()
+
+
+def test_batch_host_merged_copies(torch_cuda):
+    """Host batch whose images are packed at the staging pitch and laid out back to back
+    (one merged copy), and the same images in an order that breaks the runs (several
+    copies): both equal the oracle."""
+    from paper_2604_07980_gb300 import binding as B
+    w = wl.batch32x1200(n_frames=4, W=1024, H=256, mean_boxes=8, side_range=(12, 160))
+    ref = orc.match_batch([(f.left, f.right, f.f_px, f.baseline_m) for f in w.frames], w.boxes,
+                          orc.Params(**w.params))
+    ctx = B.Context(w.params, 4, 1024, 256, w.n_boxes)
+    packed = np.empty((4, 2, 256, 1024), np.uint8)
+    for i, f in enumerate(w.frames):
+        packed[i, 0], packed[i, 1] = f.left, f.right
+    fpx = [f.f_px for f in w.frames]
+    bm = [f.baseline_m for f in w.frames]
+    got = ctx.match_batch_host([(packed[i, 0], packed[i, 1]) for i in range(4)], w.boxes, fpx, bm)
+    compare_box_outputs(got, ref, "host, one merged copy")
+    swapped = np.empty_like(packed)  # right image first in memory: no run continues
+    swapped[:, 0], swapped[:, 1] = packed[:, 1], packed[:, 0]
+    got = ctx.match_batch_host([(swapped[i, 1], swapped[i, 0]) for i in range(4)], w.boxes, fpx, bm)
+    compare_box_outputs(got, ref, "host, separate copies")
+    ctx.close()
