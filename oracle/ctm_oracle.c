@@ -165,6 +165,28 @@ static int inside(rect_t r, int x, int y) { return x >= r.x0 && x < r.x1 && y >=
 
 static int ceil_div(int a, int b) { return (a + b - 1) / b; } /* a >= 0, b > 0 */
 
+/* Priority rule of Sec. 4.3.5 when there are more occluders than slots: an
+ * occluder is frontal if its clipped box centre lies in the centred crop
+ * [W (1 - c) / 2, W (1 + c) / 2) x [H (1 - c) / 2, H (1 + c) / 2); compared on
+ * doubled coordinates, x0 + x1 against W (1 - c) and W (1 + c), in fp32. */
+static int frontal(rect_t q, int W, int H, float c)
+{
+    if (!(c > 0.0f)) return 0;
+    const float sx = (float)(q.x0 + q.x1), sy = (float)(q.y0 + q.y1);
+    return sx >= (float)W * (1.0f - c) && sx < (float)W * (1.0f + c) &&
+           sy >= (float)H * (1.0f - c) && sy < (float)H * (1.0f + c);
+}
+
+/* 1 if occluder a ranks before occluder b: frontal first, then larger bottom y,
+ * then lower index. */
+static int occluder_before(int a, int b, const rect_t *cb, int W, int H, float c)
+{
+    const int fa = frontal(cb[a], W, H, c), fb = frontal(cb[b], W, H, c);
+    if (fa != fb) return fa > fb;
+    if (cb[a].y1 != cb[b].y1) return cb[a].y1 > cb[b].y1;
+    return a < b;
+}
+
 /* Code of a census plane at (x, y); positions outside the plane read as 0, the
  * same value an undefined census pixel holds. */
 static uint64_t code_at(const uint64_t *c, int Ws, int Hs, int x, int y)
@@ -210,6 +232,7 @@ static int params_ok(const orc_params *p)
     if (p->dy_min > p->dy_max) return 0;
     if (p->grid_g < 1 || p->pts_side < 1 || p->min_pts < 1) return 0;
     if (p->fb_tol < 0 || p->agg_nmin < 1 || p->max_occluders < 0) return 0;
+    if (!(p->frontal_crop >= 0.0f && p->frontal_crop <= 1.0f)) return 0;
     if (p->agg_mode != 0 && p->agg_mode != 1) return 0;
     if (!(p->trim_frac >= 0.0f && p->trim_frac < 0.5f)) return 0;
     return 1;
@@ -302,17 +325,17 @@ int orc_match_frame(const uint8_t *L, const uint8_t *R, int W, int H, int pitch,
             }
 
             /* Sec. 4.3.5: B_j occludes B_i iff they overlap and B_j's bottom y is
-             * larger.  At most max_occluders are kept, the ones with the largest
-             * bottom y (nearest first; ties by index). */
+             * larger.  At most max_occluders are kept: frontal ones first (box
+             * centre inside the centred crop, when frontal_crop > 0), then the
+             * others, each group nearest first (largest bottom y), ties by index. */
             int nocc = 0;
             for (int j = 0; j < n; ++j) {
                 if (j == i) continue;
                 if (rects_overlap(r, cb[j]) && cb[j].y1 > r.y1) occ[nocc++] = j;
             }
-            for (int a = 1; a < nocc; ++a) { /* insertion sort: bottom desc, index asc */
+            for (int a = 1; a < nocc; ++a) { /* insertion sort: frontal, bottom desc, index asc */
                 int t = occ[a], b = a - 1;
-                while (b >= 0 && (cb[occ[b]].y1 < cb[t].y1 ||
-                                  (cb[occ[b]].y1 == cb[t].y1 && occ[b] > t))) {
+                while (b >= 0 && occluder_before(t, occ[b], cb, W, H, p->frontal_crop)) {
                     occ[b + 1] = occ[b];
                     --b;
                 }

@@ -40,6 +40,9 @@ typedef struct {
     int32_t agg_mode;          /* 0 = median of the run, 1 = trimmed mean of the run      */
     float   trim_frac;         /* trimmed mean drops floor(trim_frac*m) from each end     */
     int32_t max_occluders;     /* keep at most this many occluders per box                */
+    float   frontal_crop;      /* 0: occluders ranked nearest first; c in (0, 1]: those
+                                  whose clipped box centre lies in the centred crop of
+                                  c W x c H rank first (each group nearest first)      */
 } orc_params;
 
 /* Per-block result (one per box x block slot; FAR boxes use slot 0). */

@@ -92,6 +92,7 @@ class Params:
     agg_mode: int = 0
     trim_frac: float = 0.2
     max_occluders: int = 16
+    frontal_crop: float = 0.0
 
 
 class _CParams(ctypes.Structure):

@@ -238,6 +238,41 @@ def test_equal_bottoms_do_not_occlude_and_cap_keeps_nearest():
     assert cap1["blocks"][0]["n_valid"].sum() == (~inside(near1)).sum()
 
 
+def test_frontal_crop_priority_when_occluders_exceed_the_cap():
+    """Sec. 4.3.5 priority rule: with more occluders than slots, occluders whose box
+    centre lies in the centred crop are kept first, the others fill the remaining slots
+    nearest first; with frontal_crop = 0 the nearest are kept."""
+    rng = np.random.default_rng(12)
+    L = np.clip(np.rint(wl.texture(rng, 120, 200)), 0, 255).astype(np.uint8)
+    a = [100, 20, 148, 68]
+    f1 = [70, 30, 110, 80]     # centre (90, 55): inside the 0.2 crop [80, 120) x [48, 72); bottom 80
+    f2 = [90, 50, 130, 75]     # centre (110, 62.5): inside; bottom 75
+    n1 = [140, 10, 190, 110]   # centre (165, 60): outside; bottom 110
+    n2 = [120, 60, 200, 100]   # centre (160, 80): outside; bottom 100
+    boxes = np.array([b + [0] for b in (a, f1, f2, n1, n2)], np.int32)
+    xs, ys = np.meshgrid(np.arange(100, 148), np.arange(20, 68))
+    inside = lambda r: (xs >= r[0]) & (xs < r[2]) & (ys >= r[1]) & (ys < r[3])
+
+    def usable(kept):
+        m = np.zeros_like(xs, bool)
+        for r in kept:
+            m |= inside(r)
+        return int((~m).sum())
+
+    def n_valid(**kw):
+        out = orc.match_frame(L, L, boxes, 2000.0, 0.3, _params(**kw), debug=True)
+        return int(out["blocks"][0]["n_valid"].sum())
+
+    assert n_valid(max_occluders=2) == usable([n1, n2])
+    assert n_valid(max_occluders=2, frontal_crop=0.2) == usable([f1, f2])
+    assert n_valid(max_occluders=3, frontal_crop=0.2) == usable([f1, f2, n1])
+    assert n_valid(max_occluders=1, frontal_crop=0.2) == usable([f1])
+    # a crop that holds every centre ranks by proximity alone again
+    assert n_valid(max_occluders=2, frontal_crop=1.0) == usable([n1, n2])
+    with pytest.raises(ValueError):
+        n_valid(frontal_crop=1.5)
+
+
 def test_far_close_threshold_and_empty_boxes():
     rng = np.random.default_rng(6)
     L = np.clip(np.rint(wl.texture(rng, 200, 300)), 0, 255).astype(np.uint8)
