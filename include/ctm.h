@@ -86,7 +86,7 @@ typedef struct {
  * odd win_w, win_h <= 15 with win_w*win_h + sentinel <= 64; close_factor 1..8;
  * grid_g 1..8; pts_side 1..16; (dmax-dmin+1)*(dy_max-dy_min+1) <= 256 for both
  * ranges; min_pts >= 1; fb_tol >= 0; agg_nmin >= 1; 0 <= trim_frac < 0.5;
- * 0 <= max_occluders <= 32. */
+ * 0 <= max_occluders <= 32, 0 <= frontal_crop <= 1. */
 typedef struct {
     int32_t win_w, win_h;     /* census window (Sec. 4.3.1: S_x = win_w/2, S_y = win_h/2) */
     int32_t sentinel;         /* 1: leading 1 bit above the comparison bits (Algorithm 1) */
@@ -103,7 +103,11 @@ typedef struct {
     int32_t agg_nmin;         /* run must hold >= agg_nmin blocks (N_min)                 */
     int32_t agg_mode;         /* 0: median of the run; 1: trimmed mean of the run         */
     float trim_frac;          /* trimmed mean drops floor(trim_frac * m) per end          */
-    int32_t max_occluders;    /* at most this many occluders per box, nearest first       */
+    int32_t max_occluders;    /* at most this many occluders per box (Sec. 4.3.5)         */
+    float frontal_crop;       /* ranking of occluders beyond the cap: 0 = nearest (largest
+                                 bottom y) first; c in (0, 1] = those whose clipped box
+                                 centre lies in the centred c W x c H crop first, each
+                                 group nearest first (ties: lower index)                 */
 } ctm_params;
 
 /* Per-block diagnostic record (ctm_debug.blocks), slot = block index in

@@ -45,7 +45,7 @@ class ctm_params(ctypes.Structure):
                 ("pts_side", ctypes.c_int32), ("min_pts", ctypes.c_int32), ("fb_tol", ctypes.c_int32),
                 ("agg_tau_d", ctypes.c_float), ("agg_nmin", ctypes.c_int32),
                 ("agg_mode", ctypes.c_int32), ("trim_frac", ctypes.c_float),
-                ("max_occluders", ctypes.c_int32)]
+                ("max_occluders", ctypes.c_int32), ("frontal_crop", ctypes.c_float)]
 
 
 class ctm_frame(ctypes.Structure):

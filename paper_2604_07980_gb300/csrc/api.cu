@@ -79,6 +79,7 @@ bool params_valid(const ctm_params &p)
     if (!(p.trim_frac >= 0.0f && p.trim_frac < 0.5f)) return false;
     if (!(p.agg_tau_d == p.agg_tau_d)) return false;
     if (p.max_occluders < 0 || p.max_occluders > kMaxOcc) return false;
+    if (!(p.frontal_crop >= 0.0f && p.frontal_crop <= 1.0f)) return false;
     return true;
 }
 
@@ -182,6 +183,7 @@ int ctm_default_params(ctm_params *p)
     p->agg_mode = 0;
     p->trim_frac = 0.2f;
     p->max_occluders = 16;
+    p->frontal_crop = 0.0f;
     return CTM_OK;
 }
 

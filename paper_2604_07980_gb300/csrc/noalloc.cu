@@ -57,6 +57,7 @@ bool params_ok(const ctm_params &p)
     if (!(p.trim_frac >= 0.0f && p.trim_frac < 0.5f)) return false;
     if (!(p.agg_tau_d == p.agg_tau_d)) return false;
     if (p.max_occluders < 0 || p.max_occluders > kMaxOcc) return false;
+    if (!(p.frontal_crop >= 0.0f && p.frontal_crop <= 1.0f)) return false;
     return true;
 }
 

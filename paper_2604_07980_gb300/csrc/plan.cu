@@ -35,6 +35,18 @@ __device__ __forceinline__ int4 clip_box(const ctm_box &b, int W, int H)
     return r;
 }
 
+// Priority rule of Sec. 4.3.5: an occluder is frontal if its clipped box
+// centre lies in the centred crop [W (1 - c) / 2, W (1 + c) / 2) x [H (1 - c) / 2,
+// H (1 + c) / 2), compared on doubled coordinates in fp32.
+__device__ __forceinline__ bool frontal(int4 q, int W, int H, float c)
+{
+    if (!(c > 0.0f)) return false;
+    const float sx = (float)(q.x + q.z), sy = (float)(q.y + q.w);
+    const float om = __fsub_rn(1.0f, c), op = __fadd_rn(1.0f, c);
+    return sx >= __fmul_rn((float)W, om) && sx < __fmul_rn((float)W, op) && sy >= __fmul_rn((float)H, om) &&
+           sy < __fmul_rn((float)H, op);
+}
+
 __device__ __forceinline__ bool overlaps(int4 a, int4 b)
 {
     const int ix0 = max(a.x, b.x), ix1 = min(a.z, b.z);
@@ -129,9 +141,10 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(MatchArgs a)
         P.nblk = empty ? 0 : P.g * P.g;
 
         // occluders: overlap with positive area and strictly larger bottom y; keep
-        // the K with the largest bottom y, ties to the lower index.  Key
-        // (bottom y, -index) is unique per box, so round t takes the largest key
-        // below round t-1's: each lane scans its share of the frame's boxes.
+        // K of them: frontal ones first (frontal_crop > 0), then by largest bottom
+        // y, ties to the lower index.  Key (frontal, bottom y, -index) is unique
+        // per box, so round t takes the largest key below round t-1's: each lane
+        // scans its share of the frame's boxes.
         int nocc = 0;
         if (!empty && K > 0) {
             unsigned long long prev = ~0ull;
@@ -141,8 +154,9 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(MatchArgs a)
                     if (j == i) continue;
                     const int4 q = staged ? sbox[j - begin] : clip_box(a.boxes[j], fr.width, fr.height);
                     if (!(q.w > r.w) || !overlaps(r, q)) continue;
+                    const unsigned front = frontal(q, fr.width, fr.height, p.frontal_crop) ? 0x80000000u : 0u;
                     const unsigned long long key =
-                        ((unsigned long long)(unsigned)q.w << 32) | (unsigned)(0x7fffffff - (j - begin));
+                        ((unsigned long long)(front | (unsigned)q.w) << 32) | (unsigned)(0x7fffffff - (j - begin));
                     if (key < prev && key > best) best = key;
                 }
                 // warp maximum of the 64-bit keys (two 32-bit reductions)

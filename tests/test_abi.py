@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(built):
 
 def test_struct_layouts():
     from paper_2604_07980_gb300 import binding as B
-    assert ctypes.sizeof(B.ctm_params) == 20 * 4
+    assert ctypes.sizeof(B.ctm_params) == 21 * 4
     assert ctypes.sizeof(B.ctm_frame) == 48
     assert B.BLOCK_DTYPE.itemsize == B.BLOCK_BYTES == 48
     assert ctypes.sizeof(B.ctm_debug) == 24

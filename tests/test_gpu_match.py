@@ -215,3 +215,23 @@ def test_batch_host_merged_copies(torch_cuda):
     got = ctx.match_batch_host([(swapped[i, 1], swapped[i, 0]) for i in range(4)], w.boxes, fpx, bm)
     compare_box_outputs(got, ref, "host, separate copies")
     ctx.close()
+
+
+def test_frontal_crop_occluder_priority(torch_cuda):
+    """Occluder cap of 2 with the frontal-crop priority on a batch with many overlapping
+    boxes: block records and outputs equal the oracle's (and differ from proximity-only
+    ranking somewhere, so the rule is exercised)."""
+    from paper_2604_07980_gb300 import binding as B
+    w = wl.batch32x1200(n_frames=3)
+    params = dict(w.params, max_occluders=2, frontal_crop=0.4)
+    frames = [(f.left, f.right, f.f_px, f.baseline_m) for f in w.frames]
+    ref = orc.match_batch(frames, w.boxes, orc.Params(**params), debug=True)
+    near = orc.match_batch(frames, w.boxes, orc.Params(**dict(params, frontal_crop=0.0)), debug=True)
+    assert not np.array_equal(ref["blocks"]["n_valid"], near["blocks"]["n_valid"])
+    ctx = B.Context(params, len(w.frames), 1920, 1200, w.n_boxes)
+    batch = B.DeviceBatch(torch_frames(w.frames), w.boxes, [(f.f_px, f.baseline_m) for f in w.frames])
+    got = ctx.match_batch(batch, use_graph=True, debug=True)
+    torch_cuda.cuda.synchronize()
+    compare_box_outputs({k: v.cpu().numpy() for k, v in got.items() if k != "debug"}, ref, "frontal crop")
+    compare_debug(got["debug"], ref, B.n_candidates(ctx.params), "frontal crop")
+    ctx.close()
