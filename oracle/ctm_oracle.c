@@ -509,3 +509,67 @@ void orc_box_points(const int32_t *boxes, const float *disp, const uint8_t *flag
         o[7] = h[3];
     }
 }
+
+/* Sec. 5.1: vertical offset search, census matching per ROI pixel. */
+int orc_auto_rect(const uint8_t *L, const uint8_t *R, int W, int H, int pitch, int win_w, int win_h,
+                  int sentinel, int rx0, int ry0, int rx1, int ry1, int dmin, int dmax, int delta_min,
+                  int delta_max, int d_thresh, int fb_tol, int64_t *counts)
+{
+    if (dmin > dmax || delta_min > delta_max || rx0 >= rx1 || ry0 >= ry1) return delta_min;
+    uint64_t *CL = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)W * H);
+    uint64_t *CR = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)W * H);
+    orc_census(L, W, H, pitch, 1, win_w, win_h, sentinel, CL);
+    orc_census(R, W, H, pitch, 1, win_w, win_h, sentinel, CR);
+    int best = delta_min;
+    int64_t best_count = -1;
+    for (int delta = delta_min; delta <= delta_max; ++delta) {
+        int64_t count = 0;
+        for (int y = ry0; y < ry1; ++y) {
+            for (int x = rx0; x < rx1; ++x) {
+                const int yl = y + delta;
+                if (x - win_w / 2 < 0 || x + win_w / 2 >= W || yl - win_h / 2 < 0 || yl + win_h / 2 >= H)
+                    continue; /* left census undefined */
+                const uint64_t cl = code_at(CL, W, H, x, yl);
+                int d_f = dmin, s_best = 1 << 30;
+                for (int d = dmin; d <= dmax; ++d) {
+                    const int s_d = popc64(cl ^ code_at(CR, W, H, x - d, y));
+                    if (s_d < s_best) { s_best = s_d; d_f = d; }
+                }
+                const uint64_t cq = code_at(CR, W, H, x - d_f, y);
+                int d_b = dmin;
+                s_best = 1 << 30;
+                for (int d = dmin; d <= dmax; ++d) {
+                    const int s_d = popc64(cq ^ code_at(CL, W, H, x - d_f + d, y + delta));
+                    if (s_d < s_best) { s_best = s_d; d_b = d; }
+                }
+                const int dx = d_b > d_f ? d_b - d_f : d_f - d_b;
+                if (dx <= fb_tol && d_f > d_thresh) ++count;
+            }
+        }
+        counts[delta - delta_min] = count;
+        if (count > best_count) { best_count = count; best = delta; }
+    }
+    free(CL);
+    free(CR);
+    return best;
+}
+
+/* Sec. 5.1 temporal filter: sliding-window median, clamped step. */
+int orc_rect_filter(const int *estimates, int n, int prev, int max_step)
+{
+    if (n < 1) return prev;
+    int *v = (int *)malloc(sizeof(int) * (size_t)n);
+    for (int i = 0; i < n; ++i) v[i] = estimates[i];
+    for (int i = 1; i < n; ++i) { /* insertion sort ascending */
+        const int t = v[i];
+        int j = i - 1;
+        while (j >= 0 && v[j] > t) { v[j + 1] = v[j]; --j; }
+        v[j + 1] = t;
+    }
+    const int med = v[(n - 1) / 2];
+    free(v);
+    int step = med - prev;
+    if (step > max_step) step = max_step;
+    if (step < -max_step) step = -max_step;
+    return prev + step;
+}

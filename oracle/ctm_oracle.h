@@ -126,6 +126,26 @@ typedef struct {
 void orc_box_points(const int32_t *boxes, const float *disp, const uint8_t *flags, int n,
                     const orc_geometry *geo, int n_geo, double *out);
 
+/* Sec. 5.1 auto-rectification offset, with census matching in place of BM.
+ * For every delta in [delta_min, delta_max] and every pixel (x, y) of the ROI
+ * [rx0, rx1) x [ry0, ry1): the left image is read shifted down by delta rows
+ * (left pixel (x, y + delta)); d_f = first argmin over d in [dmin, dmax] of
+ * popcount(C_L(x, y + delta) ^ C_R(x - d, y)); the backward search from the
+ * right pixel q = (x - d_f, y) gives d_b = first argmin over d' of
+ * popcount(C_R(q) ^ C_L(q.x + d', y + delta)); the pixel counts when its left
+ * census is defined (window inside the image), |d_b - d_f| <= fb_tol and
+ * d_f > d_thresh.  Codes outside
+ * the image read as 0 (as in the box search).  counts[i] = the count for
+ * delta_min + i; returns delta* = the first delta with the largest count. */
+int orc_auto_rect(const uint8_t *L, const uint8_t *R, int W, int H, int pitch, int win_w, int win_h,
+                  int sentinel, int rx0, int ry0, int rx1, int ry1, int dmin, int dmax, int delta_min,
+                  int delta_max, int d_thresh, int fb_tol, int64_t *counts);
+
+/* Temporal filter of the per-frame estimates (Sec. 5.1): delta_t = median of the
+ * last n estimates (n >= 1; even n: the lower of the middle two), and the step
+ * from prev is clamped to [-max_step, max_step].  Returns prev + clamped step. */
+int orc_rect_filter(const int *estimates, int n, int prev, int max_step);
+
 #ifdef __cplusplus
 }
 #endif

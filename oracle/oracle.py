@@ -57,6 +57,10 @@ def lib():
         L.orc_aggregate.restype = ctypes.c_int
         L.orc_depth.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_float]
         L.orc_depth.restype = ctypes.c_float
+        L.orc_auto_rect.argtypes = [ctypes.c_void_p, ctypes.c_void_p] + [ctypes.c_int] * 16 + [ctypes.c_void_p]
+        L.orc_auto_rect.restype = ctypes.c_int
+        L.orc_rect_filter.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.orc_rect_filter.restype = ctypes.c_int
         L.orc_box_points.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                      ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
         L.orc_box_points.restype = None
@@ -229,3 +233,21 @@ def box_points(boxes: np.ndarray, disp: np.ndarray, flags: np.ndarray, geometrie
     lib().orc_box_points(boxes.ctypes.data, disp.ctypes.data, flags.ctypes.data, n,
                          ctypes.addressof(arr), len(geometries), out.ctypes.data)
     return out[:n]
+
+
+def auto_rect(L: np.ndarray, R: np.ndarray, roi, dmin: int, dmax: int, delta_min: int, delta_max: int,
+              d_thresh: int, fb_tol: int = 1, win_w: int = 9, win_h: int = 7, sentinel: int = 1):
+    """Sec. 5.1 offset search with census matching; returns (delta*, counts per delta)."""
+    L = np.ascontiguousarray(L, dtype=np.uint8)
+    R = np.ascontiguousarray(R, dtype=np.uint8)
+    H, W = L.shape
+    counts = np.zeros(delta_max - delta_min + 1, np.int64)
+    best = lib().orc_auto_rect(L.ctypes.data, R.ctypes.data, W, H, W, win_w, win_h, sentinel,
+                               roi[0], roi[1], roi[2], roi[3], dmin, dmax, delta_min, delta_max,
+                               d_thresh, fb_tol, counts.ctypes.data)
+    return int(best), counts
+
+
+def rect_filter(estimates, prev: int, max_step: int) -> int:
+    v = np.ascontiguousarray(estimates, dtype=np.int32)
+    return int(lib().orc_rect_filter(v.ctypes.data, len(v), prev, max_step))
