@@ -289,6 +289,30 @@ int ctm_box_points(const ctm_box *boxes_dev, const float *disp_dev, const uint8_
                    int n_boxes, const ctm_geometry *geo_dev, int n_geo, float *out_dev,
                    ctm_stream stream);
 
+/* Sec. 5.1 auto-rectification offset, with census matching in place of BM (no
+ * counterpart in the paper's own design, which uses BM disparities).  For every
+ * delta in [delta_min, delta_max] and every pixel (x, y) of the ROI
+ * [rx0, rx1) x [ry0, ry1) (clipped to the image): the left pixel is read at
+ * (x, y + delta); d_f = first argmin over d in [dmin, dmax] of
+ * popcount(C_L(x, y + delta) ^ C_R(x - d, y)); d_b = first argmin over d' of
+ * popcount(C_R(x - d_f, y) ^ C_L(x - d_f + d', y + delta)); the pixel counts when
+ * its left census is defined (window inside the image), |d_b - d_f| <= fb_tol and
+ * d_f > d_thresh.  Codes outside the image read as 0.  The census window is
+ * p's (win_w, win_h, sentinel).  census_dev: caller-owned scratch of
+ * 2 * width * height uint64 (overwritten); counts_dev: delta_max - delta_min + 1
+ * counters (zeroed, then the counts); *delta_dev: the first delta with the
+ * largest count (device int).  Asynchronous on `stream`.  Errors: CTM_EINVAL
+ * (null pointer, bad sizes or window, more than 1024 disparities), CTM_ECUDA. */
+int ctm_auto_rect(const ctm_params *p, const uint8_t *left_dev, const uint8_t *right_dev, int width,
+                  int height, int pitch, int rx0, int ry0, int rx1, int ry1, int dmin, int dmax,
+                  int delta_min, int delta_max, int d_thresh, int fb_tol, uint64_t *census_dev,
+                  unsigned long long *counts_dev, int *delta_dev, ctm_stream stream);
+
+/* Sec. 5.1 temporal filter (host): the median of the last n per-frame offsets
+ * (even n: the lower of the middle two), with the change from prev clamped to
+ * [-max_step, max_step].  Returns the filtered offset; prev for n < 1. */
+int ctm_rect_filter(const int *estimates, int n, int prev, int max_step);
+
 /* Current tuning of a context. */
 int ctm_get_tuning(const ctm_ctx *ctx, ctm_tuning *out);
 

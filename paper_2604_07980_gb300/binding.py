@@ -27,7 +27,7 @@ EXPORTS = ("ctm_status_str", "ctm_default_params", "ctm_create", "ctm_destroy",
            "ctm_census_build", "ctm_match_boxes", "ctm_match_boxes_plain", "ctm_match_batch",
            "ctm_match_batch_profiled", "ctm_match_batch_host", "ctm_match_boxes_noalloc",
            "ctm_get_stats", "ctm_probe_int_rate", "ctm_get_tuning", "ctm_set_tuning", "ctm_autotune",
-           "ctm_box_points",
+           "ctm_box_points", "ctm_auto_rect", "ctm_rect_filter",
            "ctm_server_default_config", "ctm_server_create", "ctm_server_submit", "ctm_server_poll",
            "ctm_server_outstanding", "ctm_server_get_stats", "ctm_server_destroy", "ctm_server_now_ns")
 
@@ -156,6 +156,10 @@ def lib():
     L.ctm_get_stats.restype = i32
     L.ctm_probe_int_rate.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double)]
     L.ctm_probe_int_rate.restype = i32
+    L.ctm_auto_rect.argtypes = [ctypes.POINTER(ctm_params), vp, vp] + [i32] * 13 + [vp, vp, vp, vp]
+    L.ctm_auto_rect.restype = i32
+    L.ctm_rect_filter.argtypes = [vp, i32, i32, i32]
+    L.ctm_rect_filter.restype = i32
     L.ctm_box_points.argtypes = [vp, vp, vp, i32, vp, i32, vp, vp]
     L.ctm_box_points.restype = i32
     L.ctm_get_tuning.argtypes = [vp, ctypes.POINTER(ctm_tuning)]
@@ -455,6 +459,27 @@ def box_points(boxes, disp, flags, geo, n_geo: int, out=None, stream=None):
     _check(lib().ctm_box_points(_ptr(boxes), _ptr(disp), _ptr(flags), n, _ptr(geo), int(n_geo), _ptr(out),
                                 _stream(stream)), "ctm_box_points")
     return out[:n]
+
+
+def auto_rect(left, right, roi, dmin: int, dmax: int, delta_min: int, delta_max: int, d_thresh: int,
+              fb_tol: int = 1, params: dict | None = None, stream=None):
+    """Sec. 5.1 offset search on the device (census matching): returns (delta*, counts) as
+    device tensors; left/right uint8 [H, W] device tensors, roi = (x0, y0, x1, y1)."""
+    torch = _torch()
+    p = make_params(params)
+    H, W = left.shape
+    census = torch.empty((2, H, W), dtype=torch.int64, device=left.device)
+    counts = torch.empty(delta_max - delta_min + 1, dtype=torch.int64, device=left.device)
+    delta = torch.empty(1, dtype=torch.int32, device=left.device)
+    _check(lib().ctm_auto_rect(ctypes.byref(p), _ptr(left), _ptr(right), W, H, left.stride(0), roi[0], roi[1],
+                               roi[2], roi[3], dmin, dmax, delta_min, delta_max, d_thresh, fb_tol, _ptr(census),
+                               _ptr(counts), _ptr(delta), _stream(stream)), "ctm_auto_rect")
+    return delta, counts
+
+
+def rect_filter(estimates, prev: int, max_step: int) -> int:
+    v = np.ascontiguousarray(estimates, dtype=np.int32)
+    return int(lib().ctm_rect_filter(v.ctypes.data if len(v) else None, len(v), prev, max_step))
 
 
 def _host_ptr(a):
