@@ -1,21 +1,19 @@
 // census.cu -- census transform kernels (Sec. 4.3.1, Algorithm 1).
 //
-// Work unit: one warp computes a 64-pixel row tile of codes on the grid
-// I_k(x, y) = I(k x, k y) (k = 1 is the image itself; k > 1 is the
-// multi-resolution census of Sec. 4.3.1 taken by decimation).  The warp stages
-// the tile's window rows in shared memory as fp16 bit patterns 0x6400 | v, which
-// is exactly 1024 + v, so fp16 order equals pixel order with no conversion.  Each
-// lane owns two adjacent pixels: one packed compare (__hgt2_mask) gives xi for
-// both pixels at one window offset, and one LOP3 ORs it into the bit position of
-// that offset in a 16-bit-per-pixel accumulator.  Bits follow the raster order of
-// the window (row j outer, column i inner), first neighbour in the highest
-// comparison bit, with the optional sentinel above them; pixels whose window
-// leaves the grid get 0.
+// Codes on the grid I_k(x, y) = I(k x, k y) (k = 1 is the image itself; k > 1
+// is the multi-resolution census of Sec. 4.3.1 taken by decimation).  Bits
+// follow the raster order of the window (row j outer, column i inner), first
+// neighbour in the highest comparison bit, with the optional sentinel above
+// them; pixels whose window leaves the grid get 0.
 //
-// Two drivers: the full-image kernel (ctm_census_build, one warp per tile) and
-// the region-of-interest kernel of the matching path, which computes only the
-// tiles the planner marked in a per-plane bitmap (one bit per 64-pixel tile of
-// a row) and clears the marks it consumed.
+// Fixed windows (5x5, 7x7, 9x7) use census4: four pixels per lane, compares on
+// the integer multiply-add pipe, rows loaded straight into registers.  The
+// full-image kernel (ctm_census_build) gives a half-warp a 64-pixel row tile;
+// the region-of-interest kernel of the matching path gives eight lanes a
+// 32-pixel tile from the list of tiles the planner marked.  Other windows use
+// a warp per 64-pixel tile, staging the window rows in shared memory as fp16
+// bit patterns 0x6400 | v (exactly 1024 + v, so fp16 order is pixel order) and
+// comparing two pixels per __hgt2_mask.
 #include <cuda_fp16.h>
 
 #include "ctm_internal.cuh"
@@ -23,7 +21,7 @@
 namespace ctm {
 namespace {
 
-constexpr int kTile = kCensusTilePx;               // pixels per warp tile
+constexpr int kTile = 64;                          // pixels per warp tile of the full-image kernels
 constexpr int kColsMax = kTile + kMaxWin - 1;      // staged columns (78)
 constexpr int kWordsMax = (kColsMax + 1) / 2 + 1;  // half2 words per staged row (40)
 constexpr int kWarpsPerCta = 8;
@@ -218,9 +216,9 @@ __device__ __forceinline__ void store_pair(const Plane &pl, int x, int y, uint64
 
 
 // ---------------------------------------------------------------------------
-// Fixed windows (5x5, 7x7, 9x7): four pixels per lane, a half-warp per tile.
+// Fixed windows (5x5, 7x7, 9x7): four pixels per lane.
 //
-// Lane l of a half-warp owns pixels x .. x+3 of its tile (x = x0 + 4 l).  It
+// Lane l of a tile's lane group owns pixels x .. x+3 (x = x0 + 4 l).  It
 // loads the twelve pixels I_k(x-4 .. x+7) of every window row straight into
 // registers (three 32-bit loads at k = 1, three 64-bit loads compacted with
 // PRMT at k = 2; adjacent lanes share bytes through L1) and forms the eleven
@@ -465,14 +463,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) census_full_kernel(Plane pl
     census_tile_any(pl, blockIdx.x * kTile, y, win_w, win_h, sentinel, st);
 }
 
-// Region of interest.  The planner marks, per plane row, the 64-pixel tiles the
+// Region of interest.  The planner marks, per plane row, the 32-pixel tiles the
 // search reads (bitmap, one bit per tile).  tile_list_kernel compacts the
 // marks into a dense list (one packed entry per tile, row-major within each
 // 256-word chunk of the bitmap) and clears the bitmap for the next call; the
 // census kernels then take tiles from the list, so every warp gets the same
 // share of work and no warp scans empty bitmap words.
 //
-// Entry: bits 0-9 tile (x0 / 64), 10-25 row, 26-27 plane (L1, R1, Lk, Rk), 28- frame.
+// Entry: bits 0-9 tile (x0 / 32), 10-25 row, 26-27 plane (L1, R1, Lk, Rk), 28- frame.
 __device__ __forceinline__ unsigned long long tile_entry(int f, int q, int y, int tile)
 {
     return ((unsigned long long)f << 28) | ((unsigned long long)q << 26) | ((unsigned long long)y << 10) |
@@ -486,7 +484,7 @@ __device__ __forceinline__ bool tile_of(const MatchArgs &a, unsigned long long e
     const int tile = (int)(e & 1023u);
     y = (int)((e >> 10) & 0xffffu);
     d = a.ws.planes[e >> 26];  // frame * 4 + plane
-    x0 = tile * kTile;
+    x0 = tile * kCensusTilePx;
     return x0 < d.Ws && y < d.Hs;
 }
 
@@ -539,23 +537,25 @@ __global__ void __launch_bounds__(256) tile_list_kernel(MatchArgs a)
     }
 }
 
-// Fixed windows: warp w takes list entries 2p and 2p + 1 (p = w, w + warps, ...),
-// the first for lanes 0-15 and the second for lanes 16-31, so both halves run
-// the same instructions in lockstep.  MODE: 0 = 4 CTAs per SM (64 registers),
+// Fixed windows: warp w takes list entries kPer p .. kPer p + kPer - 1 (p = w,
+// w + warps, ...), one per group of kLanes lanes, so all groups run the same
+// instructions in lockstep.  MODE: 0 = 4 CTAs per SM (64 registers),
 // otherwise 3 CTAs per SM.
 template <int WW, int WH, int MODE>
 __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 3) census_roi4_kernel(MatchArgs a)
 {
-    const int lane = threadIdx.x & 31, hl = lane & 15;
+    constexpr int kLanes = kCensusTilePx / 4;  // lanes per tile (4 pixels each)
+    constexpr int kPer = 32 / kLanes;          // tiles per warp step
+    const int lane = threadIdx.x & 31, hl = lane % kLanes;
     const int n = a.ws.counts->n_tiles;
-    const int npairs = (n + 1) >> 1;
+    const int nsteps = (n + kPer - 1) / kPer;
     const int nw = gridDim.x * (blockDim.x >> 5);
     const int sentinel = a.p.sentinel;
-    for (int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < npairs; p += nw) {
-        const int t = 2 * p + (lane >> 4);
+    for (int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); p < nsteps; p += nw) {
+        const int t = kPer * p + lane / kLanes;
         PlaneDesc d;
         int x0, y;
-        const bool ok = tile_of(a, a.ws.tiles[t < n ? t : 2 * p], d, x0, y) && t < n;
+        const bool ok = tile_of(a, a.ws.tiles[t < n ? t : kPer * p], d, x0, y) && t < n;
         census4<WW, WH>(d, x0, y, hl, ok, sentinel);
     }
 }

@@ -160,7 +160,7 @@ __device__ __forceinline__ BlockRect block_rect(const BoxPlan &P, int slot, int 
 }
 
 // Census launches (census.cu)
-constexpr int kCensusTilePx = 64;   // pixels per bitmap bit (one warp tile)
+constexpr int kCensusTilePx = 32;   // pixels per bitmap bit (a census tile: 8 lanes x 4 pixels)
 cudaError_t launch_census_single(const uint8_t *img, int W, int H, int pitch, int k, int win_w,
                                  int win_h, int sentinel, uint64_t *out, long long out_pitch,
                                  cudaStream_t s);
