@@ -41,6 +41,7 @@ struct Shared {
     int next;               // queue index of the next block
     int next_b;             // its block
     int gpend;              // a geometry copy is in flight on mbar_g
+    int spend;              // a strip copy is in flight on mbar
     unsigned cstart;        // bit j set: a strip column chunk starts at point column j
     int abort;              // a bounded wait expired: stop this CTA
 };
@@ -55,62 +56,76 @@ struct BlockCtx {
     const uint64_t *CR;
 };
 
-// Load one strip chunk: rows (m, e) of the right plane at Y_m + dy_min + e
-// (forward) or of the left plane at Y_m + dy_f - (dy_min + e) (backward).
-// Warp 0 issues one bulk copy per row for its in-plane part; lane 0 first
-// registers the total byte count on the CTA's mbarrier.  After the copies land,
-// positions outside the plane are zero-filled (only edge chunks have any).
-// Returns false if the bounded wait expired.
+// Row r = (m, e) of a strip chunk: the right plane at Y_m + dy_min + e (forward)
+// or the left plane at Y_m + dy_f - (dy_min + e) (backward).
+__device__ __forceinline__ int chunk_row_y(const MatchArgs &a, const BlockCtx &bc, const int *Y, bool fwd,
+                                           int dy_f, int r)
+{
+    const int m = bc.ndy == 1 ? r : r / bc.ndy;
+    const int e = r - m * bc.ndy;
+    return fwd ? Y[m] + a.p.dy_min + e : Y[m] + dy_f - (a.p.dy_min + e);
+}
+
+// Warp 0: issue the bulk copies of one strip chunk (completion on sh.mbar).
 template <int NT>
-__device__ __forceinline__ bool load_chunk(const MatchArgs &a, const BlockCtx &bc, const Smem &sm,
-                                           Shared<NT / 32> &sh, unsigned &phase, bool fwd, int dy_f,
-                                           const ChunkGeom &g)
+__device__ __forceinline__ void issue_chunk(const MatchArgs &a, const BlockCtx &bc, const Smem &sm,
+                                            Shared<NT / 32> &sh, bool fwd, int dy_f, const ChunkGeom &g)
 {
     const int tid = threadIdx.x, lane = tid & 31;
+    if (tid >= 32) return;
     const int rows = bc.ny * bc.ndy;
     const uint64_t *plane = fwd ? bc.CR : bc.CL;
     const int Ws_even = (bc.Ws + 1) & ~1;   // the padding column after an odd width is readable
     const int x_lo = max(g.colbase_a, 0);
     const int x_hi = min(g.colbase_a + g.SWa, Ws_even);
     const unsigned row_bytes = x_hi > x_lo ? 8u * (unsigned)(x_hi - x_lo) : 0u;
-    if (tid < 32) {
-        unsigned total = 0;
+    unsigned total = 0;
+    for (int r = lane; r < rows; r += 32) {
+        const int y = chunk_row_y(a, bc, sh.Y, fwd, dy_f, r);
+        if (y >= 0 && y < bc.Hs) total += row_bytes;
+    }
+    total = __reduce_add_sync(0xffffffffu, total);
+    // order earlier generic-proxy accesses of the strip before the bulk writes
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    if (lane == 0) {
+        mbar_arrive_expect_tx(&sh.mbar, total);
+        sh.spend = 1;
+    }
+    __syncwarp();
+    if (row_bytes > 0) {
         for (int r = lane; r < rows; r += 32) {
-            const int m = bc.ndy == 1 ? r : r / bc.ndy;
-            const int e = r - m * bc.ndy;
-            const int y = fwd ? sh.Y[m] + a.p.dy_min + e : sh.Y[m] + dy_f - (a.p.dy_min + e);
-            if (y >= 0 && y < bc.Hs) total += row_bytes;
-        }
-        total = __reduce_add_sync(0xffffffffu, total);
-        // order earlier generic-proxy accesses of the strip before the bulk writes
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        if (lane == 0) mbar_arrive_expect_tx(&sh.mbar, total);
-        __syncwarp();
-        if (row_bytes > 0) {
-            for (int r = lane; r < rows; r += 32) {
-                const int m = bc.ndy == 1 ? r : r / bc.ndy;
-                const int e = r - m * bc.ndy;
-                const int y = fwd ? sh.Y[m] + a.p.dy_min + e : sh.Y[m] + dy_f - (a.p.dy_min + e);
-                if (y >= 0 && y < bc.Hs)
-                    bulk_g2s(sm.strip + r * g.SWa + (x_lo - g.colbase_a), plane + (long long)y * bc.pitch + x_lo,
-                             row_bytes, &sh.mbar);
-            }
+            const int y = chunk_row_y(a, bc, sh.Y, fwd, dy_f, r);
+            if (y >= 0 && y < bc.Hs)
+                bulk_g2s(sm.strip + r * g.SWa + (x_lo - g.colbase_a), plane + (long long)y * bc.pitch + x_lo,
+                         row_bytes, &sh.mbar);
         }
     }
+}
+
+// All threads: wait for the chunk issued last, then zero what lies outside the
+// plane (rows outside it; columns < 0 or >= Ws), a warp per row (only edge
+// chunks have any).  Returns false if the bounded wait expired.  The phase is
+// only consumed when the wait succeeded, so a drain after a failure waits for
+// the same copies.
+template <int NT>
+__device__ __forceinline__ bool land_chunk(const MatchArgs &a, const BlockCtx &bc, const Smem &sm,
+                                           Shared<NT / 32> &sh, unsigned &phase, bool fwd, int dy_f,
+                                           const ChunkGeom &g)
+{
+    const int tid = threadIdx.x, lane = tid & 31;
     const bool ok = mbar_wait_bounded(&sh.mbar, phase, &a.ws.counts->error);
-    phase ^= 1u;
-    // zero-fill what lies outside the plane (rows outside it; columns < 0 or >= Ws)
+    if (ok) phase ^= 1u;
+    if (ok && tid == 0) sh.spend = 0;
+    const int rows = bc.ny * bc.ndy;
     const bool edge = g.colbase_a < 0 || g.colbase_a + g.SWa > bc.Ws ||
                       sh.Y[0] + (fwd ? a.p.dy_min : dy_f - a.p.dy_max) < 0 ||
                       sh.Y[bc.ny - 1] + (fwd ? a.p.dy_max : dy_f - a.p.dy_min) >= bc.Hs;
-    if (edge) {  // a warp per row: whole rows outside the plane, else the columns outside it
+    if (edge) {
         const int warp = tid >> 5;
         const int c_lo = min(max(-g.colbase_a, 0), g.SWa);             // [0, c_lo): x < 0
         const int c_hi = max(min(bc.Ws - g.colbase_a, g.SWa), c_lo);   // [c_hi, SWa): x >= Ws
         for (int r = warp; r < rows; r += NT / 32) {
-            const int m = bc.ndy == 1 ? r : r / bc.ndy;
-            const int e = r - m * bc.ndy;
-            const int y = fwd ? sh.Y[m] + a.p.dy_min + e : sh.Y[m] + dy_f - (a.p.dy_min + e);
+            const int y = chunk_row_y(a, bc, sh.Y, fwd, dy_f, r);
             uint64_t *row = sm.strip + r * g.SWa;
             if (y < 0 || y >= bc.Hs) {
                 for (int c = lane; c < g.SWa; c += 32) row[c] = 0ull;
@@ -121,6 +136,18 @@ __device__ __forceinline__ bool load_chunk(const MatchArgs &a, const BlockCtx &b
         }
     }
     return ok;
+}
+
+// Load one strip chunk: rows (m, e) of the right plane at Y_m + dy_min + e
+// (forward) or of the left plane at Y_m + dy_f - (dy_min + e) (backward);
+// issue, wait, zero-fill.
+template <int NT>
+__device__ __forceinline__ bool load_chunk(const MatchArgs &a, const BlockCtx &bc, const Smem &sm,
+                                           Shared<NT / 32> &sh, unsigned &phase, bool fwd, int dy_f,
+                                           const ChunkGeom &g)
+{
+    issue_chunk<NT>(a, bc, sm, sh, fwd, dy_f, g);
+    return land_chunk<NT>(a, bc, sm, sh, phase, fwd, dy_f, g);
 }
 
 // Warp and CTA minimum of the keys (cost << 16 | c) over the candidates; the
@@ -151,17 +178,18 @@ __device__ __forceinline__ void argmin_pass(const MatchArgs &a, const BlockCtx &
     __syncthreads();
 }
 
-// One search pass after its first strip chunk has landed and the point bases of
-// the first chunk are set.  Returns false if a bounded wait expired.
+// The scans of one search pass after its first strip chunk has landed and the
+// point bases of the first chunk are set: every chunk (later ones loaded into
+// the strip after the previous chunk's scan), sums kept in registers.  Returns
+// false if a bounded wait expired.
 template <int NT>
-__device__ bool search_pass(const MatchArgs &a, const BlockCtx &bc, const Smem &sm,
-                            Shared<NT / 32> &sh, unsigned &phase, bool fwd, ChunkGeom g)
+__device__ bool scan_chunks(const MatchArgs &a, const BlockCtx &bc, const Smem &sm, Shared<NT / 32> &sh,
+                            unsigned &phase, bool fwd, ChunkGeom g, int (&acc)[8])
 {
     constexpr int NW = NT / 32;
     const int lane = threadIdx.x & 31;
     const int T = (bc.nc + 31) >> 5;
     const bool fast = bc.ndy == 1 && (bc.nd & 31) == 0;
-    int acc[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) acc[t] = 0;
     const int d_f = sh.d_f, dy_f = sh.dy_f;
@@ -203,6 +231,17 @@ __device__ bool search_pass(const MatchArgs &a, const BlockCtx &bc, const Smem &
         __syncthreads();
         j0 = j1;
     }
+    return ok;
+}
+
+// The end of a pass: warps combine their sums in sm.cost (zeroed when the
+// block started) and the first argmin lands in sh.warp_min[0].
+template <int NT>
+__device__ __forceinline__ void finish_pass(const MatchArgs &a, const BlockCtx &bc, const Smem &sm,
+                                            Shared<NT / 32> &sh, bool fwd, const int (&acc)[8])
+{
+    const int lane = threadIdx.x & 31;
+    const int T = (bc.nc + 31) >> 5;
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
         const int c = t * 32 + lane;
@@ -210,7 +249,6 @@ __device__ bool search_pass(const MatchArgs &a, const BlockCtx &bc, const Smem &
     }
     __syncthreads();
     argmin_pass<NT>(a, bc, sm, sh, fwd);
-    return ok;
 }
 
 // Queue entry i: large work from the front, small work from the back.
@@ -219,63 +257,48 @@ __device__ __forceinline__ int queue_block(const MatchArgs &a, int i, int n_big)
     return i < n_big ? a.ws.queue[i] : a.ws.queue[a.caps.max_blocks - 1 - (i - n_big)];
 }
 
-// Prefetch state of the persistent kernel: the queue index taken for the next
-// block and the geometry buffer it goes to.  A single-block launch has none.
-struct Prefetch {
-    bool on;
-    int n_big, nq;
-    int buf;  // geometry buffer of the next block
-};
-
-// One block end to end.  Its geometry is in sh.geom[gbuf] (landed).  With
-// pf.on, thread 0 takes the next queue index at the start, and once the
-// forward pass is done issues the next block's geometry copy into the other
-// buffer (completion on sh.mbar_g), so that round trip overlaps this block.
-// Returns false if a bounded wait expired.  evals: thread 0 adds this block's
-// evaluation count.
-template <int NT>
-__device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<NT / 32> &sh,
-                              unsigned &phase, int gbuf, const Prefetch &pf, unsigned long long &evals)
+// Block context from the block's sampling record (which carries its box plan).
+__device__ __forceinline__ BlockCtx make_ctx(const MatchArgs &a, const BlockGeom &g, int b)
 {
-    int next_i = 0;
-    if (pf.on && threadIdx.x == 0) next_i = atomicAdd(&a.ws.counts->queue_head, 1);
-    const int tid = threadIdx.x;
-    const int2 bs = a.ws.blocks[b];
-    const BoxPlan P = a.ws.plans[bs.x];
     BlockCtx bc;
-    bc.box = bs.x;
-    bc.slot = bs.y;
+    bc.box = g.box;
+    bc.slot = g.slot;
     bc.b = b;
-    bc.k = P.k;
-    bc.far = P.far;
-    bc.dmin = P.dmin;
-    bc.dmax = P.dmax;
-    bc.nd = P.dmax - P.dmin + 1;
+    bc.k = g.k;
+    bc.far = g.far;
+    bc.dmin = g.dmin;
+    bc.dmax = g.dmax;
+    bc.nd = g.dmax - g.dmin + 1;
     bc.ndy = a.p.dy_max - a.p.dy_min + 1;
     bc.nc = bc.nd * bc.ndy;
-    bc.Ws = P.Ws;
-    bc.Hs = P.Hs;
-    {
-        const bool full = P.far || a.p.close_factor == 1;
-        const uint64_t *base = a.ws.census + (long long)P.frame * a.ws.frame_stride;
-        bc.CL = full ? base : base + 2 * a.ws.plane1_elems;
-        bc.CR = full ? base + a.ws.plane1_elems : base + 2 * a.ws.plane1_elems + a.ws.planek_elems;
-        bc.pitch = full ? a.ws.pitch1 : a.ws.pitchk;
-    }
-
-    // 1a. the block's sampled grid and usable points (from the sampling kernel)
-    for (int c = tid; c < bc.nc; c += NT) sm.cost[c] = 0;
-    const BlockGeom &g = sh.geom[gbuf];
+    bc.Ws = g.Ws;
+    bc.Hs = g.Hs;
     bc.nx = g.nx;
     bc.ny = g.ny;
+    const bool full = g.far || a.p.close_factor == 1;
+    const uint64_t *base = a.ws.census + (long long)g.frame * a.ws.frame_stride;
+    bc.CL = full ? base : base + 2 * a.ws.plane1_elems;
+    bc.CR = full ? base + a.ws.plane1_elems : base + 2 * a.ws.plane1_elems + a.ws.planek_elems;
+    bc.pitch = full ? a.ws.pitch1 : a.ws.pitchk;
+    return bc;
+}
+
+// Start block b, whose sampling record has landed in sh.geom[gbuf]: its point
+// layout (column-major compaction of the usable points), its sampled columns
+// and rows, the left codes at its points (cp.async) and its first forward strip
+// chunk (bulk copies on sh.mbar).  Nothing is waited for here; the strip, the
+// point arrays and sh.X / sh.Y must be free (the previous block's scans done).
+template <int NT>
+__device__ void begin_block(const MatchArgs &a, int b, const Smem &sm, Shared<NT / 32> &sh, int gbuf)
+{
+    const int tid = threadIdx.x;
+    const BlockGeom &g = sh.geom[gbuf];
+    const BlockCtx bc = make_ctx(a, g, b);
     const int total = g.n_valid;
     const unsigned later0 = g.cstart & ~1u;
     const int j1_first = later0 ? __ffs(later0) - 1 : bc.nx;
     const int x0 = g.X[0];
-    const int SW0 = g.X[j1_first - 1] - x0 + bc.nd;
-    const ChunkGeom g0 = chunk_geom(x0 - bc.dmax, SW0);
-
-    // 1b. usable points at their compacted (column-major) index, left codes in flight
+    const ChunkGeom g0 = chunk_geom(x0 - bc.dmax, g.X[j1_first - 1] - x0 + bc.nd);
     for (int t = tid; t < kMaxPts; t += NT) {
         const int j = t >> 4, m = t & 15;
         if (j < bc.nx && ((g.colmask[j] >> m) & 1u)) {
@@ -292,21 +315,53 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
     }
     if (tid <= kMaxPtsSide) sh.colstart[tid] = tid < bc.nx ? g.colprefix[tid] : total;
     if (tid == 0) sh.cstart = g.cstart;
-    __syncthreads();
-    // 1c. the first forward strip chunk
-    bool ok = load_chunk<NT>(a, bc, sm, sh, phase, true, 0, g0);
+    __syncthreads();  // sh.Y is read by the issuing warp
+    issue_chunk<NT>(a, bc, sm, sh, true, 0, g0);
+}
+
+// Prefetch state of the persistent kernel.  A single-block launch has none.
+struct Prefetch {
+    bool on;
+    int n_big, nq;
+    int buf;  // geometry buffer of the next block
+};
+
+// One block end to end, after begin_block.  With pf.on, thread 0 takes the next
+// queue index at the start and issues the next block's record copy once the
+// forward pass is done; when the backward scans are over, the CTA waits for
+// that record and begins the next block (its codes and first strip in flight)
+// before it combines its own backward sums and writes its record, so the next
+// block's first round trip overlaps this block's end.  Returns false if a
+// bounded wait expired.  evals: thread 0 adds this block's evaluation count.
+template <int NT>
+__device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<NT / 32> &sh,
+                              unsigned &phase, int gbuf, Prefetch &pf, unsigned &gphase,
+                              unsigned long long &evals)
+{
+    const int tid = threadIdx.x;
+    int next_i = 0;
+    if (pf.on && tid == 0) next_i = atomicAdd(&a.ws.counts->queue_head, 1);
+    const BlockGeom &g = sh.geom[gbuf];
+    const BlockCtx bc = make_ctx(a, g, b);
+    const int total = g.n_valid;
+    const unsigned later0 = g.cstart & ~1u;
+    const int j1_first = later0 ? __ffs(later0) - 1 : bc.nx;
+    const int x0 = g.X[0];
+    const int SW0 = g.X[j1_first - 1] - x0 + bc.nd;
+    const ChunkGeom g0 = chunk_geom(x0 - bc.dmax, SW0);
+    for (int c = tid; c < bc.nc; c += NT) sm.cost[c] = 0;
+
+    // 1. the left codes and the first forward strip chunk (issued by begin_block)
+    bool ok = land_chunk<NT>(a, bc, sm, sh, phase, true, 0, g0);
     cp_async_wait_all();
     int next_b = 0;
     if (pf.on && tid == 0 && next_i < pf.nq) next_b = queue_block(a, next_i, pf.n_big);
     if (!__syncthreads_and(ok)) return false;
 
-    ctm_block rec;
-    rec.n_pts = bc.nx * bc.ny;
-    rec.n_valid = total;
-    rec.flags = CTM_BLK_PRESENT;
-
     // 2-3. forward pass, argmin, parabola
-    ok = search_pass<NT>(a, bc, sm, sh, phase, true, g0);
+    int acc[8];
+    ok = scan_chunks<NT>(a, bc, sm, sh, phase, true, g0, acc);
+    finish_pass<NT>(a, bc, sm, sh, true, acc);
     if (!__syncthreads_and(ok)) return false;
     if (tid == 0) {
         const unsigned key = sh.warp_min[0];
@@ -320,7 +375,7 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
         if (pf.on) {
             sh.next = next_i;
             sh.next_b = next_b;
-            if (next_i < pf.nq) {  // the next block's geometry, in flight during this backward pass
+            if (next_i < pf.nq) {  // the next block's record, in flight during this backward pass
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 mbar_arrive_expect_tx(&sh.mbar_g, (unsigned)sizeof(BlockGeom));
                 bulk_g2s(&sh.geom[pf.buf], a.ws.geom + next_b, (unsigned)sizeof(BlockGeom), &sh.mbar_g);
@@ -345,23 +400,33 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
     set_bases<NT>(sm, sh.X, 0, sh.colstart[j1_first], bc.ndy, gb.SWa, x0, gb.delta);
     cp_async_wait_all();
     if (!__syncthreads_and(ok)) return false;
-    ok = search_pass<NT>(a, bc, sm, sh, phase, false, gb);
+    ok = scan_chunks<NT>(a, bc, sm, sh, phase, false, gb, acc);
     if (!__syncthreads_and(ok)) return false;
+
+    // the next block starts now: its record (wait) and its first loads (issued)
+    const bool has_next = pf.on && sh.gpend;
+    if (has_next) {
+        const bool landed = mbar_wait_bounded(&sh.mbar_g, gphase, &a.ws.counts->error);
+        if (landed) gphase ^= 1u;
+        if (!__syncthreads_and(landed)) return false;
+        if (tid == 0) sh.gpend = 0;
+        begin_block<NT>(a, sh.next_b, sm, sh, pf.buf);
+    }
+
+    finish_pass<NT>(a, bc, sm, sh, false, acc);
     if (tid == 0) {
         const unsigned key = sh.warp_min[0];
         const int c = (int)(key & 0xffffu);
         const int e = c / bc.nd;
-        sh.d_b = bc.dmin + (c - e * bc.nd);
-        sh.dy_b = a.p.dy_min + e;
-    }
-    __syncthreads();
-
-    // 5. block record (thread 0); boxes are aggregated by aggregate_kernel
-    if (tid == 0) {
+        // 5. block record; boxes are aggregated by aggregate_kernel
+        ctm_block rec;
+        rec.n_pts = bc.nx * bc.ny;
+        rec.n_valid = total;
+        rec.flags = CTM_BLK_PRESENT;
         rec.d_f = sh.d_f;
         rec.dy_f = sh.dy_f;
-        rec.d_b = sh.d_b;
-        rec.dy_b = sh.dy_b;
+        rec.d_b = bc.dmin + (c - e * bc.nd);
+        rec.dy_b = a.p.dy_min + e;
         rec.s_m = sh.s_m;
         rec.s_0 = sh.s_0;
         rec.s_p = sh.s_p;
@@ -400,6 +465,17 @@ __device__ __forceinline__ Smem carve(const MatchArgs &a, unsigned char *raw)
     return sm;
 }
 
+// After a failed bounded wait: let every copy still in flight land before the
+// CTA leaves (its shared memory may go to another CTA).
+template <int NT>
+__device__ __forceinline__ void drain(const MatchArgs &a, Shared<NT / 32> &sh, unsigned phase, unsigned gphase)
+{
+    cp_async_wait_all();
+    __syncthreads();
+    if (sh.gpend) mbar_wait_bounded(&sh.mbar_g, gphase, &a.ws.counts->error);
+    if (sh.spend) mbar_wait_bounded(&sh.mbar, phase, &a.ws.counts->error);
+}
+
 template <int NT>
 __global__ void __launch_bounds__(NT, 1024 / NT)
     match_persistent_kernel(MatchArgs a)
@@ -419,6 +495,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
         const int i = atomicAdd(&a.ws.counts->queue_head, 1);
         sh.next = i;
         sh.gpend = 0;
+        sh.spend = 0;
         if (i < pf.nq) {
             sh.next_b = queue_block(a, i, pf.n_big);
             mbar_arrive_expect_tx(&sh.mbar_g, (unsigned)sizeof(BlockGeom));
@@ -429,21 +506,28 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
     __syncthreads();
     unsigned phase = 0, gphase = 0;
     unsigned long long evals = 0ull;
-    int buf = 0;
-    while (sh.gpend) {
-        const int b = sh.next_b;
+    if (sh.gpend) {
+        // the first block: wait for its record, begin it
         const bool landed = mbar_wait_bounded(&sh.mbar_g, gphase, &a.ws.counts->error);
-        gphase ^= 1u;
-        if (!__syncthreads_and(landed)) break;  // (its copy landed or the wait gave up twice)
-        if (threadIdx.x == 0) sh.gpend = 0;     // read by all threads before the barrier above
-        pf.buf = buf ^ 1;
-        if (!process_block<NT>(a, b, sm, sh, phase, buf, pf, evals)) {
-            // a bounded wait expired: let a geometry copy in flight land before leaving
-            __syncthreads();
-            if (sh.gpend) mbar_wait_bounded(&sh.mbar_g, gphase, &a.ws.counts->error);
-            break;
+        if (landed) gphase ^= 1u;
+        if (__syncthreads_and(landed)) {
+            if (threadIdx.x == 0) sh.gpend = 0;
+            int b = sh.next_b;
+            int buf = 0;
+            begin_block<NT>(a, b, sm, sh, buf);
+            for (;;) {
+                pf.buf = buf ^ 1;
+                if (!process_block<NT>(a, b, sm, sh, phase, buf, pf, gphase, evals)) {
+                    drain<NT>(a, sh, phase, gphase);
+                    break;
+                }
+                if (sh.next >= pf.nq) break;  // no block was begun
+                b = sh.next_b;
+                buf ^= 1;
+            }
+        } else {
+            drain<NT>(a, sh, phase, gphase);
         }
-        buf ^= 1;
     }
     if (threadIdx.x == 0 && evals) atomicAdd(&a.ws.counts->evals, evals);
 }
@@ -460,16 +544,21 @@ __global__ void __launch_bounds__(NT) match_box_kernel(MatchArgs a, int box)
     if (threadIdx.x < (int)(sizeof(BlockGeom) / 16))
         cp_async16(reinterpret_cast<char *>(&sh.geom[0]) + 16 * threadIdx.x,
                    reinterpret_cast<const char *>(a.ws.geom + b) + 16 * threadIdx.x);
-    if (threadIdx.x == 0) mbar_init(&sh.mbar, 1);
+    if (threadIdx.x == 0) {
+        mbar_init(&sh.mbar, 1);
+        sh.gpend = 0;
+        sh.spend = 0;
+    }
     cp_async_wait_all();
     __syncthreads();
-    unsigned phase = 0;
+    unsigned phase = 0, gphase = 0;
     unsigned long long evals = 0ull;
     Prefetch pf;
     pf.on = false;
     pf.n_big = pf.nq = 0;
     pf.buf = 1;
-    process_block<NT>(a, b, sm, sh, phase, 0, pf, evals);
+    begin_block<NT>(a, b, sm, sh, 0);
+    if (!process_block<NT>(a, b, sm, sh, phase, 0, pf, gphase, evals)) drain<NT>(a, sh, phase, gphase);
     if (threadIdx.x == 0 && evals) atomicAdd(&a.ws.counts->evals, evals);
 }
 
