@@ -226,6 +226,38 @@ __device__ __forceinline__ void store_pair(const Plane &pl, int x, int y, uint64
 // memory is involved.  Pixel pairs (x, x+1) and (x+2, x+3) are compared two at
 // a time in the 16-bit halves of a word (codes4).
 
+// Pixels xs .. xs+3 of a row at k = 1 (one aligned word; xs is a multiple of 4):
+// 0 where the word lies outside [0, W), bytes where it straddles W.
+__device__ __forceinline__ uint32_t word_k1(const uint8_t *row, int xs, int W)
+{
+    if (xs >= 0 && xs + 4 <= W) return __ldg(reinterpret_cast<const uint32_t *>(row + xs));
+    if (xs + 4 <= 0 || xs >= W) return 0u;
+    uint32_t w = 0u;
+    for (int t = 0; t < 4; ++t) {
+        const int xt = xs + t;
+        if (xt >= 0 && xt < W) w |= (uint32_t)__ldg(row + xt) << (8 * t);
+    }
+    return w;
+}
+
+// Decimated pixels xs .. xs+3 of a row at k = 2 (source bytes 2 xs .. 2 xs + 7,
+// one aligned 8-byte word compacted with PRMT): 0 outside the grid [0, Ws),
+// bytes where the word straddles the source row end W.
+__device__ __forceinline__ uint32_t word_k2(const uint8_t *row, int xs, int W, int Ws)
+{
+    if (xs >= 0 && 2 * xs + 8 <= W) {
+        const uint2 u = __ldg(reinterpret_cast<const uint2 *>(row + 2 * xs));
+        return __byte_perm(u.x, u.y, 0x6420);
+    }
+    if (xs + 4 <= 0 || xs >= Ws) return 0u;
+    uint32_t w = 0u;
+    for (int t = 0; t < 4; ++t) {
+        const int xt = xs + t;
+        if (xt >= 0 && xt < Ws) w |= (uint32_t)__ldg(row + 2 * xt) << (8 * t);
+    }
+    return w;
+}
+
 // Twelve pixels I_k(x - 4 .. x + 7) of grid row `yr` for this lane, as three
 // little-endian words; pixels outside the grid read as 0 (they only feed
 // pixels whose codes are zeroed).  Lanes whose twelve pixels lie inside a
@@ -281,9 +313,13 @@ __device__ __forceinline__ void census4(const PlaneDesc &d, int x0, int y, int h
     const unsigned full = 0xffffffffu;
     const int x = x0 + 4 * hl;
     const bool active = ok && y - sy >= 0 && y + sy < d.Hs;
-    const bool inside = d.vec_load && x >= 4 && (d.k == 1 ? x + 8 <= d.W : 2 * x + 16 <= d.W);
     // one load scheme for the whole warp where possible (a uniform branch, so
-    // the other schemes are not executed predicated off)
+    // the other schemes are not executed predicated off): straight word loads
+    // when every lane's twelve pixels lie inside the row; else, at image
+    // borders, word loads where a word lies inside, 0 where it lies outside (it
+    // only feeds pixels whose codes are zeroed) and bytes where it straddles the
+    // end of a row whose width is not a multiple of the word
+    const bool inside = d.vec_load && x >= 4 && (d.k == 1 ? x + 8 <= d.W : 2 * x + 16 <= d.W);
     uint32_t rows[WH][3];
     if (__all_sync(full, !active || (inside && d.k == 1))) {
         if (active) {
@@ -307,6 +343,23 @@ __device__ __forceinline__ void census4(const PlaneDesc &d, int x0, int y, int h
                 rows[r][1] = __byte_perm(b.x, b.y, 0x6420);
                 rows[r][2] = __byte_perm(c.x, c.y, 0x6420);
             }
+        }
+    } else if (__all_sync(full, !active || (d.vec_load && d.k == 1))) {
+        if (active) {
+            const uint8_t *p = d.img + (long long)(y - sy) * d.pitch;
+#pragma unroll
+            for (int r = 0; r < WH; ++r)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) rows[r][q] = word_k1(p + (long long)r * d.pitch, x - 4 + 4 * q, d.W);
+        }
+    } else if (__all_sync(full, !active || (d.vec_load && d.k == 2))) {
+        if (active) {
+            const uint8_t *p = d.img + 2LL * (y - sy) * d.pitch;
+#pragma unroll
+            for (int r = 0; r < WH; ++r)
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+                    rows[r][q] = word_k2(p + 2LL * r * d.pitch, x - 4 + 4 * q, d.W, d.Ws);
         }
     } else if (active) {
 #pragma unroll

@@ -48,3 +48,19 @@ def test_census_pitched_input(torch_cuda):
     got = B.census_build(t, 1, 9, 7, 1).cpu().numpy().view(np.uint64)
     ref = orc.census(np.ascontiguousarray(big[:, 10:150]), 1, 9, 7, 1)
     assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("width", [201, 203, 206])
+def test_census_word_loads_straddling_the_row_end(torch_cuda, k, width):
+    """Aligned rows (pitch 208) whose width is not a multiple of the load word: the
+    words that straddle the row end are read byte by byte, codes stay bit-exact."""
+    from paper_2604_07980_gb300 import binding as B
+    rng = np.random.default_rng(width * 10 + k)
+    big = rng.integers(0, 256, size=(67, 208), dtype=np.uint8)
+    img = big[:, :width]
+    t = torch_cuda.from_numpy(big).cuda()[:, :width]
+    for win in ((9, 7), (5, 5)):
+        got = B.census_build(t, k, *win, 1).cpu().numpy().view(np.uint64)
+        ref = orc.census(np.ascontiguousarray(img), k, *win, 1)
+        assert np.array_equal(got, ref), (win, np.argwhere(got != ref)[:5].tolist())
