@@ -42,7 +42,7 @@ POPC_PER_EVAL = 2          # one u64 code pair = two 32-bit popcounts
 # DRAM bytes (read + write) of one match_persistent_kernel launch on this workload, from the
 # ncu capture summarised in profiles/match_persistent_kernel_batch32x1200.md; None once the
 # kernel changes after that capture.
-MATCH_DRAM_BYTES = (102.542 + 4.018) * 1e6
+MATCH_DRAM_BYTES = (102.538 + 3.350) * 1e6
 # kernels of one step of the batched path (ctm_box_points, timed apart, is not in it): plan,
 # sample (with census demand marking), tile_list, census_roi, match, aggregate
 KERNELS_PER_STEP = 6
