@@ -43,6 +43,11 @@ POPC_PER_EVAL = 2          # one u64 code pair = two 32-bit popcounts
 # ncu capture summarised in profiles/match_persistent_kernel_batch32x1200.md; None once the
 # kernel changes after that capture.
 MATCH_DRAM_BYTES = (102.538 + 3.350) * 1e6
+# DRAM bytes of one census_roi4_kernel launch on this workload (same capture, summarised in
+# profiles/census_roi4_kernel_batch32x1200.md) plus its tile_list_kernel launch
+CENSUS_DRAM_BYTES = (61.084 + 68.565 + 0.775) * 1e6
+CENSUS_TILE_PX = 32        # pixels per listed census tile
+CENSUS_CMPS = 9 * 7 - 1    # compares per 9x7 code (the centre bit is always 0)
 # kernels of one step of the batched path (ctm_box_points, timed apart, is not in it): plan,
 # sample (with census demand marking), tile_list, census_roi, match, aggregate
 KERNELS_PER_STEP = 6
@@ -443,6 +448,46 @@ def main():
     popc_clk = float(round(popc_rate))
     peak = sms * popc_clk / POPC_PER_EVAL * SM_MAX_MHZ * 1e6 / 1e9
     achieved = evals_per_step / (match_ms * 1e-3) / 1e9
+    # the same peak at the sampled SM clock of this run and at the median SM clock seen under a
+    # power-capped dense GEMM (MEASURED_PEAKS.json), where that file is present
+    peak_at = {"sampled_sm_mhz": clk.get("sm_mhz"),
+               "peak_at_sampled": (sms * popc_clk / POPC_PER_EVAL * clk["sm_mhz"] * 1e6 / 1e9
+                                   if clk.get("sm_mhz") else None)}
+    mp_path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    hbm_peak = 6800.0
+    hbm_basis = "fallback 6.8 TB/s"
+    if os.path.exists(mp_path):
+        with open(mp_path) as fh:
+            mp = json.load(fh)
+        load_mhz = mp.get("clocks_under_load", {}).get("sm_mhz_median")
+        if load_mhz:
+            peak_at["gemm_load_sm_mhz"] = load_mhz
+            peak_at["peak_at_gemm_load"] = sms * popc_clk / POPC_PER_EVAL * load_mhz * 1e6 / 1e9
+        if mp.get("hbm_gbs"):
+            hbm_peak = float(mp["hbm_gbs"])
+            hbm_basis = "of measured copy bandwidth (MEASURED_PEAKS.json)"
+
+    # ---- census phase (tile list + ROI census): HBM and integer-ALU fractions.  Algorithmic
+    # bytes per code: 8 written + 1 source pixel read; compares per code: win_w * win_h - 1,
+    # each half an IMAD (FMA pipe) and half a LOP3 (ALU pipe), the two pipes running side by side
+    codes = census_tiles * CENSUS_TILE_PX
+    lop3_rate = B.probe_int_rate(1, 4096)
+    imad_rate = B.probe_int_rate(4, 4096)
+    cmp_clk = min(lop3_rate, imad_rate) / 0.5
+    cmp_peak = sms * cmp_clk * SM_MAX_MHZ * 1e6 / 1e12
+    census_bytes = codes * 9
+    census_roof = {
+        "kernel": "tile_list_kernel + census_roi4_kernel (census phase)",
+        "codes_per_step": codes,
+        "hbm": {"achieved": census_bytes / (census_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                "frac": census_bytes / (census_ms * 1e-3) / 1e9 / hbm_peak,
+                "traffic": CENSUS_DRAM_BYTES if len(w.frames) == 32 else None,
+                "basis": f"9 B per code (8 B code + 1 B pixel); {hbm_basis}"},
+        "alu": {"achieved": codes * CENSUS_CMPS / (census_ms * 1e-3) / 1e12, "peak": cmp_peak,
+                "unit": "T compares/s", "frac": codes * CENSUS_CMPS / (census_ms * 1e-3) / 1e12 / cmp_peak,
+                "basis": f"{sms} SMs x {cmp_clk:.0f} compares/clk/SM (LOP3 probe {lop3_rate:.1f}, "
+                         f"IMAD probe {imad_rate:.1f}, one of each per 2 compares) x {SM_MAX_MHZ:g} MHz"},
+    }
 
     # ---- serving: 4 stereo streams at 30 Hz (batched lanes, then the plain per-box path)
     serving = serving_plain = None
@@ -489,7 +534,9 @@ def main():
                          "traffic": MATCH_DRAM_BYTES if len(w.frames) == 32 else None,
                          "kernel": "match_persistent_kernel",
                          "peak_basis": f"{sms} SMs x {popc_clk:g} popc32/clk/SM (probe {popc_rate:.2f}) / "
-                                       f"{POPC_PER_EVAL} per eval x {SM_MAX_MHZ:g} MHz"},
+                                       f"{POPC_PER_EVAL} per eval x {SM_MAX_MHZ:g} MHz",
+                         "at_other_clocks": peak_at},
+            "census_roofline": census_roof,
             "cpu_baseline": cpu,
             "gpu_launches": KERNELS_PER_STEP * args.steps,
             "clocks": clk,

@@ -601,7 +601,8 @@ def frames_to_device(frames, device="cuda"):
 
 
 def probe_int_rate(kind: int, iters: int = 4096) -> float:
-    """Operations per SM clock per SM of 32-bit popcount (kind 0) or 3-input xor (kind 1)."""
+    """Operations per SM clock per SM: 32-bit popcount (kind 0), 3-input xor (1), packed fp16
+    greater-than (2), 32-bit add (3) or 32-bit multiply-add (4)."""
     _torch()
     v = ctypes.c_double(0.0)
     _check(lib().ctm_probe_int_rate(kind, iters, ctypes.byref(v)), "ctm_probe_int_rate")
