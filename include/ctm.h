@@ -232,11 +232,16 @@ int ctm_match_batch_profiled(ctm_ctx *ctx, const ctm_frame *frames_dev, const in
 
 /* End-to-end batch from host memory: frames_host[i].left/right are HOST images
  * (page-locked for asynchronous copies), boxes_host and the outputs are host
- * arrays.  Copies the images and boxes in, runs ctm_match_batch, copies the
- * results out and synchronizes `stream` before returning.  Images packed at the
- * staging pitch (pitch == width == max_width rounded up to 128) and, for runs
- * of more than one, full height (max_height) and laid out back to back in host
- * memory as L0 R0 L1 R1 ... go in a single copy.  Errors as above. */
+ * arrays.  Copies the images and boxes in, runs the batched path, copies the
+ * results out and synchronizes `stream` before returning.  When every frame's
+ * boxes directly follow the previous frame's (box_begin of frame i + 1 = box_begin
+ * + box_count of frame i), the frames go in up to 4 sub-batches: the copies of
+ * sub-batch g + 1 (on a stream of the context) overlap the kernels of sub-batch
+ * g (on `stream`), with results equal to one batch's; ctm_get_stats afterwards
+ * sums the sub-batches.  Images packed at the staging pitch (pitch == width ==
+ * max_width rounded up to 128) and, for runs of more than one, full height
+ * (max_height) and laid out back to back in host memory as L0 R0 L1 R1 ... go
+ * in one copy per sub-batch.  Errors as above. */
 int ctm_match_batch_host(ctm_ctx *ctx, const ctm_frame *frames_host, int n_frames,
                          const ctm_box *boxes_host, int n_boxes, float *disp_host,
                          float *depth_host, uint8_t *flags_host, ctm_stream stream);

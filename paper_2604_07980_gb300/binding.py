@@ -54,6 +54,14 @@ class ctm_frame(ctypes.Structure):
                 ("box_count", ctypes.c_int32), ("f_px", ctypes.c_float), ("baseline_m", ctypes.c_float)]
 
 
+# The same layout as a numpy record, so that frame tables are built without a
+# Python loop over frames.
+FRAME_DTYPE = np.dtype([("left", np.uint64), ("right", np.uint64), ("width", np.int32), ("height", np.int32),
+                        ("pitch", np.int32), ("box_begin", np.int32), ("box_count", np.int32),
+                        ("f_px", np.float32), ("baseline_m", np.float32)], align=True)
+assert FRAME_DTYPE.itemsize == ctypes.sizeof(ctm_frame)
+
+
 class ctm_debug(ctypes.Structure):
     _fields_ = [("blocks", ctypes.c_void_p), ("cost_f", ctypes.c_void_p), ("cost_b", ctypes.c_void_p)]
 
@@ -358,23 +366,47 @@ class Context:
         """Host arrays in, host arrays out (page-locked numpy views are fastest).
         frames_np: list of (left, right) uint8 [H, W] arrays; boxes_np int32 [n, 5]
         grouped by frame (column 4 = frame index)."""
+        nf = len(frames_np)
+        tbl = np.zeros(nf, FRAME_DTYPE)
+        tbl["left"] = [L.__array_interface__["data"][0] for L, _ in frames_np]
+        tbl["right"] = [R.__array_interface__["data"][0] for _, R in frames_np]
+        tbl["width"] = [L.shape[1] for L, _ in frames_np]
+        tbl["height"] = [L.shape[0] for L, _ in frames_np]
+        tbl["pitch"] = [L.strides[0] for L, _ in frames_np]
+        return self._host_call(tbl, boxes_np, f_px, baseline_m, out, stream)
+
+    def match_batch_host_packed(self, images, boxes_np, f_px, baseline_m, out=None, stream=None):
+        """Like match_batch_host for frames packed in one host array images[F, 2, H, W]
+        (left, right; a frame-grabber ring buffer): the frame table is computed from
+        the array's strides, and frames stored back to back go in one copy per sub-batch."""
+        if images.ndim != 4 or images.shape[1] != 2 or images.dtype != np.uint8 or images.strides[3] != 1:
+            raise ValueError("images must be uint8 [F, 2, H, W] with unit column stride")
+        nf, _, H, W = images.shape
+        base = images.__array_interface__["data"][0]
+        tbl = np.zeros(nf, FRAME_DTYPE)
+        tbl["left"] = base + np.arange(nf, dtype=np.uint64) * np.uint64(images.strides[0])
+        tbl["right"] = tbl["left"] + np.uint64(images.strides[1])
+        tbl["width"] = W
+        tbl["height"] = H
+        tbl["pitch"] = images.strides[2]
+        return self._host_call(tbl, boxes_np, f_px, baseline_m, out, stream)
+
+    def _host_call(self, tbl, boxes_np, f_px, baseline_m, out, stream):
+        nf = len(tbl)
         n = int(boxes_np.shape[0])
-        counts = np.bincount(boxes_np[:, 4], minlength=len(frames_np)) if n else np.zeros(len(frames_np), int)
-        begins = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int64)
-        arr = (ctm_frame * len(frames_np))()
-        for i, (L, R) in enumerate(frames_np):
-            fp = f_px[i] if np.ndim(f_px) else f_px
-            bm = baseline_m[i] if np.ndim(baseline_m) else baseline_m
-            arr[i] = ctm_frame(L.ctypes.data, R.ctypes.data, L.shape[1], L.shape[0], L.strides[0],
-                               int(begins[i]), int(counts[i]), float(fp), float(bm))
+        counts = np.bincount(boxes_np[:, 4], minlength=nf) if n else np.zeros(nf, np.int64)
+        tbl["box_count"] = counts[:nf]
+        tbl["box_begin"][1:] = np.cumsum(counts[:nf])[:-1]
+        tbl["f_px"] = f_px
+        tbl["baseline_m"] = baseline_m
         if out is None:
             out = (np.empty(max(n, 1), np.float32), np.empty(max(n, 1), np.float32),
                    np.empty(max(n, 1), np.uint8))
         disp, depth, flags = out
         bx = np.ascontiguousarray(boxes_np, dtype=np.int32)
-        _check(lib().ctm_match_batch_host(self._h, arr, len(frames_np), bx.ctypes.data, n,
-                                          disp.ctypes.data, depth.ctypes.data, flags.ctypes.data,
-                                          _stream(stream)), "ctm_match_batch_host")
+        _check(lib().ctm_match_batch_host(self._h, tbl.ctypes.data_as(ctypes.POINTER(ctm_frame)), nf,
+                                          bx.ctypes.data, n, disp.ctypes.data, depth.ctypes.data,
+                                          flags.ctypes.data, _stream(stream)), "ctm_match_batch_host")
         return {"disp": disp[:n], "depth": depth[:n], "flags": flags[:n]}
 
     def get_tuning(self) -> dict:

@@ -24,6 +24,11 @@ struct GraphKey {
     bool operator==(const GraphKey &o) const { return memcmp(this, &o, sizeof(*this)) == 0; }
 };
 
+// Sub-batches of the host entry point: the copies of sub-batch g + 1 run
+// while sub-batch g is matched.
+constexpr int kHostGroups = 4;
+constexpr int kCopyStreams = 1;  // copy streams per sub-batch (two measured slower on GB300: 1.24 against 1.10 ms per 147 MB step)
+
 struct ctm_ctx {
     int device = 0;
     int sm_count = 0;
@@ -55,6 +60,8 @@ struct ctm_ctx {
     int32_t *counts_host_pinned = nullptr;
     ctm_frame *frames_dev2 = nullptr;
     int32_t *counts_dev2 = nullptr;
+    cudaStream_t copy_stream[kCopyStreams] = {};  // host-to-device copies of the sub-batches
+    cudaEvent_t host_ev[kHostGroups * kCopyStreams + 1] = {};  // sub-batch g's copies on stream k; last: start
 };
 
 namespace {
@@ -106,6 +113,7 @@ MatchArgs make_args(const ctm_ctx *ctx, const ctm_frame *frames, const int32_t *
     a.big_work = ctx->big_work;
     a.census_mode = ctx->census_mode;
     a.match_mode = ctx->match_mode;
+    a.stats_accumulate = 0;
     return a;
 }
 
@@ -318,6 +326,10 @@ void ctm_destroy(ctm_ctx *ctx)
     if (ctx->img_dev) cudaFree(ctx->img_dev);
     if (ctx->frames_host_pinned) cudaFreeHost(ctx->frames_host_pinned);
     if (ctx->counts_host_pinned) cudaFreeHost(ctx->counts_host_pinned);
+    for (cudaStream_t cs : ctx->copy_stream)
+        if (cs) cudaStreamDestroy(cs);
+    for (cudaEvent_t ev : ctx->host_ev)
+        if (ev) cudaEventDestroy(ev);
     cudaGetLastError();
     delete ctx;
 }
@@ -487,14 +499,25 @@ int ctm_match_batch_host(ctm_ctx *ctx, const ctm_frame *frames_host, int n_frame
         const size_t o_depth = take(sizeof(float) * (size_t)ctx->caps.max_boxes);
         const size_t o_flags = take((size_t)ctx->caps.max_boxes);
         const size_t o_frames = take(sizeof(ctm_frame) * (size_t)ctx->caps.max_frames);
-        const size_t o_counts = take(sizeof(int32_t) * 4);
+        const size_t o_counts = take(sizeof(int32_t) * 4 * kHostGroups);
         void *mem = nullptr;
         if (cudaMalloc(&mem, off) != cudaSuccess) { cudaGetLastError(); return CTM_ENOMEM; }
-        if (cudaMallocHost(&ctx->frames_host_pinned, sizeof(ctm_frame) * ctx->caps.max_frames) != cudaSuccess ||
-            cudaMallocHost(&ctx->counts_host_pinned, sizeof(int32_t) * 4) != cudaSuccess) {
+        bool okh = cudaMallocHost(&ctx->frames_host_pinned, sizeof(ctm_frame) * ctx->caps.max_frames) == cudaSuccess &&
+                   cudaMallocHost(&ctx->counts_host_pinned, sizeof(int32_t) * 4 * kHostGroups) == cudaSuccess;
+        for (cudaStream_t &cs : ctx->copy_stream)
+            okh = okh && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
+        for (cudaEvent_t &ev : ctx->host_ev)
+            okh = okh && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+        if (!okh) {
             cudaFree(mem);
             if (ctx->frames_host_pinned) cudaFreeHost(ctx->frames_host_pinned);
+            if (ctx->counts_host_pinned) cudaFreeHost(ctx->counts_host_pinned);
+            for (cudaStream_t &cs : ctx->copy_stream)
+                if (cs) { cudaStreamDestroy(cs); cs = nullptr; }
+            for (cudaEvent_t &ev : ctx->host_ev)
+                if (ev) { cudaEventDestroy(ev); ev = nullptr; }
             ctx->frames_host_pinned = nullptr;
+            ctx->counts_host_pinned = nullptr;
             cudaGetLastError();
             return CTM_ENOMEM;
         }
@@ -507,18 +530,41 @@ int ctm_match_batch_host(ctm_ctx *ctx, const ctm_frame *frames_host, int n_frame
         ctx->frames_dev2 = reinterpret_cast<ctm_frame *>(b + o_frames);
         ctx->counts_dev2 = reinterpret_cast<int32_t *>(b + o_counts);
     }
+    // Sub-batches of consecutive frames when each frame's boxes follow the previous
+    // frame's (each sub-batch then owns one slice of the boxes and outputs); else
+    // one batch.  Sub-batch g + 1's copies, on the copy stream, overlap sub-batch
+    // g's kernels on `stream`; the kernels of all sub-batches run in order on
+    // `stream` over the one workspace, so the results equal one call's.
+    bool chained = frames_host[0].box_begin >= 0;
+    for (int i = 0; i < n_frames && chained; ++i) {
+        const ctm_frame &f = frames_host[i];
+        if (f.box_count < 0 || (i > 0 && f.box_begin != frames_host[i - 1].box_begin + frames_host[i - 1].box_count))
+            chained = false;
+    }
+    if (chained && frames_host[n_frames - 1].box_begin + frames_host[n_frames - 1].box_count > n_boxes) chained = false;
+    const int groups = chained ? std::min(kHostGroups, n_frames) : 1;
+
     const size_t plane = (size_t)ctx->img_pitch * ctx->caps.max_height;
-    cudaError_t e = cudaSuccess;
+    cudaStream_t cs = ctx->copy_stream[0];
+    cudaEvent_t ev_start = ctx->host_ev[kHostGroups * kCopyStreams];
+    cudaError_t e = cudaEventRecord(ev_start, s);  // work already queued on `stream`
+    for (int k = 0; k < kCopyStreams && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(ctx->copy_stream[k], ev_start, 0);
     // Images go to the staging planes in as few copies as possible: an image
     // packed at the staging pitch is one linear run, and runs that continue one
     // another in both host and device memory are merged (one large copy moves
-    // about 210 GB/s on GB300, 64 copies of 2.3 MB about 155 GB/s).
+    // about 210 GB/s on GB300, 64 copies of 2.3 MB about 155 GB/s); a run is
+    // split evenly over the copy streams, so that more than one copy engine moves it.
     const uint8_t *run_src = nullptr;
     uint8_t *run_dst = nullptr;
     size_t run_bytes = 0;
     auto flush = [&]() {
-        if (run_bytes > 0 && e == cudaSuccess)
-            e = cudaMemcpyAsync(run_dst, run_src, run_bytes, cudaMemcpyHostToDevice, s);
+        size_t done = 0;
+        for (int k = 0; k < kCopyStreams && run_bytes > 0 && e == cudaSuccess; ++k) {
+            const size_t part = (size_t)round_up((long long)(run_bytes / kCopyStreams), 4096);
+            const size_t n = k == kCopyStreams - 1 ? run_bytes - done : std::min(part, run_bytes - done);
+            if (n > 0) e = cudaMemcpyAsync(run_dst + done, run_src + done, n, cudaMemcpyHostToDevice, ctx->copy_stream[k]);
+            done += n;
+        }
         run_bytes = 0;
     };
     auto image = [&](uint8_t *dst, const uint8_t *src, const ctm_frame &f) {
@@ -535,36 +581,50 @@ int ctm_match_batch_host(ctm_ctx *ctx, const ctm_frame *frames_host, int n_frame
         } else {
             flush();
             if (e == cudaSuccess)
-                e = cudaMemcpy2DAsync(dst, ctx->img_pitch, src, f.pitch, f.width, f.height, cudaMemcpyHostToDevice, s);
+                e = cudaMemcpy2DAsync(dst, ctx->img_pitch, src, f.pitch, f.width, f.height, cudaMemcpyHostToDevice, cs);
         }
     };
-    for (int i = 0; i < n_frames && e == cudaSuccess; ++i) {
-        const ctm_frame &f = frames_host[i];
-        uint8_t *dl = ctx->img_dev + plane * (2 * (size_t)i);
-        uint8_t *dr = dl + plane;
-        image(dl, f.left, f);
-        image(dr, f.right, f);
-        ctm_frame g = f;
-        g.left = dl;
-        g.right = dr;
-        g.pitch = (int32_t)ctx->img_pitch;
-        ctx->frames_host_pinned[i] = g;
-    }
-    flush();
-    ctx->counts_host_pinned[0] = n_frames;
-    ctx->counts_host_pinned[1] = n_boxes;
     if (e == cudaSuccess && n_boxes > 0)
-        e = cudaMemcpyAsync(ctx->boxes_dev, boxes_host, sizeof(ctm_box) * n_boxes, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ctx->frames_dev2, ctx->frames_host_pinned, sizeof(ctm_frame) * n_frames,
-                            cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ctx->counts_dev2, ctx->counts_host_pinned, sizeof(int32_t) * 2,
-                            cudaMemcpyHostToDevice, s);
+        e = cudaMemcpyAsync(ctx->boxes_dev, boxes_host, sizeof(ctm_box) * n_boxes, cudaMemcpyHostToDevice, cs);
+    const int grid = ctx->sm_count * ctx->ctas_per_sm;
+    for (int g = 0; g < groups && e == cudaSuccess; ++g) {
+        const int f0 = (int)((long long)g * n_frames / groups), f1 = (int)((long long)(g + 1) * n_frames / groups);
+        const int box0 = groups > 1 ? frames_host[f0].box_begin : 0;
+        const int nb = groups > 1 ? frames_host[f1 - 1].box_begin + frames_host[f1 - 1].box_count - box0 : n_boxes;
+        for (int i = f0; i < f1 && e == cudaSuccess; ++i) {
+            const ctm_frame &f = frames_host[i];
+            uint8_t *dl = ctx->img_dev + plane * (2 * (size_t)i);
+            uint8_t *dr = dl + plane;
+            image(dl, f.left, f);
+            image(dr, f.right, f);
+            ctm_frame t = f;
+            t.left = dl;
+            t.right = dr;
+            t.pitch = (int32_t)ctx->img_pitch;
+            t.box_begin = f.box_begin - box0;
+            ctx->frames_host_pinned[i] = t;
+        }
+        flush();
+        int32_t *cnt = ctx->counts_host_pinned + 4 * g;
+        cnt[0] = f1 - f0;
+        cnt[1] = nb;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ctx->frames_dev2 + f0, ctx->frames_host_pinned + f0, sizeof(ctm_frame) * (f1 - f0),
+                                cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ctx->counts_dev2 + 4 * g, cnt, sizeof(int32_t) * 2, cudaMemcpyHostToDevice, cs);
+        for (int k = 0; k < kCopyStreams && e == cudaSuccess; ++k) {
+            cudaEvent_t ev = ctx->host_ev[g * kCopyStreams + k];
+            e = cudaEventRecord(ev, ctx->copy_stream[k]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev, 0);
+        }
+        if (e != cudaSuccess) break;
+        MatchArgs a = make_args(ctx, ctx->frames_dev2 + f0, ctx->counts_dev2 + 4 * g, ctx->boxes_dev + box0,
+                                ctx->disp_dev + box0, ctx->depth_dev + box0, ctx->flags_dev + box0, nullptr);
+        a.stats_accumulate = g > 0;  // ctm_get_stats then covers the whole call
+        if (enqueue_match(ctx, a, f1 - f0, grid, s, false, 0) != CTM_OK) e = cudaErrorLaunchFailure;
+    }
     if (e != cudaSuccess) { cudaGetLastError(); return CTM_ECUDA; }
-    st = ctm_match_batch(ctx, ctx->frames_dev2, ctx->counts_dev2, ctx->boxes_dev, ctx->disp_dev,
-                         ctx->depth_dev, ctx->flags_dev, nullptr, 1, stream);
-    if (st != CTM_OK) return st;
     if (n_boxes > 0) {
         e = cudaMemcpyAsync(disp_host, ctx->disp_dev, sizeof(float) * n_boxes, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess)

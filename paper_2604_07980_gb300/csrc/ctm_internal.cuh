@@ -128,6 +128,7 @@ struct MatchArgs {
     int match_mode;            // 0: fused single-kernel matcher, 1: two-pass pipelined matcher
     int census_mode;           // region-of-interest census variant (census.cu)
     int strip_rows;            // rows of the shared-memory strip (pts_side * ndy)
+    int stats_accumulate;      // 1: the aggregation adds the call's counters to the stats record
 };
 
 __host__ __device__ inline int ceil_div_nn(int a, int b) { return (a + b - 1) / b; }

@@ -10,8 +10,9 @@
 //      candidate; lanes own consecutive candidates (conflict-free strip reads),
 //      warps own point subsets, each thread keeps up to 8 candidate sums in
 //      registers, and warps combine them with shared-memory atomics;
-//   3. first argmin over (dy, d) by warp min-reductions of (cost << 16 | index)
-//      keys, then Eq. subpixel in fp32 with IEEE division;
+//   3. first argmin over (dy, d): after one barrier every warp reduces the whole
+//      cost row to the minimum (cost << 16 | index) key itself, so the result
+//      needs no broadcast; Eq. subpixel in fp32 with IEEE division;
 //   4. backward pass (Sec. 4.3.3): the right codes at the matched positions and
 //      the left strip [q.x + dmin, q.x + dmax] arrive in one round trip;
 //   5. consistency |d_b - d_f| <= fb_tol and the block record; boxes are
@@ -35,9 +36,6 @@ struct Shared {
     int X[kMaxPtsSide];
     int Y[kMaxPtsSide];
     int colstart[kMaxPtsSide + 1];
-    unsigned warp_min[NW];
-    int d_f, dy_f, s_m, s_0, s_p;
-    int d_b, dy_b;
     int next;               // queue index of the next block
     int next_b;             // its block
     int gpend;              // a geometry copy is in flight on mbar_g
@@ -150,41 +148,13 @@ __device__ __forceinline__ bool load_chunk(const MatchArgs &a, const BlockCtx &b
     return land_chunk<NT>(a, bc, sm, sh, phase, fwd, dy_f, g);
 }
 
-// Warp and CTA minimum of the keys (cost << 16 | c) over the candidates; the
-// result lands in sh.warp_min[0] and the costs stay in shared memory.
-template <int NT>
-__device__ __forceinline__ void argmin_pass(const MatchArgs &a, const BlockCtx &bc, const Smem &sm,
-                                            Shared<NT / 32> &sh, bool fwd)
-{
-    constexpr int NW = NT / 32;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    unsigned key = 0xffffffffu;
-    int32_t *dbgc = fwd ? a.dbg.cost_f : a.dbg.cost_b;
-    const int slots = a.p.grid_g * a.p.grid_g;
-    for (int c = tid; c < bc.nc; c += NT) {
-        const int s = sm.cost[c];
-        key = min(key, ((unsigned)s << 16) | (unsigned)c);
-        if (dbgc) dbgc[((long long)bc.box * slots + bc.slot) * a.nc_stride + c] = s;
-    }
-    key = __reduce_min_sync(0xffffffffu, key);
-    if (lane == 0) sh.warp_min[warp] = key;
-    __syncthreads();
-    if (tid == 0) {
-        unsigned m = sh.warp_min[0];
-#pragma unroll
-        for (int w = 1; w < NW; ++w) m = min(m, sh.warp_min[w]);
-        sh.warp_min[0] = m;
-    }
-    __syncthreads();
-}
-
 // The scans of one search pass after its first strip chunk has landed and the
 // point bases of the first chunk are set: every chunk (later ones loaded into
 // the strip after the previous chunk's scan), sums kept in registers.  Returns
 // false if a bounded wait expired.
 template <int NT>
 __device__ bool scan_chunks(const MatchArgs &a, const BlockCtx &bc, const Smem &sm, Shared<NT / 32> &sh,
-                            unsigned &phase, bool fwd, ChunkGeom g, int (&acc)[8])
+                            unsigned &phase, bool fwd, ChunkGeom g, int (&acc)[8], int d_f, int dy_f)
 {
     constexpr int NW = NT / 32;
     const int lane = threadIdx.x & 31;
@@ -192,7 +162,6 @@ __device__ bool scan_chunks(const MatchArgs &a, const BlockCtx &bc, const Smem &
     const bool fast = bc.ndy == 1 && (bc.nd & 31) == 0;
 #pragma unroll
     for (int t = 0; t < 8; ++t) acc[t] = 0;
-    const int d_f = sh.d_f, dy_f = sh.dy_f;
     const unsigned cs = sh.cstart;
     int j0 = 0;
     bool ok = true;
@@ -234,21 +203,32 @@ __device__ bool scan_chunks(const MatchArgs &a, const BlockCtx &bc, const Smem &
     return ok;
 }
 
-// The end of a pass: warps combine their sums in sm.cost (zeroed when the
-// block started) and the first argmin lands in sh.warp_min[0].
+// The end of a pass: warps add their sums into `cost` (zeroed when the pass
+// started); after one barrier every warp reduces the whole row to the first
+// argmin key (cost << 16 | c), so every thread holds it without a broadcast.
+// Warp 0 writes the debug costs.  False if a bounded wait expired anywhere.
 template <int NT>
-__device__ __forceinline__ void finish_pass(const MatchArgs &a, const BlockCtx &bc, const Smem &sm,
-                                            Shared<NT / 32> &sh, bool fwd, const int (&acc)[8])
+__device__ __forceinline__ bool combine_pass(const MatchArgs &a, const BlockCtx &bc, int *cost, bool fwd,
+                                             const int (&acc)[8], bool ok, unsigned &key)
 {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int T = (bc.nc + 31) >> 5;
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
         const int c = t * 32 + lane;
-        if (t < T && c < bc.nc) atomicAdd(&sm.cost[c], acc[t]);
+        if (t < T && c < bc.nc) atomicAdd(&cost[c], acc[t]);
     }
-    __syncthreads();
-    argmin_pass<NT>(a, bc, sm, sh, fwd);
+    if (!__syncthreads_and(ok)) return false;
+    int32_t *dbgc = warp == 0 ? (fwd ? a.dbg.cost_f : a.dbg.cost_b) : nullptr;
+    const int slots = a.p.grid_g * a.p.grid_g;
+    unsigned k = 0xffffffffu;
+    for (int c = lane; c < bc.nc; c += 32) {
+        const int s = cost[c];
+        k = min(k, ((unsigned)s << 16) | (unsigned)c);
+        if (dbgc) dbgc[((long long)bc.box * slots + bc.slot) * a.nc_stride + c] = s;
+    }
+    key = __reduce_min_sync(0xffffffffu, k);
+    return true;
 }
 
 // Queue entry i: large work from the front, small work from the back.
@@ -330,9 +310,11 @@ struct Prefetch {
 // queue index at the start and issues the next block's record copy once the
 // forward pass is done; when the backward scans are over, the CTA waits for
 // that record and begins the next block (its codes and first strip in flight)
-// before it combines its own backward sums and writes its record, so the next
-// block's first round trip overlaps this block's end.  Returns false if a
-// bounded wait expired.  evals: thread 0 adds this block's evaluation count.
+// before thread 0 writes this block's record, so the next block's first round
+// trip overlaps this block's end.  Forward and backward costs have their own
+// rows, so no barrier separates one pass's argmin from the next pass's
+// zeroing.  Returns false if a bounded wait expired.  evals: thread 0 adds this
+// block's evaluation count.
 template <int NT>
 __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<NT / 32> &sh,
                               unsigned &phase, int gbuf, Prefetch &pf, unsigned &gphase,
@@ -358,20 +340,19 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
     if (pf.on && tid == 0 && next_i < pf.nq) next_b = queue_block(a, next_i, pf.n_big);
     if (!__syncthreads_and(ok)) return false;
 
-    // 2-3. forward pass, argmin, parabola
+    // 2-3. forward pass, argmin (every thread), parabola inputs
     int acc[8];
-    ok = scan_chunks<NT>(a, bc, sm, sh, phase, true, g0, acc);
-    finish_pass<NT>(a, bc, sm, sh, true, acc);
-    if (!__syncthreads_and(ok)) return false;
+    ok = scan_chunks<NT>(a, bc, sm, sh, phase, true, g0, acc, 0, 0);
+    unsigned key;
+    if (!combine_pass<NT>(a, bc, sm.cost, true, acc, ok, key)) return false;
+    const int cf = (int)(key & 0xffffu);
+    const int ef = bc.ndy == 1 ? 0 : cf / bc.nd;
+    const int dif = cf - ef * bc.nd;
+    const int d_f = bc.dmin + dif, dy_f = a.p.dy_min + ef;
+    int s_m = 0, s_p = 0;
     if (tid == 0) {
-        const unsigned key = sh.warp_min[0];
-        const int c = (int)(key & 0xffffu);
-        const int e = c / bc.nd, di = c - e * bc.nd;
-        sh.d_f = bc.dmin + di;
-        sh.dy_f = a.p.dy_min + e;
-        sh.s_0 = (int)(key >> 16);
-        sh.s_m = di > 0 ? sm.cost[c - 1] : 0;
-        sh.s_p = di < bc.nd - 1 ? sm.cost[c + 1] : 0;
+        s_m = dif > 0 ? sm.cost[cf - 1] : 0;
+        s_p = dif < bc.nd - 1 ? sm.cost[cf + 1] : 0;
         if (pf.on) {
             sh.next = next_i;
             sh.next_b = next_b;
@@ -383,9 +364,9 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
             }
         }
     }
-    __syncthreads();
+
     // 4. backward pass: right codes at the matched positions + first left strip
-    const int d_f = sh.d_f, dy_f = sh.dy_f;
+    //    (every warp's forward scans ended at combine_pass's barrier)
     for (int t = tid; t < total; t += NT) {
         const int mj = sm.pmj[t];
         const int qx = sh.X[mj & 255] - d_f, qy = sh.Y[mj >> 8] + dy_f;
@@ -394,14 +375,15 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
         else
             sm.pcode[t] = 0ull;
     }
-    for (int c = tid; c < bc.nc; c += NT) sm.cost[c] = 0;
+    for (int c = tid; c < bc.nc; c += NT) sm.cost_b[c] = 0;
     const ChunkGeom gb = chunk_geom(x0 - d_f + bc.dmin, SW0);
     ok = load_chunk<NT>(a, bc, sm, sh, phase, false, dy_f, gb);
     set_bases<NT>(sm, sh.X, 0, sh.colstart[j1_first], bc.ndy, gb.SWa, x0, gb.delta);
     cp_async_wait_all();
     if (!__syncthreads_and(ok)) return false;
-    ok = scan_chunks<NT>(a, bc, sm, sh, phase, false, gb, acc);
-    if (!__syncthreads_and(ok)) return false;
+    ok = scan_chunks<NT>(a, bc, sm, sh, phase, false, gb, acc, d_f, dy_f);
+    unsigned keyb;
+    if (!combine_pass<NT>(a, bc, sm.cost_b, false, acc, ok, keyb)) return false;
 
     // the next block starts now: its record (wait) and its first loads (issued)
     const bool has_next = pf.on && sh.gpend;
@@ -413,23 +395,21 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
         begin_block<NT>(a, sh.next_b, sm, sh, pf.buf);
     }
 
-    finish_pass<NT>(a, bc, sm, sh, false, acc);
     if (tid == 0) {
-        const unsigned key = sh.warp_min[0];
-        const int c = (int)(key & 0xffffu);
-        const int e = c / bc.nd;
+        const int cb = (int)(keyb & 0xffffu);
+        const int eb = bc.ndy == 1 ? 0 : cb / bc.nd;
         // 5. block record; boxes are aggregated by aggregate_kernel
         ctm_block rec;
         rec.n_pts = bc.nx * bc.ny;
         rec.n_valid = total;
         rec.flags = CTM_BLK_PRESENT;
-        rec.d_f = sh.d_f;
-        rec.dy_f = sh.dy_f;
-        rec.d_b = bc.dmin + (c - e * bc.nd);
-        rec.dy_b = a.p.dy_min + e;
-        rec.s_m = sh.s_m;
-        rec.s_0 = sh.s_0;
-        rec.s_p = sh.s_p;
+        rec.d_f = d_f;
+        rec.dy_f = dy_f;
+        rec.d_b = bc.dmin + (cb - eb * bc.nd);
+        rec.dy_b = a.p.dy_min + eb;
+        rec.s_m = s_m;
+        rec.s_0 = (int)(key >> 16);
+        rec.s_p = s_p;
         if (rec.d_f == bc.dmin || rec.d_f == bc.dmax) {
             rec.d_sub = (float)rec.d_f;
             rec.flags |= CTM_BLK_SUBPIX_CLAMPED;
@@ -445,7 +425,6 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
         write_block(a, bc.box, bc.slot, rec);
         evals += 2ull * (unsigned long long)total * (unsigned long long)bc.nc;
     }
-    __syncthreads();
     return true;
 }
 
@@ -458,6 +437,8 @@ __device__ __forceinline__ Smem carve(const MatchArgs &a, unsigned char *raw)
     sm.pcode = reinterpret_cast<uint64_t *>(raw + off);
     off += sizeof(uint64_t) * kMaxPts;
     sm.cost = reinterpret_cast<int *>(raw + off);
+    off += sizeof(int) * kMaxCand;
+    sm.cost_b = reinterpret_cast<int *>(raw + off);
     off += sizeof(int) * kMaxCand;
     sm.pmj = reinterpret_cast<int *>(raw + off);
     off += sizeof(int) * kMaxPts;
@@ -567,7 +548,7 @@ __global__ void __launch_bounds__(NT) match_box_kernel(MatchArgs a, int box)
 size_t match_smem_bytes(const MatchArgs &a)
 {
     return sizeof(uint64_t) * (size_t)a.strip_rows * a.strip_cols + sizeof(uint64_t) * kMaxPts +
-           sizeof(int) * kMaxCand + 2 * sizeof(int) * kMaxPts;
+           2 * sizeof(int) * kMaxCand + 2 * sizeof(int) * kMaxPts;
 }
 
 // The dynamic shared-memory limit is a per-kernel, process-wide setting: it is

@@ -94,6 +94,7 @@ struct Smem {
     uint64_t *strip;   // strip_rows * strip_cols
     uint64_t *pcode;   // kMaxPts: compacted codes (left, then right queries)
     int *cost;         // kMaxCand
+    int *cost_b;       // kMaxCand: backward costs (fused matcher; forward in cost)
     int *pmj;          // kMaxPts: (m << 8) | j
     int *pbase;        // kMaxPts: byte offset of the point's strip row + column in the chunk
 };

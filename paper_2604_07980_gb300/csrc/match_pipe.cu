@@ -55,6 +55,7 @@ __device__ __forceinline__ void carve_pipe(const MatchArgs &a, unsigned char *ra
     const size_t strip = sizeof(uint64_t) * (size_t)a.strip_rows * a.strip_cols;
     int *cost = nullptr;
     for (int i = 0; i < 2; ++i) {
+        sm[i].cost_b = nullptr;  // one cost row per pass kernel
         sm[i].strip = reinterpret_cast<uint64_t *>(raw + off);
         off += strip;
     }

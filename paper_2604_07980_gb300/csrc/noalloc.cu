@@ -183,6 +183,7 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
     for (int q = 0; q < 4; ++q) ws.bm_row_words[q] = words_q[q];
     a.caps = caps;
     a.p = *p;
+    a.stats_accumulate = 0;
     a.frames = ws.frames;
     a.counts_in = ws.counts_in;
     a.boxes = boxes_dev;

@@ -390,7 +390,22 @@ __global__ void __launch_bounds__(256) aggregate_kernel(MatchArgs a)
     __shared__ float scratch[8][2 * kMaxSlots];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        *a.ws.stats = *a.ws.counts;
+        const Counts c = *a.ws.counts;
+        if (a.stats_accumulate) {  // a later sub-batch of one call
+            Counts t = *a.ws.stats;
+            t.n_frames += c.n_frames;
+            t.n_boxes += c.n_boxes;
+            t.n_blocks += c.n_blocks;
+            t.queue_head += c.queue_head;
+            t.error |= c.error;
+            t.evals += c.evals;
+            t.n_big += c.n_big;
+            t.n_small += c.n_small;
+            t.n_tiles += c.n_tiles;
+            *a.ws.stats = t;
+        } else {
+            *a.ws.stats = c;
+        }
         *a.ws.counts = Counts{};
     }
     const int box = blockIdx.x * 8 + warp;

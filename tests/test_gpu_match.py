@@ -214,6 +214,57 @@ def test_batch_host_merged_copies(torch_cuda):
     swapped[:, 0], swapped[:, 1] = packed[:, 1], packed[:, 0]
     got = ctx.match_batch_host([(swapped[i, 1], swapped[i, 0]) for i in range(4)], w.boxes, fpx, bm)
     compare_box_outputs(got, ref, "host, separate copies")
+    got = ctx.match_batch_host_packed(packed, w.boxes, fpx, bm)
+    compare_box_outputs(got, ref, "host, packed array")
+    ctx.close()
+
+
+def test_batch_host_sub_batches_equal_device_batch(torch_cuda):
+    """The host entry point splits chained frames into sub-batches whose copies
+    overlap the previous sub-batch's kernels: outputs and summed counters equal the
+    one-launch device path bit for bit.  Boxes listed out of frame order are not
+    chained and run as one batch, with the same outputs."""
+    import ctypes
+    from paper_2604_07980_gb300 import binding as B
+    w = wl.batch32x1200(n_frames=7, W=800, H=400, mean_boxes=10, side_range=(12, 200))
+    ctx = B.Context(w.params, 7, 800, 400, w.n_boxes)
+    batch = B.DeviceBatch(B.frames_to_device(w.frames), w.boxes, [(f.f_px, f.baseline_m) for f in w.frames])
+    dev = ctx.match_batch(batch, use_graph=True)
+    torch_cuda.cuda.synchronize()
+    dev = {k: v.cpu().numpy() for k, v in dev.items()}
+    st_dev = ctx.stats()
+    fpx = [f.f_px for f in w.frames]
+    bm = [f.baseline_m for f in w.frames]
+    host = ctx.match_batch_host([(f.left, f.right) for f in w.frames], w.boxes, fpx, bm)
+    st_host = ctx.stats()
+    for k in ("disp", "depth", "flags"):
+        assert np.array_equal(host[k], dev[k], equal_nan=True), k
+    for k in ("cost_evals", "n_blocks", "n_boxes", "census_tiles", "error"):
+        assert st_host[k] == st_dev[k], (k, st_host[k], st_dev[k])
+    ref = orc.match_batch([(f.left, f.right, f.f_px, f.baseline_m) for f in w.frames], w.boxes,
+                          orc.Params(**w.params))
+    compare_box_outputs(host, ref, "host sub-batches")
+    # frame 0's boxes listed after all others: not chained, one batch
+    counts = np.bincount(w.boxes[:, 4], minlength=7)
+    order = np.concatenate([np.nonzero(w.boxes[:, 4] != 0)[0], np.nonzero(w.boxes[:, 4] == 0)[0]])
+    bx = np.ascontiguousarray(w.boxes[order], dtype=np.int32)
+    begins = np.zeros(7, np.int64)
+    begins[1:] = np.concatenate([[0], np.cumsum(counts[1:])[:-1]])
+    begins[0] = counts[1:].sum()
+    arr = (B.ctm_frame * 7)()
+    for i, f in enumerate(w.frames):
+        arr[i] = B.ctm_frame(f.left.ctypes.data, f.right.ctypes.data, 800, 400, f.left.strides[0],
+                             int(begins[i]), int(counts[i]), float(f.f_px), float(f.baseline_m))
+    n = len(bx)
+    disp = np.empty(n, np.float32)
+    depth = np.empty(n, np.float32)
+    flags = np.empty(n, np.uint8)
+    assert B.lib().ctm_match_batch_host(ctx._h, arr, 7, bx.ctypes.data, n, disp.ctypes.data,
+                                        depth.ctypes.data, flags.ctypes.data, None) == B.CTM_OK
+    assert np.array_equal(flags, dev["flags"][order])
+    assert np.array_equal(disp, dev["disp"][order], equal_nan=True)
+    assert np.array_equal(depth, dev["depth"][order], equal_nan=True)
+    assert ctx.stats()["cost_evals"] == st_dev["cost_evals"]
     ctx.close()
 
 
