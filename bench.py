@@ -156,23 +156,30 @@ def cpu_oracle(w, budget_s: float = 12.0, threads: int = 1) -> dict:
         nc = np.where(far, ncf, ncc)[:, None]
         return int(np.sum(2 * blk["n_valid"] * nc * ran)), int(sel.sum())
 
+    def timed(fi):
+        t = time.perf_counter()
+        e, nb = one(fi)
+        return e, nb, time.perf_counter() - t
+
     t0 = time.perf_counter()
     evals = frames = boxes = 0
+    lat = []
     with cf.ThreadPoolExecutor(max_workers=threads) as ex:
         pending = set()
         nxt = 0
         while nxt < len(w.frames) or pending:
             while nxt < len(w.frames) and len(pending) < threads and time.perf_counter() - t0 <= budget_s:
-                pending.add(ex.submit(one, nxt))
+                pending.add(ex.submit(timed, nxt))
                 nxt += 1
             if not pending:
                 break
             done, pending = cf.wait(pending, return_when=cf.FIRST_COMPLETED)
             for f in done:
-                e, nb = f.result()
+                e, nb, t = f.result()
                 evals += e
                 boxes += nb
                 frames += 1
+                lat.append(t)
             if time.perf_counter() - t0 > budget_s:
                 nxt = len(w.frames)
     dt = time.perf_counter() - t0
@@ -180,6 +187,9 @@ def cpu_oracle(w, budget_s: float = 12.0, threads: int = 1) -> dict:
     return {"value": evals / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{frames} of {len(w.frames)} frames ({boxes} boxes, {evals} evals), "
                       f"{dt:.1f} s, {how}; host {os.cpu_count()} cores, {_cpu_model()}",
+            "boxes_per_s": boxes / dt,
+            "frame_latency_ms": {"p50": _pct(lat, 50) * 1e3 if lat else None,
+                                 "p99": _pct(lat, 99) * 1e3 if lat else None},
             "seconds": dt, "evals": evals}
 
 
@@ -391,6 +401,7 @@ def main():
         torch.cuda.synchronize()
         pms = p0.elapsed_time(p1) / k_plain
         plain = {"value": evals_per_step / (pms * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": pms,
+                 "boxes_per_s": w.n_boxes / (pms * 1e-3),
                  "launches_per_step": len(w.frames) * 3 + w.n_boxes}
         ctx1.close()
 
