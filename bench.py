@@ -42,10 +42,10 @@ POPC_PER_EVAL = 2          # one u64 code pair = two 32-bit popcounts
 # DRAM bytes (read + write) of one match_persistent_kernel launch on this workload, from the
 # ncu capture summarised in profiles/match_persistent_kernel_batch32x1200.md; None once the
 # kernel changes after that capture.
-MATCH_DRAM_BYTES = (102.538 + 3.350) * 1e6
+MATCH_DRAM_BYTES = (102.534 + 3.243) * 1e6
 # DRAM bytes of one census_roi4_kernel launch on this workload (same capture, summarised in
 # profiles/census_roi4_kernel_batch32x1200.md) plus its tile_list_kernel launch
-CENSUS_DRAM_BYTES = (61.084 + 68.565 + 0.775) * 1e6
+CENSUS_DRAM_BYTES = (61.096 + 69.065 + 0.775) * 1e6
 CENSUS_TILE_PX = 32        # pixels per listed census tile
 CENSUS_CMPS = 9 * 7 - 1    # compares per 9x7 code (the centre bit is always 0)
 # kernels of one step of the batched path (ctm_box_points, timed apart, is not in it): plan,

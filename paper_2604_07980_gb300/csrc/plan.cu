@@ -63,6 +63,7 @@ __global__ void stage_frame_kernel(ctm_frame *frames, int *counts_in, ctm_frame 
 
 constexpr int kStageBoxes = 1024;  // boxes of one frame staged in shared memory
 constexpr int kPlanSlices = 4;     // CTAs per frame, each planning a slice of its boxes
+constexpr int kKeyCache = 8;       // occluder keys per lane held in registers
 
 // One CTA per frame: clip, classify, map to the matching grid and select the
 // occluders of every box of the frame (the frame's clipped boxes are staged in
@@ -145,19 +146,34 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(MatchArgs a)
         // y, ties to the lower index.  Key (frontal, bottom y, -index) is unique
         // per box, so round t takes the largest key below round t-1's: each lane
         // scans its share of the frame's boxes.
+        // key of box j as an occluder of box i (0: it is not one)
+        auto occ_key = [&](int j) -> unsigned long long {
+            if (j >= end || j == i) return 0ull;
+            const int4 q = staged ? sbox[j - begin] : clip_box(a.boxes[j], fr.width, fr.height);
+            if (!(q.w > r.w) || !overlaps(r, q)) return 0ull;
+            const unsigned front = frontal(q, fr.width, fr.height, p.frontal_crop) ? 0x80000000u : 0u;
+            return ((unsigned long long)(front | (unsigned)q.w) << 32) | (unsigned)(0x7fffffff - (j - begin));
+        };
         int nocc = 0;
         if (!empty && K > 0) {
+            // frames of up to 32 * kKeyCache boxes keep every lane's keys in registers,
+            // so a round is a register scan and two warp reductions
+            const bool cached = nloc <= 32 * kKeyCache;
+            unsigned long long kc[kKeyCache];
+#pragma unroll
+            for (int u = 0; u < kKeyCache; ++u) kc[u] = cached ? occ_key(begin + lane + 32 * u) : 0ull;
             unsigned long long prev = ~0ull;
             for (; nocc < K; ++nocc) {
                 unsigned long long best = 0ull;
-                for (int j = begin + lane; j < end; j += 32) {
-                    if (j == i) continue;
-                    const int4 q = staged ? sbox[j - begin] : clip_box(a.boxes[j], fr.width, fr.height);
-                    if (!(q.w > r.w) || !overlaps(r, q)) continue;
-                    const unsigned front = frontal(q, fr.width, fr.height, p.frontal_crop) ? 0x80000000u : 0u;
-                    const unsigned long long key =
-                        ((unsigned long long)(front | (unsigned)q.w) << 32) | (unsigned)(0x7fffffff - (j - begin));
-                    if (key < prev && key > best) best = key;
+                if (cached) {
+#pragma unroll
+                    for (int u = 0; u < kKeyCache; ++u)
+                        if (kc[u] < prev && kc[u] > best) best = kc[u];
+                } else {
+                    for (int j = begin + lane; j < end; j += 32) {
+                        const unsigned long long key = occ_key(j);
+                        if (key < prev && key > best) best = key;
+                    }
                 }
                 // warp maximum of the 64-bit keys (two 32-bit reductions)
                 const unsigned hi = __reduce_max_sync(0xffffffffu, (unsigned)(best >> 32));
@@ -266,12 +282,13 @@ __global__ void __launch_bounds__(256) sample_kernel(MatchArgs a)
     // Each occluder covers a column range x a row range of the point grid: lane q
     // forms the row mask of occluder q, then every column lane removes the rows
     // of the occluders whose x range holds it.
-    unsigned rowok = 0u, occrows = 0u;
-    for (int m = 0; m < ny; ++m) {
-        const int y = __shfl_sync(full, Yl, m);
-        if (y - syw >= 0 && y + syw < P.Hs) rowok |= 1u << m;
-        const int fy = P.k * y;
-        if (lane < P.nocc && fy >= occ.y && fy < occ.w) occrows |= 1u << m;
+    const unsigned rowok = __ballot_sync(full, lane < ny && Yl - syw >= 0 && Yl + syw < P.Hs);
+    unsigned occrows = 0u;
+    if (P.nocc > 0) {
+        for (int m = 0; m < ny; ++m) {
+            const int fy = P.k * __shfl_sync(full, Yl, m);
+            if (lane < P.nocc && fy >= occ.y && fy < occ.w) occrows |= 1u << m;
+        }
     }
     unsigned colmask = col_ok ? rowok : 0u;
     const int fx = P.k * Xl;
