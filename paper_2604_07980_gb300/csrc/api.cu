@@ -587,8 +587,16 @@ int ctm_match_batch_host(ctm_ctx *ctx, const ctm_frame *frames_host, int n_frame
     if (e == cudaSuccess && n_boxes > 0)
         e = cudaMemcpyAsync(ctx->boxes_dev, boxes_host, sizeof(ctm_box) * n_boxes, cudaMemcpyHostToDevice, cs);
     const int grid = ctx->sm_count * ctx->ctas_per_sm;
+    // Shrinking sub-batches (12, 10, 6, 4 of 32 frames): each sub-batch's kernels stay
+    // shorter than the next sub-batch's copy, and the last one, which nothing
+    // hides, is the smallest.  Below 8 frames, equal parts.
+    auto bound = [&](int g) -> int {
+        static const int k64ths[kHostGroups + 1] = {0, 24, 44, 56, 64};  // sub-batch bounds in 64ths
+        if (groups < kHostGroups || n_frames < 8) return (int)((long long)g * n_frames / groups);
+        return (int)(((long long)k64ths[g] * n_frames + 32) / 64);
+    };
     for (int g = 0; g < groups && e == cudaSuccess; ++g) {
-        const int f0 = (int)((long long)g * n_frames / groups), f1 = (int)((long long)(g + 1) * n_frames / groups);
+        const int f0 = bound(g), f1 = bound(g + 1);
         const int box0 = groups > 1 ? frames_host[f0].box_begin : 0;
         const int nb = groups > 1 ? frames_host[f1 - 1].box_begin + frames_host[f1 - 1].box_count - box0 : n_boxes;
         for (int i = f0; i < f1 && e == cudaSuccess; ++i) {
