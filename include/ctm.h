@@ -156,7 +156,7 @@ typedef struct {
     int32_t n_boxes;       /* boxes planned                                   */
     int32_t error;         /* nonzero: a bounded device wait expired and some
                               outputs of the call were not written            */
-    int32_t census_tiles;  /* 64-pixel census row tiles computed (region of
+    int32_t census_tiles;  /* 32-pixel census row tiles computed (region of
                               interest of the batched and single-frame calls) */
 } ctm_stats;
 

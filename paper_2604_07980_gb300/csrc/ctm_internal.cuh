@@ -96,7 +96,7 @@ struct Workspace {
     Counts *stats;             // the last finished call's counters
     ctm_frame *frames;         // staging for single-frame calls [max_frames]
     int *counts_in;            // staging {n_frames, n_boxes}
-    // census demand bitmap: one bit per 64-pixel tile of a plane row, per frame
+    // census demand bitmap: one bit per kCensusTilePx-pixel tile of a plane row, per frame
     // planes in the order L1, R1, Lk, Rk; words = 32 tiles
     uint32_t *bitmap;
     unsigned long long *tiles;  // [max_frames * bm_frame_words * 32] marked tiles, packed (census.cu)
