@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-inflight2", dest="inflight2", action="store_false",
+                    help="skip timing two batches in flight (two contexts, two streams)")
     ap.add_argument("--frames", type=int, default=32)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -378,6 +380,37 @@ def main():
     census_ms = kernels_ms["census"]
     match_ms = kernels_ms["match"]
 
+    # ---- two batches in flight: a second context on a second stream, replays alternating,
+    # so one batch's latency-bound planning kernels can share SMs with the other's census
+    # or matching (reported beside `value`, which keeps one batch at a time)
+    inflight = None
+    if args.inflight2:
+        ctx2 = B.Context(w.params, len(w.frames), 1920, 1200, w.n_boxes)
+        ctx2.set_tuning(**tuning)
+        batch2 = B.DeviceBatch(frames_dev, w.boxes, calib)
+        s2 = torch.cuda.Stream()
+        for _ in range(3):
+            ctx2.match_batch(batch2, use_graph=True, stream=s2)
+        torch.cuda.synchronize()
+        pairs = ((ctx, batch, stream), (ctx2, batch2, s2))
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        done2 = torch.cuda.Event()
+        f0.record(stream)
+        s2.wait_event(f0)
+        for i in range(args.steps):
+            c, bt_, st_ = pairs[i & 1]
+            c.match_batch(bt_, use_graph=True, stream=st_)
+        done2.record(s2)
+        stream.wait_event(done2)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ims = f0.elapsed_time(f1)
+        inflight = {"value": evals_per_step * args.steps / (ims * 1e-3) / 1e9, "unit": UNIT,
+                    "ms_per_step": ims / args.steps, "batches_in_flight": 2,
+                    "stats_equal": ctx2.stats()["cost_evals"] == evals_per_step}
+        ctx2.close()
+
     # ---- plain one-launch-per-box path, frame by frame
     plain = None
     if not args.no_plain:
@@ -451,6 +484,24 @@ def main():
     pts_ms = q0.elapsed_time(q1) / args.steps
     box_points = {"ms": pts_ms, "boxes_per_s": w.n_boxes / (pts_ms * 1e-3),
                   "valid_boxes": int(torch.isfinite(pts[:, 2]).sum().item())}
+
+    # ---- full-image census (ctm_census_build, Sec. 4.3.1) of one 1920x1200 image at full and
+    # half resolution: HBM fraction of its algorithmic bytes (8 B code + 1 B pixel per code)
+    census_full = {}
+    img0 = frames_dev[0][0]
+    for k in (1, 2):
+        for _ in range(3):
+            B.census_build(img0, factor=k)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(args.steps):
+            B.census_build(img0, factor=k)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        cms = c0.elapsed_time(c1) / args.steps
+        ncodes = (-(-1920 // k)) * (-(-1200 // k))
+        census_full[f"k{k}"] = {"ms": cms, "codes": ncodes, "GB_s": 9 * ncodes / (cms * 1e-3) / 1e9}
 
     # ---- roofline of the matching kernel (integer popcount pipe)
     sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
@@ -532,6 +583,7 @@ def main():
             "boxes_per_s": w.n_boxes * world / (ms_per_step * 1e-3),
             "phases_ms": {"plan_and_mark": plan_ms, "census_roi": census_ms, "match": match_ms},
             "kernels_ms": kernels_ms,
+            "two_batches_in_flight": inflight,
             "plain_per_box": plain,
             "box_points": box_points,
             "serving": serving,
@@ -547,6 +599,9 @@ def main():
                                        f"{POPC_PER_EVAL} per eval x {SM_MAX_MHZ:g} MHz",
                          "at_other_clocks": peak_at},
             "census_roofline": census_roof,
+            "census_full_image": {**census_full, "hbm_peak_GB_s": hbm_peak,
+                                  "note": "ctm_census_build on one 1920x1200 image (9x7, sentinel), "
+                                          "not on the batched path; 9 B per code"},
             "cpu_baseline": cpu,
             "gpu_launches": KERNELS_PER_STEP * args.steps,
             "clocks": clk,
