@@ -46,6 +46,8 @@ typedef struct CUstream_st *ctm_stream;
 #define CTM_ENODEV (-4)   /* no usable CUDA device */
 #define CTM_ETOOBIG (-5)  /* beyond a fixed limit: ctm_match_boxes_noalloc's maxima, a server's frame size or arena */
 #define CTM_EAGAIN (-6)   /* a server's admission queue is full; nothing was queued */
+#define CTM_ETIMEOUT (-7) /* a bounded device-side wait expired: the call's outputs are incomplete
+                             (returned by synchronous calls; asynchronous ones set ctm_stats.error) */
 
 /* Per-box flags (uint8), written by the match calls. */
 #define CTM_BOX_VALID 0x01           /* disparity > 0 found; disp/depth finite         */
@@ -241,7 +243,8 @@ int ctm_match_batch_profiled(ctm_ctx *ctx, const ctm_frame *frames_dev, const in
  * sums the sub-batches.  Images packed at the staging pitch (pitch == width ==
  * max_width rounded up to 128) and, for runs of more than one, full height
  * (max_height) and laid out back to back in host memory as L0 R0 L1 R1 ... go
- * in one copy per sub-batch.  Errors as above. */
+ * in one copy per sub-batch.  Errors as above, and CTM_ETIMEOUT when a bounded
+ * device wait of the call expired (outputs incomplete; the context stays usable). */
 int ctm_match_batch_host(ctm_ctx *ctx, const ctm_frame *frames_host, int n_frames,
                          const ctm_box *boxes_host, int n_boxes, float *disp_host,
                          float *depth_host, uint8_t *flags_host, ctm_stream stream);
@@ -346,6 +349,16 @@ int ctm_autotune(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *count
  * mask, 3: 32-bit add, 4: 32-bit multiply-add -- and returns the operations
  * per SM clock per SM.  Synchronizes the device.  Errors: CTM_EINVAL, CTM_ECUDA. */
 int ctm_probe_int_rate(int kind, int iters, double *ops_per_clk_per_sm);
+
+/* Bounded-wait probe (no counterpart in the paper): one CTA waits, with the
+ * matching kernels' own bounded-wait routine, on an mbarrier phase that nothing
+ * completes; the wait gives up after its time limit (about 1 s, then the same
+ * again for copies in flight, of which there are none), records the expiry in a
+ * device flag and the kernel returns.  *expired gets the flag (1), *waited_ms
+ * the kernel's duration.  Shows on a GPU that an expired wait ends the kernel
+ * with an error status and leaves the context usable.  Synchronous.
+ * Errors: CTM_EINVAL (null pointer), CTM_ECUDA. */
+int ctm_probe_bounded_wait(int *expired, float *waited_ms);
 
 #ifdef __cplusplus
 }

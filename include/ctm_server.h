@@ -75,7 +75,9 @@ typedef struct {
 /* Completion record.  Times are CLOCK_MONOTONIC nanoseconds (ctm_server_now_ns). */
 typedef struct {
     uint64_t tag;
-    int32_t status;        /* CTM_OK, or CTM_ECUDA if the frame's batch failed */
+    int32_t status;        /* CTM_OK, CTM_ECUDA if the frame's batch failed, or
+                              CTM_ETIMEOUT if a bounded device wait of its batch
+                              expired (outputs incomplete) */
     int32_t n_boxes;
     int64_t t_submit_ns;   /* ctm_server_submit() accepted it */
     int64_t t_admit_ns;    /* arena space granted, image upload issued */

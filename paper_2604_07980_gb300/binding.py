@@ -16,7 +16,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libctm.so")
 
-CTM_OK, CTM_EINVAL, CTM_ENOMEM, CTM_ECUDA, CTM_ENODEV, CTM_ETOOBIG, CTM_EAGAIN = 0, -1, -2, -3, -4, -5, -6
+CTM_OK, CTM_EINVAL, CTM_ENOMEM, CTM_ECUDA, CTM_ENODEV, CTM_ETOOBIG, CTM_EAGAIN, CTM_ETIMEOUT = \
+    0, -1, -2, -3, -4, -5, -6, -7
 
 BOX_VALID, BOX_FB_REJECT, BOX_FEW_POINTS, BOX_NO_SEGMENT = 0x01, 0x02, 0x04, 0x08
 BOX_NONPOS_DISP, BOX_EMPTY, BOX_SUBPIX_CLAMPED, BOX_FAR = 0x10, 0x20, 0x40, 0x80
@@ -26,7 +27,8 @@ BLK_VALID, BLK_FB_REJECT, BLK_FEW_POINTS, BLK_SUBPIX_CLAMPED, BLK_PRESENT = 1, 2
 EXPORTS = ("ctm_status_str", "ctm_default_params", "ctm_create", "ctm_destroy",
            "ctm_census_build", "ctm_match_boxes", "ctm_match_boxes_plain", "ctm_match_batch",
            "ctm_match_batch_profiled", "ctm_match_batch_host", "ctm_match_boxes_noalloc",
-           "ctm_get_stats", "ctm_probe_int_rate", "ctm_get_tuning", "ctm_set_tuning", "ctm_autotune",
+           "ctm_get_stats", "ctm_probe_int_rate", "ctm_probe_bounded_wait", "ctm_get_tuning",
+           "ctm_set_tuning", "ctm_autotune",
            "ctm_box_points", "ctm_auto_rect", "ctm_rect_filter",
            "ctm_server_default_config", "ctm_server_create", "ctm_server_submit", "ctm_server_poll",
            "ctm_server_outstanding", "ctm_server_get_stats", "ctm_server_destroy", "ctm_server_now_ns")
@@ -164,6 +166,8 @@ def lib():
     L.ctm_get_stats.restype = i32
     L.ctm_probe_int_rate.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double)]
     L.ctm_probe_int_rate.restype = i32
+    L.ctm_probe_bounded_wait.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
+    L.ctm_probe_bounded_wait.restype = i32
     L.ctm_auto_rect.argtypes = [ctypes.POINTER(ctm_params), vp, vp] + [i32] * 13 + [vp, vp, vp, vp]
     L.ctm_auto_rect.restype = i32
     L.ctm_rect_filter.argtypes = [vp, i32, i32, i32]
@@ -630,6 +634,15 @@ def frames_to_device(frames, device="cuda"):
     torch = _torch()
     return [(torch.from_numpy(np.ascontiguousarray(f.left)).to(device),
              torch.from_numpy(np.ascontiguousarray(f.right)).to(device)) for f in frames]
+
+
+def probe_bounded_wait() -> tuple[int, float]:
+    """Run the bounded-wait probe: (expired flag, kernel milliseconds)."""
+    _torch()
+    flag = ctypes.c_int(0)
+    ms = ctypes.c_float(0.0)
+    _check(lib().ctm_probe_bounded_wait(ctypes.byref(flag), ctypes.byref(ms)), "ctm_probe_bounded_wait")
+    return int(flag.value), float(ms.value)
 
 
 def probe_int_rate(kind: int, iters: int = 4096) -> float:

@@ -151,6 +151,7 @@ int set_device(const ctm_ctx *ctx)
 }  // namespace
 
 size_t ctm::context_device_bytes(const ctm_ctx *ctx) { return ctx ? ctx->dev_bytes : 0; }
+const int32_t *ctm::context_error_flag(const ctm_ctx *ctx) { return &ctx->ws.stats->error; }
 
 extern "C" {
 
@@ -164,6 +165,7 @@ const char *ctm_status_str(int status)
     case CTM_ENODEV: return "no usable CUDA device";
     case CTM_ETOOBIG: return "request exceeds a fixed limit (no-allocation maxima, server frame size or arena)";
     case CTM_EAGAIN: return "admission queue full, try again";
+    case CTM_ETIMEOUT: return "a bounded device wait expired (outputs incomplete)";
     default: return "unknown status";
     }
 }
@@ -640,9 +642,12 @@ int ctm_match_batch_host(ctm_ctx *ctx, const ctm_frame *frames_host, int n_frame
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(flags_host, ctx->flags_dev, (size_t)n_boxes, cudaMemcpyDeviceToHost, s);
     }
+    int32_t *err_h = ctx->counts_host_pinned + 4 * kHostGroups - 1;  // a slot no sub-batch uses
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(err_h, &ctx->ws.stats->error, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { cudaGetLastError(); return CTM_ECUDA; }
-    return CTM_OK;
+    return *err_h ? CTM_ETIMEOUT : CTM_OK;
 }
 
 int ctm_get_tuning(const ctm_ctx *ctx, ctm_tuning *out)
@@ -815,6 +820,12 @@ int ctm_probe_int_rate(int kind, int iters, double *ops_per_clk_per_sm)
 {
     if (kind < 0 || kind > 4 || iters < 1 || !ops_per_clk_per_sm) return CTM_EINVAL;
     return run_int_probe(kind, iters, ops_per_clk_per_sm) == cudaSuccess ? CTM_OK : CTM_ECUDA;
+}
+
+int ctm_probe_bounded_wait(int *expired, float *waited_ms)
+{
+    if (!expired || !waited_ms) return CTM_EINVAL;
+    return run_wait_probe(expired, waited_ms) == cudaSuccess ? CTM_OK : CTM_ECUDA;
 }
 
 }  // extern "C"

@@ -193,8 +193,13 @@ size_t match_pipe_smem_bytes(const MatchArgs &a);
 cudaError_t match_pipe_configure(const MatchArgs &a, int threads, int *ctas_per_sm);
 cudaError_t launch_match_pipe(const MatchArgs &a, int threads, int grid, cudaStream_t s);
 
-// Probe (probe.cu)
+// Probes (probe.cu)
 cudaError_t run_int_probe(int kind, int iters, double *ops_per_clk_per_sm);
+cudaError_t run_wait_probe(int *expired, float *waited_ms);
+
+// Device address of the error flag of a context's last finished call
+// (ctm_stats.error), for callers that read it back on their own stream.
+const int32_t *context_error_flag(const ctm_ctx *ctx);
 
 // Bytes of device workspace a context holds (its one allocation at creation).
 size_t context_device_bytes(const ctm_ctx *ctx);

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "ctm_internal.cuh"
+#include "match_common.cuh"
 
 namespace ctm {
 namespace {
@@ -96,7 +97,43 @@ __global__ void __launch_bounds__(kProbeThreads) int_probe_kernel(int kind, int 
     if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
+// One CTA waits on an mbarrier phase that nothing completes: no thread arrives
+// and no copy is in flight, so the bounded wait gives up and flags it.
+__global__ void wait_probe_kernel(int *flag)
+{
+    __shared__ uint64_t mbar;
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    mbar_wait_bounded(&mbar, 0u, flag);
+}
+
 }  // namespace
+
+cudaError_t run_wait_probe(int *expired, float *waited_ms)
+{
+    int *flag = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(flag, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, 0);
+    if (e == cudaSuccess) {
+        wait_probe_kernel<<<1, 32>>>(flag);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(waited_ms, e0, e1);
+    if (e == cudaSuccess) e = cudaMemcpy(expired, flag, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (flag) cudaFree(flag);
+    return e;
+}
 
 cudaError_t run_int_probe(int kind, int iters, double *ops_per_clk_per_sm)
 {

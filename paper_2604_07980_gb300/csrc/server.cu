@@ -254,6 +254,12 @@ void dispatch(ctm_server *S, Lane &L)
             e = cudaMemcpyAsync(L.flags_h, L.flags_d, (size_t)nb, cudaMemcpyDeviceToHost, L.stream);
         if (e != cudaSuccess) st = CTM_ECUDA;
     }
+    if (st == CTM_OK) {  // the batch's bounded-wait flag (ctm_stats.error) into counts_h[3]
+        L.counts_h[3] = 0;
+        e = cudaMemcpyAsync(&L.counts_h[3], ctm::context_error_flag(L.ctx), sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            L.stream);
+        if (e != cudaSuccess) st = CTM_ECUDA;
+    }
     if (st == CTM_OK) {
         e = cudaEventRecord(L.done, L.stream);
         if (e == cudaSuccess) e = cudaLaunchHostFunc(L.stream, lane_done_cb, S);
@@ -282,6 +288,7 @@ void dispatch(ctm_server *S, Lane &L)
 void finish(ctm_server *S, Lane &L, int status)
 {
     const int nf = (int)L.batch.size();
+    const bool expired = status == CTM_OK && L.counts_h[3] != 0;
     if (status == CTM_OK) {
         for (int i = 0; i < nf; ++i) {
             const ctm_request &r = L.batch[i]->r;
@@ -292,7 +299,7 @@ void finish(ctm_server *S, Lane &L, int status)
             memcpy(r.flags_host, L.flags_h + o, (size_t)n);
         }
     }
-    complete_jobs(S, L.batch, L.index, nf, status);
+    complete_jobs(S, L.batch, L.index, nf, expired ? CTM_ETIMEOUT : status);
     L.batch.clear();
     L.busy = false;
 }

@@ -65,6 +65,8 @@ def test_status_strings_and_defaults(built):
     bad = B.make_params({"win_w": 8})
     assert L.ctm_create(ctypes.byref(h), ctypes.byref(bad), 1, 64, 64, 4) == B.CTM_EINVAL
     assert L.ctm_match_batch(None, None, None, None, None, None, None, None, 0, None) == B.CTM_EINVAL
+    assert b"bounded device wait" in L.ctm_status_str(B.CTM_ETIMEOUT)
+    assert L.ctm_probe_bounded_wait(None, None) == B.CTM_EINVAL
 
 
 def test_binding_refuses_without_gpu():
