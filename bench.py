@@ -11,9 +11,12 @@ images, 1.5 GB of census planes written and re-read every step) exceed the
 129 MB L2, so no flush is needed between steps.
 
 Printed (one JSON line on rank 0): cost-evals/s of the batched path, its e2e
-number through the host-memory entry point, the per-kernel roofline of the
-matching kernel against the integer popcount pipe, the plain one-launch-per-box
-path for comparison, the oracle CPU baseline and the SM clocks seen.
+number through the host-memory entry point (packed page-locked images, copies
+overlapped with the kernels by sub-batches), the per-kernel roofline of the
+matching kernel against the integer popcount pipe and of the census phase
+against HBM and the integer pipes, the throughput with two batches in flight,
+the plain one-launch-per-box path for comparison, the serving loop's p50/p99
+latency, the oracle CPU baseline and the SM clocks seen.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
