@@ -224,7 +224,6 @@ def test_batch_host_sub_batches_equal_device_batch(torch_cuda):
     overlap the previous sub-batch's kernels: outputs and summed counters equal the
     one-launch device path bit for bit.  Boxes listed out of frame order are not
     chained and run as one batch, with the same outputs."""
-    import ctypes
     from paper_2604_07980_gb300 import binding as B
     w = wl.batch32x1200(n_frames=7, W=800, H=400, mean_boxes=10, side_range=(12, 200))
     ctx = B.Context(w.params, 7, 800, 400, w.n_boxes)

@@ -2,7 +2,6 @@
 completes, waited on with the matching kernels' own routine) ends its kernel
 with the expiry recorded in a device flag, and the context stays usable: a
 match call afterwards gives the oracle's outputs and no error."""
-import numpy as np
 import pytest
 
 from oracle import oracle as orc
