@@ -63,9 +63,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--no-inflight2", dest="inflight2", action="store_false",
-                    help="time one batch at a time only (default: two batches in flight on two "
-                         "contexts and streams, one batch at a time reported beside)")
+    ap.add_argument("--inflight", type=int, default=2,
+                    help="batches in flight during the timed steps, each on its own context and "
+                         "stream (default 2; 1 = one batch at a time, also reported beside)")
     ap.add_argument("--frames", type=int, default=32)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -356,7 +356,7 @@ def main():
     # and aggregation kernels then share SMs with the other batch's census or matching.
     # Every step is still one whole pass over one batch.
     lanes = [(ctx, batch, stream)]
-    if args.inflight2:
+    for _ in range(1, max(args.inflight, 1)):
         ctx2 = B.Context(w.params, len(w.frames), 1920, 1200, w.n_boxes)
         ctx2.set_tuning(**tuning)
         batch2 = B.DeviceBatch(frames_dev, w.boxes, calib)

@@ -27,7 +27,6 @@ struct GraphKey {
 // Sub-batches of the host entry point: the copies of sub-batch g + 1 run
 // while sub-batch g is matched.
 constexpr int kHostGroups = 4;
-constexpr int kCopyStreams = 1;  // copy streams per sub-batch (two measured slower on GB300: 1.24 against 1.10 ms per 147 MB step)
 
 struct ctm_ctx {
     int device = 0;
@@ -60,8 +59,8 @@ struct ctm_ctx {
     int32_t *counts_host_pinned = nullptr;
     ctm_frame *frames_dev2 = nullptr;
     int32_t *counts_dev2 = nullptr;
-    cudaStream_t copy_stream[kCopyStreams] = {};  // host-to-device copies of the sub-batches
-    cudaEvent_t host_ev[kHostGroups * kCopyStreams + 1] = {};  // sub-batch g's copies on stream k; last: start
+    cudaStream_t copy_stream = nullptr;         // host-to-device copies of the sub-batches
+    cudaEvent_t host_ev[kHostGroups + 1] = {};  // sub-batch g copied; [kHostGroups]: start
 };
 
 namespace {
@@ -328,8 +327,7 @@ void ctm_destroy(ctm_ctx *ctx)
     if (ctx->img_dev) cudaFree(ctx->img_dev);
     if (ctx->frames_host_pinned) cudaFreeHost(ctx->frames_host_pinned);
     if (ctx->counts_host_pinned) cudaFreeHost(ctx->counts_host_pinned);
-    for (cudaStream_t cs : ctx->copy_stream)
-        if (cs) cudaStreamDestroy(cs);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     for (cudaEvent_t ev : ctx->host_ev)
         if (ev) cudaEventDestroy(ev);
     cudaGetLastError();
@@ -505,17 +503,16 @@ int ctm_match_batch_host(ctm_ctx *ctx, const ctm_frame *frames_host, int n_frame
         void *mem = nullptr;
         if (cudaMalloc(&mem, off) != cudaSuccess) { cudaGetLastError(); return CTM_ENOMEM; }
         bool okh = cudaMallocHost(&ctx->frames_host_pinned, sizeof(ctm_frame) * ctx->caps.max_frames) == cudaSuccess &&
-                   cudaMallocHost(&ctx->counts_host_pinned, sizeof(int32_t) * 4 * kHostGroups) == cudaSuccess;
-        for (cudaStream_t &cs : ctx->copy_stream)
-            okh = okh && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) == cudaSuccess;
+                   cudaMallocHost(&ctx->counts_host_pinned, sizeof(int32_t) * 4 * kHostGroups) == cudaSuccess &&
+                   cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
         for (cudaEvent_t &ev : ctx->host_ev)
             okh = okh && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
         if (!okh) {
             cudaFree(mem);
             if (ctx->frames_host_pinned) cudaFreeHost(ctx->frames_host_pinned);
             if (ctx->counts_host_pinned) cudaFreeHost(ctx->counts_host_pinned);
-            for (cudaStream_t &cs : ctx->copy_stream)
-                if (cs) { cudaStreamDestroy(cs); cs = nullptr; }
+            if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+            ctx->copy_stream = nullptr;
             for (cudaEvent_t &ev : ctx->host_ev)
                 if (ev) { cudaEventDestroy(ev); ev = nullptr; }
             ctx->frames_host_pinned = nullptr;
@@ -547,26 +544,20 @@ int ctm_match_batch_host(ctm_ctx *ctx, const ctm_frame *frames_host, int n_frame
     const int groups = chained ? std::min(kHostGroups, n_frames) : 1;
 
     const size_t plane = (size_t)ctx->img_pitch * ctx->caps.max_height;
-    cudaStream_t cs = ctx->copy_stream[0];
-    cudaEvent_t ev_start = ctx->host_ev[kHostGroups * kCopyStreams];
-    cudaError_t e = cudaEventRecord(ev_start, s);  // work already queued on `stream`
-    for (int k = 0; k < kCopyStreams && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(ctx->copy_stream[k], ev_start, 0);
+    cudaStream_t cs = ctx->copy_stream;
+    cudaError_t e = cudaEventRecord(ctx->host_ev[kHostGroups], s);  // work already queued on `stream`
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ctx->host_ev[kHostGroups], 0);
     // Images go to the staging planes in as few copies as possible: an image
     // packed at the staging pitch is one linear run, and runs that continue one
     // another in both host and device memory are merged (one large copy moves
-    // about 210 GB/s on GB300, 64 copies of 2.3 MB about 155 GB/s); a run is
-    // split evenly over the copy streams, so that more than one copy engine moves it.
+    // about 210 GB/s on GB300, the host link's rate; 64 copies of 2.3 MB about
+    // 155 GB/s, and two copy streams were slower too).
     const uint8_t *run_src = nullptr;
     uint8_t *run_dst = nullptr;
     size_t run_bytes = 0;
     auto flush = [&]() {
-        size_t done = 0;
-        for (int k = 0; k < kCopyStreams && run_bytes > 0 && e == cudaSuccess; ++k) {
-            const size_t part = (size_t)round_up((long long)(run_bytes / kCopyStreams), 4096);
-            const size_t n = k == kCopyStreams - 1 ? run_bytes - done : std::min(part, run_bytes - done);
-            if (n > 0) e = cudaMemcpyAsync(run_dst + done, run_src + done, n, cudaMemcpyHostToDevice, ctx->copy_stream[k]);
-            done += n;
-        }
+        if (run_bytes > 0 && e == cudaSuccess)
+            e = cudaMemcpyAsync(run_dst, run_src, run_bytes, cudaMemcpyHostToDevice, cs);
         run_bytes = 0;
     };
     auto image = [&](uint8_t *dst, const uint8_t *src, const ctm_frame &f) {
@@ -623,11 +614,8 @@ int ctm_match_batch_host(ctm_ctx *ctx, const ctm_frame *frames_host, int n_frame
                                 cudaMemcpyHostToDevice, cs);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(ctx->counts_dev2 + 4 * g, cnt, sizeof(int32_t) * 2, cudaMemcpyHostToDevice, cs);
-        for (int k = 0; k < kCopyStreams && e == cudaSuccess; ++k) {
-            cudaEvent_t ev = ctx->host_ev[g * kCopyStreams + k];
-            e = cudaEventRecord(ev, ctx->copy_stream[k]);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev, 0);
-        }
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->host_ev[g], cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->host_ev[g], 0);
         if (e != cudaSuccess) break;
         MatchArgs a = make_args(ctx, ctx->frames_dev2 + f0, ctx->counts_dev2 + 4 * g, ctx->boxes_dev + box0,
                                 ctx->disp_dev + box0, ctx->depth_dev + box0, ctx->flags_dev + box0, nullptr);
