@@ -297,6 +297,20 @@ def test_two_contexts_in_flight_on_two_streams(torch_cuda):
         c.close()
 
 
+@pytest.mark.parametrize("n_boxes", [300, 1100])
+def test_many_boxes_in_one_frame(torch_cuda, n_boxes):
+    """Frames with more boxes than the planner keeps in registers (256 per warp's
+    lanes) and than it stages in shared memory (1024): the occluder selection falls
+    back to scanning the frame's boxes from shared or global memory; equal to the
+    oracle, block records included."""
+    w = wl.frame1080(W=800, H=600, n_boxes=n_boxes, side_range=(8, 90), seed=4100 + n_boxes)
+    params = dict(w.params, max_occluders=16, frontal_crop=0.3)
+    got, ref, stats, nc = _run_frame(torch_cuda, w, params=params)
+    compare_box_outputs(got, ref, f"{n_boxes} boxes")
+    compare_debug(got["debug"], ref, nc, f"{n_boxes} boxes")
+    assert stats["cost_evals"] == oracle_evals(ref["blocks"], ref["flags"], params)
+
+
 def test_frontal_crop_occluder_priority(torch_cuda):
     """Occluder cap of 2 with the frontal-crop priority on a batch with many overlapping
     boxes: block records and outputs equal the oracle's (and differ from proximity-only
