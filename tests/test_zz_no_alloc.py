@@ -94,3 +94,30 @@ def test_noalloc_rejects_sizes_beyond_its_limits(torch_cuda):
         ctypes.c_void_p(many.data_ptr()), 65, fr.f_px, fr.baseline_m, ctypes.c_void_p(out.data_ptr()),
         ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(fl.data_ptr()), None)
     assert st == B.CTM_ETOOBIG
+
+
+def test_noalloc_random_configurations_equal_oracle(torch_cuda):
+    """The seeded random parameter sets of the GPU parity sweep, first frame of each,
+    through the allocation-free entry point: equal to the oracle."""
+    from oracle import oracle as orc
+    from paper_2604_07980_gb300 import binding as B
+    from tests.test_gpu_random_configs import _random_params
+    ran = 0
+    for seed in range(40):
+        rng = np.random.default_rng(7000 + seed)
+        params = _random_params(rng)
+        n_frames = int(rng.integers(1, 4))
+        W, H = int(rng.integers(60, 260)), int(rng.integers(50, 200))
+        w = wl.multi_frame("frame1080", 8000 + seed, n_frames, W, H, int(rng.integers(3, 25)), (4.0, 120.0),
+                           (0.5, 12.0), (1.0, 24.0), strip_frac=0.3)
+        w.params = params
+        sel = w.boxes[:, 4] == 0
+        w.boxes = np.ascontiguousarray(w.boxes[sel])
+        if len(w.boxes) == 0:
+            continue
+        fr, L, R, boxes = _inputs(torch_cuda, w)
+        got = _noalloc(torch_cuda, B, w, L, R, boxes, fr)
+        ref = orc.match_frame(fr.left, fr.right, w.boxes, fr.f_px, fr.baseline_m, orc.Params(**params))
+        compare_box_outputs(got, ref, f"noalloc seed {seed} params {params}")
+        ran += 1
+    assert ran >= 35
