@@ -3,7 +3,9 @@ accepts (the fixed 5x5/7x7/9x7 tile code and the generic staged path), decimatio
 1-3, random and negative disparity ranges, vertical search, grid sizes, point
 counts, minimum points, consistency tolerances, both aggregation modes, occluder
 caps and the frontal crop, sentinel on and off; small random frames with boxes
-across the borders, several frames per batch.  Flags, block records and every
+across the borders, several frames per batch; the default tuning through the
+stream and graph paths, then the two-pass matcher with the second census variant
+and the narrowest strip (most column chunks).  Flags, block records and every
 forward and backward cost bit-exact; disparity within 1e-4 px, depth 1e-5."""
 import numpy as np
 import pytest
@@ -59,11 +61,17 @@ def test_random_configuration(seed):
     ref = orc.match_batch(frames, w.boxes, orc.Params(**params), debug=True)
     ctx = B.Context(params, n_frames, W, H, max(len(w.boxes), 1))
     batch = B.DeviceBatch(B.frames_to_device(w.frames), w.boxes, [(f.f_px, f.baseline_m) for f in w.frames])
-    for graph in (False, True):
+    nd_max = max(params["far_dmax"] - params["far_dmin"], params["close_dmax"] - params["close_dmin"]) + 1
+    narrow = ((nd_max + 2 + 7) // 8) * 8
+    runs = [dict(), dict(), dict(match_mode=1, census_mode=1, strip_cols=narrow, match_threads=256)]
+    for i, tuning in enumerate(runs):
+        graph = i == 1
+        if tuning:
+            ctx.set_tuning(**tuning)
         got = ctx.match_batch(batch, use_graph=graph, debug=True)
         torch.cuda.synchronize()
         out = {k: v.cpu().numpy() for k, v in got.items() if k != "debug"}
-        where = f"seed {seed} graph {graph} params {params}"
+        where = f"seed {seed} graph {graph} tuning {tuning} params {params}"
         compare_box_outputs(out, ref, where)
         dbg = got["debug"]
         compare_debug_arrays(dbg.blocks_np(), dbg.cost_f.cpu().numpy(), dbg.cost_b.cpu().numpy(), ref,
