@@ -46,7 +46,7 @@ POPC_PER_EVAL = 2          # one u64 code pair = two 32-bit popcounts
 # DRAM bytes (read + write) of one match_persistent_kernel launch on this workload, from the
 # ncu capture summarised in profiles/match_persistent_kernel_batch32x1200.md; None once the
 # kernel changes after that capture.
-MATCH_DRAM_BYTES = (102.534 + 3.243) * 1e6
+MATCH_DRAM_BYTES = None  # re-captured after the combine change
 # DRAM bytes of one census_roi4_kernel launch on this workload (same capture, summarised in
 # profiles/census_roi4_kernel_batch32x1200.md) plus its tile_list_kernel launch
 CENSUS_DRAM_BYTES = (61.096 + 69.065 + 0.775) * 1e6
@@ -617,7 +617,7 @@ def main():
                     "ms_per_step": e2e_s * 1e3, "host_threads": len(lanes)},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT,
                          "frac": achieved / peak,
-                         "traffic": MATCH_DRAM_BYTES if len(w.frames) == 32 else None,
+                         "traffic": MATCH_DRAM_BYTES if len(w.frames) == 32 and MATCH_DRAM_BYTES else None,
                          "kernel": "match_persistent_kernel",
                          "peak_basis": f"{sms} SMs x {popc_clk:g} popc32/clk/SM (probe {popc_rate:.2f}) / "
                                        f"{POPC_PER_EVAL} per eval x {SM_MAX_MHZ:g} MHz",

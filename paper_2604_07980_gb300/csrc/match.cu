@@ -203,27 +203,46 @@ __device__ bool scan_chunks(const MatchArgs &a, const BlockCtx &bc, const Smem &
     return ok;
 }
 
-// The end of a pass: warps add their sums into `cost` (zeroed when the pass
-// started); after one barrier every warp reduces the whole row to the first
-// argmin key (cost << 16 | c), so every thread holds it without a broadcast.
-// Warp 0 writes the debug costs.  False if a bounded wait expired anywhere.
+// The end of a pass: the warps' sums are combined in two rows, sm.cost and
+// sm.cost_b, without atomics -- warps 0 and 1 store theirs, then each further pair
+// of warps adds its sums to the rows in turn, a barrier between steps -- and
+// every warp then reduces the whole row pair to the first argmin key
+// (cost << 16 | c), so every thread holds it without a broadcast.  Warp 0 writes
+// the debug costs.  The rows' previous readers (the other pass's argmin) are
+// separated from the first store by a barrier of the caller.  False if a
+// bounded wait expired anywhere.
 template <int NT>
-__device__ __forceinline__ bool combine_pass(const MatchArgs &a, const BlockCtx &bc, int *cost, bool fwd,
+__device__ __forceinline__ bool combine_pass(const MatchArgs &a, const BlockCtx &bc, const Smem &sm, bool fwd,
                                              const int (&acc)[8], bool ok, unsigned &key)
 {
+    constexpr int NW = NT / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int T = (bc.nc + 31) >> 5;
+    int *row = (warp & 1) ? sm.cost_b : sm.cost;
+    if (warp < 2) {
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
-        const int c = t * 32 + lane;
-        if (t < T && c < bc.nc) atomicAdd(&cost[c], acc[t]);
+        for (int t = 0; t < 8; ++t) {
+            const int c = t * 32 + lane;
+            if (t < T && c < bc.nc) row[c] = acc[t];
+        }
     }
     if (!__syncthreads_and(ok)) return false;
+#pragma unroll
+    for (int step = 1; step < NW / 2; ++step) {
+        if ((warp >> 1) == step) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int c = t * 32 + lane;
+                if (t < T && c < bc.nc) row[c] += acc[t];
+            }
+        }
+        __syncthreads();
+    }
     int32_t *dbgc = warp == 0 ? (fwd ? a.dbg.cost_f : a.dbg.cost_b) : nullptr;
     const int slots = a.p.grid_g * a.p.grid_g;
     unsigned k = 0xffffffffu;
     for (int c = lane; c < bc.nc; c += 32) {
-        const int s = cost[c];
+        const int s = sm.cost[c] + sm.cost_b[c];
         k = min(k, ((unsigned)s << 16) | (unsigned)c);
         if (dbgc) dbgc[((long long)bc.box * slots + bc.slot) * a.nc_stride + c] = s;
     }
@@ -331,7 +350,6 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
     const int x0 = g.X[0];
     const int SW0 = g.X[j1_first - 1] - x0 + bc.nd;
     const ChunkGeom g0 = chunk_geom(x0 - bc.dmax, SW0);
-    for (int c = tid; c < bc.nc; c += NT) sm.cost[c] = 0;
 
     // 1. the left codes and the first forward strip chunk (issued by begin_block)
     bool ok = land_chunk<NT>(a, bc, sm, sh, phase, true, 0, g0);
@@ -344,15 +362,15 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
     int acc[8];
     ok = scan_chunks<NT>(a, bc, sm, sh, phase, true, g0, acc, 0, 0);
     unsigned key;
-    if (!combine_pass<NT>(a, bc, sm.cost, true, acc, ok, key)) return false;
+    if (!combine_pass<NT>(a, bc, sm, true, acc, ok, key)) return false;
     const int cf = (int)(key & 0xffffu);
     const int ef = bc.ndy == 1 ? 0 : cf / bc.nd;
     const int dif = cf - ef * bc.nd;
     const int d_f = bc.dmin + dif, dy_f = a.p.dy_min + ef;
     int s_m = 0, s_p = 0;
     if (tid == 0) {
-        s_m = dif > 0 ? sm.cost[cf - 1] : 0;
-        s_p = dif < bc.nd - 1 ? sm.cost[cf + 1] : 0;
+        s_m = dif > 0 ? sm.cost[cf - 1] + sm.cost_b[cf - 1] : 0;
+        s_p = dif < bc.nd - 1 ? sm.cost[cf + 1] + sm.cost_b[cf + 1] : 0;
         if (pf.on) {
             sh.next = next_i;
             sh.next_b = next_b;
@@ -375,7 +393,6 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
         else
             sm.pcode[t] = 0ull;
     }
-    for (int c = tid; c < bc.nc; c += NT) sm.cost_b[c] = 0;
     const ChunkGeom gb = chunk_geom(x0 - d_f + bc.dmin, SW0);
     ok = load_chunk<NT>(a, bc, sm, sh, phase, false, dy_f, gb);
     set_bases<NT>(sm, sh.X, 0, sh.colstart[j1_first], bc.ndy, gb.SWa, x0, gb.delta);
@@ -383,7 +400,7 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
     if (!__syncthreads_and(ok)) return false;
     ok = scan_chunks<NT>(a, bc, sm, sh, phase, false, gb, acc, d_f, dy_f);
     unsigned keyb;
-    if (!combine_pass<NT>(a, bc, sm.cost_b, false, acc, ok, keyb)) return false;
+    if (!combine_pass<NT>(a, bc, sm, false, acc, ok, keyb)) return false;
 
     // the next block starts now: its record (wait) and its first loads (issued)
     const bool has_next = pf.on && sh.gpend;
