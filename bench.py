@@ -46,7 +46,7 @@ POPC_PER_EVAL = 2          # one u64 code pair = two 32-bit popcounts
 # DRAM bytes (read + write) of one match_persistent_kernel launch on this workload, from the
 # ncu capture summarised in profiles/match_persistent_kernel_batch32x1200.md; None once the
 # kernel changes after that capture.
-MATCH_DRAM_BYTES = None  # re-captured after the combine change
+MATCH_DRAM_BYTES = (102.463 + 3.343) * 1e6
 # DRAM bytes of one census_roi4_kernel launch on this workload (same capture, summarised in
 # profiles/census_roi4_kernel_batch32x1200.md) plus its tile_list_kernel launch
 CENSUS_DRAM_BYTES = (61.096 + 69.065 + 0.775) * 1e6
