@@ -383,20 +383,32 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
         }
     }
 
-    // 4. backward pass: right codes at the matched positions + first left strip
-    //    (every warp's forward scans ended at combine_pass's barrier)
-    for (int t = tid; t < total; t += NT) {
-        const int mj = sm.pmj[t];
-        const int qx = sh.X[mj & 255] - d_f, qy = sh.Y[mj >> 8] + dy_f;
-        if (qx >= 0 && qx < bc.Ws && qy >= 0 && qy < bc.Hs)
-            cp_async8(&sm.pcode[t], bc.CR + (long long)qy * bc.pitch + qx);
-        else
-            sm.pcode[t] = 0ull;
-    }
+    // 4. backward pass: first left strip (bulk copies, issued first), then the right
+    //    codes at the matched positions by plain loads -- the CTA waits for both, and
+    //    the loads overlap the copies' round trip (every warp's forward scans ended
+    //    at combine_pass's barrier)
     const ChunkGeom gb = chunk_geom(x0 - d_f + bc.dmin, SW0);
-    ok = load_chunk<NT>(a, bc, sm, sh, phase, false, dy_f, gb);
+    issue_chunk<NT>(a, bc, sm, sh, false, dy_f, gb);
+    {
+        constexpr int kPer = kMaxPts / NT;
+        uint64_t v[kPer];
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const int t = tid + i * NT;
+            v[i] = 0ull;
+            if (t < total) {
+                const int mj = sm.pmj[t];
+                const int qx = sh.X[mj & 255] - d_f, qy = sh.Y[mj >> 8] + dy_f;
+                if (qx >= 0 && qx < bc.Ws && qy >= 0 && qy < bc.Hs)
+                    v[i] = __ldg(bc.CR + (long long)qy * bc.pitch + qx);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kPer; ++i)
+            if (tid + i * NT < total) sm.pcode[tid + i * NT] = v[i];
+    }
+    ok = land_chunk<NT>(a, bc, sm, sh, phase, false, dy_f, gb);
     set_bases<NT>(sm, sh.X, 0, sh.colstart[j1_first], bc.ndy, gb.SWa, x0, gb.delta);
-    cp_async_wait_all();
     if (!__syncthreads_and(ok)) return false;
     ok = scan_chunks<NT>(a, bc, sm, sh, phase, false, gb, acc, d_f, dy_f);
     unsigned keyb;
