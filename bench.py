@@ -44,9 +44,9 @@ SM_COUNT_NOMINAL = 152
 SM_MAX_MHZ = 2070.0
 POPC_PER_EVAL = 2          # one u64 code pair = two 32-bit popcounts
 # DRAM bytes (read + write) of one match_persistent_kernel launch on this workload, from the
-# ncu capture summarised in profiles/match_persistent_kernel_batch32x1200.md; None once the
-# kernel changes after that capture.
-MATCH_DRAM_BYTES = (102.463 + 3.343) * 1e6
+# ncu count summarised in profiles/match_persistent_kernel_batch32x1200.md; None once the
+# kernel changes after that count.
+MATCH_DRAM_BYTES = (102.678 + 2.432) * 1e6
 # DRAM bytes of one census_roi4_kernel launch on this workload (same capture, summarised in
 # profiles/census_roi4_kernel_batch32x1200.md) plus its tile_list_kernel launch
 CENSUS_DRAM_BYTES = (61.096 + 69.065 + 0.775) * 1e6
