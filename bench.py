@@ -532,6 +532,29 @@ def main():
     box_points = {"ms": pts_ms, "boxes_per_s": w.n_boxes / (pts_ms * 1e-3),
                   "valid_boxes": int(torch.isfinite(pts[:, 2]).sum().item())}
 
+    # ---- Sec. 5.1 auto-rectification offset search (census matching) on one frame pair: a
+    # 128-row band across the image, delta in [-4, 4], d in [0, 63]; the call computes both
+    # census images into scratch, then the forward and backward scans of every
+    # (pixel, delta).  Work counted as 2 * 64 evaluations per (band pixel, delta).
+    L0, R0 = frames_dev[0]
+    band = (0, H // 3, W, min(H, H // 3 + 128))
+    n_delta, nd_rect = 9, 64
+    for _ in range(3):
+        B.auto_rect(L0, R0, band, 0, nd_rect - 1, -4, 4, 2, params=w.params)
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(args.steps):
+        delta_star, _ = B.auto_rect(L0, R0, band, 0, nd_rect - 1, -4, 4, 2, params=w.params)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    rect_ms = a0.elapsed_time(a1) / args.steps
+    rect_evals = (band[2] - band[0]) * (band[3] - band[1]) * n_delta * 2 * nd_rect
+    auto_rect = {"ms": rect_ms, "roi": list(band), "deltas": n_delta, "disparities": nd_rect,
+                 "delta_star": int(delta_star.item()),
+                 "evals_per_call": rect_evals, "value": rect_evals / (rect_ms * 1e-3) / 1e9, "unit": UNIT,
+                 "note": "one call = census of both images + forward/backward scans per (ROI pixel, delta)"}
+
     # ---- full-image census (ctm_census_build, Sec. 4.3.1) of one image of the workload at full and
     # half resolution: HBM fraction of its algorithmic bytes (8 B code + 1 B pixel per code)
     census_full = {}
@@ -638,6 +661,7 @@ def main():
             "one_batch_at_a_time": one_at_a_time,
             "plain_per_box": plain,
             "box_points": box_points,
+            "auto_rect": {**auto_rect, "frac_of_popc_peak": auto_rect["value"] / peak},
             "serving": serving,
             "serving_plain_path": serving_plain,
             "e2e": {"value": evals_per_step * world / e2e_s / 1e9, "unit": UNIT,
