@@ -9,12 +9,14 @@
 //      S(dy, d) = sum_p popc(C_L(p) ^ C_R(p.x - d, p.y + dy)), for every
 //      candidate; lanes own consecutive candidates (conflict-free strip reads),
 //      warps own point subsets, each thread keeps up to 8 candidate sums in
-//      registers, and warps combine them with shared-memory atomics;
-//   3. first argmin over (dy, d): after one barrier every warp reduces the whole
-//      cost row to the minimum (cost << 16 | index) key itself, so the result
-//      needs no broadcast; Eq. subpixel in fp32 with IEEE division;
-//   4. backward pass (Sec. 4.3.3): the right codes at the matched positions and
-//      the left strip [q.x + dmin, q.x + dmax] arrive in one round trip;
+//      registers, and the warps' sums are combined in two shared rows by ordered
+//      stores and adds (no atomics);
+//   3. first argmin over (dy, d): after the last combining barrier every warp
+//      reduces the rows to the minimum (cost << 16 | index) key itself, so the
+//      result needs no broadcast; Eq. subpixel in fp32 with IEEE division;
+//   4. backward pass (Sec. 4.3.3): the left strip [q.x + dmin, q.x + dmax] (bulk
+//      copies, issued first) and the right codes at the matched positions (plain
+//      loads) arrive in one round trip;
 //   5. consistency |d_b - d_f| <= fb_tol and the block record; boxes are
 //      aggregated afterwards (aggregate_kernel).
 // Blocks wider than the strip are split into column chunks; chunk sums add up
