@@ -5,12 +5,15 @@ import os
 import subprocess
 import sys
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_reference_arm_prints_its_line():
+@pytest.mark.parametrize("extra", [["--frames", "2"], ["--workload", "pair640"]])
+def test_reference_arm_prints_its_line(extra):
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "0", "--frames", "2"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+                        "--warmup", "0"] + extra, capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
