@@ -194,10 +194,11 @@ int ctm_census_build(const uint8_t *img_dev, int width, int height, int pitch, i
 /* Algorithm 2 on one frame.  boxes_dev: n_boxes ctm_box (0 <= n_boxes <=
  * max_boxes).  Outputs (n_boxes each): disp_dev (float, full-res px, NaN unless
  * VALID), depth_dev (float, f_px*baseline_m/disp, NaN unless VALID), flags_dev
- * (uint8 CTM_BOX_*).  dbg may be NULL.  One fused path: census of both images at
- * both resolutions, device planning, one persistent matching kernel whose last
- * CTA per box aggregates.  Errors: CTM_EINVAL, CTM_ENOMEM (beyond capacity),
- * CTM_ECUDA. */
+ * (uint8 CTM_BOX_*).  dbg may be NULL.  The launch sequence of the batch path on
+ * one frame: device planning and point sampling, the census of the row tiles the
+ * search reads (both images, both resolutions), one persistent matching kernel
+ * and a per-box aggregation kernel.  Errors: CTM_EINVAL, CTM_ENOMEM (beyond
+ * capacity), CTM_ECUDA. */
 int ctm_match_boxes(ctm_ctx *ctx, const uint8_t *left_dev, const uint8_t *right_dev,
                     int width, int height, int pitch, const ctm_box *boxes_dev, int n_boxes,
                     float f_px, float baseline_m, float *disp_dev, float *depth_dev,
