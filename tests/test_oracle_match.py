@@ -386,3 +386,80 @@ def test_half_resolution_rescale():
     assert np.all(b["d_f"] == 12)
     np.testing.assert_array_equal(b["d_full"], b["d_sub"] * np.float32(2))
     assert out["disp"][0] == pytest.approx(24.0, abs=0.2)
+
+
+# ---------------------------------------------------------------- Sec. 4.3.4 point grid
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_point_columns_located_by_one_pixel_occluders(k):
+    """Sec. 4.3.4/4.3.5: a 32-px block (on the matching grid) with 16 points per side
+    holds its points at the centres of 2-px cells, offsets 1, 3, ..., 31; an occluder
+    hides a point when the point's full-resolution position k x lies in it.  A
+    one-column occluder that reaches below the box therefore hides exactly the points
+    of one column (16 per block, two blocks deep) or none.  Which full-resolution
+    columns hide points is listed here in closed form, not from the sampling formula."""
+    side = 64 * k  # two 32-px blocks per axis on the matching grid
+    x0, y0 = 40 * k, 10 * k
+    H, W = y0 + side + 40, x0 + side + 40
+    rng = np.random.default_rng(21)
+    L = np.clip(np.rint(wl.texture(rng, H, W)), 0, 255).astype(np.uint8)
+    p = _params(far_side_px=0, close_factor=k, grid_g=2, pts_side=16, min_pts=1,
+                close_dmax=15, max_occluders=4)
+    box = [x0, y0, x0 + side, y0 + side, 0]
+    cols = {k * (40 + 1 + 2 * q) for q in range(16)} | {k * (40 + 33 + 2 * q) for q in range(16)}
+    for c in range(x0 - 1, x0 + side + 1):
+        occ = [c, y0 - 5, c + 1, y0 + side + 5, 0]
+        out = orc.match_frame(L, L, np.array([box, occ], np.int32), 2000.0, 0.3, p, debug=True)
+        nv = out["blocks"][0]["n_valid"]
+        hidden = 32 if c in cols else 0
+        assert int(nv.sum()) == 4 * 256 - hidden, c
+        assert np.all(out["blocks"][0]["n_pts"] == 256)
+
+
+def test_min_points_boundary_and_box_flags():
+    """Sec. 4.3.4: a block with fewer usable points than min_pts is not searched and
+    flags FEW_POINTS; with every block so flagged the box has no consistent segment."""
+    L, R = _textured_pair(160, 64, 7, seed=31, offset=10.0)
+    box = np.array([[90, 8, 138, 56, 0]], np.int32)  # 48x48, 3x3 blocks of 16x16 points
+    ok = orc.match_frame(L, R, box, 2000.0, 0.3, _params(min_pts=256), debug=True)
+    b = ok["blocks"][0]
+    assert np.all(b["n_valid"] == 256)
+    assert not np.any(b["flags"] & orc.BLK_FEW_POINTS) and np.all(b["flags"] & orc.BLK_VALID)
+    assert ok["flags"][0] & orc.BOX_VALID and not ok["flags"][0] & orc.BOX_FEW_POINTS
+    few = orc.match_frame(L, R, box, 2000.0, 0.3, _params(min_pts=257), debug=True)
+    b = few["blocks"][0]
+    assert np.all(b["flags"] & orc.BLK_FEW_POINTS) and not np.any(b["flags"] & orc.BLK_VALID)
+    assert np.all(few["cost_f"][0] == 0)  # never searched
+    f = few["flags"][0]
+    assert f & orc.BOX_FEW_POINTS and f & orc.BOX_NO_SEGMENT and not f & orc.BOX_VALID
+    assert np.isnan(few["disp"][0]) and np.isnan(few["depth"][0])
+
+
+def test_aggregation_needs_agg_nmin_consistent_blocks():
+    """Sec. 4.3.4: the box takes the aggregate of its longest run of consistent blocks
+    only when the run holds at least agg_nmin of them; nine agreeing blocks pass at
+    agg_nmin = 9 and fail at 10."""
+    L, R = _textured_pair(160, 64, 7, seed=32, offset=10.0)
+    box = np.array([[90, 8, 138, 56, 0]], np.int32)
+    nine = orc.match_frame(L, R, box, 2000.0, 0.3, _params(agg_nmin=9), debug=True)
+    assert np.all(nine["blocks"][0]["d_f"] == 7)
+    assert nine["flags"][0] & orc.BOX_VALID
+    assert nine["disp"][0] == pytest.approx(float(np.median(nine["blocks"][0]["d_full"])), abs=1e-6)
+    ten = orc.match_frame(L, R, box, 2000.0, 0.3, _params(agg_nmin=10), debug=True)
+    assert ten["flags"][0] & orc.BOX_NO_SEGMENT and not ten["flags"][0] & orc.BOX_VALID
+    assert np.isnan(ten["disp"][0])
+
+
+def test_far_box_is_one_block_at_full_resolution():
+    """Sec. 4.3.4: a box smaller than the far threshold is one block of up to
+    pts_side x pts_side points on the full-resolution grid, searched over the far
+    range; its disparity is that block's, with no aggregation."""
+    L, R = _textured_pair(200, 60, 5, seed=33, offset=10.0)
+    p = _params(far_side_px=40, close_factor=2, far_dmin=0, far_dmax=20, agg_nmin=9)
+    box = np.array([[120, 12, 150, 42, 0]], np.int32)  # 30 x 30 < 40: FAR
+    out = orc.match_frame(L, R, box, 2000.0, 0.3, p, debug=True)
+    b = out["blocks"][0]
+    assert out["flags"][0] & orc.BOX_FAR and out["flags"][0] & orc.BOX_VALID
+    assert b[0]["n_pts"] == 256 and b[0]["d_f"] == 5
+    assert np.all(b[1:]["flags"] == 0)  # no further blocks
+    assert out["disp"][0] == b[0]["d_full"] == b[0]["d_sub"]  # k = 1, no rescale
