@@ -25,16 +25,23 @@ _SO = os.path.join(_BUILD, "libctm_oracle.so")
 _lib = None
 
 
+def compile_source(src: str, so: str) -> str:
+    """gcc one oracle source file (plain C11, no fast-math, no FP contraction) into
+    the shared library ``so``; the header is found beside ``_SRC``."""
+    tmp = so + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-fno-fast-math",
+           "-ffp-contract=off", "-Wall", "-Wextra", "-I", _HERE, "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, so)
+    return so
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle shared library (idempotent)."""
     os.makedirs(_BUILD, exist_ok=True)
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
-        tmp = _SO + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-fno-fast-math",
-               "-ffp-contract=off", "-Wall", "-Wextra", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _SO)
+        compile_source(_SRC, _SO)
     return _SO
 
 

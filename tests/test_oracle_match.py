@@ -163,6 +163,23 @@ def test_backward_cost_at_forward_match_equals_forward_cost():
     assert checked > 20
 
 
+def test_backward_meets_forward_with_vertical_search():
+    """S_b(d_f, dy_f) = S_f(d_f, dy_f) on unrelated noise images with a vertical
+    search: the backward query sits at the matched right position (x - d_f,
+    y + dy_f), so at the forward match it pairs the same codes."""
+    rng = np.random.default_rng(41)
+    L = rng.integers(0, 256, (48, 90), dtype=np.uint8)
+    R = rng.integers(0, 256, (48, 90), dtype=np.uint8)
+    p = _params(win_w=5, win_h=5, close_dmin=-3, close_dmax=12, dy_min=-2, dy_max=2, grid_g=3,
+                pts_side=4, min_pts=1)
+    out = orc.match_frame(L, R, np.array([[30, 6, 78, 42, 0]], np.int32), 2000.0, 0.3, p, debug=True)
+    b = out["blocks"][0]
+    assert np.any(b["dy_f"] != 0)
+    for s in range(9):
+        c = (int(b[s]["dy_f"]) + 2) * 16 + int(b[s]["d_f"]) + 3
+        assert out["cost_b"][0, s, c] == out["cost_f"][0, s, c] == out["blocks"][0, s]["s_0"], s
+
+
 def test_mirrored_pair_forward_equals_original_backward():
     """Swap and mirror the pair: the object keeps its disparity, and with dense
     points the mirrored forward costs are the original backward costs of the
@@ -184,6 +201,25 @@ def test_mirrored_pair_forward_equals_original_backward():
         sm = b * 3 + (2 - a)
         assert np.array_equal(outm["cost_f"][0, sm], out["cost_b"][0, s])
     assert np.all(outm["blocks"][0]["d_f"] == d)
+
+
+@pytest.mark.parametrize("dy", [1, -2])
+def test_vertical_offset_found_forward_and_backward(dy):
+    """Sec. 4.3.3 with a vertical search: R(x - d, y + dy) = L(x, y).  The forward
+    search finds (d, dy) at zero cost; the backward search, queried at the matched
+    right position, finds the same (d, dy) at zero cost."""
+    d = 5
+    rng = np.random.default_rng(40 + dy)
+    big = np.clip(np.rint(wl.texture(rng, 80, 200)), 0, 255).astype(np.uint8)
+    L = big[10:70, 0:180]
+    R = big[10 - dy:70 - dy, d:180 + d]  # R[y + dy, x - d] = L[y, x]
+    p = _params(close_dmin=0, close_dmax=15, dy_min=-2, dy_max=2)
+    out = orc.match_frame(L, R, np.array([[90, 6, 138, 54, 0]], np.int32), 2000.0, 0.3, p, debug=True)
+    b = out["blocks"][0]
+    assert np.all(b["d_f"] == d) and np.all(b["dy_f"] == dy)
+    assert np.all(b["d_b"] == d) and np.all(b["dy_b"] == dy)
+    c = (dy + 2) * 16 + d
+    assert np.all(out["cost_f"][0, :, c] == 0) and np.all(out["cost_b"][0, :, c] == 0)
 
 
 def test_fb_rejects_inconsistent_match():
@@ -390,16 +426,19 @@ def test_half_resolution_rescale():
 
 # ---------------------------------------------------------------- Sec. 4.3.4 point grid
 
-@pytest.mark.parametrize("k", [1, 2])
-def test_point_columns_located_by_one_pixel_occluders(k):
+@pytest.mark.parametrize("k,dx", [(1, 0), (2, 0), (2, 1)])
+def test_point_grid_located_by_occluders(k, dx):
     """Sec. 4.3.4/4.3.5: a 32-px block (on the matching grid) with 16 points per side
     holds its points at the centres of 2-px cells, offsets 1, 3, ..., 31; an occluder
     hides a point when the point's full-resolution position k x lies in it.  A
     one-column occluder that reaches below the box therefore hides exactly the points
-    of one column (16 per block, two blocks deep) or none.  Which full-resolution
-    columns hide points is listed here in closed form, not from the sampling formula."""
+    of one column (16 per block, two blocks deep) or none; one reaching down from row
+    r hides the point rows at or below r.  Which full-resolution columns and rows
+    hold points is listed here in closed form, not from the sampling formula.
+    With k = 2 and an odd left edge (dx = 1) the box starts on the matching grid at
+    ceil(x0 / k): decimated pixel x is in the box iff its source pixel k x is."""
     side = 64 * k  # two 32-px blocks per axis on the matching grid
-    x0, y0 = 40 * k, 10 * k
+    x0, y0 = 40 * k - dx, 10 * k
     H, W = y0 + side + 40, x0 + side + 40
     rng = np.random.default_rng(21)
     L = np.clip(np.rint(wl.texture(rng, H, W)), 0, 255).astype(np.uint8)
@@ -414,6 +453,14 @@ def test_point_columns_located_by_one_pixel_occluders(k):
         hidden = 32 if c in cols else 0
         assert int(nv.sum()) == 4 * 256 - hidden, c
         assert np.all(out["blocks"][0]["n_pts"] == 256)
+    # rows: an occluder covering every row from r down past the box hides the 32
+    # points of each point row at or below r
+    rows = {k * (10 + 1 + 2 * m) for m in range(16)} | {k * (10 + 33 + 2 * m) for m in range(16)}
+    for r in range(y0 - 1, y0 + side + 1):
+        occ = [x0 - 3, r, x0 + side + 3, y0 + side + 5, 0]
+        out = orc.match_frame(L, L, np.array([box, occ], np.int32), 2000.0, 0.3, p, debug=True)
+        hidden = 32 * sum(1 for y in rows if y >= r)
+        assert int(out["blocks"][0]["n_valid"].sum()) == 4 * 256 - hidden, r
 
 
 def test_min_points_boundary_and_box_flags():
@@ -463,3 +510,45 @@ def test_far_box_is_one_block_at_full_resolution():
     assert b[0]["n_pts"] == 256 and b[0]["d_f"] == 5
     assert np.all(b[1:]["flags"] == 0)  # no further blocks
     assert out["disp"][0] == b[0]["d_full"] == b[0]["d_sub"]  # k = 1, no rescale
+
+
+def test_touching_box_is_no_occluder_under_the_cap():
+    """Sec. 4.3.5: occlusion needs overlapping boxes; a nearer box that only touches
+    the target's edge (half-open rectangles) takes no occluder slot."""
+    rng = np.random.default_rng(14)
+    L = np.clip(np.rint(wl.texture(rng, 120, 200)), 0, 255).astype(np.uint8)
+    a = [100, 20, 148, 68]
+    touch = [148, 10, 170, 100]  # shares a's right edge only; bottom 100
+    occ = [120, 40, 140, 80]     # overlaps; bottom 80
+    boxes = np.array([a + [0], touch + [0], occ + [0]], np.int32)
+    out = orc.match_frame(L, L, boxes, 2000.0, 0.3, _params(max_occluders=1), debug=True)
+    xs, ys = np.meshgrid(np.arange(100, 148), np.arange(20, 68))
+    hidden = (xs >= occ[0]) & (xs < occ[2]) & (ys >= occ[1]) & (ys < occ[3])
+    assert int(out["blocks"][0]["n_valid"].sum()) == int((~hidden).sum())
+
+
+def test_frontal_crop_upper_edge_is_open():
+    """Sec. 4.3.5 priority rule, crop edges: a centre on the crop's right edge
+    (doubled centre x0 + x1 = W (1 + c), exact in fp32 at c = 0.5) is not frontal, so
+    with one slot the frontal occluder is kept although the edge one is nearer."""
+    rng = np.random.default_rng(15)
+    L = np.clip(np.rint(wl.texture(rng, 120, 200)), 0, 255).astype(np.uint8)
+    a = [100, 20, 148, 68]
+    edge = [140, 30, 160, 90]   # doubled centre (300, 120): x on the open edge; bottom 90
+    front = [110, 40, 130, 75]  # doubled centre (240, 115): inside; bottom 75
+    boxes = np.array([a + [0], edge + [0], front + [0]], np.int32)
+    out = orc.match_frame(L, L, boxes, 2000.0, 0.3, _params(max_occluders=1, frontal_crop=0.5), debug=True)
+    xs, ys = np.meshgrid(np.arange(100, 148), np.arange(20, 68))
+    hidden = (xs >= front[0]) & (xs < front[2]) & (ys >= front[1]) & (ys < front[3])
+    assert int(out["blocks"][0]["n_valid"].sum()) == int((~hidden).sum())
+
+
+def test_far_box_searches_the_far_range():
+    """Sec. 4.3.4: FAR blocks search [far_dmin, far_dmax]; a shift of 1 px below
+    far_dmin = 2 is not found, the search ends at the range's lower end."""
+    L, R = _textured_pair(200, 60, 1, seed=34, offset=10.0)
+    p = _params(far_side_px=40, far_dmin=2, far_dmax=20, close_dmin=0, close_dmax=63)
+    out = orc.match_frame(L, R, np.array([[120, 12, 150, 42, 0]], np.int32), 2000.0, 0.3, p, debug=True)
+    b = out["blocks"][0][0]
+    assert out["flags"][0] & orc.BOX_FAR
+    assert b["d_f"] == 2 and b["flags"] & orc.BLK_SUBPIX_CLAMPED

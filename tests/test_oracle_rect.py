@@ -67,5 +67,19 @@ def test_filter_median_and_clamp():
     assert orc.rect_filter([3, 1, 2], 0, 5) == 2
     assert orc.rect_filter([3, 1, 2], 0, 1) == 1          # step clamped to +1
     assert orc.rect_filter([-6, -5, -7, 0], 0, 2) == -2   # even count: lower middle (-6), clamped
+    assert orc.rect_filter([-6, -5, -7, 0], 0, 10) == -6  # even count: lower middle
+    assert orc.rect_filter([2, 0], 0, 5) == 0
     assert orc.rect_filter([4], 3, 0) == 3                # no step allowed
     assert orc.rect_filter([], 7, 3) == 7
+
+
+def test_equal_counts_take_the_first_offset():
+    """delta* is the first offset with the largest count: on a pair whose rows are all
+    equal every offset counts the same ROI pixels, and the lowest offset wins."""
+    rng = np.random.default_rng(23)
+    row = np.clip(np.rint(wl.texture(rng, 1, 120)[0]), 0, 255).astype(np.uint8)
+    L = np.tile(row, (40, 1))
+    R = np.roll(L, -3, axis=1)
+    best, counts = orc.auto_rect(L, R, (20, 12, 100, 28), 0, 15, -2, 2, 1, win_w=5, win_h=3)
+    assert np.all(counts == counts[0]) and counts[0] > 0
+    assert best == -2
