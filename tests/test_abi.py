@@ -118,3 +118,57 @@ def test_box_points_argument_checks(built):
     assert L.ctm_box_points(None, None, None, 0, None, 0, None, None) == B.CTM_OK  # nothing to do
     assert L.ctm_box_points(None, None, None, 4, None, 1, None, None) == B.CTM_EINVAL
     assert L.ctm_box_points(None, None, None, -1, None, 0, None, None) == B.CTM_EINVAL
+
+
+def test_struct_fields_match_the_c_headers():
+    """Every field of every ctypes mirror (and of the numpy block and frame records)
+    sits at the offset and has the size a C compiler gives the header's struct:
+    a C program built from include/*.h prints offsetof/sizeof for each field."""
+    import shutil
+    import subprocess
+    import numpy as np
+    from paper_2604_07980_gb300 import binding as B
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    mirrors = {name: getattr(B, name) for name in
+               ("ctm_params", "ctm_frame", "ctm_debug", "ctm_stats", "ctm_geometry", "ctm_tuning",
+                "ctm_server_config", "ctm_request", "ctm_completion", "ctm_server_stats")}
+    records = {"ctm_block": B.BLOCK_DTYPE, "ctm_frame": B.FRAME_DTYPE}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ctm_server.h"', "int main(void) {"]
+    expect = {}
+    for sname, cls in mirrors.items():
+        lines.append(f'printf("{sname} %zu\\n", sizeof({sname}));')
+        expect[sname] = ctypes.sizeof(cls)
+        for fname, _ in cls._fields_:
+            key = f"{sname}.{fname}"
+            lines.append(f'printf("{key} %zu %zu\\n", offsetof({sname}, {fname}), '
+                         f'sizeof((({sname} *)0)->{fname}));')
+            d = getattr(cls, fname)
+            expect[key] = (d.offset, d.size)
+    rec_expect = {}
+    for sname, dt in records.items():
+        lines.append(f'printf("{sname} %zu\\n", sizeof({sname}));')
+        rec_expect[sname] = dt.itemsize
+        for fname in dt.names:
+            key = f"{sname}.{fname}"
+            lines.append(f'printf("{key} %zu %zu\\n", offsetof({sname}, {fname}), '
+                         f'sizeof((({sname} *)0)->{fname}));')
+            rec_expect[key] = (dt.fields[fname][1], dt.fields[fname][0].itemsize)
+    lines += ["return 0;", "}"]
+    out_dir = os.path.join(ROOT, "paper_2604_07980_gb300", "_build")
+    os.makedirs(out_dir, exist_ok=True)
+    src = os.path.join(out_dir, "abi_layout.c")
+    exe = os.path.join(out_dir, "abi_layout")
+    with open(src, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    subprocess.run([cc, "-std=c11", "-Wall", "-I", os.path.join(ROOT, "include"), "-o", exe, src], check=True)
+    got = {}
+    for line in subprocess.run([exe], check=True, capture_output=True, text=True).stdout.splitlines():
+        parts = line.split()
+        got[parts[0]] = int(parts[1]) if len(parts) == 2 else (int(parts[1]), int(parts[2]))
+    for key, want in expect.items():
+        assert got[key] == want, (key, got[key], want)
+    for key, want in rec_expect.items():
+        assert got[key] == want, (key, got[key], want)
+    assert np.dtype(B.BLOCK_DTYPE).itemsize == B.BLOCK_BYTES
