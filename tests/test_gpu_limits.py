@@ -81,3 +81,55 @@ def test_parameter_limits(name):
         else:
             assert ref["cost_f"].max() <= blk["n_valid"].max()
     ctx.close()
+
+
+def _parity_batch(torch, w, params, where):
+    from paper_2604_07980_gb300 import binding as B
+    H = max(f.left.shape[0] for f in w.frames)
+    W = max(f.left.shape[1] for f in w.frames)
+    frames = [(f.left, f.right, f.f_px, f.baseline_m) for f in w.frames]
+    ref = orc.match_batch(frames, w.boxes, orc.Params(**params), debug=True)
+    ctx = B.Context(params, len(w.frames), W, H, len(w.boxes))
+    batch = B.DeviceBatch(B.frames_to_device(w.frames), w.boxes, [(f.f_px, f.baseline_m) for f in w.frames])
+    got = ctx.match_batch(batch, use_graph=True, debug=True)
+    torch.cuda.synchronize()
+    out = {k: v.cpu().numpy() for k, v in got.items() if k != "debug"}
+    compare_box_outputs(out, ref, where)
+    dbg = got["debug"]
+    compare_debug_arrays(dbg.blocks_np(), dbg.cost_f.cpu().numpy(), dbg.cost_b.cpu().numpy(), ref,
+                         B.n_candidates(ctx.params), where)
+    st = ctx.stats()
+    assert st["error"] == 0, where
+    assert st["cost_evals"] == oracle_evals(ref["blocks"], ref["flags"], params), where
+    ctx.close()
+    return ref
+
+
+@pytest.mark.parametrize("W,H", [(32768, 40), (80, 32768)])
+def test_widest_and_tallest_frames(W, H):
+    """The largest frame sides the library accepts (32768 px): the census tile list
+    packs the tile index and the row into 10 and 16 bits; boxes at the far end of the
+    long side and across it."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    params = dict(wl.PARAMS["frame1080"])
+    params.update(far_dmax=31, close_dmax=63)
+    w = wl.multi_frame("frame1080", 9200 + W % 7, 1, W, H, 24, (6.0, 38.0), (0.5, 20.0), (2.0, 40.0))
+    extra = np.array([[W - 30, H - 36, W + 10, H - 2, 0], [W - 37, H - 39, W - 1, H - 1, 0],
+                      [-5, -5, 30, 30, 0]], np.int32)
+    w.boxes = np.concatenate([w.boxes, extra])
+    ref = _parity_batch(torch, w, params, f"{W}x{H}")
+    assert np.any(ref["flags"] & orc.BOX_VALID)
+
+
+def test_many_small_frames_in_one_batch():
+    """300 frames of 96x64 in one batch (frame indices well past a byte), two boxes each."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    params = dict(wl.PARAMS["frame1080"])
+    params.update(far_dmax=15, close_dmax=31, grid_g=2)
+    w = wl.multi_frame("frame1080", 9300, 300, 96, 64, 2, (8.0, 60.0), (0.5, 10.0), (2.0, 20.0))
+    ref = _parity_batch(torch, w, params, "300 frames")
+    assert np.any(ref["flags"] & orc.BOX_VALID)
