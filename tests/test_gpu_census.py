@@ -64,3 +64,22 @@ def test_census_word_loads_straddling_the_row_end(torch_cuda, k, width):
         got = B.census_build(t, k, *win, 1).cpu().numpy().view(np.uint64)
         ref = orc.census(np.ascontiguousarray(img), k, *win, 1)
         assert np.array_equal(got, ref), (win, np.argwhere(got != ref)[:5].tolist())
+
+
+@pytest.mark.parametrize("shape", [(70, 300), (9, 4099)])
+@pytest.mark.parametrize("win", [(15, 3), (3, 15), (13, 3), (7, 9), (1, 1)])
+@pytest.mark.parametrize("k", [1, 4, 8, 64])
+def test_census_window_and_factor_limits(torch_cuda, shape, win, k):
+    """The widest and tallest windows (15 px), 64-bit codes (7x9 plus the sentinel),
+    the 1x1 window (the sentinel alone), and decimation factors up to the largest
+    accepted (64), on a tall-enough image and on a 9-row strip 4099 px wide."""
+    from paper_2604_07980_gb300 import binding as B
+    rng = np.random.default_rng(shape[1] * 1000 + win[0] * 100 + win[1] * 10 + k)
+    img = rng.integers(0, 256, size=shape, dtype=np.uint8)
+    img[:, : shape[1] // 5] = 200  # flat region with ties
+    for s in (0, 1):
+        got = B.census_build(torch_cuda.from_numpy(img).cuda(), k, *win, s).cpu().numpy().view(np.uint64)
+        ref = orc.census(img, k, *win, s)
+        assert got.shape == ref.shape
+        bad = np.argwhere(got != ref)
+        assert bad.size == 0, f"{win} k {k} sentinel {s}: mismatch at {bad[:5].tolist()}"
