@@ -165,3 +165,40 @@ def test_serving_plain_mode_same_outputs(torch_cuda, trace):
     p.close()
     for key in alone:
         _same(plain[key], alone[key], f"plain frame {key}")
+
+
+@pytest.mark.parametrize("plain", [0, 1])
+def test_serving_frames_without_boxes(torch_cuda, trace, plain):
+    """Frames with no boxes, or only boxes outside the image, complete with status 0
+    beside ordinary frames, alone and in a mix, and leave the others' outputs unchanged."""
+    from paper_2604_07980_gb300 import binding as B
+    pinned = _pinned(torch_cuda, trace)
+    lanes, fpb = (1, 1) if plain else (2, 4)
+    srv = B.Server(trace.params, lanes=lanes, frames_per_batch=fpb, plain=plain)
+    alone = _alone(srv, trace, pinned)
+    s0 = [i for i, st_ in enumerate(trace.streams) if st_.width == 1280][0]
+    fr0 = trace.streams[s0].frames[0]
+    L0, R0 = pinned[s0][0]
+    outside = np.array([[2000, 10, 2100, 90, 0], [-50, -50, -1, 20, 0]], np.int32)
+    t_empty = srv.submit(L0, R0, np.zeros((0, 5), np.int32), fr0.f_px, fr0.baseline_m)
+    (res,) = srv.wait_all()
+    assert res["tag"] == t_empty and res["status"] == 0 and res["n_boxes"] == 0
+    tags = {}
+    for rep in range(2):
+        for s in range(len(trace.streams)):
+            fr = trace.streams[s].frames[rep]
+            tags[srv.submit(*pinned[s][rep], trace.streams[s].boxes[rep], fr.f_px, fr.baseline_m)] = (s, rep)
+            tags[srv.submit(L0, R0, np.zeros((0, 5), np.int32), fr0.f_px, fr0.baseline_m)] = "none"
+        tags[srv.submit(L0, R0, outside, fr0.f_px, fr0.baseline_m)] = "outside"
+    done = srv.wait_all()
+    assert len(done) == len(tags)
+    for r in done:
+        assert r["status"] == 0
+        key = tags[r["tag"]]
+        if key == "none":
+            assert r["n_boxes"] == 0
+        elif key == "outside":
+            assert r["n_boxes"] == 2 and np.all(r["flags"] & 32) and np.all(np.isnan(r["disp"]))
+        else:
+            _same(r, alone[key], f"frame {key} beside frames without boxes")
+    srv.close()
