@@ -61,6 +61,8 @@ MUTATIONS = [
      M, "test_point_grid_located_by_occluders", {"k": 2, "dx": 0}),
     ("frontal crop closed on the right", "sx < (float)W * (1.0f + c)", "sx <= (float)W * (1.0f + c)",
      M, "test_frontal_crop_upper_edge_is_open", {}),
+    ("frontal occluders ranked last", "if (fa != fb) return fa > fb;", "if (fa != fb) return fa < fb;",
+     M, "test_frontal_crop_priority_when_occluders_exceed_the_cap", {}),
     ("farthest occluders kept", "if (cb[a].y1 != cb[b].y1) return cb[a].y1 > cb[b].y1;",
      "if (cb[a].y1 != cb[b].y1) return cb[a].y1 < cb[b].y1;",
      M, "test_equal_bottoms_do_not_occlude_and_cap_keeps_nearest", {}),
@@ -119,6 +121,8 @@ MUTATIONS = [
      P, "test_standard_q_closed_form_and_eq1", {}),
     ("translation dropped", " + g->T[4 * r + 2] * p[2] + g->T[4 * r + 3];", " + g->T[4 * r + 2] * p[2];",
      P, "test_vehicle_transform", {}),
+    ("reprojected box not clipped", "const int x1 = b[2] < g->width ? b[2] : g->width,",
+     "const int x1 = b[2],", P, "test_invalid_cases_are_nan_and_boxes_are_clipped", {}),
     ("variance with Z squared", "o[6] = Z * Z * Z * Z * g->disp_var / (fb * fb);",
      "o[6] = Z * Z * g->disp_var / (fb * fb);", P, "test_variance_is_squared_depth_derivative", {}),
     # Sec. 5.1 offset search and filter
@@ -126,6 +130,8 @@ MUTATIONS = [
      "if (dx <= fb_tol && d_f >= d_thresh) ++count;", R, "test_counts_equal_brute_force", {}),
     ("offset backward search unshifted", "code_at(CL, W, H, x - d_f + d, y + delta));",
      "code_at(CL, W, H, x - d_f + d, y));", R, "test_counts_equal_brute_force", {}),
+    ("offset forward argmin takes the last tie", "if (s_d < s_best) { s_best = s_d; d_f = d; }",
+     "if (s_d <= s_best) { s_best = s_d; d_f = d; }", R, "test_counts_equal_brute_force", {}),
     ("offset tie takes the last", "if (count > best_count) {", "if (count >= best_count) {",
      R, "test_equal_counts_take_the_first_offset", {}),
     ("filter takes the upper middle", "const int med = v[(n - 1) / 2];", "const int med = v[n / 2];",
