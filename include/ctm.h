@@ -46,8 +46,9 @@ typedef struct CUstream_st *ctm_stream;
 #define CTM_ENODEV (-4)   /* no usable CUDA device */
 #define CTM_ETOOBIG (-5)  /* beyond a fixed limit: ctm_match_boxes_noalloc's maxima, a server's frame size or arena */
 #define CTM_EAGAIN (-6)   /* a server's admission queue is full; nothing was queued */
-#define CTM_ETIMEOUT (-7) /* a bounded device-side wait expired: the call's outputs are incomplete
-                             (returned by synchronous calls; asynchronous ones set ctm_stats.error) */
+#define CTM_ETIMEOUT (-7) /* a bounded device-side wait expired: every box of the call that needed
+                             a search has flags 0 and NaN outputs (returned by synchronous calls;
+                             asynchronous ones set ctm_stats.error) */
 
 /* Per-box flags (uint8), written by the match calls. */
 #define CTM_BOX_VALID 0x01           /* disparity > 0 found; disp/depth finite         */
@@ -58,6 +59,9 @@ typedef struct CUstream_st *ctm_stream;
 #define CTM_BOX_EMPTY 0x20           /* box empty after clipping to the image           */
 #define CTM_BOX_SUBPIX_CLAMPED 0x40  /* a valid block's argmin sat at a range end       */
 #define CTM_BOX_FAR 0x80             /* classified FAR (matched at full resolution)     */
+/* A box that needed a search carries flags 0 (neither VALID nor any reason bit)
+ * and NaN disparity and depth when a bounded device wait of its call expired:
+ * some of its blocks may not have been searched, so it is not aggregated. */
 
 /* Per-block flags (ctm_block.flags). */
 #define CTM_BLK_VALID 0x01
@@ -251,19 +255,21 @@ int ctm_match_batch_host(ctm_ctx *ctx, const ctm_frame *frames_host, int n_frame
                          float *depth_host, uint8_t *flags_host, ctm_stream stream);
 
 /* Single-frame matching that allocates no device memory -- the paper has no
- * counterpart; it exists for callers that cannot call cudaMalloc (code inside a
- * captured CUDA graph region, real-time loops that must not touch the device
- * allocator, hosts that give this library a fixed memory budget).  Same inputs,
- * outputs and results as ctm_match_boxes without a context: `p` is the parameter
- * block, all other arguments as there.  Limits: width <= 640, height <= 480,
- * n_boxes <= 64; larger requests return CTM_ETOOBIG.  The workspace is one
- * 8 MiB array in static device memory that every GPU loading the library holds
- * until exit.  The first call on a device does a one-time set-up with that device
- * current (looks up the array's device address, raises the matching kernel's
- * shared-memory limit), so make it before any stream capture.  All calls share
- * the array and it keeps the previous call's contents (each call clears what must
- * start at zero); calls that overlap on the GPU race.  Not thread-safe.  Calls no
- * cudaMalloc, cudaFree or allocating library routine.
+ * counterpart.  It is for callers that cannot call cudaMalloc while they run:
+ * real-time control loops, where an allocation can synchronize the device and
+ * take an unbounded time, and hosts that give this library a fixed memory budget
+ * when it starts.  Same inputs, outputs and results as ctm_match_boxes without a
+ * context: `p` is the parameter block, all other arguments as there.  Limits:
+ * width <= 640, height <= 480, n_boxes <= 64; larger requests return
+ * CTM_ETOOBIG.  The workspace is one 8 MiB array in static device memory that
+ * every GPU loading the library holds until exit.  The first call on a device
+ * does a one-time set-up with that device current (looks up the array's device
+ * address, raises the matching kernel's shared-memory limit), so make it before
+ * any stream capture.  All calls share the array and it keeps the previous
+ * call's contents (each call clears what must start at zero); calls that overlap
+ * on the GPU race.  Not thread-safe.  Calls no cudaMalloc, cudaFree or
+ * allocating library routine.  A bounded-wait expiry leaves the outputs as the
+ * CTM_ETIMEOUT rule says and the flag in ctm_noalloc_get_stats.
  * Errors: CTM_EINVAL, CTM_ETOOBIG, CTM_ENODEV, CTM_ECUDA. */
 int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_dev, const uint8_t *right_dev,
                             int width, int height, int pitch, const ctm_box *boxes_dev, int n_boxes,
@@ -272,6 +278,13 @@ int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_dev, const 
 
 /* Counters of the most recent match call on ctx.  Synchronizes `stream`. */
 int ctm_get_stats(ctm_ctx *ctx, ctm_stats *out, ctm_stream stream);
+
+/* Counters of the most recent ctm_match_boxes_noalloc call on the current
+ * device (error != 0: a bounded device wait of that call expired), read from
+ * the static array after synchronizing `stream`; allocates nothing.
+ * Errors: CTM_EINVAL (null out, or no such call on this device yet),
+ * CTM_ENODEV, CTM_ECUDA. */
+int ctm_noalloc_get_stats(ctm_stats *out, ctm_stream stream);
 
 /* Camera geometry of one frame for ctm_box_points (Sec. 4.3.6). */
 typedef struct {
@@ -350,6 +363,19 @@ int ctm_autotune(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *count
  * mask, 3: 32-bit add, 4: 32-bit multiply-add -- and returns the operations
  * per SM clock per SM.  Synchronizes the device.  Errors: CTM_EINVAL, CTM_ECUDA. */
 int ctm_probe_int_rate(int kind, int iters, double *ops_per_clk_per_sm);
+
+/* Fault injection for tests (no counterpart in the paper): arms ctx so that the
+ * next match call on it that launches the fused persistent matcher directly
+ * (ctm_match_boxes, ctm_match_batch with use_graph = 0, ctm_match_batch_host;
+ * tuning match_mode 0; not a graph replay, not the plain per-box path) has its
+ * first matching CTA announce a strip copy on its mbarrier without issuing it.
+ * That CTA's bounded wait then expires (about 1 s, then about 1 s more for the
+ * copies in flight, of which there are none), it records the error and stops;
+ * the other CTAs finish the queue.  The call's outputs follow the CTM_ETIMEOUT
+ * rule above, and ctm_match_batch_host returns CTM_ETIMEOUT.  The arming is
+ * consumed by that one call; the context stays usable.  No GPU fault is
+ * involved.  Errors: CTM_EINVAL (null ctx). */
+int ctm_inject_wait_expiry(ctm_ctx *ctx);
 
 /* Bounded-wait probe (no counterpart in the paper): one CTA waits, with the
  * matching kernels' own bounded-wait routine, on an mbarrier phase that nothing

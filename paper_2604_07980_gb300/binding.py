@@ -27,7 +27,9 @@ BLK_VALID, BLK_FB_REJECT, BLK_FEW_POINTS, BLK_SUBPIX_CLAMPED, BLK_PRESENT = 1, 2
 EXPORTS = ("ctm_status_str", "ctm_default_params", "ctm_create", "ctm_destroy",
            "ctm_census_build", "ctm_match_boxes", "ctm_match_boxes_plain", "ctm_match_batch",
            "ctm_match_batch_profiled", "ctm_match_batch_host", "ctm_match_boxes_noalloc",
-           "ctm_get_stats", "ctm_probe_int_rate", "ctm_probe_bounded_wait", "ctm_get_tuning",
+           "ctm_noalloc_get_stats",
+           "ctm_get_stats", "ctm_probe_int_rate", "ctm_probe_bounded_wait", "ctm_inject_wait_expiry",
+           "ctm_get_tuning",
            "ctm_set_tuning", "ctm_autotune",
            "ctm_box_points", "ctm_auto_rect", "ctm_rect_filter",
            "ctm_server_default_config", "ctm_server_create", "ctm_server_submit", "ctm_server_poll",
@@ -164,10 +166,14 @@ def lib():
     L.ctm_match_boxes_noalloc.restype = i32
     L.ctm_get_stats.argtypes = [vp, ctypes.POINTER(ctm_stats), vp]
     L.ctm_get_stats.restype = i32
+    L.ctm_noalloc_get_stats.argtypes = [ctypes.POINTER(ctm_stats), vp]
+    L.ctm_noalloc_get_stats.restype = i32
     L.ctm_probe_int_rate.argtypes = [i32, i32, ctypes.POINTER(ctypes.c_double)]
     L.ctm_probe_int_rate.restype = i32
     L.ctm_probe_bounded_wait.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
     L.ctm_probe_bounded_wait.restype = i32
+    L.ctm_inject_wait_expiry.argtypes = [vp]
+    L.ctm_inject_wait_expiry.restype = i32
     L.ctm_auto_rect.argtypes = [ctypes.POINTER(ctm_params), vp, vp] + [i32] * 13 + [vp, vp, vp, vp]
     L.ctm_auto_rect.restype = i32
     L.ctm_rect_filter.argtypes = [vp, i32, i32, i32]
@@ -207,7 +213,9 @@ def lib():
 def _check(status: int, what: str):
     if status != CTM_OK:
         msg = lib().ctm_status_str(status).decode()
-        raise CtmError(f"{what}: {msg} ({status})")
+        err = CtmError(f"{what}: {msg} ({status})")
+        err.status = status
+        raise err
 
 
 def _torch():
@@ -430,6 +438,10 @@ class Context:
                                   _ptr(batch.disp), _ptr(batch.depth), _ptr(batch.flags), int(reps),
                                   ctypes.byref(t), ctypes.byref(ms), _stream(stream)), "ctm_autotune")
         return t.as_dict(), float(ms.value)
+
+    def inject_wait_expiry(self):
+        """Arm the test-only fault injection (ctm_inject_wait_expiry) for the next direct call."""
+        _check(lib().ctm_inject_wait_expiry(self._h), "ctm_inject_wait_expiry")
 
     def stats(self, stream=None) -> dict:
         s = ctm_stats()

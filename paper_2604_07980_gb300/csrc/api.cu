@@ -43,6 +43,7 @@ struct ctm_ctx {
     int big_work = 4096;
     int match_mode = 0;
     int nd_max = 0;
+    int inject_expiry = 0;  // armed by ctm_inject_wait_expiry (tests)
     void *dev_mem = nullptr;
     size_t dev_bytes = 0;
     cudaStream_t capture_stream = nullptr;
@@ -67,7 +68,11 @@ namespace {
 
 inline long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
 
-bool params_valid(const ctm_params &p)
+}  // namespace
+
+// Parameter limits of include/ctm.h, plus the shared-memory budget of the
+// matcher's strip (shared by ctm_create and ctm_match_boxes_noalloc).
+bool ctm::params_valid(const ctm_params &p)
 {
     if (p.win_w < 1 || p.win_h < 1 || (p.win_w & 1) == 0 || (p.win_h & 1) == 0) return false;
     if (p.win_w > kMaxWin || p.win_h > kMaxWin) return false;
@@ -86,8 +91,17 @@ bool params_valid(const ctm_params &p)
     if (!(p.agg_tau_d == p.agg_tau_d)) return false;
     if (p.max_occluders < 0 || p.max_occluders > kMaxOcc) return false;
     if (!(p.frontal_crop >= 0.0f && p.frontal_crop <= 1.0f)) return false;
+    const int nd_max = std::max(p.far_dmax - p.far_dmin + 1, p.close_dmax - p.close_dmin + 1);
+    if ((long long)2 * ndy * default_strip_cols(nd_max) * 8 * 4 > 160 * 1024) return false;
     return true;
 }
+
+// Default strip width (one sampled row per piece): the disparity range plus a
+// 64-column span of points, at least 128 codes, in multiples of 32; wider
+// blocks are chunked.
+int ctm::default_strip_cols(int nd_max) { return (int)round_up(std::max(nd_max + 64, 128), 32); }
+
+namespace {
 
 MatchArgs make_args(const ctm_ctx *ctx, const ctm_frame *frames, const int32_t *counts,
                     const ctm_box *boxes, float *disp, float *depth, uint8_t *flags,
@@ -113,17 +127,24 @@ MatchArgs make_args(const ctm_ctx *ctx, const ctm_frame *frames, const int32_t *
     a.census_mode = ctx->census_mode;
     a.match_mode = ctx->match_mode;
     a.stats_accumulate = 0;
+    a.inject_expiry = 0;
     return a;
 }
 
 // The launch sequence of one match call after the frame descriptors and counts
 // are in device memory: planning, census demand marking, census of the marked
-// tiles, matching.
+// tiles, matching.  direct: launched now, not captured into a graph (an armed
+// fault injection applies to such a launch of the fused persistent matcher
+// only, and is then disarmed).
 int enqueue_match(ctm_ctx *ctx, const MatchArgs &a, int frames_grid, int match_grid, cudaStream_t s,
-                  bool plain, int n_boxes_host)
+                  bool plain, int n_boxes_host, bool direct = true)
 {
     MatchArgs b = a;
     b.caps.max_frames = std::min(ctx->caps.max_frames, frames_grid);
+    if (direct && !plain && ctx->match_mode == 0 && ctx->inject_expiry) {
+        b.inject_expiry = 1;
+        ctx->inject_expiry = 0;
+    }
     cudaError_t e = launch_plan(b, s);
     if (e == cudaSuccess) e = launch_sample(b, s);
     if (e == cudaSuccess) e = launch_census_roi(b, ctx->sm_count, s);
@@ -225,11 +246,7 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
     ctx->nc_stride = nd_max * ndy;
     ctx->nd_max = nd_max;
     ctx->strip_rows = p->pts_side * ndy;
-    // strip piece width (one sampled row per piece, double-buffered per warp): the
-    // disparity range plus a 64-column span of points; wider rows are chunked
-    const int cols = (int)round_up(std::max(nd_max + 64, 128), 32);
-    if ((long long)2 * ndy * cols * 8 * 4 > 160 * 1024) { delete ctx; return CTM_EINVAL; }
-    ctx->strip_cols = cols;
+    ctx->strip_cols = default_strip_cols(nd_max);
 
     // workspace layout (one allocation)
     const long long pitch1 = round_up(max_width, 32);
@@ -422,7 +439,7 @@ int ctm_match_batch(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *co
         cudaGraph_t graph = nullptr;
         if (cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return CTM_ECUDA;
-        const int r = enqueue_match(ctx, a, ctx->caps.max_frames, grid, ctx->capture_stream, false, 0);
+        const int r = enqueue_match(ctx, a, ctx->caps.max_frames, grid, ctx->capture_stream, false, 0, false);
         const cudaError_t e = cudaStreamEndCapture(ctx->capture_stream, &graph);
         if (r != CTM_OK || e != cudaSuccess || !graph) {
             if (graph) cudaGraphDestroy(graph);
@@ -716,9 +733,10 @@ int ctm_autotune(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *count
         if (r != CTM_OK) return r;
         MatchArgs a = make_args(ctx, frames_dev, counts_dev, boxes_dev, disp_dev, depth_dev, flags_dev, nullptr);
         const int grid = ctx->sm_count * ctx->ctas_per_sm;
-        r = enqueue_match(ctx, a, ctx->caps.max_frames, grid, s, false, 0);
+        r = enqueue_match(ctx, a, ctx->caps.max_frames, grid, s, false, 0, false);
         if (r == CTM_OK && cudaEventRecord(e0, s) != cudaSuccess) r = CTM_ECUDA;
-        for (int i = 0; i < reps && r == CTM_OK; ++i) r = enqueue_match(ctx, a, ctx->caps.max_frames, grid, s, false, 0);
+        for (int i = 0; i < reps && r == CTM_OK; ++i)
+            r = enqueue_match(ctx, a, ctx->caps.max_frames, grid, s, false, 0, false);
         if (r == CTM_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
             r = CTM_ECUDA;
         float t_ms = 0.0f;
@@ -808,6 +826,13 @@ int ctm_probe_int_rate(int kind, int iters, double *ops_per_clk_per_sm)
 {
     if (kind < 0 || kind > 4 || iters < 1 || !ops_per_clk_per_sm) return CTM_EINVAL;
     return run_int_probe(kind, iters, ops_per_clk_per_sm) == cudaSuccess ? CTM_OK : CTM_ECUDA;
+}
+
+int ctm_inject_wait_expiry(ctm_ctx *ctx)
+{
+    if (!ctx) return CTM_EINVAL;
+    ctx->inject_expiry = 1;
+    return CTM_OK;
 }
 
 int ctm_probe_bounded_wait(int *expired, float *waited_ms)

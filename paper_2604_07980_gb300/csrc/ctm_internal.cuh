@@ -129,6 +129,8 @@ struct MatchArgs {
     int census_mode;           // region-of-interest census variant (census.cu)
     int strip_rows;            // rows of the shared-memory strip (pts_side * ndy)
     int stats_accumulate;      // 1: the aggregation adds the call's counters to the stats record
+    int inject_expiry;         // fault injection for tests: CTA 0 of the fused persistent matcher
+                               // withholds its first strip copy, so its bounded wait expires
 };
 
 __host__ __device__ inline int ceil_div_nn(int a, int b) { return (a + b - 1) / b; }
@@ -196,6 +198,11 @@ cudaError_t launch_match_pipe(const MatchArgs &a, int threads, int grid, cudaStr
 // Probes (probe.cu)
 cudaError_t run_int_probe(int kind, int iters, double *ops_per_clk_per_sm);
 cudaError_t run_wait_probe(int *expired, float *waited_ms);
+
+// Parameter checks of ctm_create (limits in include/ctm.h and the matcher's
+// strip budget) and the default strip width for a disparity range (api.cu).
+bool params_valid(const ctm_params &p);
+int default_strip_cols(int nd_max);
 
 // Device address of the error flag of a context's last finished call
 // (ctm_stats.error), for callers that read it back on their own stream.

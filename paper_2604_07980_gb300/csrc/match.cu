@@ -67,9 +67,12 @@ __device__ __forceinline__ int chunk_row_y(const MatchArgs &a, const BlockCtx &b
 }
 
 // Warp 0: issue the bulk copies of one strip chunk (completion on sh.mbar).
+// withhold (fault injection for tests only): announce bytes on the mbarrier but
+// issue no copy, so the phase never completes and the bounded wait expires.
 template <int NT>
 __device__ __forceinline__ void issue_chunk(const MatchArgs &a, const BlockCtx &bc, const Smem &sm,
-                                            Shared<NT / 32> &sh, bool fwd, int dy_f, const ChunkGeom &g)
+                                            Shared<NT / 32> &sh, bool fwd, int dy_f, const ChunkGeom &g,
+                                            bool withhold = false)
 {
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid >= 32) return;
@@ -88,11 +91,11 @@ __device__ __forceinline__ void issue_chunk(const MatchArgs &a, const BlockCtx &
     // order earlier generic-proxy accesses of the strip before the bulk writes
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     if (lane == 0) {
-        mbar_arrive_expect_tx(&sh.mbar, total);
+        mbar_arrive_expect_tx(&sh.mbar, withhold ? total + 16u : total);
         sh.spend = 1;
     }
     __syncwarp();
-    if (row_bytes > 0) {
+    if (row_bytes > 0 && !withhold) {
         for (int r = lane; r < rows; r += 32) {
             const int y = chunk_row_y(a, bc, sh.Y, fwd, dy_f, r);
             if (y >= 0 && y < bc.Hs)
@@ -289,8 +292,10 @@ __device__ __forceinline__ BlockCtx make_ctx(const MatchArgs &a, const BlockGeom
 // and rows, the left codes at its points (cp.async) and its first forward strip
 // chunk (bulk copies on sh.mbar).  Nothing is waited for here; the strip, the
 // point arrays and sh.X / sh.Y must be free (the previous block's scans done).
+// withhold: see issue_chunk.
 template <int NT>
-__device__ void begin_block(const MatchArgs &a, int b, const Smem &sm, Shared<NT / 32> &sh, int gbuf)
+__device__ void begin_block(const MatchArgs &a, int b, const Smem &sm, Shared<NT / 32> &sh, int gbuf,
+                            bool withhold = false)
 {
     const int tid = threadIdx.x;
     const BlockGeom &g = sh.geom[gbuf];
@@ -317,7 +322,7 @@ __device__ void begin_block(const MatchArgs &a, int b, const Smem &sm, Shared<NT
     if (tid <= kMaxPtsSide) sh.colstart[tid] = tid < bc.nx ? g.colprefix[tid] : total;
     if (tid == 0) sh.cstart = g.cstart;
     __syncthreads();  // sh.Y is read by the issuing warp
-    issue_chunk<NT>(a, bc, sm, sh, true, 0, g0);
+    issue_chunk<NT>(a, bc, sm, sh, true, 0, g0, withhold);
 }
 
 // Prefetch state of the persistent kernel.  A single-block launch has none.
@@ -526,7 +531,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
             if (threadIdx.x == 0) sh.gpend = 0;
             int b = sh.next_b;
             int buf = 0;
-            begin_block<NT>(a, b, sm, sh, buf);
+            begin_block<NT>(a, b, sm, sh, buf, a.inject_expiry != 0 && blockIdx.x == 0);
             for (;;) {
                 pf.buf = buf ^ 1;
                 if (!process_block<NT>(a, b, sm, sh, phase, buf, pf, gphase, evals)) {

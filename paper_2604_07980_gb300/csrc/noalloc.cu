@@ -1,20 +1,24 @@
 // noalloc.cu -- single-frame matching that allocates no device memory.
 //
-// Some callers cannot call cudaMalloc: code running inside a captured CUDA
-// graph region, real-time loops that must not touch the device allocator, and
-// hosts that hand the GPU to this library with a fixed memory budget.  For them
-// ctm_match_boxes_noalloc runs the same launch sequence as ctm_match_boxes, but
-// its workspace is carved from one file-scope __device__ array of fixed size,
-// which every GPU that loads the library holds until the process exits.
+// Some callers of this library cannot call cudaMalloc while they run: a
+// real-time control loop must not enter the device allocator, because an
+// allocation can synchronize the device and take an unbounded time; and a host
+// that gives the library a fixed memory budget when it starts does not let it
+// grow its footprint later.  For them ctm_match_boxes_noalloc runs the same
+// launch sequence as ctm_match_boxes, but its workspace is carved from one
+// file-scope __device__ array of a fixed 8 MiB, which every GPU that loads the
+// library holds until the process exits; frames up to 640x480 with 64 boxes fit.
 //
 // Set-up happens on the first call on each device (with that device current):
 // the array's device address is taken with cudaGetSymbolAddress -- in host code
-// the array's name is only a host-side stand-in -- and the matching kernels'
-// shared-memory limit is raised.  That first call should therefore come before
-// any stream capture.  All calls share the one array and it keeps the previous
-// call's contents: each call clears what must start at zero (the census demand
-// bitmap; the planner resets its own counters), and calls that overlap on the
-// GPU race on the array.
+// the array's name is only a host-side stand-in, not a device address -- and
+// the matching kernel's shared-memory limit is raised.  That first call should
+// therefore come before any stream capture.  All calls share the one array and
+// it keeps the previous call's contents: each call clears what must start at
+// zero (the census demand bitmap, the counters, the block counts), and calls
+// that overlap on the GPU race on the array.  The counters of the last call
+// (its bounded-wait flag included) sit at a fixed place at the array's start,
+// where ctm_noalloc_get_stats reads them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,33 +37,16 @@ struct DeviceState {
     bool ready;
     unsigned char *base;  // device address of g_noalloc_scratch on this device
     int sm_count;
+    int match_need;       // matching kernel's shared-memory bytes last configured (0: none)
+    int match_ctas;       // its resident CTAs per SM at that size
 };
 DeviceState g_state[kMaxDevices];
 
 inline long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
 
-bool params_ok(const ctm_params &p)
-{
-    using namespace ctm;
-    if (p.win_w < 1 || p.win_h < 1 || (p.win_w & 1) == 0 || (p.win_h & 1) == 0) return false;
-    if (p.win_w > kMaxWin || p.win_h > kMaxWin) return false;
-    if (p.win_w * p.win_h + (p.sentinel ? 1 : 0) > 64) return false;
-    if (p.sentinel != 0 && p.sentinel != 1) return false;
-    if (p.close_factor < 1 || p.close_factor > 8) return false;
-    if (p.far_dmin > p.far_dmax || p.close_dmin > p.close_dmax || p.dy_min > p.dy_max) return false;
-    const long long ndy = (long long)p.dy_max - p.dy_min + 1;
-    if (((long long)p.far_dmax - p.far_dmin + 1) * ndy > kMaxCand) return false;
-    if (((long long)p.close_dmax - p.close_dmin + 1) * ndy > kMaxCand) return false;
-    if (p.grid_g < 1 || p.grid_g > kMaxGrid) return false;
-    if (p.pts_side < 1 || p.pts_side > kMaxPtsSide) return false;
-    if (p.min_pts < 1 || p.fb_tol < 0 || p.agg_nmin < 1) return false;
-    if (p.agg_mode != 0 && p.agg_mode != 1) return false;
-    if (!(p.trim_frac >= 0.0f && p.trim_frac < 0.5f)) return false;
-    if (!(p.agg_tau_d == p.agg_tau_d)) return false;
-    if (p.max_occluders < 0 || p.max_occluders > kMaxOcc) return false;
-    if (!(p.frontal_crop >= 0.0f && p.frontal_crop <= 1.0f)) return false;
-    return true;
-}
+// The counters of the call in progress and of the last finished call lead the
+// array, so their places do not depend on the parameters.
+constexpr size_t kStatsOff = (sizeof(ctm::Counts) + 255) / 256 * 256;
 
 int setup_device(int dev)
 {
@@ -96,7 +83,7 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
                                        float baseline_m, float *disp_dev, float *depth_dev,
                                        uint8_t *flags_dev, ctm_stream stream)
 {
-    if (!p || !params_ok(*p)) return CTM_EINVAL;
+    if (!p || !params_valid(*p)) return CTM_EINVAL;
     if (!left_dev || !right_dev || width < 1 || height < 1 || pitch < width || n_boxes < 0)
         return CTM_EINVAL;
     if (n_boxes > 0 && (!boxes_dev || !disp_dev || !depth_dev || !flags_dev)) return CTM_EINVAL;
@@ -119,7 +106,7 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
     caps.max_blocks = kMaxBoxes * std::max(p->grid_g * p->grid_g, 1);
     const int ndy = p->dy_max - p->dy_min + 1;
     const int nd_max = std::max(p->far_dmax - p->far_dmin + 1, p->close_dmax - p->close_dmin + 1);
-    const int strip_cols = (int)round_up(std::max(nd_max + 64, 128), 32);
+    const int strip_cols = default_strip_cols(nd_max);
     const int k = p->close_factor;
     const long long pitch1 = round_up(kMaxW, 32);
     const long long Wk = (kMaxW + k - 1) / k, Hk = (kMaxH + k - 1) / k;
@@ -136,6 +123,8 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
 
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = (size_t)round_up(off + bytes, 256); return o; };
+    const size_t o_counts = take(sizeof(Counts));  // offset 0
+    const size_t o_stats = take(sizeof(Counts));   // offset kStatsOff
     const size_t o_census = take(sizeof(uint64_t) * (size_t)(2 * plane1 + 2 * planek));
     const size_t o_plans = take(sizeof(BoxPlan) * kMaxBoxes);
     const size_t o_occ = take(sizeof(int4) * (size_t)kMaxBoxes * kMaxOcc);
@@ -145,8 +134,6 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
     const size_t o_blkres = take(sizeof(BlockResult) * (size_t)caps.max_blocks);
     const size_t o_geom = take(sizeof(BlockGeom) * (size_t)caps.max_blocks);
     const size_t o_queue = take(sizeof(int) * (size_t)caps.max_blocks);
-    const size_t o_counts = take(sizeof(Counts));
-    const size_t o_stats = take(sizeof(Counts));
     const size_t o_frames = take(sizeof(ctm_frame));
     const size_t o_cin = take(sizeof(int) * 4);
     const size_t o_bm = take(sizeof(uint32_t) * (size_t)plane_off[4]);
@@ -184,6 +171,7 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
     a.caps = caps;
     a.p = *p;
     a.stats_accumulate = 0;
+    a.inject_expiry = 0;
     a.frames = ws.frames;
     a.counts_in = ws.counts_in;
     a.boxes = boxes_dev;
@@ -201,11 +189,19 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
     a.strip_rows = p->pts_side * ndy;
 
     const int threads = 128;
-    int ctas = 0;
-    if (match_configure_raise(a, threads, &ctas) != cudaSuccess || ctas < 1) {
-        cudaGetLastError();
-        return CTM_ECUDA;
+    DeviceState &dsm = g_state[dev];
+    const int need = (int)match_smem_bytes(a);
+    if (dsm.match_need != need) {  // attribute and occupancy queries only when the size changes
+        int ctas = 0;
+        if (match_configure_raise(a, threads, &ctas) != cudaSuccess || ctas < 1) {
+            cudaGetLastError();
+            return CTM_ECUDA;
+        }
+        dsm.match_need = need;
+        dsm.match_ctas = ctas;
     }
+    const int ctas = dsm.match_ctas;
+    census_roi_ctas_per_sm(p->win_w, p->win_h, 0);  // this window's occupancy query, cached after the first
     cudaStream_t s = (cudaStream_t)stream;
     // the census demand bitmap, the counters and the block counts must start at
     // zero (a call interrupted on the device may leave them set)
@@ -225,5 +221,30 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
         cudaGetLastError();
         return CTM_ECUDA;
     }
+    return CTM_OK;
+}
+
+extern "C" int ctm_noalloc_get_stats(ctm_stats *out, ctm_stream stream)
+{
+    if (!out) return CTM_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return CTM_ENODEV;
+    }
+    const DeviceState &ds = g_state[dev];
+    if (!ds.ready) return CTM_EINVAL;  // no ctm_match_boxes_noalloc call on this device yet
+    Counts c;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(&c, ds.base + kStatsOff, sizeof(Counts), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return CTM_ECUDA;
+    }
+    out->cost_evals = c.evals;
+    out->n_blocks = c.n_blocks;
+    out->n_boxes = c.n_boxes;
+    out->error = c.error;
+    out->census_tiles = c.n_tiles;
     return CTM_OK;
 }

@@ -81,6 +81,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(MatchArgs a)
     if (blockIdx.x == 0 && tid == 0) {
         a.ws.counts->n_frames = nf;
         a.ws.counts->n_boxes = nb_total;
+        a.ws.counts->error = 0;  // the previous call's flag stays until here (see aggregate_kernel)
     }
     if (f >= nf) return;
     const ctm_frame fr = a.frames[f];
@@ -398,14 +399,21 @@ cudaError_t launch_sample(const MatchArgs &a, cudaStream_t s)
 // One warp per planned box with blocks: Sec. 4.3.4 over its block records and
 // Eq. 1 (boxes without blocks got their outputs from the planner).
 //
+// When a bounded wait of the matching kernel expired (counts->error), some
+// blocks were never searched and their records are stale, so no box with
+// blocks is aggregated: each gets NaN disparity and depth and flags 0 (neither
+// VALID nor any reason bit), and the call's status says why.
+//
 // It is the last kernel of a call, so it also leaves the workspace ready for
 // the next one: block 0 moves the counters to the stats record and zeroes
-// them, and every box's block count goes back to zero (no memset nodes at the
-// start of a call).
+// them -- all but the error flag, which every CTA reads here and the next
+// call's plan_kernel clears -- and every box's block count goes back to zero
+// (no memset nodes at the start of a call).
 __global__ void __launch_bounds__(256) aggregate_kernel(MatchArgs a)
 {
     __shared__ float scratch[8][2 * kMaxSlots];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int failed = *reinterpret_cast<volatile int *>(&a.ws.counts->error);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const Counts c = *a.ws.counts;
         if (a.stats_accumulate) {  // a later sub-batch of one call
@@ -423,12 +431,22 @@ __global__ void __launch_bounds__(256) aggregate_kernel(MatchArgs a)
         } else {
             *a.ws.stats = c;
         }
-        *a.ws.counts = Counts{};
+        Counts z{};
+        z.error = c.error;  // unchanged: other CTAs read it
+        *a.ws.counts = z;
     }
     const int box = blockIdx.x * 8 + warp;
     if (box >= clampi(a.counts_in[1], 0, a.caps.max_boxes)) return;
     if (a.ws.nblk[box] == 0) return;
-    aggregate_box(a, box, scratch[warp], lane);
+    if (failed) {
+        if (lane == 0) {
+            a.disp[box] = __int_as_float(0x7fc00000);
+            a.depth[box] = __int_as_float(0x7fc00000);
+            a.flags[box] = 0;
+        }
+    } else {
+        aggregate_box(a, box, scratch[warp], lane);
+    }
     __syncwarp();
     if (lane == 0) a.ws.nblk[box] = 0;
 }

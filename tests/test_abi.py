@@ -69,6 +69,33 @@ def test_status_strings_and_defaults(built):
     assert L.ctm_probe_bounded_wait(None, None) == B.CTM_EINVAL
 
 
+def test_create_and_noalloc_share_parameter_checks(built):
+    """Parameters whose strip exceeds the matcher's shared-memory budget (12 disparities
+    x 21 vertical offsets) are rejected with CTM_EINVAL by ctm_create and by
+    ctm_match_boxes_noalloc alike, before either touches a device; so are other
+    out-of-range fields."""
+    torch = pytest.importorskip("torch")
+    from paper_2604_07980_gb300 import binding as B
+    L = B.lib()
+    bad_sets = [{"far_dmax": 11, "close_dmax": 11, "dy_min": -10, "dy_max": 10},
+                {"win_w": 8}, {"grid_g": 9}, {"trim_frac": 0.5}, {"max_occluders": 33}]
+    for bad in bad_sets:
+        p = B.make_params(bad)
+        h = ctypes.c_void_p()
+        assert L.ctm_create(ctypes.byref(h), ctypes.byref(p), 1, 64, 64, 4) == B.CTM_EINVAL, bad
+        if torch.cuda.is_available():
+            continue  # the no-GPU form below passes placeholder pointers
+        fake = ctypes.c_void_p(256)
+        st = L.ctm_match_boxes_noalloc(ctypes.byref(p), fake, fake, 64, 64, 64, fake, 1, 1.0, 1.0,
+                                       fake, fake, fake, None)
+        assert st == B.CTM_EINVAL, bad
+    ok = B.make_params({"far_dmax": 11, "close_dmax": 11, "dy_min": -4, "dy_max": 4})
+    h = ctypes.c_void_p()
+    assert L.ctm_create(ctypes.byref(h), ctypes.byref(ok), 1, 64, 64, 4) != B.CTM_EINVAL
+    if h.value:
+        L.ctm_destroy(h)
+
+
 def test_binding_refuses_without_gpu():
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():

@@ -12,8 +12,26 @@ many small generated inputs rather than a few fixed ones.
 import numpy as np
 import pytest
 
-hyp = pytest.importorskip("hypothesis")
-from hypothesis import given, settings, strategies as st  # noqa: E402
+try:
+    from hypothesis import given, settings, strategies as st
+except ImportError:  # hypothesis is optional: without it these tests skip one by one when run
+    # (not at collection, so a run that deselects them reports no skip)
+    class _AnyStrategy:
+        def __getattr__(self, name):
+            return lambda *a, **k: None
+
+    st = _AnyStrategy()
+
+    def settings(*a, **k):
+        return lambda f: f
+
+    def given(*a, **k):
+        def deco(f):
+            def skipped():
+                pytest.skip("hypothesis is not installed")
+            skipped.__name__, skipped.__doc__ = f.__name__, f.__doc__
+            return skipped
+        return deco
 
 from oracle import oracle as orc  # noqa: E402
 from paper_2604_07980_gb300 import workloads as wl  # noqa: E402
