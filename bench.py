@@ -6,18 +6,20 @@ both resolutions, device planning, the forward/backward Hamming search with
 argmin, parabola and consistency test, aggregation and depth, for the batched
 workload "batch32x1200" (32 frames of 1920x1200 uint8, Poisson(40) boxes per
 frame, 20% occluding strips, far/close split, 9x7 census).  The timed region
-replays the captured CUDA graph of ctm_match_batch K times, alternating between
-two contexts on two streams (two batches in flight); inputs (147 MB of
-images, 1.5 GB of census planes written and re-read every step) exceed the
-129 MB L2, so no flush is needed between steps.
+replays captured CUDA graphs of ctm_match_batch K times, alternating between two
+streams (two batches in flight); each stream rotates over two distinct batches
+(other seeds: other images, boxes and counts), each on its own context, so four
+batches (588 MB of images) take turns and no step finds a recent step's data in
+the 129 MB L2; no flush is needed between steps.
 
 Printed (one JSON line on rank 0): cost-evals/s of the batched path, its e2e
 number through the host-memory entry point (packed page-locked images, copies
-overlapped with the kernels by sub-batches), the per-kernel roofline of the
-matching kernel against the integer popcount pipe and of the census phase
-against HBM and the integer pipes, the same steps one batch at a time,
-the plain one-launch-per-box path for comparison, the serving loop's p50/p99
-latency, the oracle CPU baseline and the SM clocks seen.
+overlapped with the kernels by sub-batches) with the host link's own copy rate,
+the per-kernel roofline of the matching kernel against the integer popcount
+pipe and of the census phase against HBM and the integer pipes, the same steps
+one batch at a time, the 8 x 3840x2160 workload measured the same way, the plain
+one-launch-per-box path for comparison, the serving loop's p50/p99 latency, the
+oracle CPU baseline and the SM clocks seen.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -44,16 +46,19 @@ WORKLOADS = ("batch32x1200", "batch8x2160", "frame1080", "pair640")
 WORKLOAD_SEEDS = {"pair640": 1000, "frame1080": 1001, "batch32x1200": 1002, "batch8x2160": 1003}
 METRIC = "G Hamming cost-evals/s (batched persistent path)"
 UNIT = "Gevals/s"
-SM_COUNT_NOMINAL = 152
 SM_MAX_MHZ = 2070.0
 POPC_PER_EVAL = 2          # one u64 code pair = two 32-bit popcounts
-# DRAM bytes (read + write) of one match_persistent_kernel launch on this workload, from the
-# ncu count summarised in profiles/match_persistent_kernel_batch32x1200.md; None once the
-# kernel changes after that count.
-MATCH_DRAM_BYTES = (102.678 + 2.432) * 1e6
-# DRAM bytes of one census_roi4_kernel launch on this workload (same capture, summarised in
-# profiles/census_roi4_kernel_batch32x1200.md) plus its tile_list_kernel launch
-CENSUS_DRAM_BYTES = (61.096 + 69.065 + 0.775) * 1e6
+# DRAM bytes (read + write) per launch on the default 32-frame workload, from one ncu count
+# of each kernel, valid only for the kernel sources that were counted: `sha` is the SHA-1
+# (first 12 hex digits) of those source files, concatenated in the listed order, when the
+# count was taken.  When the sources differ, or no count was taken, traffic is reported as
+# null.
+TRAFFIC = {
+    "match": {"bytes": None, "sha": None,
+              "sources": ("match.cu", "match_common.cuh", "aggregate.cuh", "ctm_internal.cuh")},
+    "census": {"bytes": None, "sha": None,
+               "sources": ("census.cu", "match_common.cuh", "ctm_internal.cuh")},
+}
 CENSUS_TILE_PX = 32        # pixels per listed census tile
 # kernels of one step of the batched path (ctm_box_points, timed apart, is not in it): plan,
 # sample (with census demand marking), tile_list, census_roi, match, aggregate
@@ -72,9 +77,14 @@ def parse():
     ap.add_argument("--inflight", type=int, default=2,
                     help="batches in flight during the timed steps, each on its own context and "
                          "stream (default 2; 1 = one batch at a time, also reported beside)")
+    ap.add_argument("--rotate", type=int, default=2,
+                    help="distinct batches each in-flight lane cycles through during the timed steps "
+                         "(default 2: with two lanes, four batches of other images and boxes)")
     ap.add_argument("--frames", type=int, default=None,
                     help="frames of a batch workload (default: the workload's own, 32 or 8)")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-other", action="store_true",
+                    help="skip the 8 x 3840x2160 workload reported beside the default one")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--tuning", type=str, default=None,
                     help="JSON object of ctm_tuning fields to set instead of autotuning")
@@ -83,6 +93,19 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the served 4-stream 30 Hz trace (0: skip the serving leg)")
     return ap.parse_args()
+
+
+def traffic_bytes(kernel: str):
+    """The counted DRAM bytes of `kernel`, or None if its sources changed since the count."""
+    import hashlib
+    t = TRAFFIC[kernel]
+    if not t["bytes"] or not t["sha"]:
+        return None
+    h = hashlib.sha1()
+    for name in t["sources"]:
+        with open(os.path.join(ROOT, "paper_2604_07980_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return t["bytes"] if h.hexdigest()[:12] == t["sha"] else None
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -277,6 +300,81 @@ def serve_trace(B, torch, tr, plain: bool) -> dict:
     return out
 
 
+# ----------------------------------------------------------------------------- other workloads
+
+def measure_other(B, torch, wl, D, dist, args, name: str, seed: int, popc_peak: float) -> dict:
+    """Another batch workload measured the same way as the default one, reported beside
+    it: autotuned, two batches in flight on two streams (two distinct batches, one per
+    lane), the same steps one at a time (both batches alternating on one stream), and the
+    matching kernel's popcount-roofline fraction from CUDA events around its launches."""
+    wks = [make_workload(wl, name, None, seed), make_workload(wl, name, None, seed + 7919)]
+    H, W = wks[0].frames[0].left.shape
+    streams = [torch.cuda.current_stream(), torch.cuda.Stream()]
+    units = []
+    tuning = None
+    for wk in wks:
+        c = B.Context(wk.params, len(wk.frames), W, H, wk.n_boxes)
+        bt = B.DeviceBatch(B.frames_to_device(wk.frames), wk.boxes, [(f.f_px, f.baseline_m) for f in wk.frames])
+        if tuning is None:
+            tuning, _ = c.autotune(bt, reps=3)
+        else:
+            c.set_tuning(**tuning)
+        units.append({"w": wk, "ctx": c, "batch": bt})
+    for un, st_ in zip(units, streams):
+        for _ in range(max(args.warmup, 3)):
+            un["ctx"].match_batch(un["batch"], use_graph=True, stream=st_)
+        torch.cuda.synchronize()
+        stt = un["ctx"].stats()
+        assert stt["error"] == 0
+        un["evals"] = stt["cost_evals"]
+
+    def run(inflight: bool):
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0.record(streams[0])
+        streams[1].wait_event(t0)
+        ev = 0
+        for i in range(args.steps):
+            un = units[i % 2]
+            un["ctx"].match_batch(un["batch"], use_graph=True, stream=streams[i % 2] if inflight else streams[0])
+            ev += un["evals"]
+        j = torch.cuda.Event()
+        j.record(streams[1])
+        streams[0].wait_event(j)
+        t1.record(streams[0])
+        torch.cuda.synchronize()
+        return D.max_over_ranks(t0.elapsed_time(t1), dist), ev
+
+    ms2, ev2 = run(True)
+    ms1, ev1 = run(False)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(args.steps)]
+    mt = 0.0
+    mev = 0
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        un = units[i % 2]
+        un["ctx"].match_batch_profiled(un["batch"], evs[i])
+        mev += un["evals"]
+    torch.cuda.synchronize()
+    for ev in evs:
+        mt += ev[3].elapsed_time(ev[4])
+    match_ach = mev / (mt * 1e-3) / 1e9
+    out = {"workload": name, "frames": len(wks[0].frames), "width": W, "height": H,
+           "boxes_per_step_mean": float(np.mean([u["w"].n_boxes for u in units])),
+           "evals_per_step_mean": ev2 / args.steps,
+           "value": ev2 / (ms2 * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms2 / args.steps,
+           "batches_in_flight": 2, "distinct_batches": 2,
+           "one_batch_at_a_time": {"value": ev1 / (ms1 * 1e-3) / 1e9, "ms_per_step": ms1 / args.steps},
+           "match_ms": mt / args.steps, "match_roofline_frac": match_ach / popc_peak,
+           "tuning": tuning}
+    for un in units:
+        un["ctx"].close()
+    return out
+
+
 # ----------------------------------------------------------------------------- main
 
 def make_workload(wl, name: str, frames, seed: int):
@@ -339,10 +437,10 @@ def main():
     from paper_2604_07980_gb300 import binding as B
     from paper_2604_07980_gb300 import dist as D
 
-    w = make_workload(wl, args.workload, args.frames, D.rank_seed(WORKLOAD_SEEDS[args.workload], rank))
+    seed0 = D.rank_seed(WORKLOAD_SEEDS[args.workload], rank)
+    w = make_workload(wl, args.workload, args.frames, seed0)
     H, W = w.frames[0].left.shape
     default_workload = args.workload == WORKLOAD and len(w.frames) == 32  # the ncu-counted launch
-    img_mb = sum(f.left.nbytes + f.right.nbytes for f in w.frames) / 1e6
     frames_dev = B.frames_to_device(w.frames)
     calib = [(f.f_px, f.baseline_m) for f in w.frames]
     ctx = B.Context(w.params, len(w.frames), W, H, w.n_boxes)
@@ -360,78 +458,101 @@ def main():
         tuning, _ = ctx.autotune(batch, reps=3)
     tune_s = time.perf_counter() - t_tune
 
-    # warm-up (captures the graph)
-    for _ in range(max(args.warmup, 3)):
-        ctx.match_batch(batch, use_graph=True)
-    torch.cuda.synchronize()
-    st = ctx.stats()
-    evals_per_step = st["cost_evals"]
-    n_blocks = st["n_blocks"]
-    census_tiles = st["census_tiles"]
-
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    # Two batches in flight (the default): a second context on a second stream, graph
-    # replays alternating between the two, as a deployment (or the serving loop's two
-    # lanes) runs consecutive batches -- one batch's latency-bound planning, tile-list
-    # and aggregation kernels then share SMs with the other batch's census or matching.
-    # Every step is still one whole pass over one batch.
-    lanes = [(ctx, batch, stream)]
-    for _ in range(1, max(args.inflight, 1)):
-        ctx2 = B.Context(w.params, len(w.frames), W, H, w.n_boxes)
-        ctx2.set_tuning(**tuning)
-        batch2 = B.DeviceBatch(frames_dev, w.boxes, calib)
-        s2 = torch.cuda.Stream()
-        for _ in range(max(args.warmup, 3)):
-            ctx2.match_batch(batch2, use_graph=True, stream=s2)
-        torch.cuda.synchronize()
-        assert ctx2.stats()["cost_evals"] == evals_per_step
-        lanes.append((ctx2, batch2, s2))
+    # Batches in flight (two by default), each lane a stream of its own, as a deployment
+    # (or the serving loop's two lanes) runs consecutive batches: one batch's
+    # latency-bound planning, tile-list and aggregation kernels then share SMs with the
+    # other batch's census or matching.  Every lane rotates over `rotate` batches of its
+    # own (distinct seeds: other images, boxes and counts), each on its own context with
+    # its own graph and census planes, so no step re-reads data a recent step brought
+    # into L2.  Every step is still one whole pass over one batch.
+    n_lanes = max(args.inflight, 1)
+    rotate = max(args.rotate, 1)
+
+    def make_unit(wk, ctx_=None, dev_frames=None):
+        fr_dev = dev_frames if dev_frames is not None else B.frames_to_device(wk.frames)
+        cal = [(f.f_px, f.baseline_m) for f in wk.frames]
+        c = ctx_ or B.Context(wk.params, len(wk.frames), W, H, wk.n_boxes)
+        if ctx_ is None:
+            c.set_tuning(**tuning)
+        bt = B.DeviceBatch(fr_dev, wk.boxes, cal)
+        return {"w": wk, "ctx": c, "batch": bt, "frames_dev": fr_dev}
+
+    units = [make_unit(w, ctx, frames_dev)]
+    units[0]["batch"] = batch
+    for u in range(1, n_lanes * rotate):
+        units.append(make_unit(make_workload(wl, args.workload, args.frames, seed0 + 7919 * u)))
+    lanes = []
+    for li in range(n_lanes):
+        st_ = stream if li == 0 else torch.cuda.Stream()
+        lanes.append({"stream": st_, "units": [units[li * rotate + r] for r in range(rotate)]})
+    for ln in lanes:  # warm-up (captures each unit's graph), counts per unit
+        for un in ln["units"]:
+            for _ in range(max(args.warmup, 3)):
+                un["ctx"].match_batch(un["batch"], use_graph=True, stream=ln["stream"])
+            torch.cuda.synchronize()
+            stt = un["ctx"].stats()
+            un["evals"], un["blocks"], un["tiles"] = stt["cost_evals"], stt["n_blocks"], stt["census_tiles"]
+            assert stt["error"] == 0
+    evals_per_step = units[0]["evals"]
+    n_blocks = units[0]["blocks"]
+    census_tiles = units[0]["tiles"]
+
+    def step_unit(lanes_, i):
+        ln = lanes_[i % len(lanes_)]
+        return ln, ln["units"][(i // len(lanes_)) % len(ln["units"])]
 
     def timed_replays(lanes_):
-        """K graph replays alternating over the lanes; CUDA events on the first
-        lane's stream, the others joined to it at both ends."""
+        """K graph replays, step i on lane i mod L, rotating over the lane's batches;
+        CUDA events on the first lane's stream, the others joined to it at both ends.
+        Returns (ms, evaluations of the K steps)."""
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         barrier()
         torch.cuda.synchronize()
         t0.record(stream)
-        for _, _, st_ in lanes_[1:]:
-            st_.wait_event(t0)
+        for ln in lanes_[1:]:
+            ln["stream"].wait_event(t0)
+        ev = 0
         for i in range(args.steps):
-            c, bt_, st_ = lanes_[i % len(lanes_)]
-            c.match_batch(bt_, use_graph=True, stream=st_)
-        for _, _, st_ in lanes_[1:]:
+            ln, un = step_unit(lanes_, i)
+            un["ctx"].match_batch(un["batch"], use_graph=True, stream=ln["stream"])
+            ev += un["evals"]
+        for ln in lanes_[1:]:
             j = torch.cuda.Event()
-            j.record(st_)
+            j.record(ln["stream"])
             stream.wait_event(j)
         t1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        return D.max_over_ranks(t0.elapsed_time(t1), dist)
+        return D.max_over_ranks(t0.elapsed_time(t1), dist), ev
 
     # ---- timed region: K graph replays
     clocks = ClockSampler(local_rank)
     clocks.start()
     time.sleep(0.3)
-    ms = timed_replays(lanes)
+    ms, ev_k = timed_replays(lanes)
     clk = clocks.stop()
     ms_per_step = ms / args.steps
-    value = evals_per_step * world * args.steps / (ms * 1e-3) / 1e9
+    value = ev_k * world / (ms * 1e-3) / 1e9
     # the same K steps one batch at a time (reported beside `value`)
-    ms1 = timed_replays(lanes[:1]) if len(lanes) > 1 else ms
-    one_at_a_time = {"value": evals_per_step * world * args.steps / (ms1 * 1e-3) / 1e9, "unit": UNIT,
-                     "ms_per_step": ms1 / args.steps}
+    ms1, ev1 = timed_replays(lanes[:1]) if len(lanes) > 1 else (ms, ev_k)
+    one_at_a_time = {"value": ev1 * world / (ms1 * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms1 / args.steps}
 
-    # ---- per-phase kernel times, same steps, events on the launching stream
+    # ---- per-phase kernel times, events on the launching stream, rotating over lane 0's batches
     names = ("plan", "sample_and_mark", "census", "match", "aggregate")
     phase = np.zeros(len(names))
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(args.steps)]
+    prof_evals = prof_tiles = 0
     torch.cuda.synchronize()
     for i in range(args.steps):
-        ctx.match_batch_profiled(batch, evs[i])
+        un = lanes[0]["units"][i % len(lanes[0]["units"])]
+        un["ctx"].match_batch_profiled(un["batch"], evs[i])
+        prof_evals += un["evals"]
+        prof_tiles += un["tiles"]
     torch.cuda.synchronize()
     for ev in evs:
         phase += [ev[k].elapsed_time(ev[k + 1]) for k in range(len(names))]
@@ -440,6 +561,8 @@ def main():
     plan_ms = kernels_ms["plan"] + kernels_ms["sample_and_mark"]
     census_ms = kernels_ms["census"]
     match_ms = kernels_ms["match"]
+    evals_per_launch = prof_evals / args.steps   # average over the profiled launches
+    tiles_per_launch = prof_tiles / args.steps
 
     # ---- plain one-launch-per-box path, frame by frame
     plain = None
@@ -469,31 +592,36 @@ def main():
         ctx1.close()
 
     # ---- e2e through the host-memory entry point (pinned host images)
-    # one page-locked buffer holding L0 R0 L1 R1 ... (a frame-grabber ring buffer layout)
-    host_all = torch.empty((len(w.frames), 2, H, W), dtype=torch.uint8).pin_memory()
-    for i, f in enumerate(w.frames):
-        host_all[i, 0].copy_(torch.from_numpy(f.left))
-        host_all[i, 1].copy_(torch.from_numpy(f.right))
-    host_np = host_all.numpy()
-    out_h = (torch.empty(w.n_boxes, dtype=torch.float32).pin_memory().numpy(),
-             torch.empty(w.n_boxes, dtype=torch.float32).pin_memory().numpy(),
-             torch.empty(w.n_boxes, dtype=torch.uint8).pin_memory().numpy())
-    fpx = [c[0] for c in calib]
-    bml = [c[1] for c in calib]
-    # as many host threads as batches in flight, each calling the host entry point on its
-    # own context and stream (each call copies its step's images in and results out)
+    # per batch, one page-locked buffer holding L0 R0 L1 R1 ... (a frame-grabber ring buffer
+    # layout); as many host threads as batches in flight, each calling the host entry point
+    # on its lane's contexts and stream, rotating over the lane's batches (each call copies
+    # its step's images in and its results out)
     import threading
-    outs = [out_h] + [tuple(torch.empty(w.n_boxes, dtype=dt).pin_memory().numpy()
-                            for dt in (torch.float32, torch.float32, torch.uint8)) for _ in lanes[1:]]
+    for un in units:
+        wk = un["w"]
+        hb = torch.empty((len(wk.frames), 2, H, W), dtype=torch.uint8).pin_memory()
+        for fi, f in enumerate(wk.frames):
+            hb[fi, 0].copy_(torch.from_numpy(f.left))
+            hb[fi, 1].copy_(torch.from_numpy(f.right))
+        un["host"] = hb.numpy()
+        un["host_out"] = tuple(torch.empty(wk.n_boxes, dtype=dt).pin_memory().numpy()
+                               for dt in (torch.float32, torch.float32, torch.uint8))
+        un["fpx"] = [f.f_px for f in wk.frames]
+        un["bml"] = [f.baseline_m for f in wk.frames]
+    e2e_evals = [0] * len(lanes)
 
     def host_steps(li, n):
-        c, _, st_ = lanes[li]
-        for _ in range(n):
-            c.match_batch_host_packed(host_np, w.boxes, fpx, bml, out=outs[li], stream=st_)
+        ln = lanes[li]
+        for k in range(n):
+            un = ln["units"][k % len(ln["units"])]
+            un["ctx"].match_batch_host_packed(un["host"], un["w"].boxes, un["fpx"], un["bml"],
+                                              out=un["host_out"], stream=ln["stream"])
+            e2e_evals[li] += un["evals"]
 
     for li in range(len(lanes)):
-        host_steps(li, 2)
-    per_lane = max(2, args.steps // (2 * len(lanes)))
+        host_steps(li, 2 * rotate)
+    per_lane = max(2 * rotate, args.steps // (2 * len(lanes)))
+    e2e_evals = [0] * len(lanes)
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -502,14 +630,36 @@ def main():
         t.start()
     for t in workers:
         t.join()
-    e2e_s = (time.perf_counter() - t0) / (per_lane * len(lanes))
+    e2e_wall = time.perf_counter() - t0
+    e2e_s = e2e_wall / (per_lane * len(lanes))
     barrier()
     e2e_s = D.max_over_ranks(e2e_s, dist)
-    assert np.array_equal(outs[-1][2][:w.n_boxes], out_h[2][:w.n_boxes])
-    for c, _, _ in lanes[1:]:
-        c.close()
-    h2d = sum(f.left.nbytes + f.right.nbytes for f in w.frames) + w.boxes.nbytes + 48 * len(w.frames) + 8
-    d2h = w.n_boxes * 9
+    e2e_value = sum(e2e_evals) * world / D.max_over_ranks(e2e_wall, dist) / 1e9
+    # the host results equal the device path's for the same batch
+    u0 = units[0]
+    assert np.array_equal(u0["host_out"][2][:w.n_boxes], u0["batch"].flags[:w.n_boxes].cpu().numpy())
+    steps_units = [step_unit(lanes, i)[1] for i in range(len(lanes) * rotate)]
+    h2d = float(np.mean([sum(f.left.nbytes + f.right.nbytes for f in un["w"].frames) + un["w"].boxes.nbytes
+                         + 48 * len(un["w"].frames) + 8 for un in steps_units]))
+    d2h = float(np.mean([un["w"].n_boxes * 9 for un in steps_units]))
+    # the host link itself: one plain page-locked copy of a batch's images, timed on the stream
+    link_dev = torch.empty(u0["host"].size, dtype=torch.uint8, device="cuda")
+    link_src = torch.from_numpy(u0["host"].reshape(-1))
+    for _ in range(2):
+        link_dev.copy_(link_src, non_blocking=True)
+    l0 = torch.cuda.Event(enable_timing=True)
+    l1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    l0.record(stream)
+    for _ in range(5):
+        link_dev.copy_(link_src, non_blocking=True)
+    l1.record(stream)
+    torch.cuda.synchronize()
+    link_gbs = 5 * link_src.numel() / (l0.elapsed_time(l1) * 1e-3) / 1e9
+    del link_dev
+    for un in units[1:]:
+        un["ctx"].close()
+        un["frames_dev"] = un["batch"] = None
 
     # ---- Sec. 4.3.6 step after matching: 3-D points in camera and vehicle frames + depth variance
     cx, cy = W / 2.0, H / 2.0
@@ -578,7 +728,7 @@ def main():
     popc_rate = B.probe_int_rate(0, 4096)
     popc_clk = float(round(popc_rate))
     peak = sms * popc_clk / POPC_PER_EVAL * SM_MAX_MHZ * 1e6 / 1e9
-    achieved = evals_per_step / (match_ms * 1e-3) / 1e9
+    achieved = evals_per_launch / (match_ms * 1e-3) / 1e9
     # the same peak at the sampled SM clock of this run and at the median SM clock seen under a
     # power-capped dense GEMM (MEASURED_PEAKS.json), where that file is present
     peak_at = {"sampled_sm_mhz": clk.get("sm_mhz"),
@@ -601,7 +751,7 @@ def main():
     # ---- census phase (tile list + ROI census): HBM and integer-ALU fractions.  Algorithmic
     # bytes per code: 8 written + 1 source pixel read; compares per code: win_w * win_h - 1,
     # each half an IMAD (FMA pipe) and half a LOP3 (ALU pipe), the two pipes running side by side
-    codes = census_tiles * CENSUS_TILE_PX
+    codes = tiles_per_launch * CENSUS_TILE_PX
     n_cmps = w.params["win_w"] * w.params["win_h"] - 1  # compares per code (the centre bit is always 0)
     lop3_rate = B.probe_int_rate(1, 4096)
     imad_rate = B.probe_int_rate(4, 4096)
@@ -613,13 +763,19 @@ def main():
         "codes_per_step": codes,
         "hbm": {"achieved": census_bytes / (census_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                 "frac": census_bytes / (census_ms * 1e-3) / 1e9 / hbm_peak,
-                "traffic": CENSUS_DRAM_BYTES if default_workload else None,
+                "traffic": traffic_bytes("census") if default_workload else None,
                 "basis": f"9 B per code (8 B code + 1 B pixel); {hbm_basis}"},
         "alu": {"achieved": codes * n_cmps / (census_ms * 1e-3) / 1e12, "peak": cmp_peak,
                 "unit": "T compares/s", "frac": codes * n_cmps / (census_ms * 1e-3) / 1e12 / cmp_peak,
                 "basis": f"{sms} SMs x {cmp_clk:.0f} compares/clk/SM (LOP3 probe {lop3_rate:.1f}, "
                          f"IMAD probe {imad_rate:.1f}, one of each per 2 compares) x {SM_MAX_MHZ:g} MHz"},
     }
+
+    # ---- the 8 x 3840x2160 workload measured the same way, reported beside the default one
+    other = None
+    if args.workload == WORKLOAD and not args.no_other:
+        other = measure_other(B, torch, wl, D, dist, args, "batch8x2160",
+                              D.rank_seed(WORKLOAD_SEEDS["batch8x2160"], rank), peak)
 
     # ---- serving: 4 stereo streams at 30 Hz (batched lanes, then the plain per-box path)
     serving = serving_plain = None
@@ -639,6 +795,20 @@ def main():
             c.pop("evals")
         cpu["single_thread"] = cpu1
 
+    boxes_mean = float(np.mean([step_unit(lanes, i)[1]["w"].n_boxes for i in range(args.steps)]))
+    all_img_mb = sum(sum(f.left.nbytes + f.right.nbytes for f in un["w"].frames) for un in units) / 1e6
+    codes_mb = census_tiles * CENSUS_TILE_PX * 8 / 1e6
+    rows_mb = census_tiles * w.params["win_h"] * (CENSUS_TILE_PX + w.params["win_w"] - 1) / 1e6
+    if all_img_mb > 129:
+        l2_note = (f"inputs larger than L2: {len(units)} distinct batches ({all_img_mb:.0f} MB of images) "
+                   f"rotate, so a batch's data is reused only every {len(units)}th step; a step writes "
+                   f"{codes_mb:.0f} MB of census codes and reads window rows of {rows_mb:.0f} MB of grid "
+                   "pixels, overlapping ones counted each time (the census computes only the tiles the "
+                   "search uses), no flush")
+    else:
+        l2_note = (f"inputs smaller than L2 ({all_img_mb:.1f} MB of images over {len(units)} batches): "
+                   "replays run from L2")
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -647,15 +817,15 @@ def main():
             "config": {"workload": args.workload, "frames": len(w.frames), "width": W, "height": H,
                        "boxes": w.n_boxes, "blocks": n_blocks, "evals_per_step": evals_per_step,
                        "census_tiles": census_tiles,
+                       "distinct_batches": len(units), "evals_per_step_mean": ev_k / args.steps,
+                       "boxes_per_step_mean": boxes_mean,
                        "tuning": tuning, "autotune_s": round(tune_s, 3),
                        "census": f"{w.params['win_w']}x{w.params['win_h']} u64"
                                  + (" + sentinel" if w.params["sentinel"] else ""),
                        "graph": True, "batches_in_flight": len(lanes),
-                       "l2": (f"inputs larger than L2 ({img_mb:.0f} MB images + census planes per step)"
-                              if img_mb > 129 else
-                              f"inputs smaller than L2 ({img_mb:.1f} MB images): replays run from L2"),
+                       "l2": l2_note,
                        "parallelism": f"frames sharded, {world} rank(s), no collective"},
-            "boxes_per_s": w.n_boxes * world / (ms_per_step * 1e-3),
+            "boxes_per_s": boxes_mean * world / (ms_per_step * 1e-3),
             "phases_ms": {"plan_and_mark": plan_ms, "census_roi": census_ms, "match": match_ms},
             "kernels_ms": kernels_ms,
             "one_batch_at_a_time": one_at_a_time,
@@ -664,17 +834,20 @@ def main():
             "auto_rect": {**auto_rect, "frac_of_popc_peak": auto_rect["value"] / peak},
             "serving": serving,
             "serving_plain_path": serving_plain,
-            "e2e": {"value": evals_per_step * world / e2e_s / 1e9, "unit": UNIT,
+            "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                    "ms_per_step": e2e_s * 1e3, "host_threads": len(lanes)},
+                    "ms_per_step": e2e_s * 1e3, "host_threads": len(lanes),
+                    "link_gbs": link_gbs,
+                    "link_floor_ms": h2d / (link_gbs * 1e9) * 1e3},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT,
                          "frac": achieved / peak,
-                         "traffic": MATCH_DRAM_BYTES if default_workload and MATCH_DRAM_BYTES else None,
+                         "traffic": traffic_bytes("match") if default_workload else None,
                          "kernel": "match_persistent_kernel",
                          "peak_basis": f"{sms} SMs x {popc_clk:g} popc32/clk/SM (probe {popc_rate:.2f}) / "
                                        f"{POPC_PER_EVAL} per eval x {SM_MAX_MHZ:g} MHz",
                          "at_other_clocks": peak_at},
             "census_roofline": census_roof,
+            "batch8x2160": other,
             "census_full_image": {**census_full, "hbm_peak_GB_s": hbm_peak,
                                   "note": f"ctm_census_build on one {W}x{H} image (9x7, sentinel), "
                                           "not on the batched path; 9 B per code"},

@@ -153,6 +153,12 @@ typedef struct {
                                1: two-pass pipelined matcher (a forward kernel, then a
                                backward kernel; each CTA loads its next block while it
                                scans the current one)                                 */
+    int32_t split_ways;     /* fused matcher only: 0 = split every block's candidate range
+                               into (block, disparity-chunk) tiles when the queue holds
+                               fewer blocks than the resident CTAs can take (about two
+                               tiles per CTA, up to 8 chunks); 1 = never split; 2, 4 or
+                               8 = always split into that many chunks.  Splitting needs
+                               one vertical offset (dy_min == dy_max)                 */
 } ctm_tuning;
 
 /* Counters of the last match call (ctm_get_stats). */
@@ -346,8 +352,8 @@ int ctm_set_tuning(ctm_ctx *ctx, const ctm_tuning *t);
 
 /* Autotuner: runs the batch of ctm_match_batch (same arguments, no debug
  * output) under candidate tunings -- every matching CTA size x strip width,
- * for each matcher, then each census variant and each queue split around the
- * best so far --
+ * for each matcher, then each census variant, each queue split and automatic
+ * or no disparity-chunk tiles around the best so far --
  * timing `reps` calls of each with CUDA events after one warm-up call, keeps
  * the fastest in the context and returns it in *best (and its time per call,
  * in ms, in *best_ms; either may be NULL).  The outputs are written by every
@@ -376,6 +382,15 @@ int ctm_probe_int_rate(int kind, int iters, double *ops_per_clk_per_sm);
  * consumed by that one call; the context stays usable.  No GPU fault is
  * involved.  Errors: CTM_EINVAL (null ctx). */
 int ctm_inject_wait_expiry(ctm_ctx *ctx);
+
+/* Fault injection for tests (no counterpart in the paper): of the device
+ * allocations the library makes from now on (context workspaces, host-path
+ * staging, server arenas and lane buffers), the first `skip` go through and the
+ * next n fail on the host as a cudaMalloc on an exhausted device does, so the
+ * call that makes them returns CTM_ENOMEM after releasing what it had
+ * allocated.  n = 0 disarms.  Process-wide; nothing runs on a GPU.
+ * Errors: CTM_EINVAL (skip < 0 or n < 0). */
+int ctm_inject_alloc_failures(int skip, int n);
 
 /* Bounded-wait probe (no counterpart in the paper): one CTA waits, with the
  * matching kernels' own bounded-wait routine, on an mbarrier phase that nothing

@@ -28,7 +28,7 @@ EXPORTS = ("ctm_status_str", "ctm_default_params", "ctm_create", "ctm_destroy",
            "ctm_census_build", "ctm_match_boxes", "ctm_match_boxes_plain", "ctm_match_batch",
            "ctm_match_batch_profiled", "ctm_match_batch_host", "ctm_match_boxes_noalloc",
            "ctm_noalloc_get_stats",
-           "ctm_get_stats", "ctm_probe_int_rate", "ctm_probe_bounded_wait", "ctm_inject_wait_expiry",
+           "ctm_get_stats", "ctm_probe_int_rate", "ctm_probe_bounded_wait", "ctm_inject_wait_expiry", "ctm_inject_alloc_failures",
            "ctm_get_tuning",
            "ctm_set_tuning", "ctm_autotune",
            "ctm_box_points", "ctm_auto_rect", "ctm_rect_filter",
@@ -84,7 +84,7 @@ class ctm_geometry(ctypes.Structure):
 class ctm_tuning(ctypes.Structure):
     _fields_ = [("match_threads", ctypes.c_int32), ("strip_cols", ctypes.c_int32),
                 ("census_mode", ctypes.c_int32), ("big_work", ctypes.c_int32),
-                ("match_mode", ctypes.c_int32)]
+                ("match_mode", ctypes.c_int32), ("split_ways", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -174,6 +174,8 @@ def lib():
     L.ctm_probe_bounded_wait.restype = i32
     L.ctm_inject_wait_expiry.argtypes = [vp]
     L.ctm_inject_wait_expiry.restype = i32
+    L.ctm_inject_alloc_failures.argtypes = [i32, i32]
+    L.ctm_inject_alloc_failures.restype = i32
     L.ctm_auto_rect.argtypes = [ctypes.POINTER(ctm_params), vp, vp] + [i32] * 13 + [vp, vp, vp, vp]
     L.ctm_auto_rect.restype = i32
     L.ctm_rect_filter.argtypes = [vp, i32, i32, i32]

@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 
 #include "ctm_internal.cuh"
@@ -44,6 +45,7 @@ struct ctm_ctx {
     int match_mode = 0;
     int nd_max = 0;
     int inject_expiry = 0;  // armed by ctm_inject_wait_expiry (tests)
+    int split_ways = 0;
     void *dev_mem = nullptr;
     size_t dev_bytes = 0;
     cudaStream_t capture_stream = nullptr;
@@ -126,6 +128,7 @@ MatchArgs make_args(const ctm_ctx *ctx, const ctm_frame *frames, const int32_t *
     a.big_work = ctx->big_work;
     a.census_mode = ctx->census_mode;
     a.match_mode = ctx->match_mode;
+    a.split_ways = ctx->split_ways;
     a.stats_accumulate = 0;
     a.inject_expiry = 0;
     return a;
@@ -169,6 +172,27 @@ int set_device(const ctm_ctx *ctx)
 }
 
 }  // namespace
+
+namespace {
+// armed by ctm_inject_alloc_failures (tests): allocations to let through, then to fail
+std::mutex g_inject_mu;
+int g_alloc_skip = 0, g_alloc_fail = 0;
+}  // namespace
+
+cudaError_t ctm::dev_alloc(void **ptr, size_t bytes)
+{
+    {
+        std::lock_guard<std::mutex> lk(g_inject_mu);
+        if (g_alloc_skip > 0) {
+            --g_alloc_skip;
+        } else if (g_alloc_fail > 0) {
+            --g_alloc_fail;
+            *ptr = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    return cudaMalloc(ptr, bytes);
+}
 
 size_t ctm::context_device_bytes(const ctm_ctx *ctx) { return ctx ? ctx->dev_bytes : 0; }
 const int32_t *ctm::context_error_flag(const ctm_ctx *ctx) { return &ctx->ws.stats->error; }
@@ -265,6 +289,8 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
     const size_t o_base = take(sizeof(int) * (size_t)max_boxes);
     const size_t o_blocks = take(sizeof(int2) * (size_t)ctx->caps.max_blocks);
     const size_t o_blkres = take(sizeof(BlockResult) * (size_t)ctx->caps.max_blocks);
+    const size_t o_chunk = take(sizeof(ChunkState) * (size_t)ctx->caps.max_blocks);
+    const size_t o_ccost = take(sizeof(int32_t) * (size_t)ctx->caps.max_blocks * ctx->nc_stride);
     const size_t o_geom = take(sizeof(BlockGeom) * (size_t)ctx->caps.max_blocks);
     const size_t o_queue = take(sizeof(int) * (size_t)ctx->caps.max_blocks);
     const size_t o_counts = take(sizeof(Counts));
@@ -282,7 +308,7 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
     const size_t o_bm = take(sizeof(uint32_t) * (size_t)plane_off[4] * max_frames);
     const size_t o_tiles = take(sizeof(unsigned long long) * 32 * (size_t)plane_off[4] * max_frames);
     const size_t o_planes = take(sizeof(PlaneDesc) * 4 * (size_t)max_frames);
-    if (cudaMalloc(&ctx->dev_mem, off) != cudaSuccess) {
+    if (dev_alloc(&ctx->dev_mem, off) != cudaSuccess) {
         cudaGetLastError();
         delete ctx;
         return CTM_ENOMEM;
@@ -302,6 +328,8 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
     ws.blk_base = reinterpret_cast<int *>(base + o_base);
     ws.blocks = reinterpret_cast<int2 *>(base + o_blocks);
     ws.blkres = reinterpret_cast<BlockResult *>(base + o_blkres);
+    ws.chunk = reinterpret_cast<ChunkState *>(base + o_chunk);
+    ws.chunk_cost = reinterpret_cast<int32_t *>(base + o_ccost);
     ws.geom = reinterpret_cast<BlockGeom *>(base + o_geom);
     ws.queue = reinterpret_cast<int *>(base + o_queue);
     ws.counts = reinterpret_cast<Counts *>(base + o_counts);
@@ -518,7 +546,7 @@ int ctm_match_batch_host(ctm_ctx *ctx, const ctm_frame *frames_host, int n_frame
         const size_t o_frames = take(sizeof(ctm_frame) * (size_t)ctx->caps.max_frames);
         const size_t o_counts = take(sizeof(int32_t) * 4 * kHostGroups);
         void *mem = nullptr;
-        if (cudaMalloc(&mem, off) != cudaSuccess) { cudaGetLastError(); return CTM_ENOMEM; }
+        if (dev_alloc(&mem, off) != cudaSuccess) { cudaGetLastError(); return CTM_ENOMEM; }
         bool okh = cudaMallocHost(&ctx->frames_host_pinned, sizeof(ctm_frame) * ctx->caps.max_frames) == cudaSuccess &&
                    cudaMallocHost(&ctx->counts_host_pinned, sizeof(int32_t) * 4 * kHostGroups) == cudaSuccess &&
                    cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
@@ -663,6 +691,7 @@ int ctm_get_tuning(const ctm_ctx *ctx, ctm_tuning *out)
     out->census_mode = ctx->census_mode;
     out->big_work = ctx->big_work;
     out->match_mode = ctx->match_mode;
+    out->split_ways = ctx->split_ways;
     return CTM_OK;
 }
 
@@ -674,6 +703,9 @@ int ctm_set_tuning(ctm_ctx *ctx, const ctm_tuning *t)
     if (t->census_mode != 0 && t->census_mode != 1) return CTM_EINVAL;
     if (t->big_work < 0) return CTM_EINVAL;
     if (t->match_mode != 0 && t->match_mode != 1) return CTM_EINVAL;
+    if (t->split_ways != 0 && t->split_ways != 1 && t->split_ways != 2 && t->split_ways != 4 &&
+        t->split_ways != 8)
+        return CTM_EINVAL;
     int st = set_device(ctx);
     if (st != CTM_OK) return st;
     ctm_ctx trial = *ctx;  // shallow: only the tuning fields are read below
@@ -696,12 +728,13 @@ int ctm_set_tuning(ctm_ctx *ctx, const ctm_tuning *t)
     }
     const bool changed = t->match_threads != ctx->match_threads || t->strip_cols != ctx->strip_cols ||
                          t->census_mode != ctx->census_mode || t->big_work != ctx->big_work ||
-                         t->match_mode != ctx->match_mode;
+                         t->match_mode != ctx->match_mode || t->split_ways != ctx->split_ways;
     ctx->match_threads = t->match_threads;
     ctx->strip_cols = t->strip_cols;
     ctx->census_mode = t->census_mode;
     ctx->big_work = t->big_work;
     ctx->match_mode = t->match_mode;
+    ctx->split_ways = t->split_ways;
     ctx->ctas_per_sm = ctas;
     if (changed && ctx->gexec) {  // the captured graph holds the old launch shapes
         cudaGraphExecDestroy(ctx->gexec);
@@ -789,6 +822,15 @@ int ctm_autotune(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *count
         if (r != CTM_OK) { status = r; break; }
         if (ms < bms) { bms = ms; bt = t; }
     }
+    // 4. disparity-chunk tiles of the fused matcher: automatic or never
+    for (int sw = 0; sw <= 1 && status == CTM_OK && bt.match_mode == 0; ++sw) {
+        ctm_tuning t = bt;
+        t.split_ways = sw;
+        float ms = 0.0f;
+        const int r = measure(t, &ms);
+        if (r != CTM_OK) { status = r; break; }
+        if (ms < bms) { bms = ms; bt = t; }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (status != CTM_OK) {
@@ -826,6 +868,15 @@ int ctm_probe_int_rate(int kind, int iters, double *ops_per_clk_per_sm)
 {
     if (kind < 0 || kind > 4 || iters < 1 || !ops_per_clk_per_sm) return CTM_EINVAL;
     return run_int_probe(kind, iters, ops_per_clk_per_sm) == cudaSuccess ? CTM_OK : CTM_ECUDA;
+}
+
+int ctm_inject_alloc_failures(int skip, int n)
+{
+    if (skip < 0 || n < 0) return CTM_EINVAL;
+    std::lock_guard<std::mutex> lk(g_inject_mu);
+    g_alloc_skip = n > 0 ? skip : 0;
+    g_alloc_fail = n;
+    return CTM_OK;
 }
 
 int ctm_inject_wait_expiry(ctm_ctx *ctx)

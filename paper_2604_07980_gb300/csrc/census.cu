@@ -291,9 +291,10 @@ __device__ __forceinline__ void load_row12(const PlaneDesc &d, bool inside, int 
     }
 }
 
-// Codes of pixels x .. x+3 of row y of plane d (4 consecutive pixels per lane;
-// bit layout as tile_codes), stored to the plane; `ok` false: this lane has
-// no tile and stores nothing.  All 32 lanes of the warp must call it together.
+// Codes of the four pixels x .. x+3 of a lane (bit layout as tile_codes) from
+// its window rows: row(j, v) gives the twelve pixels I_k(x - 4 .. x + 7) of
+// window row j as three little-endian words (row(sy, v) first, for the centre
+// pixels).
 //
 // The compares run on the integer multiply-add pipe: with both pixels of a
 // pair in the two 16-bit halves of a word w (plain values, upper bytes zero),
@@ -302,14 +303,99 @@ __device__ __forceinline__ void load_row12(const PlaneDesc &d, bool inside, int 
 // s <= 7; so no carry crosses the halves and bit 8 + s of each half is
 // [nb > c].  Code bit p = 8 a + s is taken from bit 8 + s (and 24 + s) of e
 // into accumulator a with one LOP3; accumulator a ends up holding code byte a
-// of the low pixel in its byte 1 and of the high pixel in its byte 3.  All
-// window rows are loaded before the first is used.
-template <int WW, int WH>
-__device__ __forceinline__ void census4(const PlaneDesc &d, int x0, int y, int hl, bool ok, int sentinel)
+// of the low pixel in its byte 1 and of the high pixel in its byte 3.
+template <int WW, int WH, typename RowFn>
+__device__ __forceinline__ void codes4(RowFn row, int sentinel, uint64_t (&c)[4])
 {
     constexpr int sx = WW / 2, sy = WH / 2;
     constexpr int n = WW * WH;
     constexpr int OFF = 4 - sx;  // byte index of the window's left column for pixel x
+    uint32_t vc[3];
+    row(sy, vc);
+    uint32_t accA[8], accB[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) accA[q] = accB[q] = 0u;
+    if (sentinel) {
+        accA[n >> 3] = (0x100u << (n & 7)) | (0x1000000u << (n & 7));
+        accB[n >> 3] = accA[n >> 3];
+    }
+    const uint32_t cA = __byte_perm(vc[1], 0u, 0x4140);  // pixels x, x+1
+    const uint32_t cB = __byte_perm(vc[1], 0u, 0x4342);  // pixels x+2, x+3
+    uint32_t KA[8], KB[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const uint32_t h = 0x10000u - (0x100u << q) - 1u;
+        KA[q] = (h | (h << 16)) - (cA << q);
+        KB[q] = (h | (h << 16)) - (cB << q);
+    }
+#pragma unroll
+    for (int j = 0; j < WH; ++j) {
+        uint32_t v[3];
+        row(j, v);
+        // w[t] = (b[t], b[t+1]) in the two halves, t = 0 .. 10
+        uint32_t w[11];
+        const uint32_t s1 = __funnelshift_r(v[0], v[1], 8);  // b1 .. b4
+        const uint32_t s2 = __funnelshift_r(v[1], v[2], 8);  // b5 .. b8
+        w[0] = __byte_perm(v[0], 0u, 0x4140);
+        w[1] = __byte_perm(s1, 0u, 0x4140);
+        w[2] = __byte_perm(v[0], 0u, 0x4342);
+        w[3] = __byte_perm(s1, 0u, 0x4342);
+        w[4] = __byte_perm(v[1], 0u, 0x4140);
+        w[5] = __byte_perm(s2, 0u, 0x4140);
+        w[6] = __byte_perm(v[1], 0u, 0x4342);
+        w[7] = __byte_perm(s2, 0u, 0x4342);
+        w[8] = __byte_perm(v[2], 0u, 0x4140);
+        w[9] = __byte_perm(v[2], 0u, 0x4241);
+        w[10] = __byte_perm(v[2], 0u, 0x4342);
+#pragma unroll
+        for (int i = 0; i < WW; ++i) {
+            const int p = n - 1 - (j * WW + i);  // code bit of this window offset
+            const int q = p & 7;
+            const uint32_t pos = (0x100u << q) | (0x1000000u << q);
+            accA[p >> 3] |= (w[OFF + i] * (1u << q) + KA[q]) & pos;
+            accB[p >> 3] |= (w[OFF + i + 2] * (1u << q) + KB[q]) & pos;
+        }
+    }
+    uint32_t tA[4], tB[4];  // code bytes (2q, 2q+1) of the low pixel, then of the high pixel
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        tA[q] = __byte_perm(accA[2 * q], accA[2 * q + 1], 0x7351);
+        tB[q] = __byte_perm(accB[2 * q], accB[2 * q + 1], 0x7351);
+    }
+    c[0] = ((uint64_t)__byte_perm(tA[2], tA[3], 0x5410) << 32) | __byte_perm(tA[0], tA[1], 0x5410);
+    c[1] = ((uint64_t)__byte_perm(tA[2], tA[3], 0x7632) << 32) | __byte_perm(tA[0], tA[1], 0x7632);
+    c[2] = ((uint64_t)__byte_perm(tB[2], tB[3], 0x5410) << 32) | __byte_perm(tB[0], tB[1], 0x5410);
+    c[3] = ((uint64_t)__byte_perm(tB[2], tB[3], 0x7632) << 32) | __byte_perm(tB[0], tB[1], 0x7632);
+}
+
+// Store the codes of pixels x .. x+3 of grid row y (zero where the window leaves
+// the grid, or for the whole row when `active` is false).
+template <int WW>
+__device__ __forceinline__ void store4(const PlaneDesc &d, int x, int y, bool active, uint64_t (&c)[4])
+{
+    constexpr int sx = WW / 2;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (!active || x + q - sx < 0 || x + q + sx >= d.Ws) c[q] = 0ull;
+    uint64_t *dst = d.out + (long long)y * d.opitch + x;
+    if (x + 3 < d.Ws && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
+        reinterpret_cast<ulonglong2 *>(dst)[0] = make_ulonglong2(c[0], c[1]);
+        reinterpret_cast<ulonglong2 *>(dst)[1] = make_ulonglong2(c[2], c[3]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (x + q < d.Ws) dst[q] = c[q];
+    }
+}
+
+// Codes of pixels x .. x+3 of row y of plane d (4 consecutive pixels per lane;
+// bit layout as tile_codes), stored to the plane; `ok` false: this lane has
+// no tile and stores nothing.  All 32 lanes of the warp must call it together.
+// All window rows are loaded into registers before the first is used.
+template <int WW, int WH>
+__device__ __forceinline__ void census4(const PlaneDesc &d, int x0, int y, int hl, bool ok, int sentinel)
+{
+    constexpr int sy = WH / 2;
     const unsigned full = 0xffffffffu;
     const int x = x0 + 4 * hl;
     const bool active = ok && y - sy >= 0 && y + sy < d.Hs;
@@ -366,75 +452,10 @@ __device__ __forceinline__ void census4(const PlaneDesc &d, int x0, int y, int h
         for (int r = 0; r < WH; ++r) load_row12(d, inside, x, y - sy + r, rows[r]);
     }
     uint64_t c[4] = {0ull, 0ull, 0ull, 0ull};
-    if (active) {
-        const uint32_t *vc = rows[sy];
-        uint32_t accA[8], accB[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) accA[q] = accB[q] = 0u;
-        if (sentinel) {
-            accA[n >> 3] = (0x100u << (n & 7)) | (0x1000000u << (n & 7));
-            accB[n >> 3] = accA[n >> 3];
-        }
-        const uint32_t cA = __byte_perm(vc[1], 0u, 0x4140);  // pixels x, x+1
-        const uint32_t cB = __byte_perm(vc[1], 0u, 0x4342);  // pixels x+2, x+3
-        uint32_t KA[8], KB[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const uint32_t h = 0x10000u - (0x100u << q) - 1u;
-            KA[q] = (h | (h << 16)) - (cA << q);
-            KB[q] = (h | (h << 16)) - (cB << q);
-        }
-#pragma unroll
-        for (int j = 0; j < WH; ++j) {
-            const uint32_t *v = rows[j];
-            // w[t] = (b[t], b[t+1]) in the two halves, t = 0 .. 10
-            uint32_t w[11];
-            const uint32_t s1 = __funnelshift_r(v[0], v[1], 8);  // b1 .. b4
-            const uint32_t s2 = __funnelshift_r(v[1], v[2], 8);  // b5 .. b8
-            w[0] = __byte_perm(v[0], 0u, 0x4140);
-            w[1] = __byte_perm(s1, 0u, 0x4140);
-            w[2] = __byte_perm(v[0], 0u, 0x4342);
-            w[3] = __byte_perm(s1, 0u, 0x4342);
-            w[4] = __byte_perm(v[1], 0u, 0x4140);
-            w[5] = __byte_perm(s2, 0u, 0x4140);
-            w[6] = __byte_perm(v[1], 0u, 0x4342);
-            w[7] = __byte_perm(s2, 0u, 0x4342);
-            w[8] = __byte_perm(v[2], 0u, 0x4140);
-            w[9] = __byte_perm(v[2], 0u, 0x4241);
-            w[10] = __byte_perm(v[2], 0u, 0x4342);
-#pragma unroll
-            for (int i = 0; i < WW; ++i) {
-                const int p = n - 1 - (j * WW + i);  // code bit of this window offset
-                const int q = p & 7;
-                const uint32_t pos = (0x100u << q) | (0x1000000u << q);
-                accA[p >> 3] |= (w[OFF + i] * (1u << q) + KA[q]) & pos;
-                accB[p >> 3] |= (w[OFF + i + 2] * (1u << q) + KB[q]) & pos;
-            }
-        }
-        uint32_t tA[4], tB[4];  // code bytes (2q, 2q+1) of the low pixel, then of the high pixel
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            tA[q] = __byte_perm(accA[2 * q], accA[2 * q + 1], 0x7351);
-            tB[q] = __byte_perm(accB[2 * q], accB[2 * q + 1], 0x7351);
-        }
-        c[0] = ((uint64_t)__byte_perm(tA[2], tA[3], 0x5410) << 32) | __byte_perm(tA[0], tA[1], 0x5410);
-        c[1] = ((uint64_t)__byte_perm(tA[2], tA[3], 0x7632) << 32) | __byte_perm(tA[0], tA[1], 0x7632);
-        c[2] = ((uint64_t)__byte_perm(tB[2], tB[3], 0x5410) << 32) | __byte_perm(tB[0], tB[1], 0x5410);
-        c[3] = ((uint64_t)__byte_perm(tB[2], tB[3], 0x7632) << 32) | __byte_perm(tB[0], tB[1], 0x7632);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (x + q - sx < 0 || x + q + sx >= d.Ws) c[q] = 0ull;
-    }
-    if (!ok) return;
-    uint64_t *dst = d.out + (long long)y * d.opitch + x;
-    if (x + 3 < d.Ws && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
-        reinterpret_cast<ulonglong2 *>(dst)[0] = make_ulonglong2(c[0], c[1]);
-        reinterpret_cast<ulonglong2 *>(dst)[1] = make_ulonglong2(c[2], c[3]);
-    } else {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (x + q < d.Ws) dst[q] = c[q];
-    }
+    if (active)
+        codes4<WW, WH>([&](int j, uint32_t (&v)[3]) { v[0] = rows[j][0]; v[1] = rows[j][1]; v[2] = rows[j][2]; },
+                       sentinel, c);
+    if (ok) store4<WW>(d, x, y, active, c);
 }
 
 __device__ __forceinline__ PlaneDesc desc_of(const Plane &pl)

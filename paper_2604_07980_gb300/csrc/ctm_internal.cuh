@@ -59,6 +59,18 @@ struct __align__(16) BlockGeom {
 };
 static_assert(sizeof(BlockGeom) % 16 == 0, "BlockGeom is moved by 16-byte copies");
 
+// State of a block split into disparity-chunk tiles (match.cu): first-minimum
+// keys (cost << 16 | candidate) merged by atomicMin, finished-tile tickets per
+// pass, and the forward result published to the backward tiles.  Reset by the
+// sampling kernel for every searchable block.
+struct ChunkState {
+    unsigned fkey, bkey;
+    int fdone, bdone;
+    int ready;
+    int d_f, s_m, s_0, s_p;
+    int pad[3];
+};
+
 // Result of one block kept for the aggregation (device).
 struct BlockResult {
     float d_full;
@@ -92,6 +104,8 @@ struct Workspace {
     BlockGeom *geom;           // [max_blocks] indexed like blocks
     int *queue;                // [max_blocks] searchable blocks: large from the front, small from the back
     BlockResult *blkres;       // [max_blocks]
+    ChunkState *chunk;         // [max_blocks]; null: no disparity-chunk tiles
+    int32_t *chunk_cost;       // [max_blocks * nc_stride] forward cost rows of split blocks
     Counts *counts;            // counters of the call in progress (zero between calls)
     Counts *stats;             // the last finished call's counters
     ctm_frame *frames;         // staging for single-frame calls [max_frames]
@@ -126,6 +140,7 @@ struct MatchArgs {
     int strip_cols;            // columns of the shared-memory strip
     int big_work;              // queue split: usable points x candidates of a large block
     int match_mode;            // 0: fused single-kernel matcher, 1: two-pass pipelined matcher
+    int split_ways;            // disparity-chunk tiles: 0 automatic, 1 never, 2/4/8 always
     int census_mode;           // region-of-interest census variant (census.cu)
     int strip_rows;            // rows of the shared-memory strip (pts_side * ndy)
     int stats_accumulate;      // 1: the aggregation adds the call's counters to the stats record
@@ -207,6 +222,12 @@ int default_strip_cols(int nd_max);
 // Device address of the error flag of a context's last finished call
 // (ctm_stats.error), for callers that read it back on their own stream.
 const int32_t *context_error_flag(const ctm_ctx *ctx);
+
+// Device allocation used for every workspace, staging buffer and arena of the
+// library: cudaMalloc, unless ctm_inject_alloc_failures armed a failure, which
+// this allocation then consumes (returning cudaErrorMemoryAllocation, as
+// cudaMalloc does when the device is out of memory).
+cudaError_t dev_alloc(void **ptr, size_t bytes);
 
 // Bytes of device workspace a context holds (its one allocation at creation).
 size_t context_device_bytes(const ctm_ctx *ctx);

@@ -218,7 +218,8 @@ __device__ bool scan_chunks(const MatchArgs &a, const BlockCtx &bc, const Smem &
 // bounded wait expired anywhere.
 template <int NT>
 __device__ __forceinline__ bool combine_pass(const MatchArgs &a, const BlockCtx &bc, const Smem &sm, bool fwd,
-                                             const int (&acc)[8], bool ok, unsigned &key)
+                                             const int (&acc)[8], bool ok, unsigned &key, int coff = 0,
+                                             int32_t *row_out = nullptr)
 {
     constexpr int NW = NT / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -244,12 +245,14 @@ __device__ __forceinline__ bool combine_pass(const MatchArgs &a, const BlockCtx 
         __syncthreads();
     }
     int32_t *dbgc = warp == 0 ? (fwd ? a.dbg.cost_f : a.dbg.cost_b) : nullptr;
+    if (warp != 0) row_out = nullptr;
     const int slots = a.p.grid_g * a.p.grid_g;
     unsigned k = 0xffffffffu;
     for (int c = lane; c < bc.nc; c += 32) {
         const int s = sm.cost[c] + sm.cost_b[c];
         k = min(k, ((unsigned)s << 16) | (unsigned)c);
-        if (dbgc) dbgc[((long long)bc.box * slots + bc.slot) * a.nc_stride + c] = s;
+        if (dbgc) dbgc[((long long)bc.box * slots + bc.slot) * a.nc_stride + coff + c] = s;
+        if (row_out) row_out[c] = s;
     }
     key = __reduce_min_sync(0xffffffffu, k);
     return true;
@@ -287,42 +290,99 @@ __device__ __forceinline__ BlockCtx make_ctx(const MatchArgs &a, const BlockGeom
     return bc;
 }
 
-// Start block b, whose sampling record has landed in sh.geom[gbuf]: its point
-// layout (column-major compaction of the usable points), its sampled columns
-// and rows, the left codes at its points (cp.async) and its first forward strip
-// chunk (bulk copies on sh.mbar).  Nothing is waited for here; the strip, the
-// point arrays and sh.X / sh.Y must be free (the previous block's scans done).
-// withhold: see issue_chunk.
+// Point layout of a block whose sampling record is in g: the column-major
+// compaction of its usable points (sm.pmj), its sampled columns and rows, and,
+// with left_codes, the left codes at its points (cp.async) and their strip bases
+// in its first forward strip chunk g0.  Ends with a barrier.
 template <int NT>
-__device__ void begin_block(const MatchArgs &a, int b, const Smem &sm, Shared<NT / 32> &sh, int gbuf,
-                            bool withhold = false)
+__device__ __forceinline__ void layout_block(const BlockCtx &bc, const BlockGeom &g, const Smem &sm,
+                                             Shared<NT / 32> &sh, bool left_codes, int j1_first,
+                                             const ChunkGeom &g0)
 {
     const int tid = threadIdx.x;
-    const BlockGeom &g = sh.geom[gbuf];
-    const BlockCtx bc = make_ctx(a, g, b);
-    const int total = g.n_valid;
-    const unsigned later0 = g.cstart & ~1u;
-    const int j1_first = later0 ? __ffs(later0) - 1 : bc.nx;
     const int x0 = g.X[0];
-    const ChunkGeom g0 = chunk_geom(x0 - bc.dmax, g.X[j1_first - 1] - x0 + bc.nd);
     for (int t = tid; t < kMaxPts; t += NT) {
         const int j = t >> 4, m = t & 15;
         if (j < bc.nx && ((g.colmask[j] >> m) & 1u)) {
             const int idx = g.colprefix[j] + __popc(g.colmask[j] & ((1u << m) - 1u));
             const int x = g.X[j], y = g.Y[m];
-            cp_async8(&sm.pcode[idx], bc.CL + (long long)y * bc.pitch + x);
+            if (left_codes) {
+                cp_async8(&sm.pcode[idx], bc.CL + (long long)y * bc.pitch + x);
+                if (j < j1_first) sm.pbase[idx] = 8 * (m * bc.ndy * g0.SWa + x - x0 + g0.delta);
+            }
             sm.pmj[idx] = (m << 8) | j;
-            if (j < j1_first) sm.pbase[idx] = 8 * (m * bc.ndy * g0.SWa + x - x0 + g0.delta);
         }
     }
     if (tid < kMaxPtsSide) {
         sh.X[tid] = g.X[tid];
         sh.Y[tid] = g.Y[tid];
     }
-    if (tid <= kMaxPtsSide) sh.colstart[tid] = tid < bc.nx ? g.colprefix[tid] : total;
+    if (tid <= kMaxPtsSide) sh.colstart[tid] = tid < bc.nx ? g.colprefix[tid] : g.n_valid;
     if (tid == 0) sh.cstart = g.cstart;
     __syncthreads();  // sh.Y is read by the issuing warp
+}
+
+// First column chunk of a block: its end column and its forward strip geometry.
+__device__ __forceinline__ int first_chunk_end(const BlockGeom &g, int nx)
+{
+    const unsigned later0 = g.cstart & ~1u;
+    return later0 ? __ffs(later0) - 1 : nx;
+}
+
+// Start a block (or a disparity chunk of one: bc's candidate range) whose
+// sampling record is in g: its point layout, the left codes at its points and
+// its first forward strip chunk (bulk copies on sh.mbar).  Nothing is waited for
+// here; the strip, the point arrays and sh.X / sh.Y must be free (the previous
+// block's scans done).  withhold: see issue_chunk.
+template <int NT>
+__device__ void begin_block_ctx(const MatchArgs &a, const BlockCtx &bc, const BlockGeom &g, const Smem &sm,
+                                Shared<NT / 32> &sh, bool withhold = false)
+{
+    const int j1_first = first_chunk_end(g, bc.nx);
+    const int x0 = g.X[0];
+    const ChunkGeom g0 = chunk_geom(x0 - bc.dmax, g.X[j1_first - 1] - x0 + bc.nd);
+    layout_block<NT>(bc, g, sm, sh, true, j1_first, g0);
     issue_chunk<NT>(a, bc, sm, sh, true, 0, g0, withhold);
+}
+
+// begin_block_ctx over block b's whole candidate range, its record in sh.geom[gbuf].
+template <int NT>
+__device__ void begin_block(const MatchArgs &a, int b, const Smem &sm, Shared<NT / 32> &sh, int gbuf,
+                            bool withhold = false)
+{
+    begin_block_ctx<NT>(a, make_ctx(a, sh.geom[gbuf], b), sh.geom[gbuf], sm, sh, withhold);
+}
+
+// Block record from the two passes' results (Eq. subpixel on the forward costs
+// around d_f, consistency |d_b - d_f| <= fb_tol); boxes are aggregated by
+// aggregate_kernel.  bc: the block's whole candidate range.
+__device__ __forceinline__ void write_record(const MatchArgs &a, const BlockCtx &bc, int total, int d_f, int dy_f,
+                                             int d_b, int dy_b, int s_m, int s_0, int s_p)
+{
+    ctm_block rec;
+    rec.n_pts = bc.nx * bc.ny;
+    rec.n_valid = total;
+    rec.flags = CTM_BLK_PRESENT;
+    rec.d_f = d_f;
+    rec.dy_f = dy_f;
+    rec.d_b = d_b;
+    rec.dy_b = dy_b;
+    rec.s_m = s_m;
+    rec.s_0 = s_0;
+    rec.s_p = s_p;
+    if (rec.d_f == bc.dmin || rec.d_f == bc.dmax) {
+        rec.d_sub = (float)rec.d_f;
+        rec.flags |= CTM_BLK_SUBPIX_CLAMPED;
+    } else {
+        // Eq. subpixel
+        const float num = (float)(rec.s_p - rec.s_m);
+        const float den = __fmul_rn(2.0f, (float)(rec.s_p + rec.s_m - 2 * rec.s_0));
+        rec.d_sub = den == 0.0f ? (float)rec.d_f : __fsub_rn((float)rec.d_f, __fdiv_rn(num, den));
+    }
+    rec.d_full = __fmul_rn(rec.d_sub, (float)bc.k);
+    const int dxv = abs(rec.d_b - rec.d_f);
+    rec.flags |= dxv <= a.p.fb_tol ? CTM_BLK_VALID : CTM_BLK_FB_REJECT;
+    write_block(a, bc.box, bc.slot, rec);
 }
 
 // Prefetch state of the persistent kernel.  A single-block launch has none.
@@ -435,31 +495,141 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
         const int cb = (int)(keyb & 0xffffu);
         const int eb = bc.ndy == 1 ? 0 : cb / bc.nd;
         // 5. block record; boxes are aggregated by aggregate_kernel
-        ctm_block rec;
-        rec.n_pts = bc.nx * bc.ny;
-        rec.n_valid = total;
-        rec.flags = CTM_BLK_PRESENT;
-        rec.d_f = d_f;
-        rec.dy_f = dy_f;
-        rec.d_b = bc.dmin + (cb - eb * bc.nd);
-        rec.dy_b = a.p.dy_min + eb;
-        rec.s_m = s_m;
-        rec.s_0 = (int)(key >> 16);
-        rec.s_p = s_p;
-        if (rec.d_f == bc.dmin || rec.d_f == bc.dmax) {
-            rec.d_sub = (float)rec.d_f;
-            rec.flags |= CTM_BLK_SUBPIX_CLAMPED;
-        } else {
-            // Eq. subpixel
-            const float num = (float)(rec.s_p - rec.s_m);
-            const float den = __fmul_rn(2.0f, (float)(rec.s_p + rec.s_m - 2 * rec.s_0));
-            rec.d_sub = den == 0.0f ? (float)rec.d_f : __fsub_rn((float)rec.d_f, __fdiv_rn(num, den));
-        }
-        rec.d_full = __fmul_rn(rec.d_sub, (float)bc.k);
-        const int dxv = abs(rec.d_b - rec.d_f);
-        rec.flags |= dxv <= a.p.fb_tol ? CTM_BLK_VALID : CTM_BLK_FB_REJECT;
-        write_block(a, bc.box, bc.slot, rec);
+        write_record(a, bc, total, d_f, dy_f, bc.dmin + (cb - eb * bc.nd), a.p.dy_min + eb, s_m,
+                     (int)(key >> 16), s_p);
         evals += 2ull * (unsigned long long)total * (unsigned long long)bc.nc;
+    }
+    return true;
+}
+
+// Disparity-chunk tiles.  When the work queue holds few blocks for the resident
+// CTAs (a single frame, a small batch), the persistent kernel splits every
+// searchable block's candidate range into `ways` chunks of whole 32-candidate
+// slices and takes (block, chunk) tiles: first the forward tiles of every block,
+// then the backward tiles, in queue order.  A forward tile scans its candidates,
+// stores its costs in the block's cost row and merges its first minimum into the
+// block's key with atomicMin on (cost << 16 | candidate) -- the minimum of the
+// keys is the first minimum of the whole row whatever order the tiles finish
+// in; the tile that finishes last (a ticket counter) reads the merged key, the
+// costs beside it (Eq. subpixel) and publishes d_f.  A backward tile waits for
+// that (bounded: every forward tile of its block was taken earlier by a running
+// CTA, none of which waits on anything), scans its share of the backward
+// candidates around d_f and merges its minimum the same way; the last one writes
+// the block record.  Results equal the unsplit block's bit for bit.
+
+// Bounded wait, by thread 0, for a flag another CTA of this launch sets: about
+// one second of the global timer (an iteration cap as a backstop); false, with
+// the error recorded, on expiry.
+__device__ __forceinline__ bool wait_flag(const int *flag, int *error_flag)
+{
+    const volatile int *f = flag;
+    if (*f) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 1; it < kWaitIters; ++it) {
+        __nanosleep(64);
+        if (*f) return true;
+        if ((it & 15u) == 0 && global_ns() - t0 > kWaitNs) break;
+    }
+    atomicOr(error_flag, 1);
+    return false;
+}
+
+__device__ __forceinline__ int ld_cg(const int *p) { return __ldcg(p); }
+
+// Candidate range [c0, c1) of chunk c of `ways` over nd candidates: whole
+// 32-candidate slices, the last chunk ragged, trailing chunks possibly empty.
+__device__ __forceinline__ void chunk_range(int nd, int ways, int c, int &c0, int &c1)
+{
+    const int cw = (((nd + ways - 1) / ways) + 31) & ~31;
+    c0 = min(c * cw, nd);
+    c1 = min(c0 + cw, nd);
+}
+
+// One tile after its record has landed in sh.geom[0].  False if a bounded wait
+// expired (nothing of this tile is merged then).
+template <int NT>
+__device__ bool process_tile(const MatchArgs &a, int b, int c, int ways, bool bwd, const Smem &sm,
+                             Shared<NT / 32> &sh, unsigned &phase, unsigned long long &evals, bool withhold)
+{
+    const int tid = threadIdx.x;
+    const BlockGeom &g = sh.geom[0];
+    const BlockCtx full = make_ctx(a, g, b);
+    ChunkState *st = a.ws.chunk + b;
+    int c0, c1;
+    chunk_range(full.nd, ways, c, c0, c1);
+    BlockCtx bc = full;
+    bc.dmin = full.dmin + c0;
+    bc.dmax = full.dmin + c1 - 1;
+    bc.nd = c1 - c0;
+    bc.nc = bc.nd;  // one dy row (ways > 1 only then)
+    int d_f = 0;
+    if (bwd) {  // the block's forward merge
+        bool ready = true;
+        if (tid == 0) ready = wait_flag(&st->ready, &a.ws.counts->error);
+        if (!__syncthreads_and(ready)) return false;
+        __threadfence();
+        d_f = ld_cg(&st->d_f);
+    }
+    unsigned key = 0xffffffffu;
+    if (c0 < c1) {
+        const int total = g.n_valid;
+        const int j1_first = first_chunk_end(g, bc.nx);
+        const int x0 = g.X[0];
+        const int SW0 = g.X[j1_first - 1] - x0 + bc.nd;
+        int acc[8];
+        bool ok;
+        if (!bwd) {
+            begin_block_ctx<NT>(a, bc, g, sm, sh, withhold);
+            ok = land_chunk<NT>(a, bc, sm, sh, phase, true, 0, chunk_geom(x0 - bc.dmax, SW0));
+            cp_async_wait_all();
+            if (!__syncthreads_and(ok)) return false;
+            ok = scan_chunks<NT>(a, bc, sm, sh, phase, true, chunk_geom(x0 - bc.dmax, SW0), acc, 0, 0);
+            if (!combine_pass<NT>(a, bc, sm, true, acc, ok, key, c0, a.ws.chunk_cost + (long long)b * a.nc_stride + c0))
+                return false;
+        } else {
+            const int dy_f = a.p.dy_min;
+            const ChunkGeom gb = chunk_geom(x0 - d_f + bc.dmin, SW0);
+            layout_block<NT>(bc, g, sm, sh, false, j1_first, gb);
+            issue_chunk<NT>(a, bc, sm, sh, false, dy_f, gb);
+            for (int t = tid; t < total; t += NT) {  // right codes at the matched positions
+                const int mj = sm.pmj[t];
+                const int qx = sh.X[mj & 255] - d_f, qy = sh.Y[mj >> 8] + dy_f;
+                sm.pcode[t] = (qx >= 0 && qx < bc.Ws && qy >= 0 && qy < bc.Hs)
+                                  ? __ldg(bc.CR + (long long)qy * bc.pitch + qx) : 0ull;
+            }
+            ok = land_chunk<NT>(a, bc, sm, sh, phase, false, dy_f, gb);
+            set_bases<NT>(sm, sh.X, 0, sh.colstart[j1_first], bc.ndy, gb.SWa, x0, gb.delta);
+            if (!__syncthreads_and(ok)) return false;
+            ok = scan_chunks<NT>(a, bc, sm, sh, phase, false, gb, acc, d_f, dy_f);
+            if (!combine_pass<NT>(a, bc, sm, false, acc, ok, key, c0)) return false;
+        }
+        if (tid == 0) evals += (unsigned long long)total * (unsigned long long)bc.nd;
+        key += (unsigned)c0;  // candidate index within the block
+    }
+    __threadfence();  // warp 0's cost-row stores, before the ticket below
+    __syncthreads();
+    if (tid == 0) {
+        if (key != 0xffffffffu) atomicMin(bwd ? &st->bkey : &st->fkey, key);
+        __threadfence();
+        const int ticket = atomicAdd(bwd ? &st->bdone : &st->fdone, 1);
+        if (ticket == ways - 1) {  // the last tile of this pass merges
+            __threadfence();
+            const int32_t *row = a.ws.chunk_cost + (long long)b * a.nc_stride;
+            if (!bwd) {
+                const unsigned k = (unsigned)atomicOr(&st->fkey, 0u);
+                const int cf = (int)(k & 0xffffu);
+                st->s_0 = (int)(k >> 16);
+                st->s_m = cf > 0 ? ld_cg(row + cf - 1) : 0;
+                st->s_p = cf < full.nd - 1 ? ld_cg(row + cf + 1) : 0;
+                st->d_f = full.dmin + cf;
+                __threadfence();
+                atomicExch(&st->ready, 1);
+            } else {
+                const unsigned k = (unsigned)atomicOr(&st->bkey, 0u);
+                write_record(a, full, g.n_valid, ld_cg(&st->d_f), a.p.dy_min, full.dmin + (int)(k & 0xffffu),
+                             a.p.dy_min, ld_cg(&st->s_m), ld_cg(&st->s_0), ld_cg(&st->s_p));
+            }
+        }
     }
     return true;
 }
@@ -493,6 +663,59 @@ __device__ __forceinline__ void drain(const MatchArgs &a, Shared<NT / 32> &sh, u
     if (sh.spend) mbar_wait_bounded(&sh.mbar, phase, &a.ws.counts->error);
 }
 
+// The persistent kernel over disparity-chunk tiles (see process_tile): thread 0
+// takes the next tile index and fetches its block's record; no look-ahead.
+template <int NT>
+__device__ void run_tiles(const MatchArgs &a, const Smem &sm, Shared<NT / 32> &sh, int n_big, int nq, int ways)
+{
+    if (threadIdx.x == 0) {
+        mbar_init(&sh.mbar, 1);
+        mbar_init(&sh.mbar_g, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        sh.gpend = 0;
+        sh.spend = 0;
+    }
+    __syncthreads();
+    unsigned phase = 0, gphase = 0;
+    unsigned long long evals = 0ull;
+    const int n_fwd = nq * ways, n_tiles = 2 * n_fwd;
+    bool first = true;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int i = atomicAdd(&a.ws.counts->queue_head, 1);
+            sh.next = i;
+            if (i < n_tiles) {
+                const int j = i < n_fwd ? i : i - n_fwd;
+                sh.next_b = queue_block(a, j / ways, n_big);
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                mbar_arrive_expect_tx(&sh.mbar_g, (unsigned)sizeof(BlockGeom));
+                bulk_g2s(&sh.geom[0], a.ws.geom + sh.next_b, (unsigned)sizeof(BlockGeom), &sh.mbar_g);
+                sh.gpend = 1;
+            }
+        }
+        __syncthreads();
+        const int i = sh.next;
+        if (i >= n_tiles) break;
+        const bool landed = mbar_wait_bounded(&sh.mbar_g, gphase, &a.ws.counts->error);
+        if (landed) gphase ^= 1u;
+        if (!__syncthreads_and(landed)) {
+            drain<NT>(a, sh, phase, gphase);
+            break;
+        }
+        if (threadIdx.x == 0) sh.gpend = 0;
+        const bool bwd = i >= n_fwd;
+        const int j = bwd ? i - n_fwd : i;
+        const bool withhold = first && a.inject_expiry != 0 && blockIdx.x == 0 && !bwd;
+        first = false;
+        if (!process_tile<NT>(a, sh.next_b, j % ways, ways, bwd, sm, sh, phase, evals, withhold)) {
+            drain<NT>(a, sh, phase, gphase);
+            break;
+        }
+        __syncthreads();  // the tile's shared data is done with before the next record lands
+    }
+    if (threadIdx.x == 0 && evals) atomicAdd(&a.ws.counts->evals, evals);
+}
+
 template <int NT>
 __global__ void __launch_bounds__(NT, 1024 / NT)
     match_persistent_kernel(MatchArgs a)
@@ -504,6 +727,16 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
     pf.on = true;
     pf.n_big = a.ws.counts->n_big;
     pf.nq = pf.n_big + a.ws.counts->n_small;
+    // few blocks for the resident CTAs: (block, disparity-chunk) tiles, about two
+    // per CTA (one vertical offset only; not in the allocation-free path)
+    if (a.ws.chunk != nullptr && a.p.dy_min == a.p.dy_max && pf.nq > 0 && a.split_ways != 1) {
+        const int w = a.split_ways > 1 ? a.split_ways : 2 * (int)gridDim.x / pf.nq;
+        const int ways = w >= 8 ? 8 : (w >= 4 ? 4 : (w >= 2 ? 2 : 1));
+        if (ways > 1) {
+            run_tiles<NT>(a, sm, sh, pf.n_big, pf.nq, ways);
+            return;
+        }
+    }
     if (threadIdx.x == 0) {
         mbar_init(&sh.mbar, 1);
         mbar_init(&sh.mbar_g, 1);

@@ -156,6 +156,8 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
     ws.blk_base = reinterpret_cast<int *>(b + o_base);
     ws.blocks = reinterpret_cast<int2 *>(b + o_blocks);
     ws.blkres = reinterpret_cast<BlockResult *>(b + o_blkres);
+    ws.chunk = nullptr;  // no disparity-chunk tiles: their state does not fit the array
+    ws.chunk_cost = nullptr;
     ws.geom = reinterpret_cast<BlockGeom *>(b + o_geom);
     ws.queue = reinterpret_cast<int *>(b + o_queue);
     ws.counts = reinterpret_cast<Counts *>(b + o_counts);
@@ -186,6 +188,7 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
     a.big_work = 4096;
     a.census_mode = 0;
     a.match_mode = 0;
+    a.split_ways = 1;
     a.strip_rows = p->pts_side * ndy;
 
     const int threads = 128;

@@ -356,6 +356,11 @@ __global__ void __launch_bounds__(256) sample_kernel(MatchArgs a)
         }
     } else {
         if (lane == 0) {
+            if (a.ws.chunk) {  // state for disparity-chunk tiles (used only when the queue is short)
+                ChunkState cs{};
+                cs.fkey = cs.bkey = 0xffffffffu;
+                a.ws.chunk[b] = cs;
+            }
             if (n_valid * nd * ndy >= a.big_work) {
                 const int q = atomicAdd(&a.ws.counts->n_big, 1);
                 a.ws.queue[q] = b;

@@ -406,7 +406,7 @@ int create_lane(ctm_server *S, Lane &L, int index)
     const size_t o_disp = take(sizeof(float) * B);
     const size_t o_depth = take(sizeof(float) * B);
     const size_t o_flags = take((size_t)B);
-    if (cudaMalloc(&L.dev_mem, off) != cudaSuccess || cudaHostAlloc(&L.host_mem, off, cudaHostAllocDefault) != cudaSuccess) {
+    if (ctm::dev_alloc(&L.dev_mem, off) != cudaSuccess || cudaHostAlloc(&L.host_mem, off, cudaHostAllocDefault) != cudaSuccess) {
         cudaGetLastError();
         return CTM_ENOMEM;
     }
@@ -481,7 +481,7 @@ int ctm_server_create(ctm_server **out, const ctm_params *p, const ctm_server_co
     S->cfg = *cfg;
     S->arena.reset(cfg->image_budget_bytes, 256);
     int st = CTM_OK;
-    if (cudaMalloc(&S->arena_d, (size_t)S->arena.size()) != cudaSuccess) st = CTM_ENOMEM;
+    if (ctm::dev_alloc(reinterpret_cast<void **>(&S->arena_d), (size_t)S->arena.size()) != cudaSuccess) st = CTM_ENOMEM;
     if (st == CTM_OK && cudaStreamCreateWithFlags(&S->upload, cudaStreamNonBlocking) != cudaSuccess) st = CTM_ECUDA;
     if (st == CTM_OK) {
         S->lanes.resize(cfg->lanes);

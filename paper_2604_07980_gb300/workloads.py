@@ -19,6 +19,8 @@ Recipe (all numpy, PCG64, seed = 1000 + workload index, per-frame sub-seeds):
 """
 from __future__ import annotations
 
+import concurrent.futures as cf
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -230,8 +232,8 @@ def multi_frame(name: str, seed: int, n_frames: int, W: int, H: int, boxes_per_f
                 gain_range=(0.8, 1.2), offset_range=(-20.0, 20.0), sigma: float = 2.0,
                 poisson: bool = False, max_boxes: int | None = None) -> Workload:
     params = dict(PARAMS[name])
-    frames, all_boxes, all_d = [], [], []
-    for fi in range(n_frames):
+
+    def one(fi):
         rng = _frame_rng(seed, fi)
         n_obj = int(rng.poisson(boxes_per_frame)) if poisson else int(boxes_per_frame)
         if max_boxes is not None:
@@ -241,7 +243,19 @@ def multi_frame(name: str, seed: int, n_frames: int, W: int, H: int, boxes_per_f
         gain = rng.uniform(*gain_range)
         offset = rng.uniform(*offset_range)
         L, R = _render(rng, W, H, boxes, d, gain, offset, sigma)
-        frames.append(Frame(L, R))
+        return Frame(L, R), boxes, d
+
+    # every frame draws from its own generator, so frames can be made side by side
+    # (numpy releases the interpreter lock) with the same result as in order
+    workers = min(n_frames, os.cpu_count() or 1, 16)
+    if workers > 1 and W * H >= 1 << 20:
+        with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+            made = list(ex.map(one, range(n_frames)))
+    else:
+        made = [one(fi) for fi in range(n_frames)]
+    frames, all_boxes, all_d = [], [], []
+    for fi, (fr, boxes, d) in enumerate(made):
+        frames.append(fr)
         all_boxes += [b + [fi] for b in boxes]
         all_d += d
     bx = np.array(all_boxes, dtype=np.int32).reshape(-1, 5)

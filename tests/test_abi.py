@@ -43,7 +43,7 @@ def test_struct_layouts():
     assert ctypes.sizeof(B.ctm_frame) == 48
     assert B.BLOCK_DTYPE.itemsize == B.BLOCK_BYTES == 48
     assert ctypes.sizeof(B.ctm_debug) == 24
-    assert ctypes.sizeof(B.ctm_tuning) == 20
+    assert ctypes.sizeof(B.ctm_tuning) == 24
     assert ctypes.sizeof(B.ctm_geometry) == 136
     assert ctypes.sizeof(B.ctm_server_config) == 40
     assert ctypes.sizeof(B.ctm_request) == 80

@@ -329,3 +329,36 @@ def test_frontal_crop_occluder_priority(torch_cuda):
     compare_box_outputs({k: v.cpu().numpy() for k, v in got.items() if k != "debug"}, ref, "frontal crop")
     compare_debug(got["debug"], ref, B.n_candidates(ctx.params), "frontal crop")
     ctx.close()
+
+
+@pytest.mark.parametrize("name", ["pair640", "frame1080", "batch32x1200", "batch8x2160"])
+def test_disparity_chunk_tiles_bit_exact(torch_cuda, name):
+    """(block, disparity-chunk) tiles of the fused matcher: forced 2, 4 and 8 ways,
+    the automatic choice and no splitting all give the oracle's block records, every
+    forward and backward cost, box outputs and evaluation count (ties included: the
+    chunk minima merge as (cost, candidate) keys)."""
+    from paper_2604_07980_gb300 import binding as B
+    if name == "batch32x1200":
+        w = wl.batch32x1200(n_frames=3)
+    elif name == "batch8x2160":
+        w = wl.batch8x2160(n_frames=1, n_boxes=48)
+    else:
+        w = wl.by_name(name)
+    frames = [(f.left, f.right, f.f_px, f.baseline_m) for f in w.frames]
+    ref = orc.match_batch(frames, w.boxes, orc.Params(**w.params), debug=True)
+    H, W = w.frames[0].left.shape
+    ctx = B.Context(w.params, len(w.frames), W, H, w.n_boxes)
+    batch = B.DeviceBatch(B.frames_to_device(w.frames), w.boxes, [(f.f_px, f.baseline_m) for f in w.frames])
+    for ways in (0, 1, 2, 4, 8):
+        ctx.set_tuning(split_ways=ways)
+        for graph in (False, True):
+            got = ctx.match_batch(batch, use_graph=graph, debug=True)
+            torch_cuda.cuda.synchronize()
+            where = f"{name} split_ways {ways} graph {graph}"
+            out = {k: v.cpu().numpy() for k, v in got.items() if k != "debug"}
+            compare_box_outputs(out, ref, where)
+            compare_debug(got["debug"], ref, B.n_candidates(ctx.params), where)
+            st = ctx.stats()
+            assert st["error"] == 0, where
+            assert st["cost_evals"] == oracle_evals(ref["blocks"], ref["flags"], w.params), where
+    ctx.close()
