@@ -146,7 +146,10 @@ typedef struct {
                                of a block: a multiple of 8, at least the larger
                                disparity range + 2; larger values mean fewer chunks
                                and more shared memory per CTA                         */
-    int32_t census_mode;    /* region-of-interest census: 0 = 4 CTAs per SM, 1 = 3    */
+    int32_t census_mode;    /* region-of-interest census (5x5, 7x7, 9x7 windows): 0 =
+                               integer multiply-add compares, 4 CTAs per SM; 1 = the
+                               same, 3 CTAs per SM; 2 = packed fp16 compares with
+                               saturation, 4 CTAs per SM                              */
     int32_t big_work;       /* blocks with usable points x candidates >= big_work are
                                queued first (largest work first)                      */
     int32_t match_mode;     /* 0: fused matcher (one CTA runs both passes of a block);
@@ -154,11 +157,11 @@ typedef struct {
                                backward kernel; each CTA loads its next block while it
                                scans the current one)                                 */
     int32_t split_ways;     /* fused matcher only: 0 = split every block's candidate range
-                               into (block, disparity-chunk) tiles when the queue holds
-                               fewer blocks than the resident CTAs can take (about two
-                               tiles per CTA, up to 8 chunks); 1 = never split; 2, 4 or
-                               8 = always split into that many chunks.  Splitting needs
-                               one vertical offset (dy_min == dy_max)                 */
+                               into two (block, disparity-chunk) tiles when the queue
+                               holds fewer than about 0.6 blocks per resident CTA; 1 =
+                               never split; 2, 4 or 8 = always split into that many
+                               chunks.  Splitting needs one vertical offset
+                               (dy_min == dy_max)                                     */
 } ctm_tuning;
 
 /* Counters of the last match call (ctm_get_stats). */
@@ -366,8 +369,9 @@ int ctm_autotune(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *count
 /* Integer-pipe probe for roofline denominators (no counterpart in the paper):
  * runs `iters` iterations of independent chains of one instruction on every
  * SM -- kind 0: 32-bit popcount, 1: 3-input xor, 2: packed fp16 greater-than
- * mask, 3: 32-bit add, 4: 32-bit multiply-add -- and returns the operations
- * per SM clock per SM.  Synchronizes the device.  Errors: CTM_EINVAL, CTM_ECUDA. */
+ * mask, 3: 32-bit add, 4: 32-bit multiply-add, 5: packed fp16 fused
+ * multiply-add with saturation -- and returns the operations (packed
+ * instructions for kinds 2 and 5) per SM clock per SM.  Synchronizes the device.  Errors: CTM_EINVAL, CTM_ECUDA. */
 int ctm_probe_int_rate(int kind, int iters, double *ops_per_clk_per_sm);
 
 /* Fault injection for tests (no counterpart in the paper): arms ctx so that the

@@ -661,7 +661,8 @@ def probe_bounded_wait() -> tuple[int, float]:
 
 def probe_int_rate(kind: int, iters: int = 4096) -> float:
     """Operations per SM clock per SM: 32-bit popcount (kind 0), 3-input xor (1), packed fp16
-    greater-than (2), 32-bit add (3) or 32-bit multiply-add (4)."""
+    greater-than (2), 32-bit add (3), 32-bit multiply-add (4) or packed fp16 fused
+    multiply-add with saturation (5)."""
     _torch()
     v = ctypes.c_double(0.0)
     _check(lib().ctm_probe_int_rate(kind, iters, ctypes.byref(v)), "ctm_probe_int_rate")

@@ -356,7 +356,7 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
         ctm_destroy(ctx);
         return CTM_ECUDA;
     }
-    for (int m = 0; m < 2; ++m) census_roi_ctas_per_sm(p->win_w, p->win_h, m);  // outside any capture
+    for (int m = 0; m < 3; ++m) census_roi_ctas_per_sm(p->win_w, p->win_h, m);  // outside any capture
     *out = ctx;
     return CTM_OK;
 }
@@ -700,7 +700,7 @@ int ctm_set_tuning(ctm_ctx *ctx, const ctm_tuning *t)
     if (!ctx || !t) return CTM_EINVAL;
     if (t->match_threads != 128 && t->match_threads != 256) return CTM_EINVAL;
     if (t->strip_cols < ctx->nd_max + 2 || (t->strip_cols & 7) != 0 || t->strip_cols > 4096) return CTM_EINVAL;
-    if (t->census_mode != 0 && t->census_mode != 1) return CTM_EINVAL;
+    if (t->census_mode < 0 || t->census_mode > 2) return CTM_EINVAL;
     if (t->big_work < 0) return CTM_EINVAL;
     if (t->match_mode != 0 && t->match_mode != 1) return CTM_EINVAL;
     if (t->split_ways != 0 && t->split_ways != 1 && t->split_ways != 2 && t->split_ways != 4 &&
@@ -804,8 +804,8 @@ int ctm_autotune(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *count
       }
     }
     // 2. census variant, 3. queue split, one at a time around the best so far
-    const int modes[2] = {0, 1};
-    for (int i = 0; i < 2 && status == CTM_OK; ++i) {
+    const int modes[3] = {0, 1, 2};
+    for (int i = 0; i < 3 && status == CTM_OK; ++i) {
         ctm_tuning t = bt;
         t.census_mode = modes[i];
         float ms = 0.0f;
@@ -866,7 +866,7 @@ int ctm_get_stats(ctm_ctx *ctx, ctm_stats *out, ctm_stream stream)
 
 int ctm_probe_int_rate(int kind, int iters, double *ops_per_clk_per_sm)
 {
-    if (kind < 0 || kind > 4 || iters < 1 || !ops_per_clk_per_sm) return CTM_EINVAL;
+    if (kind < 0 || kind > 5 || iters < 1 || !ops_per_clk_per_sm) return CTM_EINVAL;
     return run_int_probe(kind, iters, ops_per_clk_per_sm) == cudaSuccess ? CTM_OK : CTM_ECUDA;
 }
 

@@ -368,6 +368,75 @@ __device__ __forceinline__ void codes4(RowFn row, int sentinel, uint64_t (&c)[4]
     c[3] = ((uint64_t)__byte_perm(tB[2], tB[3], 0x7632) << 32) | __byte_perm(tB[0], tB[1], 0x7632);
 }
 
+// codes4 with the compares in packed fp16 (census mode 2).  Grid pixels are
+// exact fp16 integers 1024 + v (bit pattern 0x6400 | v), two per register, as
+// the spread words of codes4 with 0x64 in place of the zero bytes.  One compare
+// pair is one packed fused multiply-add with saturation, sat(nb * 1 - c): 1.0
+// where nb > c, else +0.0 -- exact, as every operand and difference is a small
+// integer.  A window row's compares accumulate as acc * 2 + r (fp16, exact below
+// 1024; a row holds at most 9 bits, first neighbour highest); adding 1024 to a
+// row's sum puts its bits in the low bits of each half, from where they go to
+// their code bits.  Both operations run on the FMA pipe, which leaves the ALU
+// pipe the byte spreading and the code assembly.
+template <int WW, int WH, typename RowFn>
+__device__ __forceinline__ void codes4_h(RowFn row, int sentinel, uint64_t (&c)[4])
+{
+    constexpr int sy = WH / 2;
+    constexpr int n = WW * WH;
+    constexpr int OFF = 4 - WW / 2;  // byte index of the window's left column for pixel x
+    static_assert(WW <= 10, "a window row's bits must stay below 1024");
+    const uint32_t H = 0x64646464u;
+    uint32_t vc[3];
+    row(sy, vc);
+    // -(1024 + c) for the centre pixels (x, x+1) and (x+2, x+3)
+    const uint32_t nA = __byte_perm(vc[1], H, 0x4140) ^ 0x80008000u;
+    const uint32_t nB = __byte_perm(vc[1], H, 0x4342) ^ 0x80008000u;
+    const __half2 one2 = __floats2half2_rn(1.0f, 1.0f), two2 = __floats2half2_rn(2.0f, 2.0f);
+    const __half2 bias2 = __floats2half2_rn(1024.0f, 1024.0f);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) c[q] = 0ull;
+#pragma unroll
+    for (int j = 0; j < WH; ++j) {
+        uint32_t v[3];
+        row(j, v);
+        uint32_t w[11];
+        const uint32_t s1 = __funnelshift_r(v[0], v[1], 8);  // b1 .. b4
+        const uint32_t s2 = __funnelshift_r(v[1], v[2], 8);  // b5 .. b8
+        w[0] = __byte_perm(v[0], H, 0x4140);
+        w[1] = __byte_perm(s1, H, 0x4140);
+        w[2] = __byte_perm(v[0], H, 0x4342);
+        w[3] = __byte_perm(s1, H, 0x4342);
+        w[4] = __byte_perm(v[1], H, 0x4140);
+        w[5] = __byte_perm(s2, H, 0x4140);
+        w[6] = __byte_perm(v[1], H, 0x4342);
+        w[7] = __byte_perm(s2, H, 0x4342);
+        w[8] = __byte_perm(v[2], H, 0x4140);
+        w[9] = __byte_perm(v[2], H, 0x4241);
+        w[10] = __byte_perm(v[2], H, 0x4342);
+        __half2 aA, aB;
+#pragma unroll
+        for (int i = 0; i < WW; ++i) {
+            const __half2 rA = __hfma2_sat(as_h2(w[OFF + i]), one2, as_h2(nA));
+            const __half2 rB = __hfma2_sat(as_h2(w[OFF + i + 2]), one2, as_h2(nB));
+            aA = i == 0 ? rA : __hfma2(aA, two2, rA);
+            aB = i == 0 ? rB : __hfma2(aB, two2, rB);
+        }
+        const __half2 hA = __hadd2(aA, bias2), hB = __hadd2(aB, bias2);
+        const uint32_t uA = *reinterpret_cast<const uint32_t *>(&hA);
+        const uint32_t uB = *reinterpret_cast<const uint32_t *>(&hB);
+        constexpr uint32_t m = (1u << WW) - 1u;
+        const int p_lo = n - WW * (j + 1);  // code bit of the row's last neighbour
+        c[0] |= (uint64_t)(uA & m) << p_lo;
+        c[1] |= (uint64_t)((uA >> 16) & m) << p_lo;
+        c[2] |= (uint64_t)(uB & m) << p_lo;
+        c[3] |= (uint64_t)((uB >> 16) & m) << p_lo;
+    }
+    if (sentinel) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) c[q] |= 1ull << n;
+    }
+}
+
 // Store the codes of pixels x .. x+3 of grid row y (zero where the window leaves
 // the grid, or for the whole row when `active` is false).
 template <int WW>
@@ -392,7 +461,7 @@ __device__ __forceinline__ void store4(const PlaneDesc &d, int x, int y, bool ac
 // bit layout as tile_codes), stored to the plane; `ok` false: this lane has
 // no tile and stores nothing.  All 32 lanes of the warp must call it together.
 // All window rows are loaded into registers before the first is used.
-template <int WW, int WH>
+template <int WW, int WH, bool F16 = false>
 __device__ __forceinline__ void census4(const PlaneDesc &d, int x0, int y, int hl, bool ok, int sentinel)
 {
     constexpr int sy = WH / 2;
@@ -452,9 +521,13 @@ __device__ __forceinline__ void census4(const PlaneDesc &d, int x0, int y, int h
         for (int r = 0; r < WH; ++r) load_row12(d, inside, x, y - sy + r, rows[r]);
     }
     uint64_t c[4] = {0ull, 0ull, 0ull, 0ull};
-    if (active)
-        codes4<WW, WH>([&](int j, uint32_t (&v)[3]) { v[0] = rows[j][0]; v[1] = rows[j][1]; v[2] = rows[j][2]; },
-                       sentinel, c);
+    if (active) {
+        auto row = [&](int j, uint32_t (&v)[3]) { v[0] = rows[j][0]; v[1] = rows[j][1]; v[2] = rows[j][2]; };
+        if constexpr (F16)
+            codes4_h<WW, WH>(row, sentinel, c);
+        else
+            codes4<WW, WH>(row, sentinel, c);
+    }
     if (ok) store4<WW>(d, x, y, active, c);
 }
 
@@ -616,7 +689,7 @@ __global__ void __launch_bounds__(256) tile_list_kernel(MatchArgs a)
 // instructions in lockstep.  MODE: 0 = 4 CTAs per SM (64 registers),
 // otherwise 3 CTAs per SM.
 template <int WW, int WH, int MODE>
-__global__ void __launch_bounds__(256, MODE == 0 ? 4 : 3) census_roi4_kernel(MatchArgs a)
+__global__ void __launch_bounds__(256, MODE == 1 ? 3 : 4) census_roi4_kernel(MatchArgs a)
 {
     constexpr int kLanes = kCensusTilePx / 4;  // lanes per tile (4 pixels each)
     constexpr int kPer = 32 / kLanes;          // tiles per warp step
@@ -630,7 +703,7 @@ __global__ void __launch_bounds__(256, MODE == 0 ? 4 : 3) census_roi4_kernel(Mat
         PlaneDesc d;
         int x0, y;
         const bool ok = tile_of(a, a.ws.tiles[t < n ? t : kPer * p], d, x0, y) && t < n;
-        census4<WW, WH>(d, x0, y, hl, ok, sentinel);
+        census4<WW, WH, MODE == 2>(d, x0, y, hl, ok, sentinel);
     }
 }
 
@@ -715,7 +788,8 @@ static int roi4_ctas(int mode)
 {
     static const int n0 = resident_ctas(census_roi4_kernel<WW, WH, 0>, 256, 0);
     static const int n1 = resident_ctas(census_roi4_kernel<WW, WH, 1>, 256, 0);
-    return mode == 0 ? n0 : n1;
+    static const int n2 = resident_ctas(census_roi4_kernel<WW, WH, 2>, 256, 0);
+    return mode == 0 ? n0 : (mode == 1 ? n1 : n2);
 }
 
 int census_roi_ctas_per_sm(int win_w, int win_h, int mode)
@@ -732,8 +806,10 @@ static void launch_roi4(const MatchArgs &a, int grid, cudaStream_t s)
 {
     if (a.census_mode == 0)
         census_roi4_kernel<WW, WH, 0><<<grid, 256, 0, s>>>(a);
-    else
+    else if (a.census_mode == 1)
         census_roi4_kernel<WW, WH, 1><<<grid, 256, 0, s>>>(a);
+    else
+        census_roi4_kernel<WW, WH, 2><<<grid, 256, 0, s>>>(a);
 }
 
 cudaError_t launch_census_roi(const MatchArgs &a, int sm_count, cudaStream_t s)

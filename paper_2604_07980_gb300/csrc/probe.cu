@@ -2,7 +2,8 @@
 //
 // Every SM runs one CTA of 1024 threads; each thread advances 8 independent
 // chains of the probed instruction (0: 32-bit popcount, 1: 3-input xor,
-// 2: packed fp16 greater-than mask, 3: 32-bit add, 4: 32-bit multiply-add), and the
+// 2: packed fp16 greater-than mask, 3: 32-bit add, 4: 32-bit multiply-add,
+// 5: packed fp16 fused multiply-add with saturation), and the
 // CTA's SM-clock cycle count gives operations per clock per SM.  Inline PTX with
 // volatile asm keeps the compiler from folding the chains.
 #include <algorithm>
@@ -45,6 +46,13 @@ __device__ __forceinline__ unsigned imad_op(unsigned x, unsigned y, unsigned z)
     return r;
 }
 
+__device__ __forceinline__ unsigned hfma2_sat_op(unsigned x, unsigned y, unsigned z)
+{
+    unsigned r;
+    asm volatile("fma.rn.sat.f16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(x), "r"(y), "r"(z));
+    return r;
+}
+
 __device__ __forceinline__ unsigned xor3_op(unsigned x, unsigned y, unsigned z)
 {
     unsigned r;
@@ -82,10 +90,15 @@ __global__ void __launch_bounds__(kProbeThreads) int_probe_kernel(int kind, int 
 #pragma unroll
             for (int c = 0; c < kChains; ++c) v[c] = iadd_op(v[c], y);
         }
-    } else {
+    } else if (kind == 4) {
         for (int i = 0; i < iters; ++i) {
 #pragma unroll
             for (int c = 0; c < kChains; ++c) v[c] = imad_op(v[c], y, z);
+        }
+    } else {
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) v[c] = hfma2_sat_op(v[c], y, z);
         }
     }
     __syncthreads();

@@ -63,7 +63,7 @@ def test_random_configuration(seed):
     batch = B.DeviceBatch(B.frames_to_device(w.frames), w.boxes, [(f.f_px, f.baseline_m) for f in w.frames])
     nd_max = max(params["far_dmax"] - params["far_dmin"], params["close_dmax"] - params["close_dmin"]) + 1
     narrow = ((nd_max + 2 + 7) // 8) * 8
-    runs = [dict(census_mode=0), dict(census_mode=1),
+    runs = [dict(census_mode=2), dict(census_mode=0),
             dict(match_mode=1, census_mode=1, strip_cols=narrow, match_threads=256)]
     for i, tuning in enumerate(runs):
         graph = i == 1

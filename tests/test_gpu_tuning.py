@@ -34,7 +34,7 @@ def test_tunings_do_not_change_results(torch_cuda):
     for matcher in (0, 1):
       for th in (128, 256):
         for cols in (base, base + 64, base + 192):
-            for mode in (0, 1):
+            for mode in (0, 1, 2):
                 for split in (1024, 1 << 30):
                     ctx.set_tuning(match_threads=th, strip_cols=cols, census_mode=mode, big_work=split,
                                    match_mode=matcher)
@@ -45,7 +45,7 @@ def test_tunings_do_not_change_results(torch_cuda):
                     assert np.array_equal(out["disp"], ref["disp"], equal_nan=True), where
                     assert np.array_equal(out["depth"], ref["depth"], equal_nan=True), where
     best, ms = ctx.autotune(batch, reps=2)
-    assert ms > 0 and best["match_threads"] in (128, 256) and best["census_mode"] in (0, 1)
+    assert ms > 0 and best["match_threads"] in (128, 256) and best["census_mode"] in (0, 1, 2)
     assert best["match_mode"] in (0, 1)
     assert best["strip_cols"] % 32 == 0 and best["strip_cols"] >= nd + 2
     assert ctx.get_tuning() == best
