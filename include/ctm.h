@@ -158,10 +158,10 @@ typedef struct {
                                scans the current one)                                 */
     int32_t split_ways;     /* fused matcher only: 0 = split every block's candidate range
                                into two (block, disparity-chunk) tiles when the queue
-                               holds fewer than about 0.6 blocks per resident CTA; 1 =
-                               never split; 2, 4 or 8 = always split into that many
-                               chunks.  Splitting needs one vertical offset
-                               (dy_min == dy_max)                                     */
+                               holds fewer than about 0.6 blocks per resident CTA and
+                               the CLOSE range has at least 128 candidates; 1 = never
+                               split; 2, 4 or 8 = always split into that many chunks.
+                               Splitting needs one vertical offset (dy_min == dy_max) */
 } ctm_tuning;
 
 /* Counters of the last match call (ctm_get_stats). */

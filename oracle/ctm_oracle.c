@@ -11,8 +11,8 @@
  *   search, backward search, consistency test, parabola) -> FAR disparity from its
  *   block, CLOSE disparity by robust aggregation -> depth by Eq. 1.
  *
- * Readings of points the paper leaves open are stated where they are used; the
- * same list is in the design notes.  Pins: Fig. 2's printed census code, the
+ * Readings of points the paper leaves open are stated where they are used.
+ * Pins: Fig. 2's printed census code, the
  * invariants the paper states, closed forms and brute force on tiny inputs
  * (tests/test_oracle_*.py).
  */

@@ -727,11 +727,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
     pf.on = true;
     pf.n_big = a.ws.counts->n_big;
     pf.nq = pf.n_big + a.ws.counts->n_small;
-    // fewer blocks than about 0.6 per resident CTA: (block, disparity-chunk) tiles, two
-    // per block (measured: more chunks only add per-tile cost); one vertical offset
-    // only, not in the allocation-free path
+    // fewer blocks than about 0.6 per resident CTA, and CLOSE blocks with at least 128
+    // candidates: (block, disparity-chunk) tiles, two per block (measured: narrower
+    // chunks and more of them only add per-tile cost); one vertical offset only, not
+    // in the allocation-free path
     if (a.ws.chunk != nullptr && a.p.dy_min == a.p.dy_max && pf.nq > 0 && a.split_ways != 1) {
-        const int w = a.split_ways > 1 ? a.split_ways : (8 * pf.nq <= 5 * (int)gridDim.x ? 2 : 1);
+        const bool short_queue = 8 * pf.nq <= 5 * (int)gridDim.x && a.p.close_dmax - a.p.close_dmin + 1 >= 128;
+        const int w = a.split_ways > 1 ? a.split_ways : (short_queue ? 2 : 1);
         const int ways = w >= 8 ? 8 : (w >= 4 ? 4 : (w >= 2 ? 2 : 1));
         if (ways > 1) {
             run_tiles<NT>(a, sm, sh, pf.n_big, pf.nq, ways);
