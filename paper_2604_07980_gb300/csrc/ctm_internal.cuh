@@ -1,6 +1,7 @@
 // ctm_internal.cuh -- shared declarations of the CUDA library (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -104,6 +105,9 @@ struct Workspace {
     BlockGeom *geom;           // [max_blocks] indexed like blocks
     int *queue;                // [max_blocks] searchable blocks: large from the front, small from the back
     BlockResult *blkres;       // [max_blocks]
+    const CUtensorMap *tmaps;  // [max_frames * 4] census planes L1, R1, Lk, Rk as 2-D tensors whose
+                               // box is one row of strip_cols codes (strip loads by tile::gather4);
+                               // null: strips load by 1-D bulk copies, one per row
     ChunkState *chunk;         // [max_blocks]; null: no disparity-chunk tiles
     int32_t *chunk_cost;       // [max_blocks * nc_stride] forward cost rows of split blocks
     Counts *counts;            // counters of the call in progress (zero between calls)
@@ -142,7 +146,7 @@ struct MatchArgs {
     int match_mode;            // 0: fused single-kernel matcher, 1: two-pass pipelined matcher
     int split_ways;            // disparity-chunk tiles: 0 automatic, 1 never, 2/4/8 always
     int census_mode;           // region-of-interest census variant (census.cu)
-    int strip_rows;            // rows of the shared-memory strip (pts_side * ndy)
+    int strip_rows;            // rows of the shared-memory strip (pts_side * ndy, rounded up to 4)
     int stats_accumulate;      // 1: the aggregation adds the call's counters to the stats record
     int inject_expiry;         // fault injection for tests: CTA 0 of the fused persistent matcher
                                // withholds its first strip copy, so its bounded wait expires
@@ -213,6 +217,15 @@ cudaError_t launch_match_pipe(const MatchArgs &a, int threads, int grid, cudaStr
 // Probes (probe.cu)
 cudaError_t run_int_probe(int kind, int iters, double *ops_per_clk_per_sm);
 cudaError_t run_wait_probe(int *expired, float *waited_ms);
+
+// Strip widths (codes) whose rows can load by tile::gather4 (a one-row box of at
+// most 256 elements whose rows stay 128-byte aligned in shared memory).
+__host__ __device__ inline bool gather_strip_ok(int strip_cols) { return strip_cols <= 256 && strip_cols % 16 == 0; }
+
+// Build the census planes' tensor maps of a workspace (api.cu): host-encoded and
+// copied to ws.tmaps; false if the driver's encoder is unavailable.
+bool encode_plane_maps(const Workspace &ws, const Caps &caps, int close_factor, int strip_cols,
+                       CUtensorMap *dev_maps);
 
 // Parameter checks of ctm_create (limits in include/ctm.h and the matcher's
 // strip budget) and the default strip width for a disparity range (api.cu).

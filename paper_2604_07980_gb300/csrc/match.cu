@@ -51,10 +51,18 @@ struct BlockCtx {
     int k, far;
     int dmin, dmax, nd, ndy, nc;
     int nx, ny, Ws, Hs;
+    int tm_l, tm_r;           // tensor maps of the left and right planes (tile::gather4 loads)
     long long pitch;
     const uint64_t *CL;
     const uint64_t *CR;
 };
+
+// Geometry of a strip chunk whose columns start at colbase, SWc wide: rows are stored
+// at the fixed strip width when they load by tile::gather4, else at the chunk's width.
+__device__ __forceinline__ ChunkGeom strip_geom(const MatchArgs &a, int colbase, int SWc)
+{
+    return chunk_geom(colbase, SWc, a.ws.tmaps != nullptr ? a.strip_cols : 0);
+}
 
 // Row r = (m, e) of a strip chunk: the right plane at Y_m + dy_min + e (forward)
 // or the left plane at Y_m + dy_f - (dy_min + e) (backward).
@@ -77,6 +85,34 @@ __device__ __forceinline__ void issue_chunk(const MatchArgs &a, const BlockCtx &
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid >= 32) return;
     const int rows = bc.ny * bc.ndy;
+    if (a.ws.tmaps != nullptr) {
+        // tile::gather4: four rows per copy, each the map's box of strip_cols codes from
+        // colbase_a (columns outside the plane's allocation read as zero); rows outside
+        // the grid are fetched as row 0 and zeroed by land_chunk, like the other columns
+        // outside [0, Ws)
+        const CUtensorMap *tm = a.ws.tmaps + (fwd ? bc.tm_r : bc.tm_l);
+        const int groups = (rows + 3) >> 2;
+        const unsigned total = (unsigned)groups * 4u * (unsigned)a.strip_cols * 8u;
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        if (lane == 0) {
+            mbar_arrive_expect_tx(&sh.mbar, withhold ? total + 16u : total);
+            sh.spend = 1;
+        }
+        __syncwarp();
+        if (!withhold) {
+            for (int q = lane; q < groups; q += 32) {
+                int y[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int r = min(4 * q + i, rows - 1);
+                    const int yy = chunk_row_y(a, bc, sh.Y, fwd, dy_f, r);
+                    y[i] = (yy >= 0 && yy < bc.Hs) ? yy : 0;
+                }
+                gather4_g2s(sm.strip + 4 * q * g.stride, tm, g.colbase_a, y[0], y[1], y[2], y[3], &sh.mbar);
+            }
+        }
+        return;
+    }
     const uint64_t *plane = fwd ? bc.CR : bc.CL;
     const int Ws_even = (bc.Ws + 1) & ~1;   // the padding column after an odd width is readable
     const int x_lo = max(g.colbase_a, 0);
@@ -99,7 +135,7 @@ __device__ __forceinline__ void issue_chunk(const MatchArgs &a, const BlockCtx &
         for (int r = lane; r < rows; r += 32) {
             const int y = chunk_row_y(a, bc, sh.Y, fwd, dy_f, r);
             if (y >= 0 && y < bc.Hs)
-                bulk_g2s(sm.strip + r * g.SWa + (x_lo - g.colbase_a), plane + (long long)y * bc.pitch + x_lo,
+                bulk_g2s(sm.strip + r * g.stride + (x_lo - g.colbase_a), plane + (long long)y * bc.pitch + x_lo,
                          row_bytes, &sh.mbar);
         }
     }
@@ -129,7 +165,7 @@ __device__ __forceinline__ bool land_chunk(const MatchArgs &a, const BlockCtx &b
         const int c_hi = max(min(bc.Ws - g.colbase_a, g.SWa), c_lo);   // [c_hi, SWa): x >= Ws
         for (int r = warp; r < rows; r += NT / 32) {
             const int y = chunk_row_y(a, bc, sh.Y, fwd, dy_f, r);
-            uint64_t *row = sm.strip + r * g.SWa;
+            uint64_t *row = sm.strip + r * g.stride;
             if (y < 0 || y >= bc.Hs) {
                 for (int c = lane; c < g.SWa; c += 32) row[c] = 0ull;
             } else {
@@ -177,9 +213,9 @@ __device__ bool scan_chunks(const MatchArgs &a, const BlockCtx &bc, const Smem &
         const int p0 = sh.colstart[j0], p1 = sh.colstart[j1];
         if (j0 > 0) {  // later chunks: load now (the first chunk was prefetched)
             const int SWc = sh.X[j1 - 1] - xj0 + bc.nd;
-            g = chunk_geom(fwd ? xj0 - bc.dmax : xj0 - d_f + bc.dmin, SWc);
+            g = strip_geom(a, fwd ? xj0 - bc.dmax : xj0 - d_f + bc.dmin, SWc);
             ok = load_chunk<NT>(a, bc, sm, sh, phase, fwd, dy_f, g) && ok;
-            set_bases<NT>(sm, sh.X, p0, p1, bc.ndy, g.SWa, xj0, g.delta);
+            set_bases<NT>(sm, sh.X, p0, p1, bc.ndy, g.stride, xj0, g.delta);
             __syncthreads();
         }
         if (fast) {
@@ -196,7 +232,7 @@ __device__ bool scan_chunks(const MatchArgs &a, const BlockCtx &bc, const Smem &
                 if (c < bc.nc) {
                     int e = 0;
                     while (c >= bc.nd) { c -= bc.nd; ++e; }
-                    o = e * g.SWa + (fwd ? (bc.nd - 1 - c) : c);
+                    o = e * g.stride + (fwd ? (bc.nd - 1 - c) : c);
                 }
                 coff[t] = o;
             }
@@ -283,6 +319,8 @@ __device__ __forceinline__ BlockCtx make_ctx(const MatchArgs &a, const BlockGeom
     bc.nx = g.nx;
     bc.ny = g.ny;
     const bool full = g.far || a.p.close_factor == 1;
+    bc.tm_l = 4 * g.frame + (full ? 0 : 2);
+    bc.tm_r = bc.tm_l + 1;
     const uint64_t *base = a.ws.census + (long long)g.frame * a.ws.frame_stride;
     bc.CL = full ? base : base + 2 * a.ws.plane1_elems;
     bc.CR = full ? base + a.ws.plane1_elems : base + 2 * a.ws.plane1_elems + a.ws.planek_elems;
@@ -308,7 +346,7 @@ __device__ __forceinline__ void layout_block(const BlockCtx &bc, const BlockGeom
             const int x = g.X[j], y = g.Y[m];
             if (left_codes) {
                 cp_async8(&sm.pcode[idx], bc.CL + (long long)y * bc.pitch + x);
-                if (j < j1_first) sm.pbase[idx] = 8 * (m * bc.ndy * g0.SWa + x - x0 + g0.delta);
+                if (j < j1_first) sm.pbase[idx] = 8 * (m * bc.ndy * g0.stride + x - x0 + g0.delta);
             }
             sm.pmj[idx] = (m << 8) | j;
         }
@@ -340,7 +378,7 @@ __device__ void begin_block_ctx(const MatchArgs &a, const BlockCtx &bc, const Bl
 {
     const int j1_first = first_chunk_end(g, bc.nx);
     const int x0 = g.X[0];
-    const ChunkGeom g0 = chunk_geom(x0 - bc.dmax, g.X[j1_first - 1] - x0 + bc.nd);
+    const ChunkGeom g0 = strip_geom(a, x0 - bc.dmax, g.X[j1_first - 1] - x0 + bc.nd);
     layout_block<NT>(bc, g, sm, sh, true, j1_first, g0);
     issue_chunk<NT>(a, bc, sm, sh, true, 0, g0, withhold);
 }
@@ -416,7 +454,7 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
     const int j1_first = later0 ? __ffs(later0) - 1 : bc.nx;
     const int x0 = g.X[0];
     const int SW0 = g.X[j1_first - 1] - x0 + bc.nd;
-    const ChunkGeom g0 = chunk_geom(x0 - bc.dmax, SW0);
+    const ChunkGeom g0 = strip_geom(a, x0 - bc.dmax, SW0);
 
     // 1. the left codes and the first forward strip chunk (issued by begin_block)
     bool ok = land_chunk<NT>(a, bc, sm, sh, phase, true, 0, g0);
@@ -450,24 +488,44 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
         }
     }
 
-    // 4. backward pass: first left strip (bulk copies, issued first), then the right
-    //    codes at the matched positions by plain loads -- the CTA waits for both, and
-    //    the loads overlap the copies' round trip (every warp's forward scans ended
-    //    at combine_pass's barrier)
-    const ChunkGeom gb = chunk_geom(x0 - d_f + bc.dmin, SW0);
-    issue_chunk<NT>(a, bc, sm, sh, false, dy_f, gb);
+    // 4. backward pass: the right codes at the matched positions and the first left
+    //    strip (every warp's forward scans ended at combine_pass's barrier).  A block
+    //    whose forward strip was one chunk still holds every matched position in it
+    //    (X_j - d_f lies in [X_j - dmax, X_j - dmin], row Y_m + dy_f among its rows,
+    //    zero where outside the plane as a global read gives), so its codes come from
+    //    shared memory before the backward copies overwrite the strip; otherwise they
+    //    are plain global loads that overlap the copies' round trip.
+    const ChunkGeom gb = strip_geom(a, x0 - d_f + bc.dmin, SW0);
     {
         constexpr int kPer = kMaxPts / NT;
         uint64_t v[kPer];
+        if (j1_first == bc.nx) {
+            const int col0 = bc.dmax + g0.delta - x0 - d_f;  // strip column of X_j - d_f is X_j + col0
+            const int row_e = dy_f - a.p.dy_min;
 #pragma unroll
-        for (int i = 0; i < kPer; ++i) {
-            const int t = tid + i * NT;
-            v[i] = 0ull;
-            if (t < total) {
-                const int mj = sm.pmj[t];
-                const int qx = sh.X[mj & 255] - d_f, qy = sh.Y[mj >> 8] + dy_f;
-                if (qx >= 0 && qx < bc.Ws && qy >= 0 && qy < bc.Hs)
-                    v[i] = __ldg(bc.CR + (long long)qy * bc.pitch + qx);
+            for (int i = 0; i < kPer; ++i) {
+                const int t = tid + i * NT;
+                v[i] = 0ull;
+                if (t < total) {
+                    const int mj = sm.pmj[t];
+                    const int r = (mj >> 8) * bc.ndy + row_e;
+                    v[i] = sm.strip[r * g0.stride + sh.X[mj & 255] + col0];
+                }
+            }
+            __syncthreads();  // the strip's reads are done before the backward copies
+            issue_chunk<NT>(a, bc, sm, sh, false, dy_f, gb);
+        } else {
+            issue_chunk<NT>(a, bc, sm, sh, false, dy_f, gb);
+#pragma unroll
+            for (int i = 0; i < kPer; ++i) {
+                const int t = tid + i * NT;
+                v[i] = 0ull;
+                if (t < total) {
+                    const int mj = sm.pmj[t];
+                    const int qx = sh.X[mj & 255] - d_f, qy = sh.Y[mj >> 8] + dy_f;
+                    if (qx >= 0 && qx < bc.Ws && qy >= 0 && qy < bc.Hs)
+                        v[i] = __ldg(bc.CR + (long long)qy * bc.pitch + qx);
+                }
             }
         }
 #pragma unroll
@@ -475,7 +533,7 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
             if (tid + i * NT < total) sm.pcode[tid + i * NT] = v[i];
     }
     ok = land_chunk<NT>(a, bc, sm, sh, phase, false, dy_f, gb);
-    set_bases<NT>(sm, sh.X, 0, sh.colstart[j1_first], bc.ndy, gb.SWa, x0, gb.delta);
+    set_bases<NT>(sm, sh.X, 0, sh.colstart[j1_first], bc.ndy, gb.stride, x0, gb.delta);
     if (!__syncthreads_and(ok)) return false;
     ok = scan_chunks<NT>(a, bc, sm, sh, phase, false, gb, acc, d_f, dy_f);
     unsigned keyb;
@@ -580,15 +638,15 @@ __device__ bool process_tile(const MatchArgs &a, int b, int c, int ways, bool bw
         bool ok;
         if (!bwd) {
             begin_block_ctx<NT>(a, bc, g, sm, sh, withhold);
-            ok = land_chunk<NT>(a, bc, sm, sh, phase, true, 0, chunk_geom(x0 - bc.dmax, SW0));
+            ok = land_chunk<NT>(a, bc, sm, sh, phase, true, 0, strip_geom(a, x0 - bc.dmax, SW0));
             cp_async_wait_all();
             if (!__syncthreads_and(ok)) return false;
-            ok = scan_chunks<NT>(a, bc, sm, sh, phase, true, chunk_geom(x0 - bc.dmax, SW0), acc, 0, 0);
+            ok = scan_chunks<NT>(a, bc, sm, sh, phase, true, strip_geom(a, x0 - bc.dmax, SW0), acc, 0, 0);
             if (!combine_pass<NT>(a, bc, sm, true, acc, ok, key, c0, a.ws.chunk_cost + (long long)b * a.nc_stride + c0))
                 return false;
         } else {
             const int dy_f = a.p.dy_min;
-            const ChunkGeom gb = chunk_geom(x0 - d_f + bc.dmin, SW0);
+            const ChunkGeom gb = strip_geom(a, x0 - d_f + bc.dmin, SW0);
             layout_block<NT>(bc, g, sm, sh, false, j1_first, gb);
             issue_chunk<NT>(a, bc, sm, sh, false, dy_f, gb);
             for (int t = tid; t < total; t += NT) {  // right codes at the matched positions
@@ -598,7 +656,7 @@ __device__ bool process_tile(const MatchArgs &a, int b, int c, int ways, bool bw
                                   ? __ldg(bc.CR + (long long)qy * bc.pitch + qx) : 0ull;
             }
             ok = land_chunk<NT>(a, bc, sm, sh, phase, false, dy_f, gb);
-            set_bases<NT>(sm, sh.X, 0, sh.colstart[j1_first], bc.ndy, gb.SWa, x0, gb.delta);
+            set_bases<NT>(sm, sh.X, 0, sh.colstart[j1_first], bc.ndy, gb.stride, x0, gb.delta);
             if (!__syncthreads_and(ok)) return false;
             ok = scan_chunks<NT>(a, bc, sm, sh, phase, false, gb, acc, d_f, dy_f);
             if (!combine_pass<NT>(a, bc, sm, false, acc, ok, key, c0)) return false;

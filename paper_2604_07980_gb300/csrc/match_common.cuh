@@ -220,16 +220,31 @@ __device__ __forceinline__ void set_bases(const Smem &sm, const int *X, int p0, 
 struct ChunkGeom {
     int colbase_a;  // first stored column (even)
     int delta;      // colbase - colbase_a (0 or 1)
-    int SWa;        // row stride in elements (even)
+    int SWa;        // stored width in elements (even)
+    int stride;     // row stride of the strip in shared memory, elements (SWa, or the fixed
+                    // strip width when rows load by tile::gather4)
 };
 
-__device__ __forceinline__ ChunkGeom chunk_geom(int colbase, int SWc)
+__device__ __forceinline__ ChunkGeom chunk_geom(int colbase, int SWc, int fixed_stride = 0)
 {
     ChunkGeom g;
     g.colbase_a = colbase & ~1;
     g.delta = colbase - g.colbase_a;
     g.SWa = (SWc + g.delta + 1) & ~1;
+    g.stride = fixed_stride > 0 ? fixed_stride : g.SWa;
     return g;
+}
+
+// tile::gather4: rows y0..y3 of a 2-D tensor, one box of columns from x (the
+// tensor map's one-row box), into four consecutive rows of shared memory at dst.
+__device__ __forceinline__ void gather4_g2s(void *dst, const CUtensorMap *tm, int x, int y0, int y1, int y2,
+                                           int y3, uint64_t *mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cta.global.tile::gather4.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];\n"
+        ::"r"(smem_addr(dst)), "l"(tm), "r"(x), "r"(y0), "r"(y1), "r"(y2), "r"(y3), "r"(smem_addr(mbar))
+        : "memory");
 }
 
 }  // namespace

@@ -157,6 +157,7 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
     ws.blocks = reinterpret_cast<int2 *>(b + o_blocks);
     ws.blkres = reinterpret_cast<BlockResult *>(b + o_blkres);
     ws.chunk = nullptr;  // no disparity-chunk tiles: their state does not fit the array
+    ws.tmaps = nullptr;  // strips load by 1-D bulk copies
     ws.chunk_cost = nullptr;
     ws.geom = reinterpret_cast<BlockGeom *>(b + o_geom);
     ws.queue = reinterpret_cast<int *>(b + o_queue);
