@@ -49,7 +49,7 @@ struct ctm_ctx {
     int nd_max = 0;
     int inject_expiry = 0;  // armed by ctm_inject_wait_expiry (tests)
     int split_ways = 0;
-    bool maps_ok = false;    // ws.tmaps hold the planes' maps for the current strip width
+    bool maps_ok = false;    // ws.tmaps hold the planes' maps
     void *dev_mem = nullptr;
     size_t dev_bytes = 0;
     cudaStream_t capture_stream = nullptr;
@@ -96,15 +96,16 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 }  // namespace
 
 // Each census plane of each frame slot as a 2-D tensor of uint64 codes (pitch x
-// rows of the workspace plane), with a one-row box of strip_cols codes: a strip
-// chunk's rows load four at a time by tile::gather4.  Columns beyond the pitch and
-// rows beyond the workspace plane read as zero; codes between a frame's width and
-// the pitch are zeroed by the matcher after landing, as for 1-D copies.
-bool ctm::encode_plane_maps(const Workspace &ws, const Caps &caps, int k, int strip_cols, CUtensorMap *dev_maps)
+// rows of the workspace plane), once per box width of one row of 32, 64, ... 256
+// codes: a strip chunk's rows load four at a time by tile::gather4 with the
+// narrowest box that holds them.  Columns beyond the pitch and rows beyond the
+// workspace plane read as zero; codes between a frame's width and the pitch are
+// zeroed by the matcher after landing, as for 1-D copies.
+bool ctm::encode_plane_maps(const Workspace &ws, const Caps &caps, int k, CUtensorMap *dev_maps)
 {
     const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-    if (!enc || !gather_strip_ok(strip_cols) || !dev_maps) return false;
-    std::vector<CUtensorMap> maps((size_t)4 * caps.max_frames);
+    if (!enc || !dev_maps || caps.max_frames > kMaxMapFrames) return false;
+    std::vector<CUtensorMap> maps((size_t)4 * kBoxClasses * caps.max_frames);
     memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
     const long long rows1 = caps.max_height, rowsk = (caps.max_height + k - 1) / k;
     for (int f = 0; f < caps.max_frames; ++f) {
@@ -115,12 +116,14 @@ bool ctm::encode_plane_maps(const Workspace &ws, const Caps &caps, int k, int st
             const long long pitch = q < 2 ? ws.pitch1 : ws.pitchk;
             const cuuint64_t dims[2] = {(cuuint64_t)pitch, (cuuint64_t)(q < 2 ? rows1 : rowsk)};
             const cuuint64_t strides[1] = {(cuuint64_t)pitch * 8u};
-            const cuuint32_t box[2] = {(cuuint32_t)strip_cols, 1u};
             const cuuint32_t estr[2] = {1u, 1u};
-            if (enc(&maps[(size_t)4 * f + q], CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, base, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-                return false;
+            for (int c = 0; c < kBoxClasses; ++c) {
+                const cuuint32_t box[2] = {(cuuint32_t)(32 * (c + 1)), 1u};
+                if (enc(&maps[((size_t)4 * f + q) * kBoxClasses + c], CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, base,
+                        dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                    return false;
+            }
         }
     }
     if (cudaMemcpy(dev_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -187,7 +190,7 @@ MatchArgs make_args(const ctm_ctx *ctx, const ctm_frame *frames, const int32_t *
     a.census_mode = ctx->census_mode;
     a.match_mode = ctx->match_mode;
     a.split_ways = ctx->split_ways;
-    if (!ctx->maps_ok || !gather_strip_ok(ctx->strip_cols)) a.ws.tmaps = nullptr;
+    if (!ctx->maps_ok) a.ws.tmaps = nullptr;
     a.stats_accumulate = 0;
     a.inject_expiry = 0;
     return a;
@@ -349,7 +352,8 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
     const size_t o_blocks = take(sizeof(int2) * (size_t)ctx->caps.max_blocks);
     const size_t o_blkres = take(sizeof(BlockResult) * (size_t)ctx->caps.max_blocks);
     const size_t o_chunk = take(sizeof(ChunkState) * (size_t)ctx->caps.max_blocks);
-    const size_t o_tmaps = take(sizeof(CUtensorMap) * 4 * (size_t)max_frames);
+    const size_t o_tmaps =
+        take(max_frames <= kMaxMapFrames ? sizeof(CUtensorMap) * 4 * kBoxClasses * (size_t)max_frames : 0);
     const size_t o_ccost = take(sizeof(int32_t) * (size_t)ctx->caps.max_blocks * ctx->nc_stride);
     const size_t o_geom = take(sizeof(BlockGeom) * (size_t)ctx->caps.max_blocks);
     const size_t o_queue = take(sizeof(int) * (size_t)ctx->caps.max_blocks);
@@ -407,7 +411,7 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
         ctm_destroy(ctx);
         return CTM_ECUDA;
     }
-    ctx->maps_ok = encode_plane_maps(ws, ctx->caps, k, ctx->strip_cols, const_cast<CUtensorMap *>(ws.tmaps));
+    ctx->maps_ok = encode_plane_maps(ws, ctx->caps, k, const_cast<CUtensorMap *>(ws.tmaps));
     MatchArgs a = make_args(ctx, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
     if (match_configure(a, ctx->match_threads, &ctx->ctas_per_sm) != cudaSuccess || ctx->ctas_per_sm < 1) {
         cudaGetLastError();
@@ -791,11 +795,6 @@ int ctm_set_tuning(ctm_ctx *ctx, const ctm_tuning *t)
     const bool changed = t->match_threads != ctx->match_threads || t->strip_cols != ctx->strip_cols ||
                          t->census_mode != ctx->census_mode || t->big_work != ctx->big_work ||
                          t->match_mode != ctx->match_mode || t->split_ways != ctx->split_ways;
-    if (t->strip_cols != ctx->strip_cols) {  // the maps' box is the strip width: none of this
-        cudaDeviceSynchronize();             // context's kernels may be reading them
-        ctx->maps_ok = encode_plane_maps(ctx->ws, ctx->caps, ctx->p.close_factor, t->strip_cols,
-                                         const_cast<CUtensorMap *>(ctx->ws.tmaps));
-    }
     ctx->match_threads = t->match_threads;
     ctx->strip_cols = t->strip_cols;
     ctx->census_mode = t->census_mode;

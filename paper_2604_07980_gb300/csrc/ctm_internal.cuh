@@ -105,9 +105,9 @@ struct Workspace {
     BlockGeom *geom;           // [max_blocks] indexed like blocks
     int *queue;                // [max_blocks] searchable blocks: large from the front, small from the back
     BlockResult *blkres;       // [max_blocks]
-    const CUtensorMap *tmaps;  // [max_frames * 4] census planes L1, R1, Lk, Rk as 2-D tensors whose
-                               // box is one row of strip_cols codes (strip loads by tile::gather4);
-                               // null: strips load by 1-D bulk copies, one per row
+    const CUtensorMap *tmaps;  // [max_frames * 4 * kBoxClasses] census planes L1, R1, Lk, Rk as 2-D
+                               // tensors, one map per box width of one row of 32 c codes (strip
+                               // loads by tile::gather4); null: 1-D bulk copies, one per row
     ChunkState *chunk;         // [max_blocks]; null: no disparity-chunk tiles
     int32_t *chunk_cost;       // [max_blocks * nc_stride] forward cost rows of split blocks
     Counts *counts;            // counters of the call in progress (zero between calls)
@@ -218,14 +218,17 @@ cudaError_t launch_match_pipe(const MatchArgs &a, int threads, int grid, cudaStr
 cudaError_t run_int_probe(int kind, int iters, double *ops_per_clk_per_sm);
 cudaError_t run_wait_probe(int *expired, float *waited_ms);
 
-// Strip widths (codes) whose rows can load by tile::gather4 (a one-row box of at
-// most 256 elements whose rows stay 128-byte aligned in shared memory).
-__host__ __device__ inline bool gather_strip_ok(int strip_cols) { return strip_cols <= 256 && strip_cols % 16 == 0; }
+// Tensor-map box widths of the strip loads: 32, 64, ..., 256 codes (a box row is at
+// most 256 elements).  A strip chunk stored SWa codes wide loads by tile::gather4
+// with the narrowest box that holds it, its rows then kBox apart in shared memory
+// (a multiple of 32 codes, so every four-row group starts 128-byte aligned).
+constexpr int kBoxClasses = 8;
+constexpr int kMaxMapFrames = 256;  // contexts with more frame slots use 1-D copies only
+__host__ __device__ inline int box_width(int SWa) { return (SWa + 31) & ~31; }
 
 // Build the census planes' tensor maps of a workspace (api.cu): host-encoded and
 // copied to ws.tmaps; false if the driver's encoder is unavailable.
-bool encode_plane_maps(const Workspace &ws, const Caps &caps, int close_factor, int strip_cols,
-                       CUtensorMap *dev_maps);
+bool encode_plane_maps(const Workspace &ws, const Caps &caps, int close_factor, CUtensorMap *dev_maps);
 
 // Parameter checks of ctm_create (limits in include/ctm.h and the matcher's
 // strip budget) and the default strip width for a disparity range (api.cu).

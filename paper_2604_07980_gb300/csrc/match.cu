@@ -57,11 +57,12 @@ struct BlockCtx {
     const uint64_t *CR;
 };
 
-// Geometry of a strip chunk whose columns start at colbase, SWc wide: rows are stored
-// at the fixed strip width when they load by tile::gather4, else at the chunk's width.
+// Geometry of a strip chunk whose columns start at colbase, SWc wide: rows load by
+// tile::gather4 with the narrowest box that holds them when it fits the strip's
+// shared-memory width, else by 1-D copies at the chunk's own width.
 __device__ __forceinline__ ChunkGeom strip_geom(const MatchArgs &a, int colbase, int SWc)
 {
-    return chunk_geom(colbase, SWc, a.ws.tmaps != nullptr ? a.strip_cols : 0);
+    return chunk_geom(colbase, SWc, a.ws.tmaps != nullptr ? min(a.strip_cols, 32 * kBoxClasses) : 0);
 }
 
 // Row r = (m, e) of a strip chunk: the right plane at Y_m + dy_min + e (forward)
@@ -85,14 +86,14 @@ __device__ __forceinline__ void issue_chunk(const MatchArgs &a, const BlockCtx &
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid >= 32) return;
     const int rows = bc.ny * bc.ndy;
-    if (a.ws.tmaps != nullptr) {
-        // tile::gather4: four rows per copy, each the map's box of strip_cols codes from
+    if (g.box > 0) {
+        // tile::gather4: four rows per copy, each the map's box of g.box codes from
         // colbase_a (columns outside the plane's allocation read as zero); rows outside
         // the grid are fetched as row 0 and zeroed by land_chunk, like the other columns
         // outside [0, Ws)
-        const CUtensorMap *tm = a.ws.tmaps + (fwd ? bc.tm_r : bc.tm_l);
+        const CUtensorMap *tm = a.ws.tmaps + (fwd ? bc.tm_r : bc.tm_l) * kBoxClasses + (g.box / 32 - 1);
         const int groups = (rows + 3) >> 2;
-        const unsigned total = (unsigned)groups * 4u * (unsigned)a.strip_cols * 8u;
+        const unsigned total = (unsigned)groups * 4u * (unsigned)g.box * 8u;
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         if (lane == 0) {
             mbar_arrive_expect_tx(&sh.mbar, withhold ? total + 16u : total);

@@ -221,17 +221,20 @@ struct ChunkGeom {
     int colbase_a;  // first stored column (even)
     int delta;      // colbase - colbase_a (0 or 1)
     int SWa;        // stored width in elements (even)
-    int stride;     // row stride of the strip in shared memory, elements (SWa, or the fixed
-                    // strip width when rows load by tile::gather4)
+    int box;        // tensor-map box width when the rows load by tile::gather4, else 0
+    int stride;     // row stride of the strip in shared memory, elements (box or SWa)
 };
 
-__device__ __forceinline__ ChunkGeom chunk_geom(int colbase, int SWc, int fixed_stride = 0)
+// gather_max: the widest box the caller's strip holds (0: 1-D copies only).
+__device__ __forceinline__ ChunkGeom chunk_geom(int colbase, int SWc, int gather_max = 0)
 {
     ChunkGeom g;
     g.colbase_a = colbase & ~1;
     g.delta = colbase - g.colbase_a;
     g.SWa = (SWc + g.delta + 1) & ~1;
-    g.stride = fixed_stride > 0 ? fixed_stride : g.SWa;
+    const int box = box_width(g.SWa);
+    g.box = gather_max > 0 && box <= gather_max ? box : 0;
+    g.stride = g.box > 0 ? g.box : g.SWa;
     return g;
 }
 
