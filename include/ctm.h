@@ -150,8 +150,10 @@ typedef struct {
                                integer multiply-add compares, 4 CTAs per SM; 1 = the
                                same, 3 CTAs per SM; 2 = packed fp16 compares with
                                saturation, 4 CTAs per SM                              */
-    int32_t big_work;       /* blocks with usable points x candidates >= big_work are
-                               queued first (largest work first)                      */
+    int32_t queue_rounds;   /* fused matcher: 1 = the first blocks of a launch go out in
+                               per-SM rounds (every SM one block of each round; the
+                               queue runs from the largest blocks down), 0 = one
+                               dynamic queue                                          */
     int32_t match_mode;     /* 0: fused matcher (one CTA runs both passes of a block);
                                1: two-pass pipelined matcher (a forward kernel, then a
                                backward kernel; each CTA loads its next block while it
@@ -355,7 +357,7 @@ int ctm_set_tuning(ctm_ctx *ctx, const ctm_tuning *t);
 
 /* Autotuner: runs the batch of ctm_match_batch (same arguments, no debug
  * output) under candidate tunings -- every matching CTA size x strip width,
- * for each matcher, then each census variant, each queue split and automatic
+ * for each matcher, then each census variant, rounds on and off and automatic
  * or no disparity-chunk tiles around the best so far --
  * timing `reps` calls of each with CUDA events after one warm-up call, keeps
  * the fastest in the context and returns it in *best (and its time per call,
@@ -378,8 +380,8 @@ int ctm_probe_int_rate(int kind, int iters, double *ops_per_clk_per_sm);
  * next match call on it that launches the fused persistent matcher directly
  * (ctm_match_boxes, ctm_match_batch with use_graph = 0, ctm_match_batch_host;
  * tuning match_mode 0; not a graph replay, not the plain per-box path) has its
- * first matching CTA announce a strip copy on its mbarrier without issuing it.
- * That CTA's bounded wait then expires (about 1 s, then about 1 s more for the
+ * CTA that takes the queue's first block (or first tile) announce a strip copy
+ * on its mbarrier without issuing it.  That CTA's bounded wait then expires (about 1 s, then about 1 s more for the
  * copies in flight, of which there are none), it records the error and stops;
  * the other CTAs finish the queue.  The call's outputs follow the CTM_ETIMEOUT
  * rule above, and ctm_match_batch_host returns CTM_ETIMEOUT.  The arming is

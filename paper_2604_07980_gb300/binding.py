@@ -83,7 +83,7 @@ class ctm_geometry(ctypes.Structure):
 
 class ctm_tuning(ctypes.Structure):
     _fields_ = [("match_threads", ctypes.c_int32), ("strip_cols", ctypes.c_int32),
-                ("census_mode", ctypes.c_int32), ("big_work", ctypes.c_int32),
+                ("census_mode", ctypes.c_int32), ("queue_rounds", ctypes.c_int32),
                 ("match_mode", ctypes.c_int32), ("split_ways", ctypes.c_int32)]
 
     def as_dict(self) -> dict:

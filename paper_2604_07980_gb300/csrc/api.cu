@@ -44,7 +44,7 @@ struct ctm_ctx {
     int strip_cols = 0;
     int strip_rows = 0;
     int census_mode = 0;
-    int big_work = 4096;
+    int queue_rounds = 1;
     int match_mode = 0;
     int nd_max = 0;
     int inject_expiry = 0;  // armed by ctm_inject_wait_expiry (tests)
@@ -186,7 +186,8 @@ MatchArgs make_args(const ctm_ctx *ctx, const ctm_frame *frames, const int32_t *
     a.nc_stride = ctx->nc_stride;
     a.strip_cols = ctx->strip_cols;
     a.strip_rows = ctx->strip_rows;
-    a.big_work = ctx->big_work;
+    a.queue_rounds = ctx->queue_rounds;
+    a.sm_count = ctx->sm_count;
     a.census_mode = ctx->census_mode;
     a.match_mode = ctx->match_mode;
     a.split_ways = ctx->split_ways;
@@ -357,6 +358,8 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
     const size_t o_ccost = take(sizeof(int32_t) * (size_t)ctx->caps.max_blocks * ctx->nc_stride);
     const size_t o_geom = take(sizeof(BlockGeom) * (size_t)ctx->caps.max_blocks);
     const size_t o_queue = take(sizeof(int) * (size_t)ctx->caps.max_blocks);
+    const size_t o_queue_w = take(sizeof(int) * kQueueClasses * (size_t)ctx->caps.max_blocks);
+    const size_t o_sched = take(sizeof(int) * kSchedInts);
     const size_t o_counts = take(sizeof(Counts));
     const size_t o_stats = take(sizeof(Counts));
     const size_t o_frames = take(sizeof(ctm_frame) * (size_t)max_frames);
@@ -397,6 +400,8 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
     ws.chunk_cost = reinterpret_cast<int32_t *>(base + o_ccost);
     ws.geom = reinterpret_cast<BlockGeom *>(base + o_geom);
     ws.queue = reinterpret_cast<int *>(base + o_queue);
+    ws.queue_w = reinterpret_cast<int *>(base + o_queue_w);
+    ws.sched = reinterpret_cast<int *>(base + o_sched);
     ws.counts = reinterpret_cast<Counts *>(base + o_counts);
     ws.stats = reinterpret_cast<Counts *>(base + o_stats);
     ws.frames = reinterpret_cast<ctm_frame *>(base + o_frames);
@@ -755,7 +760,7 @@ int ctm_get_tuning(const ctm_ctx *ctx, ctm_tuning *out)
     out->match_threads = ctx->match_threads;
     out->strip_cols = ctx->strip_cols;
     out->census_mode = ctx->census_mode;
-    out->big_work = ctx->big_work;
+    out->queue_rounds = ctx->queue_rounds;
     out->match_mode = ctx->match_mode;
     out->split_ways = ctx->split_ways;
     return CTM_OK;
@@ -767,7 +772,7 @@ int ctm_set_tuning(ctm_ctx *ctx, const ctm_tuning *t)
     if (t->match_threads != 128 && t->match_threads != 256) return CTM_EINVAL;
     if (t->strip_cols < ctx->nd_max + 2 || (t->strip_cols & 7) != 0 || t->strip_cols > 4096) return CTM_EINVAL;
     if (t->census_mode < 0 || t->census_mode > 2) return CTM_EINVAL;
-    if (t->big_work < 0) return CTM_EINVAL;
+    if (t->queue_rounds != 0 && t->queue_rounds != 1) return CTM_EINVAL;
     if (t->match_mode != 0 && t->match_mode != 1) return CTM_EINVAL;
     if (t->split_ways != 0 && t->split_ways != 1 && t->split_ways != 2 && t->split_ways != 4 &&
         t->split_ways != 8)
@@ -793,12 +798,12 @@ int ctm_set_tuning(ctm_ctx *ctx, const ctm_tuning *t)
         }
     }
     const bool changed = t->match_threads != ctx->match_threads || t->strip_cols != ctx->strip_cols ||
-                         t->census_mode != ctx->census_mode || t->big_work != ctx->big_work ||
+                         t->census_mode != ctx->census_mode || t->queue_rounds != ctx->queue_rounds ||
                          t->match_mode != ctx->match_mode || t->split_ways != ctx->split_ways;
     ctx->match_threads = t->match_threads;
     ctx->strip_cols = t->strip_cols;
     ctx->census_mode = t->census_mode;
-    ctx->big_work = t->big_work;
+    ctx->queue_rounds = t->queue_rounds;
     ctx->match_mode = t->match_mode;
     ctx->split_ways = t->split_ways;
     ctx->ctas_per_sm = ctas;
@@ -869,7 +874,7 @@ int ctm_autotune(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *count
         }
       }
     }
-    // 2. census variant, 3. queue split, one at a time around the best so far
+    // 2. census variant, 3. per-SM rounds, one at a time around the best so far
     const int modes[3] = {0, 1, 2};
     for (int i = 0; i < 3 && status == CTM_OK; ++i) {
         ctm_tuning t = bt;
@@ -879,10 +884,9 @@ int ctm_autotune(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *count
         if (r != CTM_OK) { status = r; break; }
         if (ms < bms) { bms = ms; bt = t; }
     }
-    const int splits[5] = {1024, 2048, 4096, 8192, 1 << 30};
-    for (int i = 0; i < 5 && status == CTM_OK; ++i) {
+    for (int i = 0; i < 2 && status == CTM_OK; ++i) {
         ctm_tuning t = bt;
-        t.big_work = splits[i];
+        t.queue_rounds = i;
         float ms = 0.0f;
         const int r = measure(t, &ms);
         if (r != CTM_OK) { status = r; break; }

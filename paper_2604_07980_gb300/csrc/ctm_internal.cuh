@@ -18,6 +18,24 @@ constexpr int kMaxOcc = 32;
 constexpr int kMaxWin = 15;
 constexpr int kPlanThreads = 256;
 
+// The sampling kernel queues every searchable block twice.  The first queue
+// keeps the blocks near their neighbours (sampling order: boxes of a frame
+// together, so blocks whose strips overlap run close in time and share the L2):
+// blocks with at least kBigWork usable points x candidates from the front, the
+// others from the back.  The second is ordered by decreasing work without a
+// sort: one of kQueueClasses classes of usable points x candidates per block
+// (half-octave classes down from the largest possible block, kMaxPts x
+// kMaxCand), each class a region of max_blocks entries, positions running
+// through the classes in order.  The fused persistent matcher takes the second
+// when the whole queue goes out in its first wave (see match.cu).
+constexpr int kBigWork = 4096;
+constexpr int kQueueClasses = 16;
+// Per-SM rounds of the fused persistent matcher: arrival counters for SM ids below
+// kSchedSMs, then one claim counter per round.
+constexpr int kSchedSMs = 256;
+constexpr int kMaxRounds = 8;
+constexpr int kSchedInts = kSchedSMs + kMaxRounds;
+
 // Device-side counters of one call.
 struct Counts {
     int n_frames;    // clamped to capacity
@@ -29,6 +47,7 @@ struct Counts {
     int n_big;       // searchable blocks queued from the front (large work)
     int n_small;     // searchable blocks queued from the back (small work)
     int n_tiles;     // census tiles listed for the region-of-interest census
+    int n_class[kQueueClasses];  // searchable blocks in each work class (ws.queue_w)
 };
 
 // Planned box (device).
@@ -104,6 +123,8 @@ struct Workspace {
     int2 *blocks;              // [max_blocks] (box, slot), flat in box order
     BlockGeom *geom;           // [max_blocks] indexed like blocks
     int *queue;                // [max_blocks] searchable blocks: large from the front, small from the back
+    int *queue_w;              // [kQueueClasses * max_blocks] the same blocks by work class; null: none
+    int *sched;                // [kSchedInts] rounds of the fused persistent matcher; null: none
     BlockResult *blkres;       // [max_blocks]
     const CUtensorMap *tmaps;  // [max_frames * 4 * kBoxClasses] census planes L1, R1, Lk, Rk as 2-D
                                // tensors, one map per box width of one row of 32 c codes (strip
@@ -142,17 +163,71 @@ struct MatchArgs {
     ctm_debug dbg;
     int nc_stride;
     int strip_cols;            // columns of the shared-memory strip
-    int big_work;              // queue split: usable points x candidates of a large block
+    int queue_rounds;          // 1: when its whole queue fits its first wave, the fused persistent
+                               // matcher hands the blocks out in per-SM rounds from the
+                               // work-ordered queue (needs ws.queue_w, ws.sched); 0: never
+    int sm_count;              // SMs of the device (rounds are sm_count positions wide)
     int match_mode;            // 0: fused single-kernel matcher, 1: two-pass pipelined matcher
     int split_ways;            // disparity-chunk tiles: 0 automatic, 1 never, 2/4/8 always
     int census_mode;           // region-of-interest census variant (census.cu)
     int strip_rows;            // rows of the shared-memory strip (pts_side * ndy, rounded up to 4)
     int stats_accumulate;      // 1: the aggregation adds the call's counters to the stats record
-    int inject_expiry;         // fault injection for tests: CTA 0 of the fused persistent matcher
-                               // withholds its first strip copy, so its bounded wait expires
+    int inject_expiry;         // fault injection for tests: the CTA of the fused persistent matcher
+                               // that takes queue position 0 withholds that block's first strip
+                               // copy, so its bounded wait expires
 };
 
 __host__ __device__ inline int ceil_div_nn(int a, int b) { return (a + b - 1) / b; }
+
+// Work class of a searchable block with `work` = usable points x candidates of
+// one pass: 0 for the largest possible block, one class per half octave below.
+__device__ __forceinline__ int queue_class(int work)
+{
+    if (work < 2) return kQueueClasses - 1;
+    const int l = 31 - __clz(work);                   // floor(log2(work))
+    const int s = 2 * l + ((work >> (l - 1)) & 1);    // + 1 from 1.5 * 2^l on
+    constexpr int kTop = 2 * 16;                      // s of kMaxPts * kMaxCand = 2^16
+    return min(max(kTop - s, 0), kQueueClasses - 1);
+}
+
+// Start of each class's positions in the work-ordered queue
+// (start[kQueueClasses] = queue length), from the counters of the call.
+__device__ __forceinline__ void queue_starts(const Counts *c, int *start)
+{
+    int n[kQueueClasses];
+#pragma unroll
+    for (int i = 0; i < kQueueClasses; ++i) n[i] = c->n_class[i];
+    int acc = 0;
+#pragma unroll
+    for (int i = 0; i < kQueueClasses; ++i) {
+        start[i] = acc;
+        acc += n[i];
+    }
+    start[kQueueClasses] = acc;
+}
+
+// The work-ordered queue is written (by the sampling kernel) and read (by the
+// fused persistent matcher) only when the call plans at most kMaxRounds blocks per
+// SM: only then can the whole queue fit in the matcher's first wave, and larger
+// calls skip its atomics.
+__device__ __forceinline__ bool work_queue_on(const MatchArgs &a, int n_blocks)
+{
+    return a.ws.queue_w != nullptr && a.sm_count > 0 && n_blocks <= kMaxRounds * a.sm_count;
+}
+
+// Block at position p of the work-ordered queue (0 <= p < start[kQueueClasses]).
+__device__ __forceinline__ int queue_w_at(const MatchArgs &a, const int *start, int p)
+{
+    int c = 0;
+    while (c < kQueueClasses - 1 && p >= start[c + 1]) ++c;
+    return a.ws.queue_w[(long long)c * a.caps.max_blocks + (p - start[c])];
+}
+
+// Block at position p of the first queue (n_big blocks from the front).
+__device__ __forceinline__ int queue_at(const MatchArgs &a, int n_big, int p)
+{
+    return p < n_big ? a.ws.queue[p] : a.ws.queue[a.caps.max_blocks - 1 - (p - n_big)];
+}
 
 // Sampled coordinate j of n on [b0, b1): the centre of the j-th of n equal cells
 // (Sec. 4.3.4's regular point grid).

@@ -38,8 +38,9 @@ struct Shared {
     int X[kMaxPtsSide];
     int Y[kMaxPtsSide];
     int colstart[kMaxPtsSide + 1];
-    int next;               // queue index of the next block
+    int next;               // queue position of the next block
     int next_b;             // its block
+    int qstart[kQueueClasses + 1];  // position of each work class's first block (work-ordered queue)
     int gpend;              // a geometry copy is in flight on mbar_g
     int spend;              // a strip copy is in flight on mbar
     unsigned cstart;        // bit j set: a strip column chunk starts at point column j
@@ -295,11 +296,59 @@ __device__ __forceinline__ bool combine_pass(const MatchArgs &a, const BlockCtx 
     return true;
 }
 
-// Queue entry i: large work from the front, small work from the back.
-__device__ __forceinline__ int queue_block(const MatchArgs &a, int i, int n_big)
+// Work distribution of the fused persistent kernel.  With more queued blocks
+// than CTAs, every CTA takes blocks from the first queue (sampling order, for
+// L2 locality) as it frees up, and the load evens out over the many blocks.
+// When the whole queue goes out in the first wave (a single frame, a small
+// batch), the dynamic queue alone lets one SM's CTAs take several of the
+// largest blocks while another SM gets small ones, and the kernel lasts as long
+// as the most loaded SM.  Then the blocks come from the work-ordered queue (the
+// largest first) in rounds of sm_count positions: the r-th CTA to start on an
+// SM takes a position of round r, so every SM gets one block of each round, of
+// similar work.  A position of a round that no CTA of that rank took (an SM that
+// ran fewer CTAs) is swept up by the next CTA that asks for work, so every
+// position is taken exactly once whichever SMs the CTAs land on.
+constexpr unsigned kRoundPauseNs = 1500;
+
+__device__ __forceinline__ unsigned sm_id()
 {
-    return i < n_big ? a.ws.queue[i] : a.ws.queue[a.caps.max_blocks - 1 - (i - n_big)];
+    unsigned r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    return r;
 }
+
+// Thread 0, rounds mode (every position belongs to a round): a round position
+// that no CTA of that rank took; nq when every position is taken.
+__device__ __forceinline__ int sweep_rounds(int *sched, int nq, int R, int n_sm)
+{
+    for (int r = 0; r < R; ++r) {
+        const int lim = min(n_sm, nq - r * n_sm);
+        if (*reinterpret_cast<volatile int *>(sched + kSchedSMs + r) < lim) {
+            const int k = atomicAdd(sched + kSchedSMs + r, 1);
+            if (k < lim) return r * n_sm + k;
+        }
+    }
+    return nq;
+}
+
+// Thread 0: first queue position of this CTA -- its SM rank's round position,
+// if any; CTAs without one pause briefly (bounded by the timer and an
+// iteration cap) so that they do not sweep up positions before the CTAs of
+// lower ranks that are still starting take them.
+__device__ __forceinline__ int take_first_round(int *sched, int nq, int R, int n_sm)
+{
+    const unsigned sid = sm_id();
+    const int rank = sid < (unsigned)kSchedSMs ? atomicAdd(sched + sid, 1) : R;
+    if (rank < R) {
+        const int lim = min(n_sm, nq - rank * n_sm);
+        const int k = atomicAdd(sched + kSchedSMs + rank, 1);
+        if (k < lim) return rank * n_sm + k;
+    }
+    const unsigned long long t0 = global_ns();
+    for (int it = 0; it < 64 && global_ns() - t0 < kRoundPauseNs; ++it) __nanosleep(128);
+    return sweep_rounds(sched, nq, R, n_sm);
+}
+
 
 // Block context from the block's sampling record (which carries its box plan).
 __device__ __forceinline__ BlockCtx make_ctx(const MatchArgs &a, const BlockGeom &g, int b)
@@ -427,9 +476,25 @@ __device__ __forceinline__ void write_record(const MatchArgs &a, const BlockCtx 
 // Prefetch state of the persistent kernel.  A single-block launch has none.
 struct Prefetch {
     bool on;
-    int n_big, nq;
-    int buf;  // geometry buffer of the next block
+    int n_big, nq;  // first queue: blocks from the front; queue length
+    int R;          // rounds (rounds mode only)
+    int buf;        // geometry buffer of the next block
 };
+
+// Thread 0: the next queue position of a CTA and the block there (ROUNDS: the
+// work-ordered queue, positions swept from the rounds; else the first queue,
+// positions from the dynamic queue head).
+template <bool ROUNDS>
+__device__ __forceinline__ int next_position(const MatchArgs &a, const Prefetch &pf)
+{
+    return ROUNDS ? sweep_rounds(a.ws.sched, pf.nq, pf.R, a.sm_count) : atomicAdd(&a.ws.counts->queue_head, 1);
+}
+
+template <bool ROUNDS, int NW>
+__device__ __forceinline__ int queue_block(const MatchArgs &a, const Shared<NW> &sh, const Prefetch &pf, int p)
+{
+    return ROUNDS ? queue_w_at(a, sh.qstart, p) : queue_at(a, pf.n_big, p);
+}
 
 // One block end to end, after begin_block.  With pf.on, thread 0 takes the next
 // queue index at the start and issues the next block's record copy once the
@@ -440,14 +505,14 @@ struct Prefetch {
 // rows, so no barrier separates one pass's argmin from the next pass's
 // zeroing.  Returns false if a bounded wait expired.  evals: thread 0 adds this
 // block's evaluation count.
-template <int NT>
+template <int NT, bool ROUNDS = false>
 __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<NT / 32> &sh,
                               unsigned &phase, int gbuf, Prefetch &pf, unsigned &gphase,
                               unsigned long long &evals)
 {
     const int tid = threadIdx.x;
     int next_i = 0;
-    if (pf.on && tid == 0) next_i = atomicAdd(&a.ws.counts->queue_head, 1);
+    if (pf.on && tid == 0) next_i = next_position<ROUNDS>(a, pf);
     const BlockGeom &g = sh.geom[gbuf];
     const BlockCtx bc = make_ctx(a, g, b);
     const int total = g.n_valid;
@@ -461,7 +526,7 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
     bool ok = land_chunk<NT>(a, bc, sm, sh, phase, true, 0, g0);
     cp_async_wait_all();
     int next_b = 0;
-    if (pf.on && tid == 0 && next_i < pf.nq) next_b = queue_block(a, next_i, pf.n_big);
+    if (pf.on && tid == 0 && next_i < pf.nq) next_b = queue_block<ROUNDS>(a, sh, pf, next_i);
     if (!__syncthreads_and(ok)) return false;
 
     // 2-3. forward pass, argmin (every thread), parabola inputs
@@ -738,14 +803,13 @@ __device__ void run_tiles(const MatchArgs &a, const Smem &sm, Shared<NT / 32> &s
     unsigned phase = 0, gphase = 0;
     unsigned long long evals = 0ull;
     const int n_fwd = nq * ways, n_tiles = 2 * n_fwd;
-    bool first = true;
     for (;;) {
         if (threadIdx.x == 0) {
             const int i = atomicAdd(&a.ws.counts->queue_head, 1);
             sh.next = i;
             if (i < n_tiles) {
                 const int j = i < n_fwd ? i : i - n_fwd;
-                sh.next_b = queue_block(a, j / ways, n_big);
+                sh.next_b = queue_at(a, n_big, j / ways);
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 mbar_arrive_expect_tx(&sh.mbar_g, (unsigned)sizeof(BlockGeom));
                 bulk_g2s(&sh.geom[0], a.ws.geom + sh.next_b, (unsigned)sizeof(BlockGeom), &sh.mbar_g);
@@ -764,8 +828,7 @@ __device__ void run_tiles(const MatchArgs &a, const Smem &sm, Shared<NT / 32> &s
         if (threadIdx.x == 0) sh.gpend = 0;
         const bool bwd = i >= n_fwd;
         const int j = bwd ? i - n_fwd : i;
-        const bool withhold = first && a.inject_expiry != 0 && blockIdx.x == 0 && !bwd;
-        first = false;
+        const bool withhold = a.inject_expiry != 0 && i == 0;  // the first forward tile
         if (!process_tile<NT>(a, sh.next_b, j % ways, ways, bwd, sm, sh, phase, evals, withhold)) {
             drain<NT>(a, sh, phase, gphase);
             break;
@@ -775,41 +838,25 @@ __device__ void run_tiles(const MatchArgs &a, const Smem &sm, Shared<NT / 32> &s
     if (threadIdx.x == 0 && evals) atomicAdd(&a.ws.counts->evals, evals);
 }
 
-template <int NT>
-__global__ void __launch_bounds__(NT, 1024 / NT)
-    match_persistent_kernel(MatchArgs a)
+// The persistent kernel's block loop: thread 0 takes the first queue position
+// (ROUNDS: its SM rank's round) and fetches that block's record; then block after
+// block, each taking and beginning the next one (process_block).
+template <int NT, bool ROUNDS>
+__device__ void run_blocks(const MatchArgs &a, const Smem &sm, Shared<NT / 32> &sh, Prefetch &pf)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ Shared<NT / 32> sh;
-    const Smem sm = carve(a, smem_raw);
-    Prefetch pf;
-    pf.on = true;
-    pf.n_big = a.ws.counts->n_big;
-    pf.nq = pf.n_big + a.ws.counts->n_small;
-    // fewer blocks than about 0.6 per resident CTA, and CLOSE blocks with at least 128
-    // candidates: (block, disparity-chunk) tiles, two per block (measured: narrower
-    // chunks and more of them only add per-tile cost); one vertical offset only, not
-    // in the allocation-free path
-    if (a.ws.chunk != nullptr && a.p.dy_min == a.p.dy_max && pf.nq > 0 && a.split_ways != 1) {
-        const bool short_queue = 8 * pf.nq <= 5 * (int)gridDim.x && a.p.close_dmax - a.p.close_dmin + 1 >= 128;
-        const int w = a.split_ways > 1 ? a.split_ways : (short_queue ? 2 : 1);
-        const int ways = w >= 8 ? 8 : (w >= 4 ? 4 : (w >= 2 ? 2 : 1));
-        if (ways > 1) {
-            run_tiles<NT>(a, sm, sh, pf.n_big, pf.nq, ways);
-            return;
-        }
-    }
     if (threadIdx.x == 0) {
         mbar_init(&sh.mbar, 1);
         mbar_init(&sh.mbar_g, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        const int i = atomicAdd(&a.ws.counts->queue_head, 1);
+        if (ROUNDS) queue_starts(a.ws.counts, sh.qstart);
+        const int i = ROUNDS ? take_first_round(a.ws.sched, pf.nq, pf.R, a.sm_count)
+                             : atomicAdd(&a.ws.counts->queue_head, 1);
         sh.next = i;
         sh.gpend = 0;
         sh.spend = 0;
         if (i < pf.nq) {
-            sh.next_b = queue_block(a, i, pf.n_big);
+            sh.next_b = queue_block<ROUNDS>(a, sh, pf, i);
             mbar_arrive_expect_tx(&sh.mbar_g, (unsigned)sizeof(BlockGeom));
             bulk_g2s(&sh.geom[0], a.ws.geom + sh.next_b, (unsigned)sizeof(BlockGeom), &sh.mbar_g);
             sh.gpend = 1;
@@ -826,10 +873,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
             if (threadIdx.x == 0) sh.gpend = 0;
             int b = sh.next_b;
             int buf = 0;
-            begin_block<NT>(a, b, sm, sh, buf, a.inject_expiry != 0 && blockIdx.x == 0);
+            begin_block<NT>(a, b, sm, sh, buf, a.inject_expiry != 0 && sh.next == 0);
             for (;;) {
                 pf.buf = buf ^ 1;
-                if (!process_block<NT>(a, b, sm, sh, phase, buf, pf, gphase, evals)) {
+                if (!process_block<NT, ROUNDS>(a, b, sm, sh, phase, buf, pf, gphase, evals)) {
                     drain<NT>(a, sh, phase, gphase);
                     break;
                 }
@@ -842,6 +889,49 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
         }
     }
     if (threadIdx.x == 0 && evals) atomicAdd(&a.ws.counts->evals, evals);
+}
+
+// ROUNDS (chosen by the host, see rounds_kernel): the work-ordered queue in
+// per-SM rounds; else the first queue, or disparity-chunk tiles.
+template <int NT, bool ROUNDS>
+__global__ void __launch_bounds__(NT, 1024 / NT)
+    match_persistent_kernel(MatchArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ Shared<NT / 32> sh;
+    const Smem sm = carve(a, smem_raw);
+    Prefetch pf;
+    pf.on = true;
+    const int n_big = a.ws.counts->n_big;
+    pf.nq = n_big + a.ws.counts->n_small;
+    pf.n_big = n_big;
+    if (ROUNDS) {
+        if (pf.nq < 1) return;
+        // the host's choice guarantees a written work-ordered queue of at most
+        // kMaxRounds rounds; should it not hold, the call reports an error
+        pf.R = ceil_div_nn(pf.nq, a.sm_count);
+        if (pf.R > kMaxRounds || !work_queue_on(a, a.ws.counts->n_blocks)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.ws.counts->error, 1);
+            return;
+        }
+        run_blocks<NT, true>(a, sm, sh, pf);
+        return;
+    }
+    pf.R = 0;
+    // fewer blocks than about 0.6 per resident CTA, and CLOSE blocks with at least 128
+    // candidates: (block, disparity-chunk) tiles, two per block (measured: narrower
+    // chunks and more of them only add per-tile cost); one vertical offset only, not
+    // in the allocation-free path
+    if (a.ws.chunk != nullptr && a.p.dy_min == a.p.dy_max && pf.nq > 0 && a.split_ways != 1) {
+        const bool short_queue = 8 * pf.nq <= 5 * (int)gridDim.x && a.p.close_dmax - a.p.close_dmin + 1 >= 128;
+        const int w = a.split_ways > 1 ? a.split_ways : (short_queue ? 2 : 1);
+        const int ways = w >= 8 ? 8 : (w >= 4 ? 4 : (w >= 2 ? 2 : 1));
+        if (ways > 1) {
+            run_tiles<NT>(a, sm, sh, n_big, pf.nq, ways);
+            return;
+        }
+    }
+    run_blocks<NT, false>(a, sm, sh, pf);
 }
 
 template <int NT>
@@ -867,7 +957,7 @@ __global__ void __launch_bounds__(NT) match_box_kernel(MatchArgs a, int box)
     unsigned long long evals = 0ull;
     Prefetch pf;
     pf.on = false;
-    pf.n_big = pf.nq = 0;
+    pf.n_big = pf.nq = pf.R = 0;
     pf.buf = 1;
     begin_block<NT>(a, b, sm, sh, 0);
     if (!process_block<NT>(a, b, sm, sh, phase, 0, pf, gphase, evals)) drain<NT>(a, sh, phase, gphase);
@@ -902,33 +992,67 @@ cudaError_t match_configure(const MatchArgs &a, int threads, int *ctas_per_sm)
     return match_configure_raise(a, threads, ctas_per_sm);
 }
 
+namespace {
+
+// Raise one persistent kernel's shared-memory limit to `need` and query its
+// resident CTAs per SM.
+template <int NT, bool ROUNDS>
+cudaError_t raise_persistent(int need, int *ctas_per_sm)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, match_persistent_kernel<NT, ROUNDS>);
+    if (e == cudaSuccess && fa.maxDynamicSharedSizeBytes < need)
+        e = cudaFuncSetAttribute(match_persistent_kernel<NT, ROUNDS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 need);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm,
+                                                                           match_persistent_kernel<NT, ROUNDS>, NT, need);
+    return e;
+}
+
+template <int NT>
+cudaError_t raise_persistent_both(int need, int *ctas_per_sm)
+{
+    int c0 = 0, c1 = 0;
+    cudaError_t e = raise_persistent<NT, false>(need, &c0);
+    if (e == cudaSuccess) e = raise_persistent<NT, true>(need, &c1);
+    *ctas_per_sm = c0 < c1 ? c0 : c1;
+    return e;
+}
+
+// The rounds variant of the persistent kernel serves contexts whose whole
+// capacity of blocks fits in kMaxRounds rounds (then the sampling kernel always
+// writes the work-ordered queue, and every call's queue fits in them), unless
+// rounds are tuned off or disparity-chunk tiles are forced.
+bool rounds_kernel(const MatchArgs &a)
+{
+    return a.queue_rounds && a.ws.sched != nullptr && a.ws.queue_w != nullptr && a.split_ways <= 1 &&
+           a.sm_count > 0 && a.caps.max_blocks <= kMaxRounds * a.sm_count;
+}
+
+}  // namespace
+
 cudaError_t match_configure_raise(const MatchArgs &a, int threads, int *ctas_per_sm)
 {
     const int need = (int)match_smem_bytes(a);
-    cudaFuncAttributes fa;
-    cudaError_t e = cudaSuccess;
-    if (threads == 128) {
-        e = cudaFuncGetAttributes(&fa, match_persistent_kernel<128>);
-        if (e == cudaSuccess && fa.maxDynamicSharedSizeBytes < need)
-            e = cudaFuncSetAttribute(match_persistent_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, match_persistent_kernel<128>, 128, need);
-    } else {
-        e = cudaFuncGetAttributes(&fa, match_persistent_kernel<256>);
-        if (e == cudaSuccess && fa.maxDynamicSharedSizeBytes < need)
-            e = cudaFuncSetAttribute(match_persistent_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, need);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, match_persistent_kernel<256>, 256, need);
-    }
-    return e;
+    return threads == 128 ? raise_persistent_both<128>(need, ctas_per_sm)
+                          : raise_persistent_both<256>(need, ctas_per_sm);
 }
 
 cudaError_t launch_match_persistent(const MatchArgs &a, int threads, int grid, cudaStream_t s)
 {
-    if (threads == 128)
-        match_persistent_kernel<128><<<grid, 128, match_smem_bytes(a), s>>>(a);
-    else
-        match_persistent_kernel<256><<<grid, 256, match_smem_bytes(a), s>>>(a);
+    const size_t smem = match_smem_bytes(a);
+    const bool r = rounds_kernel(a);
+    if (threads == 128) {
+        if (r)
+            match_persistent_kernel<128, true><<<grid, 128, smem, s>>>(a);
+        else
+            match_persistent_kernel<128, false><<<grid, 128, smem, s>>>(a);
+    } else {
+        if (r)
+            match_persistent_kernel<256, true><<<grid, 256, smem, s>>>(a);
+        else
+            match_persistent_kernel<256, false><<<grid, 256, smem, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -74,11 +74,6 @@ __device__ __forceinline__ void carve_pipe(const MatchArgs &a, unsigned char *ra
     }
 }
 
-__device__ __forceinline__ int pipe_queue_block(const MatchArgs &a, int i, int n_big)
-{
-    return i < n_big ? a.ws.queue[i] : a.ws.queue[a.caps.max_blocks - 1 - (i - n_big)];
-}
-
 // Thread 0: start the copy of block b's sampling record into record buffer gb.
 template <int NW>
 __device__ __forceinline__ void issue_record(const MatchArgs &a, PipeShared<NW> &sh, int gb, int b)
@@ -387,7 +382,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) match_pass_kernel(MatchArgs a)
     const int G = gridDim.x;
     auto qblock = [&](int k) -> int {
         const long long i = (long long)blockIdx.x + (long long)k * G;
-        return i < nq ? pipe_queue_block(a, (int)i, n_big) : -1;
+        return i < nq ? queue_at(a, n_big, (int)i) : -1;
     };
     const int b0 = qblock(0);
     if (b0 < 0) return;

@@ -161,6 +161,8 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
     ws.chunk_cost = nullptr;
     ws.geom = reinterpret_cast<BlockGeom *>(b + o_geom);
     ws.queue = reinterpret_cast<int *>(b + o_queue);
+    ws.queue_w = nullptr;  // one dynamic queue in sampling order (no per-SM rounds)
+    ws.sched = nullptr;
     ws.counts = reinterpret_cast<Counts *>(b + o_counts);
     ws.stats = reinterpret_cast<Counts *>(b + o_stats);
     ws.frames = reinterpret_cast<ctm_frame *>(b + o_frames);
@@ -186,7 +188,8 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
     a.dbg.cost_b = nullptr;
     a.nc_stride = nd_max * ndy;
     a.strip_cols = strip_cols;
-    a.big_work = 4096;
+    a.queue_rounds = 0;
+    a.sm_count = ds.sm_count;
     a.census_mode = 0;
     a.match_mode = 0;
     a.split_ways = 1;

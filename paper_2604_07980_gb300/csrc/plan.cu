@@ -361,12 +361,18 @@ __global__ void __launch_bounds__(256) sample_kernel(MatchArgs a)
                 cs.fkey = cs.bkey = 0xffffffffu;
                 a.ws.chunk[b] = cs;
             }
-            if (n_valid * nd * ndy >= a.big_work) {
+            const int work = n_valid * nd * ndy;
+            if (work >= kBigWork) {
                 const int q = atomicAdd(&a.ws.counts->n_big, 1);
                 a.ws.queue[q] = b;
             } else {
                 const int q = atomicAdd(&a.ws.counts->n_small, 1);
                 a.ws.queue[a.caps.max_blocks - 1 - q] = b;
+            }
+            if (work_queue_on(a, a.ws.counts->n_blocks)) {
+                const int c = queue_class(work);
+                const int q = atomicAdd(&a.ws.counts->n_class[c], 1);
+                a.ws.queue_w[(long long)c * a.caps.max_blocks + q] = b;
             }
         }
         // census demand of the searchable block (see mark_range)
@@ -412,13 +418,15 @@ cudaError_t launch_sample(const MatchArgs &a, cudaStream_t s)
 // It is the last kernel of a call, so it also leaves the workspace ready for
 // the next one: block 0 moves the counters to the stats record and zeroes
 // them -- all but the error flag, which every CTA reads here and the next
-// call's plan_kernel clears -- and every box's block count goes back to zero
-// (no memset nodes at the start of a call).
+// call's plan_kernel clears -- and the matcher's round counters, and every
+// box's block count goes back to zero (no memset nodes at the start of a call).
 __global__ void __launch_bounds__(256) aggregate_kernel(MatchArgs a)
 {
     __shared__ float scratch[8][2 * kMaxSlots];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int failed = *reinterpret_cast<volatile int *>(&a.ws.counts->error);
+    if (blockIdx.x == 0 && a.ws.sched)
+        for (int i = threadIdx.x; i < kSchedInts; i += blockDim.x) a.ws.sched[i] = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const Counts c = *a.ws.counts;
         if (a.stats_accumulate) {  // a later sub-batch of one call
@@ -432,6 +440,7 @@ __global__ void __launch_bounds__(256) aggregate_kernel(MatchArgs a)
             t.n_big += c.n_big;
             t.n_small += c.n_small;
             t.n_tiles += c.n_tiles;
+            for (int i = 0; i < kQueueClasses; ++i) t.n_class[i] += c.n_class[i];
             *a.ws.stats = t;
         } else {
             *a.ws.stats = c;

@@ -362,3 +362,38 @@ def test_disparity_chunk_tiles_bit_exact(torch_cuda, name):
             assert st["error"] == 0, where
             assert st["cost_evals"] == oracle_evals(ref["blocks"], ref["flags"], w.params), where
     ctx.close()
+
+
+@pytest.mark.parametrize("threads,strip_extra", [(128, 0), (256, 0), (256, 320)])
+def test_queue_rounds_bit_exact(torch_cuda, threads, strip_extra):
+    """Per-SM rounds over the work-ordered queue (a context whose capacity fits in
+    the rounds, so the rounds variant of the persistent matcher runs) against the
+    oracle and against one dynamic queue: block records, every cost, box outputs and
+    the evaluation count.  With 256 threads and a wide strip only three CTAs fit an
+    SM, so the fourth round has no CTA of its rank anywhere and every one of its
+    positions is swept up by CTAs asking for their next block."""
+    from paper_2604_07980_gb300 import binding as B
+    sms = torch_cuda.cuda.get_device_properties(0).multi_processor_count
+    w = wl.frame1080()
+    slots = w.params.get("grid_g", 4) ** 2
+    if w.n_boxes * slots > 8 * sms:
+        pytest.skip("the context's capacity does not fit in the rounds on this GPU")
+    frames = [(f.left, f.right, f.f_px, f.baseline_m) for f in w.frames]
+    ref = orc.match_batch(frames, w.boxes, orc.Params(**w.params), debug=True)
+    H, W = w.frames[0].left.shape
+    ctx = B.Context(w.params, len(w.frames), W, H, w.n_boxes)
+    batch = B.DeviceBatch(B.frames_to_device(w.frames), w.boxes, [(f.f_px, f.baseline_m) for f in w.frames])
+    cols = ctx.get_tuning()["strip_cols"] + strip_extra
+    for rounds in (1, 0):
+        ctx.set_tuning(match_threads=threads, strip_cols=cols, split_ways=1, queue_rounds=rounds)
+        for graph in (False, True):
+            got = ctx.match_batch(batch, use_graph=graph, debug=True)
+            torch_cuda.cuda.synchronize()
+            where = f"threads {threads} strip {cols} rounds {rounds} graph {graph}"
+            out = {k: v.cpu().numpy() for k, v in got.items() if k != "debug"}
+            compare_box_outputs(out, ref, where)
+            compare_debug(got["debug"], ref, B.n_candidates(ctx.params), where)
+            st = ctx.stats()
+            assert st["error"] == 0, where
+            assert st["cost_evals"] == oracle_evals(ref["blocks"], ref["flags"], w.params), where
+    ctx.close()

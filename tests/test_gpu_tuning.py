@@ -35,11 +35,11 @@ def test_tunings_do_not_change_results(torch_cuda):
       for th in (128, 256):
         for cols in (base, base + 64, base + 192):
             for mode in (0, 1, 2):
-                for split in (1024, 1 << 30):
-                    ctx.set_tuning(match_threads=th, strip_cols=cols, census_mode=mode, big_work=split,
+                for split in (0, 1):
+                    ctx.set_tuning(match_threads=th, strip_cols=cols, census_mode=mode, queue_rounds=split,
                                    match_mode=matcher)
                     out, st = _outputs(torch_cuda, ctx, batch)
-                    where = f"matcher {matcher} threads {th} cols {cols} census {mode} split {split}"
+                    where = f"matcher {matcher} threads {th} cols {cols} census {mode} rounds {split}"
                     assert st["cost_evals"] == st0["cost_evals"] and st["error"] == 0, where
                     assert np.array_equal(out["flags"], ref["flags"]), where
                     assert np.array_equal(out["disp"], ref["disp"], equal_nan=True), where
