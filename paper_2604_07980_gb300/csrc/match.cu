@@ -44,7 +44,7 @@ struct Shared {
     int gpend;              // a geometry copy is in flight on mbar_g
     int spend;              // a strip copy is in flight on mbar
     unsigned cstart;        // bit j set: a strip column chunk starts at point column j
-    int abort;              // a bounded wait expired: stop this CTA
+    int nq;                 // rounds mode: queue length, -1 without a work-ordered queue
 };
 
 struct BlockCtx {
@@ -331,14 +331,12 @@ __device__ __forceinline__ int sweep_rounds(int *sched, int nq, int R, int n_sm)
     return nq;
 }
 
-// Thread 0: first queue position of this CTA -- its SM rank's round position,
-// if any; CTAs without one pause briefly (bounded by the timer and an
+// Thread 0: first queue position of this CTA -- the round position of its rank
+// on its SM (the order in which the SM's CTAs started), if any; CTAs without one pause briefly (bounded by the timer and an
 // iteration cap) so that they do not sweep up positions before the CTAs of
 // lower ranks that are still starting take them.
-__device__ __forceinline__ int take_first_round(int *sched, int nq, int R, int n_sm)
+__device__ __forceinline__ int take_first_round(int *sched, int rank, int nq, int R, int n_sm)
 {
-    const unsigned sid = sm_id();
-    const int rank = sid < (unsigned)kSchedSMs ? atomicAdd(sched + sid, 1) : R;
     if (rank < R) {
         const int lim = min(n_sm, nq - rank * n_sm);
         const int k = atomicAdd(sched + kSchedSMs + rank, 1);
@@ -477,17 +475,33 @@ __device__ __forceinline__ void write_record(const MatchArgs &a, const BlockCtx 
 struct Prefetch {
     bool on;
     int n_big, nq;  // first queue: blocks from the front; queue length
-    int R;          // rounds (rounds mode only)
+    int R, rank;    // rounds mode: rounds; thread 0: this CTA's rank on its SM
     int buf;        // geometry buffer of the next block
 };
 
-// Thread 0: the next queue position of a CTA and the block there (ROUNDS: the
-// work-ordered queue, positions swept from the rounds; else the first queue,
-// positions from the dynamic queue head).
-template <bool ROUNDS>
-__device__ __forceinline__ int next_position(const MatchArgs &a, const Prefetch &pf)
+// Rounds mode, warp 0 after a block's forward pass: a round position that no CTA
+// of that rank took, from the round counters lane r read (into h) when the block
+// started -- a counter seen full stays full, one seen with room is claimed by an
+// atomic that may still lose -- so the sweep adds no round trip to a block unless
+// it finds one.  Lane 0 gets the position (nq: none).
+__device__ __forceinline__ int sweep_rounds_warp(int *sched, int nq, int R, int n_sm, int h)
 {
-    return ROUNDS ? sweep_rounds(a.ws.sched, pf.nq, pf.R, a.sm_count) : atomicAdd(&a.ws.counts->queue_head, 1);
+    const int lane = threadIdx.x & 31;
+    const int lim = lane < R ? min(n_sm, nq - lane * n_sm) : 0;
+    unsigned room = __ballot_sync(0xffffffffu, lane < R && h < lim);
+    int pos = nq;
+    if (lane == 0) {
+        while (room) {
+            const int r = __ffs(room) - 1;
+            const int k = atomicAdd(sched + kSchedSMs + r, 1);
+            if (k < min(n_sm, nq - r * n_sm)) {
+                pos = r * n_sm + k;
+                break;
+            }
+            room &= room - 1u;
+        }
+    }
+    return pos;
 }
 
 template <bool ROUNDS, int NW>
@@ -511,8 +525,12 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
                               unsigned long long &evals)
 {
     const int tid = threadIdx.x;
-    int next_i = 0;
-    if (pf.on && tid == 0) next_i = next_position<ROUNDS>(a, pf);
+    int next_i = 0, h = 0;
+    if (ROUNDS) {  // the round counters, read now and used after the forward pass
+        if (pf.on && tid < pf.R) h = *reinterpret_cast<volatile int *>(a.ws.sched + kSchedSMs + tid);
+    } else if (pf.on && tid == 0) {
+        next_i = atomicAdd(&a.ws.counts->queue_head, 1);
+    }
     const BlockGeom &g = sh.geom[gbuf];
     const BlockCtx bc = make_ctx(a, g, b);
     const int total = g.n_valid;
@@ -526,7 +544,7 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
     bool ok = land_chunk<NT>(a, bc, sm, sh, phase, true, 0, g0);
     cp_async_wait_all();
     int next_b = 0;
-    if (pf.on && tid == 0 && next_i < pf.nq) next_b = queue_block<ROUNDS>(a, sh, pf, next_i);
+    if (!ROUNDS && pf.on && tid == 0 && next_i < pf.nq) next_b = queue_block<false>(a, sh, pf, next_i);
     if (!__syncthreads_and(ok)) return false;
 
     // 2-3. forward pass, argmin (every thread), parabola inputs
@@ -538,6 +556,10 @@ __device__ bool process_block(const MatchArgs &a, int b, const Smem &sm, Shared<
     const int ef = bc.ndy == 1 ? 0 : cf / bc.nd;
     const int dif = cf - ef * bc.nd;
     const int d_f = bc.dmin + dif, dy_f = a.p.dy_min + ef;
+    if (ROUNDS && pf.on && tid < 32) {
+        next_i = sweep_rounds_warp(a.ws.sched, pf.nq, pf.R, a.sm_count, h);
+        if (tid == 0 && next_i < pf.nq) next_b = queue_block<true>(a, sh, pf, next_i);
+    }
     int s_m = 0, s_p = 0;
     if (tid == 0) {
         s_m = dif > 0 ? sm.cost[cf - 1] + sm.cost_b[cf - 1] : 0;
@@ -849,8 +871,7 @@ __device__ void run_blocks(const MatchArgs &a, const Smem &sm, Shared<NT / 32> &
         mbar_init(&sh.mbar_g, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        if (ROUNDS) queue_starts(a.ws.counts, sh.qstart);
-        const int i = ROUNDS ? take_first_round(a.ws.sched, pf.nq, pf.R, a.sm_count)
+        const int i = ROUNDS ? take_first_round(a.ws.sched, pf.rank, pf.nq, pf.R, a.sm_count)
                              : atomicAdd(&a.ws.counts->queue_head, 1);
         sh.next = i;
         sh.gpend = 0;
@@ -902,21 +923,32 @@ __global__ void __launch_bounds__(NT, 1024 / NT)
     const Smem sm = carve(a, smem_raw);
     Prefetch pf;
     pf.on = true;
-    const int n_big = a.ws.counts->n_big;
-    pf.nq = n_big + a.ws.counts->n_small;
-    pf.n_big = n_big;
+    pf.rank = 0;
     if (ROUNDS) {
-        if (pf.nq < 1) return;
+        // thread 0: its rank on the SM and the class counts in one round trip
+        if (threadIdx.x == 0) {
+            const unsigned sid = sm_id();
+            pf.rank = sid < (unsigned)kSchedSMs ? atomicAdd(a.ws.sched + sid, 1) : kMaxRounds;
+            queue_starts(a.ws.counts, sh.qstart);
+            sh.nq = work_queue_on(a, a.ws.counts->n_blocks) ? sh.qstart[kQueueClasses] : -1;
+        }
+        __syncthreads();
+        pf.nq = sh.nq;
+        pf.n_big = 0;
+        if (pf.nq == 0) return;
         // the host's choice guarantees a written work-ordered queue of at most
         // kMaxRounds rounds; should it not hold, the call reports an error
         pf.R = ceil_div_nn(pf.nq, a.sm_count);
-        if (pf.R > kMaxRounds || !work_queue_on(a, a.ws.counts->n_blocks)) {
+        if (pf.nq < 0 || pf.R > kMaxRounds) {
             if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&a.ws.counts->error, 1);
             return;
         }
         run_blocks<NT, true>(a, sm, sh, pf);
         return;
     }
+    const int n_big = a.ws.counts->n_big;
+    pf.nq = n_big + a.ws.counts->n_small;
+    pf.n_big = n_big;
     pf.R = 0;
     // fewer blocks than about 0.6 per resident CTA, and CLOSE blocks with at least 128
     // candidates: (block, disparity-chunk) tiles, two per block (measured: narrower
@@ -957,7 +989,7 @@ __global__ void __launch_bounds__(NT) match_box_kernel(MatchArgs a, int box)
     unsigned long long evals = 0ull;
     Prefetch pf;
     pf.on = false;
-    pf.n_big = pf.nq = pf.R = 0;
+    pf.n_big = pf.nq = pf.R = pf.rank = 0;
     pf.buf = 1;
     begin_block<NT>(a, b, sm, sh, 0);
     if (!process_block<NT>(a, b, sm, sh, phase, 0, pf, gphase, evals)) drain<NT>(a, sh, phase, gphase);
