@@ -54,11 +54,11 @@ POPC_PER_EVAL = 2          # one u64 code pair = two 32-bit popcounts
 # count was taken.  When the sources differ, or no count was taken, traffic is reported as
 # null.
 TRAFFIC = {
-    # match_persistent_kernel: 102.605 MB read + 0.122 MB written
-    "match": {"bytes": 102.7264e6, "sha": "eb3ea750c641",
+    # match_persistent_kernel: 118.150 MB read + 1.055 MB written
+    "match": {"bytes": 119.2056e6, "sha": "e63e3ac5a112",
               "sources": ("match.cu", "match_common.cuh", "aggregate.cuh", "ctm_internal.cuh")},
-    # census_roi4_kernel (61.110 MB read + 63.285 MB written) + tile_list_kernel (0.777 MB)
-    "census": {"bytes": 125.1714e6, "sha": "6db8443fe112",
+    # census_roi4_kernel (60.944 MB read + 63.564 MB written) + tile_list_kernel (0.777 MB)
+    "census": {"bytes": 125.2851e6, "sha": "118e3be34171",
                "sources": ("census.cu", "ctm_internal.cuh")},
 }
 CENSUS_TILE_PX = 32        # pixels per listed census tile
