@@ -457,7 +457,12 @@ def main():
     elif args.no_autotune:
         tuning = ctx.get_tuning()
     else:
-        tuning, _ = ctx.autotune(batch, reps=3)
+        # about 2e8 evaluations per timed candidate (3 calls of the 32-frame batch), so a
+        # single frame's candidates are not decided by the event timer's resolution
+        ctx.match_batch(batch, use_graph=False)
+        w_evals = ctx.stats(stream)["cost_evals"]
+        reps = int(min(max(3, round(2e8 / max(w_evals, 1))), 50))
+        tuning, _ = ctx.autotune(batch, reps=reps)
     tune_s = time.perf_counter() - t_tune
 
     def barrier():
