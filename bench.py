@@ -617,37 +617,55 @@ def main():
         un["bml"] = [f.baseline_m for f in wk.frames]
     e2e_evals = [0] * len(lanes)
 
-    def host_steps(li, n):
+    def host_steps(li, n, mapped):
         ln = lanes[li]
         for k in range(n):
             un = ln["units"][k % len(ln["units"])]
             un["ctx"].match_batch_host_packed(un["host"], un["w"].boxes, un["fpx"], un["bml"],
-                                              out=un["host_out"], stream=ln["stream"])
+                                              out=un["host_out"], stream=ln["stream"], mapped=mapped)
             e2e_evals[li] += un["evals"]
 
-    for li in range(len(lanes)):
-        host_steps(li, 2 * rotate)
-    per_lane = max(2 * rotate, args.steps // (2 * len(lanes)))
-    e2e_evals = [0] * len(lanes)
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    workers = [threading.Thread(target=host_steps, args=(li, per_lane)) for li in range(len(lanes))]
-    for t in workers:
-        t.start()
-    for t in workers:
-        t.join()
-    e2e_wall = time.perf_counter() - t0
-    e2e_s = e2e_wall / (per_lane * len(lanes))
-    barrier()
-    e2e_s = D.max_over_ranks(e2e_s, dist)
-    e2e_value = sum(e2e_evals) * world / D.max_over_ranks(e2e_wall, dist) / 1e9
-    # the host results equal the device path's for the same batch
+    def run_e2e(mapped):
+        for li in range(len(lanes)):
+            host_steps(li, 2 * rotate, mapped)
+        per_lane = max(2 * rotate, args.steps // (2 * len(lanes)))
+        for li in range(len(lanes)):
+            e2e_evals[li] = 0
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        workers = [threading.Thread(target=host_steps, args=(li, per_lane, mapped)) for li in range(len(lanes))]
+        for t in workers:
+            t.start()
+        for t in workers:
+            t.join()
+        wall = time.perf_counter() - t0
+        step_s = wall / (per_lane * len(lanes))
+        barrier()
+        step_s = D.max_over_ranks(step_s, dist)
+        return sum(e2e_evals) * world / D.max_over_ranks(wall, dist) / 1e9, step_s
+
+    # the copying host entry point (every image byte crosses the host link), then the
+    # mapped one (the device reads only the image bytes the census needs)
+    e2e_copy_value, e2e_copy_s = run_e2e(False)
     u0 = units[0]
     assert np.array_equal(u0["host_out"][2][:w.n_boxes], u0["batch"].flags[:w.n_boxes].cpu().numpy())
+    e2e_value, e2e_s = run_e2e(True)
+    # the host results equal the device path's for the same batch (both entry points)
+    assert np.array_equal(u0["host_out"][2][:w.n_boxes], u0["batch"].flags[:w.n_boxes].cpu().numpy())
     steps_units = [step_unit(lanes, i)[1] for i in range(len(lanes) * rotate)]
-    h2d = float(np.mean([sum(f.left.nbytes + f.right.nbytes for f in un["w"].frames) + un["w"].boxes.nbytes
-                         + 48 * len(un["w"].frames) + 8 for un in steps_units]))
+    # bytes a mapped step reads from host memory: its images' gathered segments (the
+    # context's counter after one mapped call on each batch), boxes, two frame tables
+    gathered = {}
+    for un in steps_units:
+        if id(un) not in gathered:
+            un["ctx"].match_batch_host_packed(un["host"], un["w"].boxes, un["fpx"], un["bml"], out=un["host_out"],
+                                              mapped=True)
+            gathered[id(un)] = un["ctx"].stats()["host_bytes"]
+    img_bytes = float(np.mean([sum(f.left.nbytes + f.right.nbytes for f in un["w"].frames) for un in steps_units]))
+    small_in = float(np.mean([un["w"].boxes.nbytes + 48 * len(un["w"].frames) + 8 for un in steps_units]))
+    h2d_copy = img_bytes + small_in
+    h2d = float(np.mean([gathered[id(un)] for un in steps_units])) + small_in + 48 * len(w.frames)
     d2h = float(np.mean([un["w"].n_boxes * 9 for un in steps_units]))
     # the host link itself: one plain page-locked copy of a batch's images, timed on the stream
     link_dev = torch.empty(u0["host"].size, dtype=torch.uint8, device="cuda")
@@ -844,8 +862,16 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "ms_per_step": e2e_s * 1e3, "host_threads": len(lanes),
+                    "entry_point": "ctm_match_batch_mapped (the device reads only the image bytes the "
+                                   "census needs from the page-locked host images)",
+                    "image_bytes_per_step": int(img_bytes),
                     "link_gbs": link_gbs,
                     "link_floor_ms": h2d / (link_gbs * 1e9) * 1e3},
+            "e2e_copy_path": {"value": e2e_copy_value, "unit": UNIT,
+                              "h2d_bytes_per_step": int(h2d_copy), "d2h_bytes_per_step": int(d2h),
+                              "ms_per_step": e2e_copy_s * 1e3, "host_threads": len(lanes),
+                              "entry_point": "ctm_match_batch_host (every image byte copied in)",
+                              "link_floor_ms": h2d_copy / (link_gbs * 1e9) * 1e3},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT,
                          "frac": achieved / peak,
                          "traffic": traffic_bytes("match") if default_workload else None,

@@ -175,6 +175,8 @@ typedef struct {
                               outputs of the call were not written            */
     int32_t census_tiles;  /* 32-pixel census row tiles computed (region of
                               interest of the batched and single-frame calls) */
+    uint64_t host_bytes;   /* image bytes read from host memory by the device
+                              (ctm_match_batch_mapped; 0 for other calls)      */
 } ctm_stats;
 
 /* Human-readable name of a status code (static string). */
@@ -264,6 +266,24 @@ int ctm_match_batch_profiled(ctm_ctx *ctx, const ctm_frame *frames_dev, const in
 int ctm_match_batch_host(ctm_ctx *ctx, const ctm_frame *frames_host, int n_frames,
                          const ctm_box *boxes_host, int n_boxes, float *disp_host,
                          float *depth_host, uint8_t *flags_host, ctm_stream stream);
+
+/* End-to-end batch from host memory that moves only the image bytes the census
+ * reads (no counterpart in the paper; same arguments, results and errors as
+ * ctm_match_batch_host).  The planner marks, before any pixel moves, which
+ * 32-pixel census tiles the search will read (Algorithm 2's blocks and their
+ * disparity strips); a device kernel then reads, straight from the caller's
+ * host images, the 64-byte segments of source rows those tiles' windows cover
+ * and writes them into the context's staging images, and the batched path runs
+ * on those.  The images must be readable by the device at their host address:
+ * page-locked memory, or any host memory where the device reports pageable
+ * memory access (cudaDevAttrPageableMemoryAccess, e.g. GB300 with its host);
+ * the host must not write them during the call.  left, right and pitch must be
+ * multiples of 16 bytes, and width a multiple of 16 (CTM_EINVAL otherwise).
+ * One batch, no sub-batches; ctm_get_stats reports the bytes read from host
+ * memory (host_bytes).  Synchronizes `stream` before returning. */
+int ctm_match_batch_mapped(ctm_ctx *ctx, const ctm_frame *frames_host, int n_frames,
+                           const ctm_box *boxes_host, int n_boxes, float *disp_host,
+                           float *depth_host, uint8_t *flags_host, ctm_stream stream);
 
 /* Single-frame matching that allocates no device memory -- the paper has no
  * counterpart.  It is for callers that cannot call cudaMalloc while they run:

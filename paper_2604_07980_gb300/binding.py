@@ -26,7 +26,7 @@ BLK_VALID, BLK_FB_REJECT, BLK_FEW_POINTS, BLK_SUBPIX_CLAMPED, BLK_PRESENT = 1, 2
 # every symbol include/ctm.h declares
 EXPORTS = ("ctm_status_str", "ctm_default_params", "ctm_create", "ctm_destroy",
            "ctm_census_build", "ctm_match_boxes", "ctm_match_boxes_plain", "ctm_match_batch",
-           "ctm_match_batch_profiled", "ctm_match_batch_host", "ctm_match_boxes_noalloc",
+           "ctm_match_batch_profiled", "ctm_match_batch_host", "ctm_match_batch_mapped", "ctm_match_boxes_noalloc",
            "ctm_noalloc_get_stats",
            "ctm_get_stats", "ctm_probe_int_rate", "ctm_probe_bounded_wait", "ctm_inject_wait_expiry", "ctm_inject_alloc_failures",
            "ctm_get_tuning",
@@ -72,7 +72,7 @@ class ctm_debug(ctypes.Structure):
 
 class ctm_stats(ctypes.Structure):
     _fields_ = [("cost_evals", ctypes.c_uint64), ("n_blocks", ctypes.c_int32), ("n_boxes", ctypes.c_int32),
-                ("error", ctypes.c_int32), ("census_tiles", ctypes.c_int32)]
+                ("error", ctypes.c_int32), ("census_tiles", ctypes.c_int32), ("host_bytes", ctypes.c_uint64)]
 
 
 class ctm_geometry(ctypes.Structure):
@@ -161,6 +161,8 @@ def lib():
     L.ctm_match_batch_profiled.restype = i32
     L.ctm_match_batch_host.argtypes = [vp, ctypes.POINTER(ctm_frame), i32, vp, i32, vp, vp, vp, vp]
     L.ctm_match_batch_host.restype = i32
+    L.ctm_match_batch_mapped.argtypes = [vp, ctypes.POINTER(ctm_frame), i32, vp, i32, vp, vp, vp, vp]
+    L.ctm_match_batch_mapped.restype = i32
     L.ctm_match_boxes_noalloc.argtypes = [ctypes.POINTER(ctm_params), vp, vp, i32, i32, i32, vp, i32,
                                           f32, f32, vp, vp, vp, vp]
     L.ctm_match_boxes_noalloc.restype = i32
@@ -376,10 +378,12 @@ class Context:
                                               _ptr(batch.flags), arr, _stream(stream)),
                "ctm_match_batch_profiled")
 
-    def match_batch_host(self, frames_np, boxes_np, f_px, baseline_m, out=None, stream=None):
+    def match_batch_host(self, frames_np, boxes_np, f_px, baseline_m, out=None, stream=None,
+                         mapped=False):
         """Host arrays in, host arrays out (page-locked numpy views are fastest).
         frames_np: list of (left, right) uint8 [H, W] arrays; boxes_np int32 [n, 5]
-        grouped by frame (column 4 = frame index)."""
+        grouped by frame (column 4 = frame index).  mapped: ctm_match_batch_mapped
+        (the device reads only the image bytes the census needs)."""
         nf = len(frames_np)
         tbl = np.zeros(nf, FRAME_DTYPE)
         tbl["left"] = [L.__array_interface__["data"][0] for L, _ in frames_np]
@@ -387,9 +391,10 @@ class Context:
         tbl["width"] = [L.shape[1] for L, _ in frames_np]
         tbl["height"] = [L.shape[0] for L, _ in frames_np]
         tbl["pitch"] = [L.strides[0] for L, _ in frames_np]
-        return self._host_call(tbl, boxes_np, f_px, baseline_m, out, stream)
+        return self._host_call(tbl, boxes_np, f_px, baseline_m, out, stream, mapped)
 
-    def match_batch_host_packed(self, images, boxes_np, f_px, baseline_m, out=None, stream=None):
+    def match_batch_host_packed(self, images, boxes_np, f_px, baseline_m, out=None, stream=None,
+                                mapped=False):
         """Like match_batch_host for frames packed in one host array images[F, 2, H, W]
         (left, right; a frame-grabber ring buffer): the frame table is computed from
         the array's strides, and frames stored back to back go in one copy per sub-batch."""
@@ -403,9 +408,9 @@ class Context:
         tbl["width"] = W
         tbl["height"] = H
         tbl["pitch"] = images.strides[2]
-        return self._host_call(tbl, boxes_np, f_px, baseline_m, out, stream)
+        return self._host_call(tbl, boxes_np, f_px, baseline_m, out, stream, mapped)
 
-    def _host_call(self, tbl, boxes_np, f_px, baseline_m, out, stream):
+    def _host_call(self, tbl, boxes_np, f_px, baseline_m, out, stream, mapped=False):
         nf = len(tbl)
         n = int(boxes_np.shape[0])
         counts = np.bincount(boxes_np[:, 4], minlength=nf) if n else np.zeros(nf, np.int64)
@@ -418,9 +423,10 @@ class Context:
                    np.empty(max(n, 1), np.uint8))
         disp, depth, flags = out
         bx = np.ascontiguousarray(boxes_np, dtype=np.int32)
-        _check(lib().ctm_match_batch_host(self._h, tbl.ctypes.data_as(ctypes.POINTER(ctm_frame)), nf,
-                                          bx.ctypes.data, n, disp.ctypes.data, depth.ctypes.data,
-                                          flags.ctypes.data, _stream(stream)), "ctm_match_batch_host")
+        fn = lib().ctm_match_batch_mapped if mapped else lib().ctm_match_batch_host
+        _check(fn(self._h, tbl.ctypes.data_as(ctypes.POINTER(ctm_frame)), nf, bx.ctypes.data, n,
+                  disp.ctypes.data, depth.ctypes.data, flags.ctypes.data, _stream(stream)),
+               "ctm_match_batch_mapped" if mapped else "ctm_match_batch_host")
         return {"disp": disp[:n], "depth": depth[:n], "flags": flags[:n]}
 
     def get_tuning(self) -> dict:
@@ -449,7 +455,7 @@ class Context:
         s = ctm_stats()
         _check(lib().ctm_get_stats(self._h, ctypes.byref(s), _stream(stream)), "ctm_get_stats")
         return {"cost_evals": int(s.cost_evals), "n_blocks": int(s.n_blocks), "n_boxes": int(s.n_boxes),
-                "error": int(s.error), "census_tiles": int(s.census_tiles)}
+                "error": int(s.error), "census_tiles": int(s.census_tiles), "host_bytes": int(s.host_bytes)}
 
 
 class DeviceBatch:

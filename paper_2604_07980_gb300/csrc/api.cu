@@ -50,6 +50,7 @@ struct ctm_ctx {
     int inject_expiry = 0;  // armed by ctm_inject_wait_expiry (tests)
     int split_ways = 0;
     bool maps_ok = false;    // ws.tmaps hold the planes' maps
+    int pageable_access = 0; // the device reads pageable host memory (mapped calls need no page-locking)
     void *dev_mem = nullptr;
     size_t dev_bytes = 0;
     cudaStream_t capture_stream = nullptr;
@@ -194,6 +195,7 @@ MatchArgs make_args(const ctm_ctx *ctx, const ctm_frame *frames, const int32_t *
     if (!ctx->maps_ok) a.ws.tmaps = nullptr;
     a.stats_accumulate = 0;
     a.inject_expiry = 0;
+    a.gather_src = nullptr;
     return a;
 }
 
@@ -213,6 +215,7 @@ int enqueue_match(ctm_ctx *ctx, const MatchArgs &a, int frames_grid, int match_g
     }
     cudaError_t e = launch_plan(b, s);
     if (e == cudaSuccess) e = launch_sample(b, s);
+    if (e == cudaSuccess && b.gather_src) e = launch_gather(b, ctx->sm_count, s);
     if (e == cudaSuccess) e = launch_census_roi(b, ctx->sm_count, s);
     if (!plain) {
         if (e == cudaSuccess)
@@ -322,6 +325,7 @@ int ctm_create(ctm_ctx **out, const ctm_params *p, int max_frames, int max_width
     ctx->device = dev;
     ctx->p = *p;
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&ctx->pageable_access, cudaDevAttrPageableMemoryAccess, dev);
     const int slots = p->grid_g * p->grid_g;
     ctx->caps.max_frames = max_frames;
     ctx->caps.max_width = max_width;
@@ -589,6 +593,88 @@ int ctm_match_batch_profiled(ctm_ctx *ctx, const ctm_frame *frames_dev, const in
     return CTM_OK;
 }
 
+// Staging of the host entry points (allocated on first use): device images at
+// a pitch of 128 bytes, boxes and outputs, two frame tables (the staging images'
+// and, for mapped calls, the caller's) in device and page-locked memory, per
+// sub-batch counts, a copy stream and its events.
+static int ensure_host_staging(ctm_ctx *ctx)
+{
+    if (ctx->img_dev) return CTM_OK;
+    ctx->img_pitch = round_up(ctx->caps.max_width, 128);
+    const size_t img_bytes = (size_t)ctx->img_pitch * ctx->caps.max_height * 2 * ctx->caps.max_frames;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = (size_t)round_up(off + bytes, 256); return o; };
+    const size_t o_img = take(img_bytes);
+    const size_t o_boxes = take(sizeof(ctm_box) * (size_t)ctx->caps.max_boxes);
+    const size_t o_disp = take(sizeof(float) * (size_t)ctx->caps.max_boxes);
+    const size_t o_depth = take(sizeof(float) * (size_t)ctx->caps.max_boxes);
+    const size_t o_flags = take((size_t)ctx->caps.max_boxes);
+    const size_t o_frames = take(sizeof(ctm_frame) * 2 * (size_t)ctx->caps.max_frames);
+    const size_t o_counts = take(sizeof(int32_t) * 4 * kHostGroups);
+    void *mem = nullptr;
+    if (dev_alloc(&mem, off) != cudaSuccess) { cudaGetLastError(); return CTM_ENOMEM; }
+    bool okh = cudaMallocHost(&ctx->frames_host_pinned, sizeof(ctm_frame) * 2 * ctx->caps.max_frames) == cudaSuccess &&
+               cudaMallocHost(&ctx->counts_host_pinned, sizeof(int32_t) * 4 * kHostGroups) == cudaSuccess &&
+               cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
+    for (cudaEvent_t &ev : ctx->host_ev)
+        okh = okh && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+    if (!okh) {
+        cudaFree(mem);
+        if (ctx->frames_host_pinned) cudaFreeHost(ctx->frames_host_pinned);
+        if (ctx->counts_host_pinned) cudaFreeHost(ctx->counts_host_pinned);
+        if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+        ctx->copy_stream = nullptr;
+        for (cudaEvent_t &ev : ctx->host_ev)
+            if (ev) { cudaEventDestroy(ev); ev = nullptr; }
+        ctx->frames_host_pinned = nullptr;
+        ctx->counts_host_pinned = nullptr;
+        cudaGetLastError();
+        return CTM_ENOMEM;
+    }
+    char *b = static_cast<char *>(mem);
+    ctx->img_dev = reinterpret_cast<uint8_t *>(b + o_img);
+    ctx->boxes_dev = reinterpret_cast<ctm_box *>(b + o_boxes);
+    ctx->disp_dev = reinterpret_cast<float *>(b + o_disp);
+    ctx->depth_dev = reinterpret_cast<float *>(b + o_depth);
+    ctx->flags_dev = reinterpret_cast<uint8_t *>(b + o_flags);
+    ctx->frames_dev2 = reinterpret_cast<ctm_frame *>(b + o_frames);
+    ctx->counts_dev2 = reinterpret_cast<int32_t *>(b + o_counts);
+    return CTM_OK;
+}
+
+// The end of a host call, after its kernels are queued on s: outputs and the
+// call's bounded-wait flag back to host memory, then wait for s.
+static int host_results(ctm_ctx *ctx, cudaStream_t s, int n_boxes, float *disp_host, float *depth_host,
+                        uint8_t *flags_host)
+{
+    cudaError_t e = cudaSuccess;
+    if (n_boxes > 0) {
+        e = cudaMemcpyAsync(disp_host, ctx->disp_dev, sizeof(float) * n_boxes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(depth_host, ctx->depth_dev, sizeof(float) * n_boxes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(flags_host, ctx->flags_dev, (size_t)n_boxes, cudaMemcpyDeviceToHost, s);
+    }
+    int32_t *err_h = ctx->counts_host_pinned + 4 * kHostGroups - 1;  // a slot no sub-batch uses
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(err_h, &ctx->ws.stats->error, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { cudaGetLastError(); return CTM_ECUDA; }
+    return *err_h ? CTM_ETIMEOUT : CTM_OK;
+}
+
+// Host memory a kernel may read at the same address: page-locked (allocated or
+// registered) memory, with unified addressing.
+static bool device_readable(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost && at.devicePointer == p;
+}
+
 int ctm_match_batch_host(ctm_ctx *ctx, const ctm_frame *frames_host, int n_frames,
                          const ctm_box *boxes_host, int n_boxes, float *disp_host,
                          float *depth_host, uint8_t *flags_host, ctm_stream stream)
@@ -604,47 +690,8 @@ int ctm_match_batch_host(ctm_ctx *ctx, const ctm_frame *frames_host, int n_frame
     int st = set_device(ctx);
     if (st != CTM_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    if (!ctx->img_dev) {
-        ctx->img_pitch = round_up(ctx->caps.max_width, 128);
-        const size_t img_bytes = (size_t)ctx->img_pitch * ctx->caps.max_height * 2 * ctx->caps.max_frames;
-        size_t off = 0;
-        auto take = [&](size_t bytes) { size_t o = off; off = (size_t)round_up(off + bytes, 256); return o; };
-        const size_t o_img = take(img_bytes);
-        const size_t o_boxes = take(sizeof(ctm_box) * (size_t)ctx->caps.max_boxes);
-        const size_t o_disp = take(sizeof(float) * (size_t)ctx->caps.max_boxes);
-        const size_t o_depth = take(sizeof(float) * (size_t)ctx->caps.max_boxes);
-        const size_t o_flags = take((size_t)ctx->caps.max_boxes);
-        const size_t o_frames = take(sizeof(ctm_frame) * (size_t)ctx->caps.max_frames);
-        const size_t o_counts = take(sizeof(int32_t) * 4 * kHostGroups);
-        void *mem = nullptr;
-        if (dev_alloc(&mem, off) != cudaSuccess) { cudaGetLastError(); return CTM_ENOMEM; }
-        bool okh = cudaMallocHost(&ctx->frames_host_pinned, sizeof(ctm_frame) * ctx->caps.max_frames) == cudaSuccess &&
-                   cudaMallocHost(&ctx->counts_host_pinned, sizeof(int32_t) * 4 * kHostGroups) == cudaSuccess &&
-                   cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) == cudaSuccess;
-        for (cudaEvent_t &ev : ctx->host_ev)
-            okh = okh && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
-        if (!okh) {
-            cudaFree(mem);
-            if (ctx->frames_host_pinned) cudaFreeHost(ctx->frames_host_pinned);
-            if (ctx->counts_host_pinned) cudaFreeHost(ctx->counts_host_pinned);
-            if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
-            ctx->copy_stream = nullptr;
-            for (cudaEvent_t &ev : ctx->host_ev)
-                if (ev) { cudaEventDestroy(ev); ev = nullptr; }
-            ctx->frames_host_pinned = nullptr;
-            ctx->counts_host_pinned = nullptr;
-            cudaGetLastError();
-            return CTM_ENOMEM;
-        }
-        char *b = static_cast<char *>(mem);
-        ctx->img_dev = reinterpret_cast<uint8_t *>(b + o_img);
-        ctx->boxes_dev = reinterpret_cast<ctm_box *>(b + o_boxes);
-        ctx->disp_dev = reinterpret_cast<float *>(b + o_disp);
-        ctx->depth_dev = reinterpret_cast<float *>(b + o_depth);
-        ctx->flags_dev = reinterpret_cast<uint8_t *>(b + o_flags);
-        ctx->frames_dev2 = reinterpret_cast<ctm_frame *>(b + o_frames);
-        ctx->counts_dev2 = reinterpret_cast<int32_t *>(b + o_counts);
-    }
+    st = ensure_host_staging(ctx);
+    if (st != CTM_OK) return st;
     // Sub-batches of consecutive frames when each frame's boxes follow the previous
     // frame's (each sub-batch then owns one slice of the boxes and outputs); else
     // one batch.  Sub-batch g + 1's copies, on the copy stream, overlap sub-batch
@@ -739,19 +786,61 @@ int ctm_match_batch_host(ctm_ctx *ctx, const ctm_frame *frames_host, int n_frame
         if (enqueue_match(ctx, a, f1 - f0, grid, s, false, 0) != CTM_OK) e = cudaErrorLaunchFailure;
     }
     if (e != cudaSuccess) { cudaGetLastError(); return CTM_ECUDA; }
-    if (n_boxes > 0) {
-        e = cudaMemcpyAsync(disp_host, ctx->disp_dev, sizeof(float) * n_boxes, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(depth_host, ctx->depth_dev, sizeof(float) * n_boxes, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(flags_host, ctx->flags_dev, (size_t)n_boxes, cudaMemcpyDeviceToHost, s);
+    return host_results(ctx, s, n_boxes, disp_host, depth_host, flags_host);
+}
+
+int ctm_match_batch_mapped(ctm_ctx *ctx, const ctm_frame *frames_host, int n_frames,
+                           const ctm_box *boxes_host, int n_boxes, float *disp_host,
+                           float *depth_host, uint8_t *flags_host, ctm_stream stream)
+{
+    if (!ctx || !frames_host || n_frames < 1 || n_boxes < 0) return CTM_EINVAL;
+    if (n_boxes > 0 && (!boxes_host || !disp_host || !depth_host || !flags_host)) return CTM_EINVAL;
+    if (n_frames > ctx->caps.max_frames || n_boxes > ctx->caps.max_boxes) return CTM_ENOMEM;
+    int st = set_device(ctx);
+    if (st != CTM_OK) return st;
+    for (int i = 0; i < n_frames; ++i) {
+        const ctm_frame &f = frames_host[i];
+        if (!f.left || !f.right || f.width < 1 || f.height < 1 || f.pitch < f.width) return CTM_EINVAL;
+        if (f.width > ctx->caps.max_width || f.height > ctx->caps.max_height) return CTM_ENOMEM;
+        // the gather moves aligned 16-byte pieces of rows
+        if ((reinterpret_cast<uintptr_t>(f.left) | reinterpret_cast<uintptr_t>(f.right) | (uintptr_t)f.pitch |
+             (uintptr_t)f.width) & 15u)
+            return CTM_EINVAL;
+        if (!ctx->pageable_access && (!device_readable(f.left) || !device_readable(f.right))) return CTM_EINVAL;
     }
-    int32_t *err_h = ctx->counts_host_pinned + 4 * kHostGroups - 1;  // a slot no sub-batch uses
+    cudaStream_t s = (cudaStream_t)stream;
+    st = ensure_host_staging(ctx);
+    if (st != CTM_OK) return st;
+    // the staging images' frame table and the caller's (second half of the tables)
+    const size_t plane = (size_t)ctx->img_pitch * ctx->caps.max_height;
+    ctm_frame *stage = ctx->frames_host_pinned, *src = ctx->frames_host_pinned + ctx->caps.max_frames;
+    for (int i = 0; i < n_frames; ++i) {
+        ctm_frame t = frames_host[i];
+        src[i] = t;
+        t.left = ctx->img_dev + plane * (2 * (size_t)i);
+        t.right = t.left + plane;
+        t.pitch = (int32_t)ctx->img_pitch;
+        stage[i] = t;
+    }
+    int32_t *cnt = ctx->counts_host_pinned;
+    cnt[0] = n_frames;
+    cnt[1] = n_boxes;
+    cudaError_t e = cudaMemcpyAsync(ctx->frames_dev2, stage, sizeof(ctm_frame) * n_frames, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(err_h, &ctx->ws.stats->error, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        e = cudaMemcpyAsync(ctx->frames_dev2 + ctx->caps.max_frames, src, sizeof(ctm_frame) * n_frames,
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n_boxes > 0)
+        e = cudaMemcpyAsync(ctx->boxes_dev, boxes_host, sizeof(ctm_box) * n_boxes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->counts_dev2, cnt, sizeof(int32_t) * 2, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        MatchArgs a = make_args(ctx, ctx->frames_dev2, ctx->counts_dev2, ctx->boxes_dev, ctx->disp_dev,
+                                ctx->depth_dev, ctx->flags_dev, nullptr);
+        a.gather_src = ctx->frames_dev2 + ctx->caps.max_frames;
+        const int grid = ctx->sm_count * ctx->ctas_per_sm;
+        if (enqueue_match(ctx, a, n_frames, grid, s, false, 0) != CTM_OK) e = cudaErrorLaunchFailure;
+    }
     if (e != cudaSuccess) { cudaGetLastError(); return CTM_ECUDA; }
-    return *err_h ? CTM_ETIMEOUT : CTM_OK;
+    return host_results(ctx, s, n_boxes, disp_host, depth_host, flags_host);
 }
 
 int ctm_get_tuning(const ctm_ctx *ctx, ctm_tuning *out)
@@ -931,6 +1020,7 @@ int ctm_get_stats(ctm_ctx *ctx, ctm_stats *out, ctm_stream stream)
     out->n_boxes = c.n_boxes;
     out->error = c.error;
     out->census_tiles = c.n_tiles;
+    out->host_bytes = c.host_bytes;
     return CTM_OK;
 }
 

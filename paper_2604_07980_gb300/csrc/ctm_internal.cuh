@@ -48,6 +48,7 @@ struct Counts {
     int n_small;     // searchable blocks queued from the back (small work)
     int n_tiles;     // census tiles listed for the region-of-interest census
     int n_class[kQueueClasses];  // searchable blocks in each work class (ws.queue_w)
+    unsigned long long host_bytes;  // image bytes the gather read from host memory (mapped calls)
 };
 
 // Planned box (device).
@@ -172,6 +173,9 @@ struct MatchArgs {
     int census_mode;           // region-of-interest census variant (census.cu)
     int strip_rows;            // rows of the shared-memory strip (pts_side * ndy, rounded up to 4)
     int stats_accumulate;      // 1: the aggregation adds the call's counters to the stats record
+    const ctm_frame *gather_src;  // mapped calls: device copy of the caller's frame table (host
+                                  // image pointers the device reads); the census then reads the
+                                  // staging images of `frames`, filled by the gather.  Else null
     int inject_expiry;         // fault injection for tests: the CTA of the fused persistent matcher
                                // that takes queue position 0 withholds that block's first strip
                                // copy, so its bounded wait expires
@@ -258,6 +262,22 @@ __device__ __forceinline__ BlockRect block_rect(const BoxPlan &P, int slot, int 
 
 // Census launches (census.cu)
 constexpr int kCensusTilePx = 32;   // pixels per bitmap bit (a census tile: 8 lanes x 4 pixels)
+// Grid columns a census tile x0 .. x0 + 31 reads: [x0 - L, x0 + R).  The fixed
+// windows (5x5, 7x7, 9x7; census_roi4_kernel) load twelve pixels x - 4 .. x + 7
+// per lane of four pixels; the other windows (census_roi_kernel) load 21 words
+// of four pixels from x0 - 8.  Rows: the window's rows around the tile's row.
+__host__ __device__ inline bool census_fixed_window(int win_w, int win_h)
+{
+    return (win_w == 9 && win_h == 7) || (win_w == 7 && win_h == 7) || (win_w == 5 && win_h == 5);
+}
+__host__ __device__ inline int census_reach_left(int win_w, int win_h) { return census_fixed_window(win_w, win_h) ? 4 : 8; }
+__host__ __device__ inline int census_reach_right(int win_w, int win_h) { return census_fixed_window(win_w, win_h) ? 36 : 76; }
+
+// Mapped calls (gather.cu): after the sampling kernel has marked the census
+// tiles, copy from the caller's host images into the staging images the source
+// bytes those tiles' census reads (64-byte segments of each source row).
+cudaError_t launch_gather(const MatchArgs &a, int sm_count, cudaStream_t s);
+constexpr int kGatherSegBytes = 64;
 cudaError_t launch_census_single(const uint8_t *img, int W, int H, int pitch, int k, int win_w,
                                  int win_h, int sentinel, uint64_t *out, long long out_pitch,
                                  cudaStream_t s);

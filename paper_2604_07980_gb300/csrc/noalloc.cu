@@ -177,6 +177,7 @@ extern "C" int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_
     a.p = *p;
     a.stats_accumulate = 0;
     a.inject_expiry = 0;
+    a.gather_src = nullptr;
     a.frames = ws.frames;
     a.counts_in = ws.counts_in;
     a.boxes = boxes_dev;
@@ -253,5 +254,6 @@ extern "C" int ctm_noalloc_get_stats(ctm_stats *out, ctm_stream stream)
     out->n_boxes = c.n_boxes;
     out->error = c.error;
     out->census_tiles = c.n_tiles;
+    out->host_bytes = c.host_bytes;
     return CTM_OK;
 }

@@ -440,6 +440,7 @@ __global__ void __launch_bounds__(256) aggregate_kernel(MatchArgs a)
             t.n_big += c.n_big;
             t.n_small += c.n_small;
             t.n_tiles += c.n_tiles;
+            t.host_bytes += c.host_bytes;
             for (int i = 0; i < kQueueClasses; ++i) t.n_class[i] += c.n_class[i];
             *a.ws.stats = t;
         } else {
