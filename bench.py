@@ -13,8 +13,10 @@ batches (588 MB of images) take turns and no step finds a recent step's data in
 the 129 MB L2; no flush is needed between steps.
 
 Printed (one JSON line on rank 0): cost-evals/s of the batched path, its e2e
-number through the host-memory entry point (packed page-locked images, copies
-overlapped with the kernels by sub-batches) with the host link's own copy rate,
+number through the mapped host-memory entry point (packed page-locked images of
+which the device reads only the bytes the census needs) and through the copying
+one (every image byte copied in, overlapped with the kernels by sub-batches),
+with the host link's own copy rate,
 the per-kernel roofline of the matching kernel against the integer popcount
 pipe and of the census phase against HBM and the integer pipes, the same steps
 one batch at a time, the 8 x 3840x2160 workload measured the same way, the plain
