@@ -240,17 +240,19 @@ def _pct(x, q):
     return float(np.percentile(np.asarray(x, dtype=np.float64), q)) if len(x) else None
 
 
-def serve_trace(B, torch, tr, plain: bool) -> dict:
+def serve_trace(B, torch, tr, plain: bool, mapped: bool = False) -> dict:
     """Replay a camera trace through the serving loop: every frame is submitted at
     its arrival time (pinned host images, host boxes); latency is submit to the
     outputs written in host memory, from the server's own timestamps.  Then the
-    same frames are offered all at once to measure the server's saturated boxes/s."""
+    same frames are offered all at once to measure the server's saturated boxes/s.
+    mapped: the server reads each frame's needed image bytes in place instead of
+    uploading the images."""
     pinned = [[(torch.from_numpy(f.left).pin_memory(), torch.from_numpy(f.right).pin_memory())
                for f in st.frames] for st in tr.streams]
     W = max(st.width for st in tr.streams)
     H = max(st.height for st in tr.streams)
     srv = B.Server(tr.params, lanes=1 if plain else 2, frames_per_batch=1 if plain else 8,
-                   plain=int(plain), max_width=W, max_height=H, max_boxes_per_frame=256,
+                   plain=int(plain), mapped=int(mapped), max_width=W, max_height=H, max_boxes_per_frame=256,
                    max_queue=1024, image_budget_bytes=1 << 30)
 
     def submit(s, k):
@@ -804,11 +806,14 @@ def main():
         other = measure_other(B, torch, wl, D, dist, args, "batch8x2160",
                               D.rank_seed(WORKLOAD_SEEDS["batch8x2160"], rank), peak)
 
-    # ---- serving: 4 stereo streams at 30 Hz (batched lanes, then the plain per-box path)
-    serving = serving_plain = None
+    # ---- serving: 4 stereo streams at 30 Hz (batched lanes reading the images' needed bytes in
+    # place -- the default configuration -- the same uploading whole images, then the plain
+    # per-box path)
+    serving = serving_upload = serving_plain = None
     if args.serve_seconds > 0:
         tr = wl.serving(seed=D.rank_seed(1004, rank), duration_s=args.serve_seconds)
-        serving = serve_trace(B, torch, tr, plain=False)
+        serving = serve_trace(B, torch, tr, plain=False, mapped=True)
+        serving_upload = serve_trace(B, torch, tr, plain=False, mapped=False)
         serving_plain = serve_trace(B, torch, tr, plain=True)
         serving["streams"] = [f"{st.width}x{st.height}" for st in tr.streams]
         serving["p99_ms_max_over_ranks"] = D.max_over_ranks(serving["paced"]["p99_ms"], dist)
@@ -860,6 +865,7 @@ def main():
             "box_points": box_points,
             "auto_rect": {**auto_rect, "frac_of_popc_peak": auto_rect["value"] / peak},
             "serving": serving,
+            "serving_upload_path": serving_upload,
             "serving_plain_path": serving_plain,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),

@@ -51,14 +51,22 @@ typedef struct {
     int32_t max_queue;           /* submitted-but-not-admitted frames; beyond: CTM_EAGAIN */
     int64_t image_budget_bytes;  /* device arena for admitted frames' images */
     int32_t plain;               /* 1: run batches through the plain per-box path (comparison) */
-    int32_t reserved;
+    int32_t mapped;              /* 1: a frame whose images the device can read in host memory
+                                    (page-locked, or any memory where the device reports
+                                    pageable memory access) and whose left, right, pitch and
+                                    width are multiples of 16 bytes is not uploaded: its batch
+                                    reads only the bytes its census needs straight from the
+                                    host images, as ctm_match_batch_mapped does; other frames
+                                    are uploaded whole.  0: every frame uploaded whole.
+                                    Ignored with plain = 1 (frames are uploaded) */
 } ctm_server_config;
 
-/* One frame to serve.  Host pointers; pinned host memory (cudaHostAlloc or a
- * pinned torch tensor) lets the image copies run asynchronously, pageable
- * memory works but the copy then blocks the worker thread.  Every pointer must
- * stay valid, and the output arrays untouched, until the frame's completion
- * has been returned by ctm_server_poll().  Boxes use full-resolution pixels of
+/* One frame to serve.  Host pointers; with mapped = 1 the device reads the
+ * images in place where it can (see ctm_server_config.mapped); an uploaded
+ * frame's copy runs asynchronously from pinned host memory (cudaHostAlloc or a
+ * pinned torch tensor), while from pageable memory it blocks the worker thread.
+ * Every pointer must stay valid, the images unchanged and the output arrays
+ * untouched, until the frame's completion has been returned by ctm_server_poll().  Boxes use full-resolution pixels of
  * this frame; their `frame` field is ignored. */
 typedef struct {
     const uint8_t *left_host, *right_host;  /* width x height, `pitch` bytes per row */
@@ -97,7 +105,8 @@ typedef struct {
 } ctm_server_stats;
 
 /* Default configuration: 2 lanes, 8 frames per batch, 3840x2160, 256 boxes,
- * queue 256, arena 1 GiB, batched path. */
+ * queue 256, arena 1 GiB, batched path, images read in place where possible
+ * (mapped = 1). */
 int ctm_server_default_config(ctm_server_config *cfg);
 
 /* Create a server on the current device: validates `p` (CTM_EINVAL as

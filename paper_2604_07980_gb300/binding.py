@@ -95,7 +95,7 @@ class ctm_server_config(ctypes.Structure):
                 ("max_width", ctypes.c_int32), ("max_height", ctypes.c_int32),
                 ("max_boxes_per_frame", ctypes.c_int32), ("max_queue", ctypes.c_int32),
                 ("image_budget_bytes", ctypes.c_int64), ("plain", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("mapped", ctypes.c_int32)]
 
 
 class ctm_request(ctypes.Structure):

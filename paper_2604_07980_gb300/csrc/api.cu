@@ -24,7 +24,7 @@
 using namespace ctm;
 
 struct GraphKey {
-    const void *frames, *counts, *boxes, *disp, *depth, *flags, *dbg_blocks, *dbg_cf, *dbg_cb;
+    const void *frames, *counts, *boxes, *disp, *depth, *flags, *dbg_blocks, *dbg_cf, *dbg_cb, *gather;
     bool operator==(const GraphKey &o) const { return memcmp(this, &o, sizeof(*this)) == 0; }
 };
 
@@ -522,18 +522,31 @@ int ctm_match_batch(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *co
                     const ctm_box *boxes_dev, float *disp_dev, float *depth_dev, uint8_t *flags_dev,
                     const ctm_debug *dbg, int use_graph, ctm_stream stream)
 {
+    return ctm::match_batch_dev(ctx, frames_dev, nullptr, counts_dev, boxes_dev, disp_dev, depth_dev, flags_dev,
+                                dbg, use_graph, stream);
+}
+
+}  // extern "C"
+
+namespace ctm {
+
+int match_batch_dev(ctm_ctx *ctx, const ctm_frame *frames_dev, const ctm_frame *gather_src_dev,
+                    const int32_t *counts_dev, const ctm_box *boxes_dev, float *disp_dev, float *depth_dev,
+                    uint8_t *flags_dev, const ctm_debug *dbg, int use_graph, ctm_stream stream)
+{
     if (!ctx || !frames_dev || !counts_dev || !boxes_dev || !disp_dev || !depth_dev || !flags_dev)
         return CTM_EINVAL;
     int st = set_device(ctx);
     if (st != CTM_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     MatchArgs a = make_args(ctx, frames_dev, counts_dev, boxes_dev, disp_dev, depth_dev, flags_dev, dbg);
+    a.gather_src = gather_src_dev;
     const int grid = ctx->sm_count * ctx->ctas_per_sm;
     if (!use_graph) return enqueue_match(ctx, a, ctx->caps.max_frames, grid, s, false, 0);
 
     GraphKey key{frames_dev, counts_dev, boxes_dev, disp_dev, depth_dev, flags_dev,
                  dbg ? (const void *)dbg->blocks : nullptr, dbg ? (const void *)dbg->cost_f : nullptr,
-                 dbg ? (const void *)dbg->cost_b : nullptr};
+                 dbg ? (const void *)dbg->cost_b : nullptr, gather_src_dev};
     if (!ctx->gexec || !(key == ctx->gkey)) {
         if (ctx->gexec) {
             cudaGraphExecDestroy(ctx->gexec);
@@ -560,6 +573,10 @@ int ctm_match_batch(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *co
     }
     return cudaGraphLaunch(ctx->gexec, s) == cudaSuccess ? CTM_OK : CTM_ECUDA;
 }
+
+}  // namespace ctm
+
+extern "C" {
 
 int ctm_match_batch_profiled(ctm_ctx *ctx, const ctm_frame *frames_dev, const int32_t *counts_dev,
                              const ctm_box *boxes_dev, float *disp_dev, float *depth_dev,

@@ -330,6 +330,14 @@ bool encode_plane_maps(const Workspace &ws, const Caps &caps, int close_factor, 
 bool params_valid(const ctm_params &p);
 int default_strip_cols(int nd_max);
 
+// ctm_match_batch with an optional gather (gather_src_dev: a device copy of a
+// frame table holding each frame's host images, read by the gather of
+// ctm_match_batch_mapped into the images of frames_dev; a frame with height 0
+// there is not gathered).  Used by the serving loop.
+int match_batch_dev(ctm_ctx *ctx, const ctm_frame *frames_dev, const ctm_frame *gather_src_dev,
+                    const int32_t *counts_dev, const ctm_box *boxes_dev, float *disp_dev, float *depth_dev,
+                    uint8_t *flags_dev, const ctm_debug *dbg, int use_graph, ctm_stream stream);
+
 // Device address of the error flag of a context's last finished call
 // (ctm_stats.error), for callers that read it back on their own stream.
 const int32_t *context_error_flag(const ctm_ctx *ctx);

@@ -125,8 +125,10 @@ __global__ void __launch_bounds__(kGatherThreads) gather_kernel(MatchArgs a, int
     const int lane = threadIdx.x & 31;
     const int nf = min(max(a.counts_in[0], 0), a.caps.max_frames);
     const long long warps = (long long)gridDim.x * (kGatherThreads / 32);
+    // items run frame-major: the call's frames are the first nf of the capacity's
+    const long long lim = min(items, (long long)nf * 2 * a.caps.max_height * chunks);
     unsigned long long bytes = 0ull;
-    for (long long it = (long long)blockIdx.x * (kGatherThreads / 32) + (threadIdx.x >> 5); it < items; it += warps)
+    for (long long it = (long long)blockIdx.x * (kGatherThreads / 32) + (threadIdx.x >> 5); it < lim; it += warps)
         bytes += gather_item(a, it, chunks, nf, lane);
     if (bytes) atomicAdd(&cta_bytes, bytes);
     __syncthreads();

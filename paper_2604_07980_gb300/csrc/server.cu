@@ -3,7 +3,9 @@
 // One native worker thread owns the GPU side.  Submitted frames wait in an
 // arrival queue; the worker admits them in arrival order while their images
 // fit in a fixed device arena (admission by device memory), uploads the images
-// on a copy stream, and keeps up to `lanes` batches in flight: an idle lane
+// on a copy stream (mapped servers: only frames the device cannot read in place;
+// the others' batches gather the bytes their census needs from host memory into
+// the arena), and keeps up to `lanes` batches in flight: an idle lane
 // takes every admitted frame (up to frames_per_batch) and replays its captured
 // CUDA graph of the batched launch sequence over them.  Each lane owns a
 // workspace created once (census planes, plans, counters), so census buffers
@@ -45,7 +47,8 @@ struct Job {
     int64_t t_submit = 0, t_admit = 0, t_launch = 0;
     int64_t arena_off = -1;
     int64_t pitch = 0;  // device image pitch
-    cudaEvent_t uploaded = nullptr;
+    cudaEvent_t uploaded = nullptr;  // null for a gathered frame (nothing uploaded)
+    bool gather = false;             // its batch reads its images from host memory
     int status = CTM_OK;
 };
 
@@ -57,6 +60,7 @@ struct Lane {
     int max_boxes = 0;
     // pinned host staging
     ctm_frame *frames_h = nullptr;
+    ctm_frame *src_h = nullptr;  // mapped servers: the frames' host images (height 0: uploaded)
     ctm_box *boxes_h = nullptr;
     int32_t *counts_h = nullptr;
     float *disp_h = nullptr, *depth_h = nullptr;
@@ -65,6 +69,7 @@ struct Lane {
     // device tables and outputs (one allocation)
     void *dev_mem = nullptr;
     ctm_frame *frames_d = nullptr;
+    ctm_frame *src_d = nullptr;
     int32_t *counts_d = nullptr;
     ctm_box *boxes_d = nullptr;
     float *disp_d = nullptr, *depth_d = nullptr;
@@ -87,6 +92,7 @@ struct ctm_server {
     ctm::Arena arena;
     uint8_t *arena_d = nullptr;
     cudaStream_t upload = nullptr;
+    int pageable_access = 0;  // the device reads pageable host memory
     std::vector<Lane> lanes;
     std::vector<cudaEvent_t> event_pool;  // worker only
     std::deque<Job *> admitted;           // worker only: uploaded or uploading, not yet batched
@@ -217,6 +223,14 @@ void dispatch(ctm_server *S, Lane &L)
         f.box_count = r.n_boxes;
         f.f_px = r.f_px;
         f.baseline_m = r.baseline_m;
+        if (S->cfg.mapped) {  // gathered frames: their host images; uploaded ones: height 0
+            ctm_frame &g = L.src_h[i];
+            g = f;
+            g.left = r.left_host;
+            g.right = r.right_host;
+            g.pitch = r.pitch;
+            if (!j->gather) g.height = 0;
+        }
         if (r.n_boxes > 0) memcpy(L.boxes_h + L.box_off[i], r.boxes_host, sizeof(ctm_box) * (size_t)r.n_boxes);
         for (int b = 0; b < r.n_boxes; ++b) L.boxes_h[L.box_off[i] + b].frame = i;
         j->t_launch = t;
@@ -224,13 +238,16 @@ void dispatch(ctm_server *S, Lane &L)
     L.counts_h[0] = nf;
     L.counts_h[1] = nb;
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < nf && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(L.stream, L.batch[i]->uploaded, 0);
+    for (int i = 0; i < nf && e == cudaSuccess; ++i)
+        if (L.batch[i]->uploaded) e = cudaStreamWaitEvent(L.stream, L.batch[i]->uploaded, 0);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(L.frames_d, L.frames_h, sizeof(ctm_frame) * nf, cudaMemcpyHostToDevice, L.stream);
     if (e == cudaSuccess && nb > 0)
         e = cudaMemcpyAsync(L.boxes_d, L.boxes_h, sizeof(ctm_box) * nb, cudaMemcpyHostToDevice, L.stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(L.counts_d, L.counts_h, sizeof(int32_t) * 2, cudaMemcpyHostToDevice, L.stream);
+    if (e == cudaSuccess && S->cfg.mapped)
+        e = cudaMemcpyAsync(L.src_d, L.src_h, sizeof(ctm_frame) * nf, cudaMemcpyHostToDevice, L.stream);
     int st = e == cudaSuccess ? CTM_OK : CTM_ECUDA;
     if (st == CTM_OK) {
         if (S->cfg.plain) {
@@ -242,8 +259,8 @@ void dispatch(ctm_server *S, Lane &L)
                                            L.flags_d + o, (ctm_stream)L.stream);
             }
         } else {
-            st = ctm_match_batch(L.ctx, L.frames_d, L.counts_d, L.boxes_d, L.disp_d, L.depth_d, L.flags_d,
-                                 nullptr, 1, (ctm_stream)L.stream);
+            st = ctm::match_batch_dev(L.ctx, L.frames_d, S->cfg.mapped ? L.src_d : nullptr, L.counts_d, L.boxes_d,
+                                      L.disp_d, L.depth_d, L.flags_d, nullptr, 1, (ctm_stream)L.stream);
         }
     }
     if (st == CTM_OK && nb > 0) {
@@ -338,7 +355,7 @@ void worker_main(ctm_server *S)
         }
         progress = false;
         for (Job *j : newly) {
-            if (dev_ok && upload(S, j)) {
+            if (dev_ok && (j->gather || upload(S, j))) {
                 S->admitted.push_back(j);
             } else {
                 complete_jobs(S, std::vector<Job *>{j}, -1, 0, CTM_ECUDA);
@@ -401,6 +418,7 @@ int create_lane(ctm_server *S, Lane &L, int index)
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = (size_t)round_up((int64_t)(off + bytes), 256); return o; };
     const size_t o_frames = take(sizeof(ctm_frame) * F);
+    const size_t o_src = take(sizeof(ctm_frame) * F);
     const size_t o_boxes = take(sizeof(ctm_box) * B);
     const size_t o_counts = take(sizeof(int32_t) * 4);
     const size_t o_disp = take(sizeof(float) * B);
@@ -412,12 +430,14 @@ int create_lane(ctm_server *S, Lane &L, int index)
     }
     char *d = static_cast<char *>(L.dev_mem), *h = static_cast<char *>(L.host_mem);
     L.frames_d = reinterpret_cast<ctm_frame *>(d + o_frames);
+    L.src_d = reinterpret_cast<ctm_frame *>(d + o_src);
     L.boxes_d = reinterpret_cast<ctm_box *>(d + o_boxes);
     L.counts_d = reinterpret_cast<int32_t *>(d + o_counts);
     L.disp_d = reinterpret_cast<float *>(d + o_disp);
     L.depth_d = reinterpret_cast<float *>(d + o_depth);
     L.flags_d = reinterpret_cast<uint8_t *>(d + o_flags);
     L.frames_h = reinterpret_cast<ctm_frame *>(h + o_frames);
+    L.src_h = reinterpret_cast<ctm_frame *>(h + o_src);
     L.boxes_h = reinterpret_cast<ctm_box *>(h + o_boxes);
     L.counts_h = reinterpret_cast<int32_t *>(h + o_counts);
     L.disp_h = reinterpret_cast<float *>(h + o_disp);
@@ -429,8 +449,8 @@ int create_lane(ctm_server *S, Lane &L, int index)
     cudaError_t e = cudaMemcpyAsync(L.dev_mem, L.host_mem, off, cudaMemcpyHostToDevice, L.stream);
     if (e != cudaSuccess) { cudaGetLastError(); return CTM_ECUDA; }
     if (!c.plain) {
-        st = ctm_match_batch(L.ctx, L.frames_d, L.counts_d, L.boxes_d, L.disp_d, L.depth_d, L.flags_d, nullptr, 1,
-                             (ctm_stream)L.stream);
+        st = ctm::match_batch_dev(L.ctx, L.frames_d, c.mapped ? L.src_d : nullptr, L.counts_d, L.boxes_d, L.disp_d,
+                                  L.depth_d, L.flags_d, nullptr, 1, (ctm_stream)L.stream);
         if (st != CTM_OK) return st;
     }
     if (cudaStreamSynchronize(L.stream) != cudaSuccess) { cudaGetLastError(); return CTM_ECUDA; }
@@ -442,8 +462,28 @@ bool config_ok(const ctm_server_config &c)
     return c.lanes >= 1 && c.lanes <= 8 && c.frames_per_batch >= 1 && c.frames_per_batch <= 64 &&
            c.max_width >= 1 && c.max_width <= 32768 && c.max_height >= 1 && c.max_height <= 32768 &&
            c.max_boxes_per_frame >= 1 && c.max_boxes_per_frame <= 65536 && c.max_queue >= 1 &&
-           c.image_budget_bytes >= 256 && (c.plain == 0 || c.plain == 1) &&
+           c.image_budget_bytes >= 256 && (c.plain == 0 || c.plain == 1) && (c.mapped == 0 || c.mapped == 1) &&
            (int64_t)c.frames_per_batch * c.max_boxes_per_frame <= (1 << 22);
+}
+
+// Mapped servers: a frame the gather can read in place -- 16-byte aligned rows
+// and width, in memory the device reads at the host address (page-locked, or any
+// memory where the device has pageable memory access).
+bool gatherable(const ctm_server *S, const ctm_request &r)
+{
+    if ((reinterpret_cast<uintptr_t>(r.left_host) | reinterpret_cast<uintptr_t>(r.right_host) | (uintptr_t)r.pitch |
+         (uintptr_t)r.width) & 15u)
+        return false;
+    if (S->pageable_access) return true;
+    for (const void *p : {(const void *)r.left_host, (const void *)r.right_host}) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (at.type != cudaMemoryTypeHost || at.devicePointer != p) return false;
+    }
+    return true;
 }
 
 }  // namespace
@@ -463,7 +503,7 @@ int ctm_server_default_config(ctm_server_config *cfg)
     cfg->max_queue = 256;
     cfg->image_budget_bytes = 1LL << 30;
     cfg->plain = 0;
-    cfg->reserved = 0;
+    cfg->mapped = 1;
     return CTM_OK;
 }
 
@@ -479,7 +519,10 @@ int ctm_server_create(ctm_server **out, const ctm_params *p, const ctm_server_co
     S->device = dev;
     S->p = *p;
     S->cfg = *cfg;
+    if (S->cfg.plain) S->cfg.mapped = 0;  // the plain path uploads
     S->arena.reset(cfg->image_budget_bytes, 256);
+    cudaDeviceGetAttribute(&S->pageable_access, cudaDevAttrPageableMemoryAccess, dev);
+    cudaGetLastError();
     int st = CTM_OK;
     if (ctm::dev_alloc(reinterpret_cast<void **>(&S->arena_d), (size_t)S->arena.size()) != cudaSuccess) st = CTM_ENOMEM;
     if (st == CTM_OK && cudaStreamCreateWithFlags(&S->upload, cudaStreamNonBlocking) != cudaSuccess) st = CTM_ECUDA;
@@ -522,6 +565,7 @@ int ctm_server_submit(ctm_server *S, const ctm_request *r)
     if (!j) return CTM_ENOMEM;
     j->r = *r;
     j->pitch = pitch;
+    if (S->cfg.mapped) j->gather = gatherable(S, *r);
     {
         std::lock_guard<std::mutex> lk(S->mu);
         if (S->stopping) {

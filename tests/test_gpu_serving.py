@@ -202,3 +202,49 @@ def test_serving_frames_without_boxes(torch_cuda, trace, plain):
         else:
             _same(r, alone[key], f"frame {key} beside frames without boxes")
     srv.close()
+
+
+def test_serving_mapped_same_outputs(torch_cuda, trace):
+    """A mapped server reads a gatherable frame's image bytes in place (only those
+    its census needs): outputs equal the uploading server's bit for bit, for pinned
+    and pageable images, alone and in a mix with frames it cannot gather (views
+    8 bytes off a 16-byte boundary), which it uploads whole.  A plain server
+    uploads whatever mapped says."""
+    from paper_2604_07980_gb300 import binding as B
+    pinned = _pinned(torch_cuda, trace)
+    a = B.Server(trace.params, lanes=2, frames_per_batch=4, mapped=0)
+    alone = _alone(a, trace, pinned)
+    a.close()
+    m = B.Server(trace.params, lanes=2, frames_per_batch=4, mapped=1)
+    mapped = _alone(m, trace, pinned)
+    for key in alone:
+        _same(mapped[key], alone[key], f"mapped frame {key}, pinned")
+
+    def off8(img):
+        buf = np.empty(img.size + 32, np.uint8)
+        o = (16 - buf.ctypes.data % 16) % 16 + 8
+        view = buf[o:o + img.size].reshape(img.shape)
+        view[...] = img
+        return view
+
+    tags = {}
+    for s, st_ in enumerate(trace.streams):
+        for k, fr in enumerate(st_.frames):
+            tags[m.submit(np.ascontiguousarray(fr.left), np.ascontiguousarray(fr.right), st_.boxes[k], fr.f_px,
+                          fr.baseline_m)] = (s, k)
+            tags[m.submit(off8(fr.left), off8(fr.right), st_.boxes[k], fr.f_px, fr.baseline_m)] = (s, k)
+    done = m.wait_all()
+    assert len(done) == len(tags)
+    for r in done:
+        assert r["status"] == 0
+        _same(r, alone[tags[r["tag"]]], f"mapped frame {tags[r['tag']]} in the mix")
+    m.close()
+    p = B.Server(trace.params, lanes=1, frames_per_batch=1, plain=1, mapped=1)  # plain servers upload
+    assert p.config.mapped == 1
+    key = next(iter(alone))
+    s, k = key
+    fr = trace.streams[s].frames[k]
+    p.submit(*pinned[s][k], trace.streams[s].boxes[k], fr.f_px, fr.baseline_m)
+    (res,) = p.wait_all()
+    _same(res, alone[key], "plain server asked for mapped")
+    p.close()
