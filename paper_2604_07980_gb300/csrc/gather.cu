@@ -59,9 +59,9 @@ __device__ __forceinline__ bool plane_needs(const MatchArgs &a, const uint32_t *
 }
 
 // One (frame, image, source row, chunk of 32 segments) per warp: the needed
-// segments (a ballot of the lanes' plane_needs), then their bytes, four lanes per
-// segment and eight segments (512 contiguous bytes) per pass, all reads before
-// the writes.  Returns the bytes this lane copied.
+// segments (a ballot of the lanes' plane_needs), then their bytes, 16 per lane
+// (kGatherSegBytes / 16 lanes per segment, 512 contiguous bytes per pass), all
+// reads before the writes.  Returns the bytes this lane copied.
 __device__ __forceinline__ unsigned long long gather_item(const MatchArgs &a, long long item, int chunks, int nf,
                                                           int lane)
 {
@@ -91,23 +91,25 @@ __device__ __forceinline__ unsigned long long gather_item(const MatchArgs &a, lo
     const unsigned needm = __ballot_sync(0xffffffffu, need);
     if (!needm) return 0ull;
     const ctm_frame dst = a.frames[f];
-    const int part = lane & 3;
+    constexpr int kLanesPerSeg = kGatherSegBytes / 16, kSegsPerPass = 32 / kLanesPerSeg;
+    constexpr int kPasses = kSegsPerWarp / kSegsPerPass;
+    const int part = lane % kLanesPerSeg;
     const long long off = (long long)chunk * kSegsPerWarp * kGatherSegBytes + 16 * part;
     const uint8_t *srow = (img ? src.right : src.left) + (long long)sy * src.pitch + off;
     uint8_t *drow = const_cast<uint8_t *>(img ? dst.right : dst.left) + (long long)sy * dst.pitch + off;
-    uint4 v[4];
-    bool on[4];
+    uint4 v[kPasses];
+    bool on[kPasses];
 #pragma unroll
-    for (int pass = 0; pass < 4; ++pass) {
-        const int sl = pass * 8 + (lane >> 2);  // segment within the chunk
+    for (int pass = 0; pass < kPasses; ++pass) {
+        const int sl = pass * kSegsPerPass + lane / kLanesPerSeg;  // segment within the chunk
         on[pass] = ((needm >> sl) & 1u) && off + sl * kGatherSegBytes < W;
         if (on[pass]) v[pass] = *reinterpret_cast<const uint4 *>(srow + sl * kGatherSegBytes);
     }
     unsigned long long bytes = 0ull;
 #pragma unroll
-    for (int pass = 0; pass < 4; ++pass) {
+    for (int pass = 0; pass < kPasses; ++pass) {
         if (on[pass]) {
-            *reinterpret_cast<uint4 *>(drow + (pass * 8 + (lane >> 2)) * kGatherSegBytes) = v[pass];
+            *reinterpret_cast<uint4 *>(drow + (pass * kSegsPerPass + lane / kLanesPerSeg) * kGatherSegBytes) = v[pass];
             bytes += 16;
         }
     }
