@@ -56,11 +56,11 @@ POPC_PER_EVAL = 2          # one u64 code pair = two 32-bit popcounts
 # count was taken.  When the sources differ, or no count was taken, traffic is reported as
 # null.
 TRAFFIC = {
-    # match_persistent_kernel: 118.150 MB read + 1.055 MB written
-    "match": {"bytes": 119.2056e6, "sha": "e63e3ac5a112",
+    # match_persistent_kernel: 118.189 MB read + 1.353 MB written
+    "match": {"bytes": 119.5423e6, "sha": "1f4c15893fcc",
               "sources": ("match.cu", "match_common.cuh", "aggregate.cuh", "ctm_internal.cuh")},
-    # census_roi4_kernel (60.944 MB read + 63.564 MB written) + tile_list_kernel (0.777 MB)
-    "census": {"bytes": 125.2851e6, "sha": "118e3be34171",
+    # census_roi4_kernel (60.870 MB read + 62.914 MB written) + tile_list_kernel (0.776 MB)
+    "census": {"bytes": 124.5596e6, "sha": "4d6bf5c98452",
                "sources": ("census.cu", "ctm_internal.cuh")},
 }
 CENSUS_TILE_PX = 32        # pixels per listed census tile
@@ -86,6 +86,8 @@ def parse():
                          "(default 2: with two lanes, four batches of other images and boxes)")
     ap.add_argument("--frames", type=int, default=None,
                     help="frames of a batch workload (default: the workload's own, 32 or 8)")
+    ap.add_argument("--e2e-threads", type=int, default=4,
+                    help="host threads of the end-to-end legs, each with its own context and stream")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-other", action="store_true",
                     help="skip the 8 x 3840x2160 workload reported beside the default one")
@@ -602,11 +604,11 @@ def main():
                  "launches_per_step": len(w.frames) * 3 + w.n_boxes}
         ctx1.close()
 
-    # ---- e2e through the host-memory entry point (pinned host images)
+    # ---- e2e through the host-memory entry points (pinned host images)
     # per batch, one page-locked buffer holding L0 R0 L1 R1 ... (a frame-grabber ring buffer
-    # layout); as many host threads as batches in flight, each calling the host entry point
-    # on its lane's contexts and stream, rotating over the lane's batches (each call copies
-    # its step's images in and its results out)
+    # layout); --e2e-threads host threads, each with its own context and stream, calling the
+    # entry point on the batches of lane (thread mod lanes) in turn (each call moves its step's
+    # images in and its results out)
     import threading
     for un in units:
         wk = un["w"]
@@ -615,57 +617,69 @@ def main():
             hb[fi, 0].copy_(torch.from_numpy(f.left))
             hb[fi, 1].copy_(torch.from_numpy(f.right))
         un["host"] = hb.numpy()
-        un["host_out"] = tuple(torch.empty(wk.n_boxes, dtype=dt).pin_memory().numpy()
-                               for dt in (torch.float32, torch.float32, torch.uint8))
         un["fpx"] = [f.f_px for f in wk.frames]
         un["bml"] = [f.baseline_m for f in wk.frames]
-    e2e_evals = [0] * len(lanes)
+    host_workers = []
+    for ti in range(max(args.e2e_threads, 1)):
+        ln = lanes[ti % len(lanes)]
+        nb_max = max(un["w"].n_boxes for un in ln["units"])
+        c = B.Context(w.params, len(w.frames), W, H, nb_max)
+        c.set_tuning(**tuning)
+        host_workers.append({"ctx": c, "units": ln["units"], "stream": torch.cuda.Stream(),
+                             "out": [tuple(torch.empty(max(un["w"].n_boxes, 1), dtype=dt).pin_memory().numpy()
+                                           for dt in (torch.float32, torch.float32, torch.uint8))
+                                     for un in ln["units"]]})
+    e2e_evals = [0] * len(host_workers)
 
-    def host_steps(li, n, mapped):
-        ln = lanes[li]
+    def host_steps(ti, n, mapped):
+        hw = host_workers[ti]
         for k in range(n):
-            un = ln["units"][k % len(ln["units"])]
-            un["ctx"].match_batch_host_packed(un["host"], un["w"].boxes, un["fpx"], un["bml"],
-                                              out=un["host_out"], stream=ln["stream"], mapped=mapped)
-            e2e_evals[li] += un["evals"]
+            j = k % len(hw["units"])
+            un = hw["units"][j]
+            hw["ctx"].match_batch_host_packed(un["host"], un["w"].boxes, un["fpx"], un["bml"],
+                                              out=hw["out"][j], stream=hw["stream"], mapped=mapped)
+            e2e_evals[ti] += un["evals"]
 
     def run_e2e(mapped):
-        for li in range(len(lanes)):
-            host_steps(li, 2 * rotate, mapped)
-        per_lane = max(2 * rotate, args.steps // (2 * len(lanes)))
-        for li in range(len(lanes)):
-            e2e_evals[li] = 0
+        nt = len(host_workers)
+        for ti in range(nt):
+            host_steps(ti, 2 * rotate, mapped)
+        per_thread = max(2 * rotate, args.steps // nt)
+        for ti in range(nt):
+            e2e_evals[ti] = 0
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        workers = [threading.Thread(target=host_steps, args=(li, per_lane, mapped)) for li in range(len(lanes))]
-        for t in workers:
+        threads = [threading.Thread(target=host_steps, args=(ti, per_thread, mapped)) for ti in range(nt)]
+        for t in threads:
             t.start()
-        for t in workers:
+        for t in threads:
             t.join()
         wall = time.perf_counter() - t0
-        step_s = wall / (per_lane * len(lanes))
+        step_s = wall / (per_thread * nt)
         barrier()
         step_s = D.max_over_ranks(step_s, dist)
         return sum(e2e_evals) * world / D.max_over_ranks(wall, dist) / 1e9, step_s
 
     # the copying host entry point (every image byte crosses the host link), then the
-    # mapped one (the device reads only the image bytes the census needs)
-    e2e_copy_value, e2e_copy_s = run_e2e(False)
+    # mapped one (the device reads only the image bytes the census needs); thread 0's
+    # outputs for lane 0's first batch are compared with the device path's after each
     u0 = units[0]
-    assert np.array_equal(u0["host_out"][2][:w.n_boxes], u0["batch"].flags[:w.n_boxes].cpu().numpy())
+    out0 = host_workers[0]["out"][0]
+    e2e_copy_value, e2e_copy_s = run_e2e(False)
+    assert np.array_equal(out0[2][:w.n_boxes], u0["batch"].flags[:w.n_boxes].cpu().numpy())
     e2e_value, e2e_s = run_e2e(True)
-    # the host results equal the device path's for the same batch (both entry points)
-    assert np.array_equal(u0["host_out"][2][:w.n_boxes], u0["batch"].flags[:w.n_boxes].cpu().numpy())
+    assert np.array_equal(out0[2][:w.n_boxes], u0["batch"].flags[:w.n_boxes].cpu().numpy())
     steps_units = [step_unit(lanes, i)[1] for i in range(len(lanes) * rotate)]
     # bytes a mapped step reads from host memory: its images' gathered segments (the
     # context's counter after one mapped call on each batch), boxes, two frame tables
     gathered = {}
-    for un in steps_units:
-        if id(un) not in gathered:
-            un["ctx"].match_batch_host_packed(un["host"], un["w"].boxes, un["fpx"], un["bml"], out=un["host_out"],
-                                              mapped=True)
-            gathered[id(un)] = un["ctx"].stats()["host_bytes"]
+    for li, ln in enumerate(lanes):  # worker li's context holds lane li's batches
+        hw = host_workers[li % len(host_workers)]
+        for un in ln["units"]:
+            o = tuple(np.empty(max(un["w"].n_boxes, 1), dt) for dt in (np.float32, np.float32, np.uint8))
+            hw["ctx"].match_batch_host_packed(un["host"], un["w"].boxes, un["fpx"], un["bml"], out=o, mapped=True)
+            gathered[id(un)] = hw["ctx"].stats()["host_bytes"]
     img_bytes = float(np.mean([sum(f.left.nbytes + f.right.nbytes for f in un["w"].frames) for un in steps_units]))
     small_in = float(np.mean([un["w"].boxes.nbytes + 48 * len(un["w"].frames) + 8 for un in steps_units]))
     h2d_copy = img_bytes + small_in
@@ -686,6 +700,8 @@ def main():
     torch.cuda.synchronize()
     link_gbs = 5 * link_src.numel() / (l0.elapsed_time(l1) * 1e-3) / 1e9
     del link_dev
+    for hw in host_workers:
+        hw["ctx"].close()
     for un in units[1:]:
         un["ctx"].close()
         un["frames_dev"] = un["batch"] = None
@@ -869,7 +885,7 @@ def main():
             "serving_plain_path": serving_plain,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                    "ms_per_step": e2e_s * 1e3, "host_threads": len(lanes),
+                    "ms_per_step": e2e_s * 1e3, "host_threads": len(host_workers),
                     "entry_point": "ctm_match_batch_mapped (the device reads only the image bytes the "
                                    "census needs from the page-locked host images)",
                     "image_bytes_per_step": int(img_bytes),
@@ -877,7 +893,7 @@ def main():
                     "link_floor_ms": h2d / (link_gbs * 1e9) * 1e3},
             "e2e_copy_path": {"value": e2e_copy_value, "unit": UNIT,
                               "h2d_bytes_per_step": int(h2d_copy), "d2h_bytes_per_step": int(d2h),
-                              "ms_per_step": e2e_copy_s * 1e3, "host_threads": len(lanes),
+                              "ms_per_step": e2e_copy_s * 1e3, "host_threads": len(host_workers),
                               "entry_point": "ctm_match_batch_host (every image byte copied in)",
                               "link_floor_ms": h2d_copy / (link_gbs * 1e9) * 1e3},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT,
