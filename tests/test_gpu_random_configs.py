@@ -81,3 +81,39 @@ def test_random_configuration(seed):
         assert st["error"] == 0, where
         assert st["cost_evals"] == oracle_evals(ref["blocks"], ref["flags"], params), where
     ctx.close()
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_configuration_mapped(seed):
+    """The mapped host entry point over random parameter sets (every window shape,
+    decimation 1-3, vertical search, ...): the gather must copy every source byte
+    the census of the marked tiles reads, whatever the window's reach and the
+    decimation.  The staging images hold noise from a copying call first."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2604_07980_gb300 import binding as B
+    rng = np.random.default_rng(9100 + seed)
+    params = _random_params(rng)
+    n_frames = int(rng.integers(1, 4))
+    W, H = 16 * int(rng.integers(4, 17)), int(rng.integers(50, 200))
+    w = wl.multi_frame("frame1080", 9300 + seed, n_frames, W, H, int(rng.integers(3, 25)), (4.0, 120.0),
+                       (0.5, 12.0), (1.0, 24.0), strip_frac=0.3)
+    frames = [(f.left, f.right, f.f_px, f.baseline_m) for f in w.frames]
+    ref = orc.match_batch(frames, w.boxes, orc.Params(**params))
+    ctx = B.Context(params, n_frames, W, H, max(len(w.boxes), 1))
+    packed = np.stack([np.stack([f.left, f.right]) for f in w.frames])
+    pinned = torch.empty(packed.shape, dtype=torch.uint8, pin_memory=True)
+    pinned.numpy()[...] = packed
+    noise = torch.empty(packed.shape, dtype=torch.uint8, pin_memory=True)
+    noise.numpy()[...] = rng.integers(0, 256, packed.shape, dtype=np.uint8)
+    fpx = [f.f_px for f in w.frames]
+    bm = [f.baseline_m for f in w.frames]
+    ctx.match_batch_host_packed(noise.numpy(), w.boxes, fpx, bm)
+    got = ctx.match_batch_host_packed(pinned.numpy(), w.boxes, fpx, bm, mapped=True)
+    where = f"seed {seed} mapped params {params}"
+    compare_box_outputs(got, ref, where)
+    st = ctx.stats()
+    assert st["error"] == 0, where
+    assert st["host_bytes"] <= packed.nbytes, where
+    ctx.close()
