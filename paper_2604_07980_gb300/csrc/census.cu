@@ -819,14 +819,17 @@ cudaError_t launch_census_roi(const MatchArgs &a, int sm_count, cudaStream_t s)
     if (list_grid > 0) tile_list_kernel<<<list_grid, 256, 0, s>>>(a);
     const int ww = a.p.win_w, wh = a.p.win_h;
     const int grid = sm_count * census_roi_ctas_per_sm(ww, wh, a.census_mode);
-    if (ww == 9 && wh == 7) {
+    // the fixed windows' kernel reads grid columns [x0 - 4, x0 + 36) of a tile, the
+    // generic one [x0 - 8, x0 + 76): census_reach_left/right, which the mapped
+    // entry point's gather copies, follow census_fixed_window's choice made here
+    if (!census_fixed_window(ww, wh)) {
+        census_roi_kernel<<<grid, 32 * kWarpsPerCta, census_smem_bytes(wh), s>>>(a);
+    } else if (ww == 9 && wh == 7) {
         launch_roi4<9, 7>(a, grid, s);
     } else if (ww == 7 && wh == 7) {
         launch_roi4<7, 7>(a, grid, s);
-    } else if (ww == 5 && wh == 5) {
-        launch_roi4<5, 5>(a, grid, s);
     } else {
-        census_roi_kernel<<<grid, 32 * kWarpsPerCta, census_smem_bytes(wh), s>>>(a);
+        launch_roi4<5, 5>(a, grid, s);
     }
     return cudaGetLastError();
 }
