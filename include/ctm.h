@@ -274,13 +274,14 @@ int ctm_match_batch_host(ctm_ctx *ctx, const ctm_frame *frames_host, int n_frame
  * disparity strips); a device kernel then reads, straight from the caller's
  * host images, the 64-byte segments of source rows those tiles' windows cover
  * and writes them into the context's staging images, and the batched path runs
- * on those.  The images must be readable by the device at their host address:
- * page-locked memory, or any host memory where the device reports pageable
- * memory access (cudaDevAttrPageableMemoryAccess, e.g. GB300 with its host);
- * the host must not write them during the call.  left, right and pitch must be
- * multiples of 16 bytes, and width a multiple of 16 (CTM_EINVAL otherwise).
- * One batch, no sub-batches; ctm_get_stats reports the bytes read from host
- * memory (host_bytes).  Synchronizes `stream` before returning. */
+ * on those.  A frame is read in place when the device can read its images at
+ * their host address (page-locked memory, or any host memory where the device
+ * reports pageable memory access, cudaDevAttrPageableMemoryAccess, e.g. GB300
+ * with its host) and left, right, pitch and width are multiples of 16 bytes;
+ * any other frame is copied whole first.  The host must not write the images
+ * during the call.  One batch, no sub-batches; ctm_get_stats reports the bytes
+ * read in place from host memory (host_bytes).  Synchronizes `stream` before
+ * returning. */
 int ctm_match_batch_mapped(ctm_ctx *ctx, const ctm_frame *frames_host, int n_frames,
                            const ctm_box *boxes_host, int n_boxes, float *disp_host,
                            float *depth_host, uint8_t *flags_host, ctm_stream stream);

@@ -819,30 +819,41 @@ int ctm_match_batch_mapped(ctm_ctx *ctx, const ctm_frame *frames_host, int n_fra
         const ctm_frame &f = frames_host[i];
         if (!f.left || !f.right || f.width < 1 || f.height < 1 || f.pitch < f.width) return CTM_EINVAL;
         if (f.width > ctx->caps.max_width || f.height > ctx->caps.max_height) return CTM_ENOMEM;
-        // the gather moves aligned 16-byte pieces of rows
-        if ((reinterpret_cast<uintptr_t>(f.left) | reinterpret_cast<uintptr_t>(f.right) | (uintptr_t)f.pitch |
-             (uintptr_t)f.width) & 15u)
-            return CTM_EINVAL;
-        if (!ctx->pageable_access && (!device_readable(f.left) || !device_readable(f.right))) return CTM_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)stream;
     st = ensure_host_staging(ctx);
     if (st != CTM_OK) return st;
-    // the staging images' frame table and the caller's (second half of the tables)
+    // the staging images' frame table and the caller's (second half of the tables); a
+    // frame the gather cannot read in place (rows or width off 16-byte multiples, or
+    // memory the device cannot read at its host address) is copied whole on s and gets
+    // height 0 in the gather's table
     const size_t plane = (size_t)ctx->img_pitch * ctx->caps.max_height;
     ctm_frame *stage = ctx->frames_host_pinned, *src = ctx->frames_host_pinned + ctx->caps.max_frames;
-    for (int i = 0; i < n_frames; ++i) {
-        ctm_frame t = frames_host[i];
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < n_frames && e == cudaSuccess; ++i) {
+        const ctm_frame &f = frames_host[i];
+        ctm_frame t = f;
         src[i] = t;
         t.left = ctx->img_dev + plane * (2 * (size_t)i);
         t.right = t.left + plane;
         t.pitch = (int32_t)ctx->img_pitch;
         stage[i] = t;
+        const bool aligned = ((reinterpret_cast<uintptr_t>(f.left) | reinterpret_cast<uintptr_t>(f.right) |
+                               (uintptr_t)f.pitch | (uintptr_t)f.width) & 15u) == 0;
+        if (!aligned || (!ctx->pageable_access && (!device_readable(f.left) || !device_readable(f.right)))) {
+            src[i].height = 0;
+            e = cudaMemcpy2DAsync(const_cast<uint8_t *>(t.left), ctx->img_pitch, f.left, f.pitch, f.width, f.height,
+                                  cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DAsync(const_cast<uint8_t *>(t.right), ctx->img_pitch, f.right, f.pitch, f.width,
+                                      f.height, cudaMemcpyHostToDevice, s);
+        }
     }
     int32_t *cnt = ctx->counts_host_pinned;
     cnt[0] = n_frames;
     cnt[1] = n_boxes;
-    cudaError_t e = cudaMemcpyAsync(ctx->frames_dev2, stage, sizeof(ctm_frame) * n_frames, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->frames_dev2, stage, sizeof(ctm_frame) * n_frames, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->frames_dev2 + ctx->caps.max_frames, src, sizeof(ctm_frame) * n_frames,
                             cudaMemcpyHostToDevice, s);
