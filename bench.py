@@ -59,8 +59,8 @@ TRAFFIC = {
     # match_persistent_kernel: 118.189 MB read + 1.353 MB written
     "match": {"bytes": 119.5423e6, "sha": "1f4c15893fcc",
               "sources": ("match.cu", "match_common.cuh", "aggregate.cuh", "ctm_internal.cuh")},
-    # census_roi4_kernel (60.870 MB read + 62.914 MB written) + tile_list_kernel (0.776 MB)
-    "census": {"bytes": 124.5596e6, "sha": "4d6bf5c98452",
+    # census_roi4_kernel (60.943 MB read + 63.234 MB written) + tile_list_kernel (0.776 MB)
+    "census": {"bytes": 124.9526e6, "sha": "eb9a08632673",
                "sources": ("census.cu", "ctm_internal.cuh")},
 }
 CENSUS_TILE_PX = 32        # pixels per listed census tile
