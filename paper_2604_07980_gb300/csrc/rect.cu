@@ -20,37 +20,46 @@ __device__ __forceinline__ uint64_t code_or_zero(const uint64_t *C, long long pi
     return (x >= 0 && x < W && y >= 0 && y < H) ? __ldg(C + (long long)y * pitch + x) : 0ull;
 }
 
+constexpr int kRectThreads = 128;
+
 // Thread per ROI pixel of one row and one offset (grid: x tiles, rows, offsets).
-__global__ void __launch_bounds__(128) rect_kernel(const uint64_t *CL, const uint64_t *CR, long long pitch, int W,
-                                                   int H, int sx, int sy, int rx0, int rx1, int ry0, int dmin,
-                                                   int dmax, int delta_min, int d_thresh, int fb_tol,
-                                                   unsigned long long *counts)
+// The CTA stages the two code rows its pixels search: the right row y over
+// columns x0 - dmax .. x0 + 127 - dmin (forward candidates x - d) and the left
+// row y + delta over x0 + dmin - dmax .. x0 + 127 + dmax - dmin (backward
+// candidates x - d_f + d for any d_f), codes outside the image as 0.  Each scan
+// keeps the first minimum as the least key (cost << 11 | candidate index).
+__global__ void __launch_bounds__(kRectThreads) rect_kernel(const uint64_t *CL, const uint64_t *CR, long long pitch,
+                                                            int W, int H, int sx, int sy, int rx0, int rx1, int ry0,
+                                                            int dmin, int dmax, int delta_min, int d_thresh,
+                                                            int fb_tol, unsigned long long *counts)
 {
-    const int x = rx0 + blockIdx.x * blockDim.x + threadIdx.x;
+    extern __shared__ uint64_t rect_smem[];
+    const int nd = dmax - dmin + 1;
+    const int x0 = rx0 + blockIdx.x * kRectThreads;
+    const int x = x0 + threadIdx.x;
     const int y = ry0 + blockIdx.y;
     const int delta = delta_min + blockIdx.z;
     const int yl = y + delta;
+    uint64_t *rrow = rect_smem;                     // columns x0 - dmax + i
+    uint64_t *lrow = rect_smem + kRectThreads + nd;  // columns x0 + dmin - dmax + i
+    const int nr = kRectThreads + nd - 1, nl = kRectThreads + 2 * (nd - 1);
+    for (int i = threadIdx.x; i < nr; i += kRectThreads) rrow[i] = code_or_zero(CR, pitch, W, H, x0 - dmax + i, y);
+    for (int i = threadIdx.x; i < nl; i += kRectThreads)
+        lrow[i] = code_or_zero(CL, pitch, W, H, x0 + dmin - dmax + i, yl);
+    __syncthreads();
     bool hit = false;
     if (x < rx1 && x - sx >= 0 && x + sx < W && yl - sy >= 0 && yl + sy < H) {
-        const uint64_t cl = CL[(long long)yl * pitch + x];
-        int d_f = dmin, best = 1 << 30;
-        for (int d = dmin; d <= dmax; ++d) {
-            const int s = __popcll(cl ^ code_or_zero(CR, pitch, W, H, x - d, y));
-            if (s < best) {
-                best = s;
-                d_f = d;
-            }
-        }
-        const uint64_t cq = code_or_zero(CR, pitch, W, H, x - d_f, y);
-        int d_b = dmin;
-        best = 1 << 30;
-        for (int d = dmin; d <= dmax; ++d) {
-            const int s = __popcll(cq ^ code_or_zero(CL, pitch, W, H, x - d_f + d, yl));
-            if (s < best) {
-                best = s;
-                d_b = d;
-            }
-        }
+        const int t = threadIdx.x;
+        const uint64_t cl = lrow[t + dmax - dmin];  // column x
+        unsigned kf = 0xffffffffu;
+        for (int i = 0; i < nd; ++i)  // candidate d = dmin + i at column x - d: rrow[t + dmax - d]
+            kf = min(kf, ((unsigned)__popcll(cl ^ rrow[t + nd - 1 - i]) << 11) | (unsigned)i);
+        const int i_f = (int)(kf & 2047u);
+        const uint64_t cq = rrow[t + nd - 1 - i_f];   // column x - d_f
+        const int b0 = t + nd - 1 - i_f;              // lrow index of column x - d_f + dmin
+        unsigned kb = 0xffffffffu;
+        for (int i = 0; i < nd; ++i) kb = min(kb, ((unsigned)__popcll(cq ^ lrow[b0 + i]) << 11) | (unsigned)i);
+        const int d_f = dmin + i_f, d_b = dmin + (int)(kb & 2047u);
         hit = abs(d_b - d_f) <= fb_tol && d_f > d_thresh;
     }
     const int n = __syncthreads_count(hit);
@@ -98,10 +107,15 @@ extern "C" int ctm_auto_rect(const ctm_params *p, const uint8_t *left_dev, const
     if (e == cudaSuccess)
         e = launch_census_single(right_dev, width, height, pitch, 1, p->win_w, p->win_h, p->sentinel, CR, cpitch, s);
     if (e == cudaSuccess && rx1 > rx0 && ry1 > ry0) {
-        const dim3 grid((rx1 - rx0 + 127) / 128, ry1 - ry0, nd);
-        rect_kernel<<<grid, 128, 0, s>>>(CL, CR, cpitch, width, height, p->win_w / 2, p->win_h / 2, rx0, rx1, ry0,
-                                         dmin, dmax, delta_min, d_thresh, fb_tol, counts_dev);
-        e = cudaGetLastError();
+        const dim3 grid((rx1 - rx0 + kRectThreads - 1) / kRectThreads, ry1 - ry0, nd);
+        const int ndisp = dmax - dmin + 1;
+        const size_t smem = sizeof(uint64_t) * (size_t)(2 * kRectThreads + 3 * ndisp);
+        e = cudaFuncSetAttribute(rect_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            rect_kernel<<<grid, kRectThreads, smem, s>>>(CL, CR, cpitch, width, height, p->win_w / 2, p->win_h / 2,
+                                                         rx0, rx1, ry0, dmin, dmax, delta_min, d_thresh, fb_tol,
+                                                         counts_dev);
+        e = e == cudaSuccess ? cudaGetLastError() : e;
     }
     if (e == cudaSuccess) {
         rect_argmax_kernel<<<1, 32, 0, s>>>(counts_dev, nd, delta_min, delta_dev);
