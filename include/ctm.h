@@ -296,12 +296,12 @@ int ctm_match_batch_mapped(ctm_ctx *ctx, const ctm_frame *frames_host, int n_fra
  * CTM_ETOOBIG.  The workspace is one 8 MiB array in static device memory that
  * every GPU loading the library holds until exit.  The first call on a device
  * does a one-time set-up with that device current (looks up the array's device
- * address, raises the matching kernel's shared-memory limit), so make it before
- * any stream capture.  All calls share the array and it keeps the previous
- * call's contents (each call clears what must start at zero); calls that overlap
- * on the GPU race.  Not thread-safe.  Calls no cudaMalloc, cudaFree or
- * allocating library routine.  A bounded-wait expiry leaves the outputs as the
- * CTM_ETIMEOUT rule says and the flag in ctm_noalloc_get_stats.
+ * address, raises the matching kernel's shared-memory limit).  All calls share
+ * the array and it keeps the previous call's contents (each call clears what
+ * must start at zero); calls that overlap on the GPU race.  Not thread-safe.
+ * Calls no cudaMalloc, cudaFree or allocating library routine.  A bounded-wait
+ * expiry leaves the outputs as the CTM_ETIMEOUT rule says and the flag in
+ * ctm_noalloc_get_stats.
  * Errors: CTM_EINVAL, CTM_ETOOBIG, CTM_ENODEV, CTM_ECUDA. */
 int ctm_match_boxes_noalloc(const ctm_params *p, const uint8_t *left_dev, const uint8_t *right_dev,
                             int width, int height, int pitch, const ctm_box *boxes_dev, int n_boxes,

@@ -12,8 +12,9 @@
 // Set-up happens on the first call on each device (with that device current):
 // the array's device address is taken with cudaGetSymbolAddress -- in host code
 // the array's name is only a host-side stand-in, not a device address -- and
-// the matching kernel's shared-memory limit is raised.  That first call should
-// therefore come before any stream capture.  All calls share the one array and
+// the matching kernel's shared-memory limit is raised, and the census kernels'
+// occupancy is looked up, so later calls make no attribute or occupancy query
+// for the fixed windows.  All calls share the one array and
 // it keeps the previous call's contents: each call clears what must start at
 // zero (the census demand bitmap, the counters, the block counts), and calls
 // that overlap on the GPU race on the array.  The counters of the last call
@@ -64,7 +65,7 @@ int setup_device(int dev)
     }
     st.base = static_cast<unsigned char *>(ptr);
     st.sm_count = sms;
-    for (int m = 0; m < 2; ++m) {  // occupancy queries outside any capture
+    for (int m = 0; m < 2; ++m) {  // occupancy queries cached here, once per process
         ctm::census_roi_ctas_per_sm(9, 7, m);
         ctm::census_roi_ctas_per_sm(7, 7, m);
         ctm::census_roi_ctas_per_sm(5, 5, m);
