@@ -1,6 +1,6 @@
 // plan.cu -- device-side planning of Algorithm 2's per-box steps.
 //
-// plan_kernel (kPlanSlices CTAs per frame, each a slice of the frame's boxes,
+// plan_kernel (plan_slices CTAs per frame, each a slice of the frame's boxes,
 // a warp per box): clip each box to its frame, classify it FAR
 // or CLOSE by its larger side against tau_s (Sec. 4.3.4), map it to its matching
 // grid (full resolution for FAR, the decimated grid for CLOSE), count its
@@ -15,6 +15,8 @@
 // their search can read.  All counts come from device memory so a captured
 // graph replays with new inputs.
 #include <math.h>
+
+#include <algorithm>
 
 #include "aggregate.cuh"
 #include "ctm_internal.cuh"
@@ -62,19 +64,20 @@ __global__ void stage_frame_kernel(ctm_frame *frames, int *counts_in, ctm_frame 
 }
 
 constexpr int kStageBoxes = 1024;  // boxes of one frame staged in shared memory
-constexpr int kPlanSlices = 4;     // CTAs per frame, each planning a slice of its boxes
 constexpr int kKeyCache = 8;       // occluder keys per lane held in registers
 
-// One CTA per frame: clip, classify, map to the matching grid and select the
-// occluders of every box of the frame (the frame's clipped boxes are staged in
-// shared memory for the pairwise test), then the frame's block counts are
-// scanned and one atomic reserves the frame's range of the flat block list.
+// plan_slices CTAs per frame, each a slice of the frame's boxes: clip, classify,
+// map to the matching grid and select the occluders of every box of the slice
+// (the frame's clipped boxes are staged in shared memory for the pairwise
+// test), then the slice's block counts are scanned and one atomic reserves the
+// slice's range of the flat block list.
 __global__ void __launch_bounds__(kPlanThreads) plan_kernel(MatchArgs a)
 {
     __shared__ int4 sbox[kStageBoxes];
     __shared__ int warp_tot[kPlanThreads / 32];
     __shared__ int s_run, s_base;
-    const int f = blockIdx.x / kPlanSlices, slice = blockIdx.x % kPlanSlices;
+    const int S = a.plan_slices;
+    const int f = blockIdx.x / S, slice = blockIdx.x % S;
     const int nf = clampi(a.counts_in[0], 0, a.caps.max_frames);
     const int nb_total = clampi(a.counts_in[1], 0, a.caps.max_boxes);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -115,7 +118,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(MatchArgs a)
     const ctm_params &p = a.p;
     const int K = p.max_occluders < kMaxOcc ? p.max_occluders : kMaxOcc;
     // this CTA's slice of the frame's boxes
-    const int per = (nloc + kPlanSlices - 1) / kPlanSlices;
+    const int per = (nloc + S - 1) / S;
     const int sb = begin + min(slice * per, nloc), se = begin + min((slice + 1) * per, nloc);
 
     // a warp per box
@@ -479,10 +482,16 @@ cudaError_t launch_stage_frame(const MatchArgs &a, ctm_frame f, int n_boxes, cud
 }
 
 // The counters and block counts start at zero: the workspace is created zeroed
-// and every call's aggregate_kernel zeroes them again.
+// and every call's aggregate_kernel zeroes them again.  A frame's boxes are
+// planned a warp per box, so a frame with many boxes gets more CTAs when the
+// call has few frames: about two CTAs per SM over the call's frame capacity,
+// at least 4 and at most 32 per frame.
 cudaError_t launch_plan(const MatchArgs &a, cudaStream_t s)
 {
-    plan_kernel<<<a.caps.max_frames * kPlanSlices, kPlanThreads, 0, s>>>(a);
+    MatchArgs b = a;
+    const int nf = a.caps.max_frames > 0 ? a.caps.max_frames : 1;
+    b.plan_slices = std::min(std::max(ceil_div_nn(2 * a.sm_count, nf), 4), 32);
+    plan_kernel<<<b.caps.max_frames * b.plan_slices, kPlanThreads, 0, s>>>(b);
     return cudaGetLastError();
 }
 
