@@ -644,7 +644,7 @@ def main():
         nt = len(host_workers)
         for ti in range(nt):
             host_steps(ti, 2 * rotate, mapped)
-        per_thread = max(2 * rotate, args.steps // nt)
+        per_thread = max(2 * rotate, args.steps)  # K calls per host thread: a longer, steadier sample
         for ti in range(nt):
             e2e_evals[ti] = 0
         barrier()
