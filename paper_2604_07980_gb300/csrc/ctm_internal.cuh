@@ -179,7 +179,6 @@ struct MatchArgs {
     int inject_expiry;         // fault injection for tests: the CTA of the fused persistent matcher
                                // that takes queue position 0 withholds that block's first strip
                                // copy, so its bounded wait expires
-    int plan_slices;           // CTAs per frame of the planning kernel (set by launch_plan)
 };
 
 __host__ __device__ inline int ceil_div_nn(int a, int b) { return (a + b - 1) / b; }

@@ -1,6 +1,6 @@
 // plan.cu -- device-side planning of Algorithm 2's per-box steps.
 //
-// plan_kernel (plan_slices CTAs per frame, each a slice of the frame's boxes,
+// plan_kernel (several CTAs per frame, each a slice of the frame's boxes,
 // a warp per box): clip each box to its frame, classify it FAR
 // or CLOSE by its larger side against tau_s (Sec. 4.3.4), map it to its matching
 // grid (full resolution for FAR, the decimated grid for CLOSE), count its
@@ -66,17 +66,16 @@ __global__ void stage_frame_kernel(ctm_frame *frames, int *counts_in, ctm_frame 
 constexpr int kStageBoxes = 1024;  // boxes of one frame staged in shared memory
 constexpr int kKeyCache = 8;       // occluder keys per lane held in registers
 
-// plan_slices CTAs per frame, each a slice of the frame's boxes: clip, classify,
+// S CTAs per frame, each a slice of the frame's boxes: clip, classify,
 // map to the matching grid and select the occluders of every box of the slice
 // (the frame's clipped boxes are staged in shared memory for the pairwise
 // test), then the slice's block counts are scanned and one atomic reserves the
 // slice's range of the flat block list.
-__global__ void __launch_bounds__(kPlanThreads) plan_kernel(MatchArgs a)
+__global__ void __launch_bounds__(kPlanThreads) plan_kernel(MatchArgs a, int S)
 {
     __shared__ int4 sbox[kStageBoxes];
     __shared__ int warp_tot[kPlanThreads / 32];
     __shared__ int s_run, s_base;
-    const int S = a.plan_slices;
     const int f = blockIdx.x / S, slice = blockIdx.x % S;
     const int nf = clampi(a.counts_in[0], 0, a.caps.max_frames);
     const int nb_total = clampi(a.counts_in[1], 0, a.caps.max_boxes);
@@ -488,10 +487,9 @@ cudaError_t launch_stage_frame(const MatchArgs &a, ctm_frame f, int n_boxes, cud
 // at least 4 and at most 32 per frame.
 cudaError_t launch_plan(const MatchArgs &a, cudaStream_t s)
 {
-    MatchArgs b = a;
     const int nf = a.caps.max_frames > 0 ? a.caps.max_frames : 1;
-    b.plan_slices = std::min(std::max(ceil_div_nn(2 * a.sm_count, nf), 4), 32);
-    plan_kernel<<<b.caps.max_frames * b.plan_slices, kPlanThreads, 0, s>>>(b);
+    const int slices = std::min(std::max(ceil_div_nn(2 * a.sm_count, nf), 4), 32);
+    plan_kernel<<<a.caps.max_frames * slices, kPlanThreads, 0, s>>>(a, slices);
     return cudaGetLastError();
 }
 
