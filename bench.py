@@ -6,10 +6,10 @@ both resolutions, device planning, the forward/backward Hamming search with
 argmin, parabola and consistency test, aggregation and depth, for the batched
 workload "batch32x1200" (32 frames of 1920x1200 uint8, Poisson(40) boxes per
 frame, 20% occluding strips, far/close split, 9x7 census).  The timed region
-replays captured CUDA graphs of ctm_match_batch K times, alternating between two
-streams (two batches in flight); each stream rotates over two distinct batches
-(other seeds: other images, boxes and counts), each on its own context, so four
-batches (588 MB of images) take turns and no step finds a recent step's data in
+replays captured CUDA graphs of ctm_match_batch K times, round robin over three
+streams (three batches in flight); each stream rotates over two distinct batches
+(other seeds: other images, boxes and counts), each on its own context, so six
+batches (885 MB of images) take turns and no step finds a recent step's data in
 the 129 MB L2; no flush is needed between steps.
 
 Printed (one JSON line on rank 0): cost-evals/s of the batched path, its e2e
@@ -78,12 +78,12 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=WORKLOAD,
                     help="synthetic workload (default: the 32-frame 1920x1200 batch the metric is quoted on; "
                          "the others are the parity configurations, measured the same way)")
-    ap.add_argument("--inflight", type=int, default=2,
+    ap.add_argument("--inflight", type=int, default=3,
                     help="batches in flight during the timed steps, each on its own context and "
-                         "stream (default 2; 1 = one batch at a time, also reported beside)")
+                         "stream (default 3; 1 = one batch at a time, also reported beside)")
     ap.add_argument("--rotate", type=int, default=2,
                     help="distinct batches each in-flight lane cycles through during the timed steps "
-                         "(default 2: with two lanes, four batches of other images and boxes)")
+                         "(default 2: with three lanes, six batches of other images and boxes)")
     ap.add_argument("--frames", type=int, default=None,
                     help="frames of a batch workload (default: the workload's own, 32 or 8)")
     ap.add_argument("--e2e-threads", type=int, default=4,
@@ -475,10 +475,10 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    # Batches in flight (two by default), each lane a stream of its own, as a deployment
-    # (or the serving loop's two lanes) runs consecutive batches: one batch's
-    # latency-bound planning, tile-list and aggregation kernels then share SMs with the
-    # other batch's census or matching.  Every lane rotates over `rotate` batches of its
+    # Batches in flight (three by default), each lane a stream of its own, as a deployment
+    # (or the serving loop's lanes) runs consecutive batches: one batch's latency-bound
+    # planning, tile-list and aggregation kernels then share SMs with the other
+    # batches' census or matching.  Every lane rotates over `rotate` batches of its
     # own (distinct seeds: other images, boxes and counts), each on its own context with
     # its own graph and census planes, so no step re-reads data a recent step brought
     # into L2.  Every step is still one whole pass over one batch.
