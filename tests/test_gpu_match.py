@@ -267,23 +267,25 @@ def test_batch_host_sub_batches_equal_device_batch(torch_cuda):
     ctx.close()
 
 
-def test_two_contexts_in_flight_on_two_streams(torch_cuda):
-    """Two contexts replaying their graphs alternately on two streams (the benchmark's
-    two batches in flight) give the same outputs and counters as one context alone."""
+@pytest.mark.parametrize("n_ctx", [2, 3])
+def test_contexts_in_flight_on_their_own_streams(torch_cuda, n_ctx):
+    """Contexts replaying their graphs round robin on streams of their own (the
+    benchmark's batches in flight) give the same outputs and counters as one context
+    alone."""
     from paper_2604_07980_gb300 import binding as B
     torch = torch_cuda
     w = wl.batch32x1200(n_frames=6, W=960, H=600, mean_boxes=12, side_range=(12, 240))
     frames = B.frames_to_device(w.frames)
     calib = [(f.f_px, f.baseline_m) for f in w.frames]
-    ctxs = [B.Context(w.params, 6, 960, 600, w.n_boxes) for _ in range(2)]
-    batches = [B.DeviceBatch(frames, w.boxes, calib) for _ in range(2)]
-    streams = [torch.cuda.current_stream(), torch.cuda.Stream()]
+    ctxs = [B.Context(w.params, 6, 960, 600, w.n_boxes) for _ in range(n_ctx)]
+    batches = [B.DeviceBatch(frames, w.boxes, calib) for _ in range(n_ctx)]
+    streams = [torch.cuda.current_stream()] + [torch.cuda.Stream() for _ in range(n_ctx - 1)]
     ref = ctxs[0].match_batch(batches[0], use_graph=True)
     torch.cuda.synchronize()
     ref = {k: v.cpu().numpy().copy() for k, v in ref.items()}
     st_ref = ctxs[0].stats()
-    for i in range(8):
-        ctxs[i % 2].match_batch(batches[i % 2], use_graph=True, stream=streams[i % 2])
+    for i in range(4 * n_ctx):
+        ctxs[i % n_ctx].match_batch(batches[i % n_ctx], use_graph=True, stream=streams[i % n_ctx])
     torch.cuda.synchronize()
     for c, b in zip(ctxs, batches):
         assert c.stats()["cost_evals"] == st_ref["cost_evals"] and c.stats()["error"] == 0
@@ -292,7 +294,7 @@ def test_two_contexts_in_flight_on_two_streams(torch_cuda):
             assert np.array_equal(got, ref[k], equal_nan=True), k
     oref = orc.match_batch([(f.left, f.right, f.f_px, f.baseline_m) for f in w.frames], w.boxes,
                            orc.Params(**w.params))
-    compare_box_outputs(ref, oref, "two contexts")
+    compare_box_outputs(ref, oref, f"{n_ctx} contexts")
     for c in ctxs:
         c.close()
 
