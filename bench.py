@@ -253,7 +253,7 @@ def serve_trace(B, torch, tr, plain: bool, mapped: bool = False) -> dict:
                for f in st.frames] for st in tr.streams]
     W = max(st.width for st in tr.streams)
     H = max(st.height for st in tr.streams)
-    srv = B.Server(tr.params, lanes=1 if plain else 2, frames_per_batch=1 if plain else 8,
+    srv = B.Server(tr.params, lanes=1 if plain else 4, frames_per_batch=1 if plain else 8,
                    plain=int(plain), mapped=int(mapped), max_width=W, max_height=H, max_boxes_per_frame=256,
                    max_queue=1024, image_budget_bytes=1 << 30)
 

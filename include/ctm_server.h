@@ -104,7 +104,7 @@ typedef struct {
     int32_t max_lanes_busy;                  /* most batches in flight at once */
 } ctm_server_stats;
 
-/* Default configuration: 2 lanes, 8 frames per batch, 3840x2160, 256 boxes,
+/* Default configuration: 4 lanes, 8 frames per batch, 3840x2160, 256 boxes,
  * queue 256, arena 1 GiB, batched path, images read in place where possible
  * (mapped = 1). */
 int ctm_server_default_config(ctm_server_config *cfg);

@@ -495,7 +495,7 @@ int64_t ctm_server_now_ns(void) { return now_ns(); }
 int ctm_server_default_config(ctm_server_config *cfg)
 {
     if (!cfg) return CTM_EINVAL;
-    cfg->lanes = 2;
+    cfg->lanes = 4;
     cfg->frames_per_batch = 8;
     cfg->max_width = 3840;
     cfg->max_height = 2160;

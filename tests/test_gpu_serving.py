@@ -51,10 +51,11 @@ def _alone(srv, tr, pinned):
     return out
 
 
-def test_serving_alone_equals_mix(torch_cuda, trace):
+@pytest.mark.parametrize("lanes", [2, 4])
+def test_serving_alone_equals_mix(torch_cuda, trace, lanes):
     from paper_2604_07980_gb300 import binding as B
     pinned = _pinned(torch_cuda, trace)
-    srv = B.Server(trace.params, lanes=2, frames_per_batch=4, image_budget_bytes=1 << 30)
+    srv = B.Server(trace.params, lanes=lanes, frames_per_batch=4, image_budget_bytes=1 << 30)
     alone = _alone(srv, trace, pinned)
     # the same frames, three times over, submitted in one burst
     keys = [(s, k) for s in range(len(trace.streams)) for k in range(2)] * 3
@@ -70,7 +71,7 @@ def test_serving_alone_equals_mix(torch_cuda, trace):
         _same(r, alone[tags[r["tag"]]], f"frame {tags[r['tag']]} in the mix")
     st = srv.stats()
     assert st["completed"] == st["submitted"] == len(alone) + len(keys)
-    assert st["max_lanes_busy"] == 2                       # batches overlapped on the device
+    assert 2 <= st["max_lanes_busy"] <= lanes              # batches overlapped on the device
     assert st["batched_frames"] == st["completed"]
     assert st["batches"] < st["completed"]                 # frames were batched together
     assert max(r["batch_frames"] for r in done) > 1
