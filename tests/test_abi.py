@@ -111,7 +111,7 @@ def test_server_argument_checks(built):
     L = B.lib()
     cfg = B.ctm_server_config()
     assert L.ctm_server_default_config(ctypes.byref(cfg)) == B.CTM_OK
-    assert (cfg.lanes, cfg.frames_per_batch, cfg.max_width, cfg.max_height) == (2, 8, 3840, 2160)
+    assert (cfg.lanes, cfg.frames_per_batch, cfg.max_width, cfg.max_height) == (4, 8, 3840, 2160)
     assert L.ctm_server_default_config(None) == B.CTM_EINVAL
     p = B.make_params()
     h = ctypes.c_void_p()
