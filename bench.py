@@ -312,12 +312,14 @@ def serve_trace(B, torch, tr, plain: bool, mapped: bool = False) -> dict:
 
 def measure_other(B, torch, wl, D, dist, args, name: str, seed: int, popc_peak: float) -> dict:
     """Another batch workload measured the same way as the default one, reported beside
-    it: autotuned, two batches in flight on two streams (two distinct batches, one per
-    lane), the same steps one at a time (both batches alternating on one stream), and the
-    matching kernel's popcount-roofline fraction from CUDA events around its launches."""
-    wks = [make_workload(wl, name, None, seed), make_workload(wl, name, None, seed + 7919)]
+    it: autotuned, `--inflight` batches in flight on as many streams (distinct batches,
+    one per lane), the same steps one at a time (the batches taking turns on one
+    stream), and the matching kernel's popcount-roofline fraction from CUDA events
+    around its launches."""
+    n_in = max(args.inflight, 1)
+    wks = [make_workload(wl, name, None, seed + 7919 * u) for u in range(n_in)]
     H, W = wks[0].frames[0].left.shape
-    streams = [torch.cuda.current_stream(), torch.cuda.Stream()]
+    streams = [torch.cuda.current_stream()] + [torch.cuda.Stream() for _ in range(n_in - 1)]
     units = []
     tuning = None
     for wk in wks:
@@ -343,15 +345,17 @@ def measure_other(B, torch, wl, D, dist, args, name: str, seed: int, popc_peak: 
             dist.barrier()
         torch.cuda.synchronize()
         t0.record(streams[0])
-        streams[1].wait_event(t0)
+        for st_ in streams[1:]:
+            st_.wait_event(t0)
         ev = 0
         for i in range(args.steps):
-            un = units[i % 2]
-            un["ctx"].match_batch(un["batch"], use_graph=True, stream=streams[i % 2] if inflight else streams[0])
+            un = units[i % n_in]
+            un["ctx"].match_batch(un["batch"], use_graph=True, stream=streams[i % n_in] if inflight else streams[0])
             ev += un["evals"]
-        j = torch.cuda.Event()
-        j.record(streams[1])
-        streams[0].wait_event(j)
+        for st_ in streams[1:]:
+            j = torch.cuda.Event()
+            j.record(st_)
+            streams[0].wait_event(j)
         t1.record(streams[0])
         torch.cuda.synchronize()
         return D.max_over_ranks(t0.elapsed_time(t1), dist), ev
@@ -363,7 +367,7 @@ def measure_other(B, torch, wl, D, dist, args, name: str, seed: int, popc_peak: 
     mev = 0
     torch.cuda.synchronize()
     for i in range(args.steps):
-        un = units[i % 2]
+        un = units[i % n_in]
         un["ctx"].match_batch_profiled(un["batch"], evs[i])
         mev += un["evals"]
     torch.cuda.synchronize()
@@ -374,7 +378,7 @@ def measure_other(B, torch, wl, D, dist, args, name: str, seed: int, popc_peak: 
            "boxes_per_step_mean": float(np.mean([u["w"].n_boxes for u in units])),
            "evals_per_step_mean": ev2 / args.steps,
            "value": ev2 / (ms2 * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms2 / args.steps,
-           "batches_in_flight": 2, "distinct_batches": 2,
+           "batches_in_flight": n_in, "distinct_batches": n_in,
            "one_batch_at_a_time": {"value": ev1 / (ms1 * 1e-3) / 1e9, "ms_per_step": ms1 / args.steps},
            "match_ms": mt / args.steps, "match_roofline_frac": match_ach / popc_peak,
            "tuning": tuning}
